@@ -1,0 +1,179 @@
+/*
+ * l2xfer — L2-projection transfer between a structured Q1 fluid grid and an
+ * unstructured P1 solid mesh, on one GB300 GPU (sm_103a).
+ *
+ * The method is the variational transfer of Sec. 2.3 ("Variational Transfer:
+ * the L2-Projection Approach"):
+ *
+ *   B_ij = ∫ psi_j phi_i         mixed coupling matrix (mortar integral),
+ *   S_ij = ∫ phi_j phi_i = M_s   solid P1 mass matrix (multipliers = V_s),
+ *   w_s  = S^{-1} B v_f = T v_f  velocity transfer, one scalar component at a time,
+ *   f_f  = s T^T f               force transfer by the transpose, s = L_ref/(rho_f U_ref^2),
+ *
+ * assembled in the current configuration of the solid mesh by the four steps
+ * given after the transfer operator: (I) overlap detection, (II) quadrature
+ * points in the intersections, (III) local contributions, (IV) assembly.
+ * phi_i is the P1 hat function of solid node i (Sec. 2.1, "Spatial
+ * Discretization"); psi_j is the Q1 function of node j of one of the velocity
+ * grids of the staggered fluid grid (Sec. 2.2, "Spatial Discretization").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array arguments are DEVICE pointers on the current CUDA device unless
+ *   said otherwise; they are read or written on `stream` (a cudaStream_t, NULL =
+ *   legacy default stream).  The caller owns them.  The library owns the memory
+ *   behind an l2x_handle and releases it in l2x_destroy().
+ * - Every call returns an l2x_status; nothing traps.  Kernels report errors
+ *   through a device status word that the call reads after synchronising
+ *   `stream`; l2x_last_error() gives a one-line description.
+ * - A handle is not thread-safe and must not be used from two streams at once.
+ * - Velocity grids: with staggered = 0 there is one nodal Q1 grid (nodes at
+ *   origin + i*h) and one scalar component; with staggered = 1 there are `dim`
+ *   grids, grid g having nodes at origin_g + i*h along axis g and at cell
+ *   centres along the other axes (so ncell-1 Q1 cells there).  A fluid array of
+ *   grid g has prod_k nnode_g[k] entries, node (i0,i1,i2) at i0 + nnode0*(i1 +
+ *   nnode1*i2).
+ * - Field precision follows l2x_opts.precision: double arrays for L2X_FP64,
+ *   float arrays for L2X_MIXED.
+ */
+#ifndef L2XFER_H
+#define L2XFER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum l2x_status {
+    L2X_OK = 0,
+    L2X_EINVAL = 1,         /* bad argument (null pointer, dim, sizes, options) */
+    L2X_ENOMEM = 2,         /* device allocation failed */
+    L2X_ECAPACITY = 3,      /* a fixed-capacity buffer overflowed */
+    L2X_EOUTOFGRID = 4,     /* a solid element leaves the cells of a velocity grid */
+    L2X_EDEGENERATE = 5,    /* a solid element has zero volume */
+    L2X_ENOTCONVERGED = 6,  /* CG did not reach cg_rtol within cg_max_iter */
+    L2X_ETIMEOUT = 7,       /* a bounded device wait gave up */
+    L2X_ECUDA = 8,          /* CUDA runtime error */
+    L2X_ENONFINITE = 9      /* NaN or Inf in an input field or coordinate */
+} l2x_status;
+
+enum { L2X_PATH_PLAIN = 0, L2X_PATH_FUSED = 1 };
+enum { L2X_FP64 = 0, L2X_MIXED = 1 };
+enum { L2X_FORCE_NODAL = 0, L2X_FORCE_DUAL = 1 };
+enum { L2X_MAT_B0 = 0, L2X_MAT_B1 = 1, L2X_MAT_B2 = 2, L2X_MAT_M = 3 };
+
+/* Base (pressure) grid: ncell[k] cells of width h[k] from origin[k], k < dim. */
+typedef struct l2x_grid {
+    int32_t dim;        /* 2 or 3 */
+    int32_t staggered;  /* 0: one nodal Q1 grid; 1: dim staggered velocity grids */
+    int32_t ncell[3];
+    double origin[3];
+    double h[3];
+} l2x_grid;
+
+/* P1 simplex mesh in its current configuration.  coords: n_nodes x dim,
+ * row-major doubles; elems: n_elems x (dim+1) row-major int32 node indices.
+ * Both are device pointers, read during the call only (the handle keeps a copy). */
+typedef struct l2x_mesh {
+    int32_t dim;
+    int32_t reserved;
+    int64_t n_nodes;
+    int64_t n_elems;
+    const double* coords;
+    const int32_t* elems;
+} l2x_mesh;
+
+typedef struct l2x_opts {
+    int32_t path;         /* L2X_PATH_PLAIN (reference GPU path) or L2X_PATH_FUSED */
+    int32_t precision;    /* L2X_FP64 or L2X_MIXED (fused path only) */
+    double cg_rtol;       /* relative residual target of the mass-matrix solve */
+    int32_t cg_max_iter;
+    int32_t force_mode;   /* L2X_FORCE_DUAL: f_f += s B^T M^-1 r; NODAL: f_f += s B^T f */
+    double force_scale;   /* s = L_ref / (rho_f U_ref^2); 1 by default */
+} l2x_opts;
+
+typedef struct l2x_info {
+    int32_t dim, n_grids, path, precision;
+    int64_t n_nodes, n_elems;
+    int64_t n_pairs[3];        /* candidate pairs per velocity grid */
+    int64_t n_pairs_total;
+    int64_t nnz_B[3];
+    int64_t nnz_M;
+    int64_t n_fluid[3];        /* nodes per velocity grid */
+    int32_t nnode[3][3];       /* nodes per axis per velocity grid */
+    int32_t cg_iters;          /* iterations of the last mass-matrix solve (max over components) */
+    int32_t reserved;
+    double cg_residual;        /* relative residual reached by the last solve (max over components) */
+} l2x_info;
+
+typedef struct l2x_coupling* l2x_handle;
+
+/* Fills *opts with the defaults: fused path, FP64, cg_rtol 1e-13, 200 iterations,
+ * DUAL force mode, scale 1. */
+void l2x_default_opts(l2x_opts* opts);
+
+/* Steps (I)-(IV) of Sec. 2.3 plus the mass matrix: candidate (element, cell)
+ * pairs from bounding boxes, exact clipping of every simplex against its cells,
+ * quadrature of lambda_a * psi_b on the clipped polytopes, CSR assembly of B_g
+ * (rows: solid nodes, columns: nodes of grid g) for every velocity grid and of
+ * M_s.  Synchronises `stream` (pair counts decide allocation sizes).
+ * Errors: EINVAL (arguments), EOUTOFGRID, EDEGENERATE, ENONFINITE, ENOMEM, ECUDA.
+ * On success *out owns all device storage of the coupling. */
+l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const l2x_opts* opts,
+                              void* stream, l2x_handle* out);
+
+/* Re-assembles B_g and M_s for new node positions (same n_nodes, same elements),
+ * as needed when the solid moves (T lives on the current configuration). */
+l2x_status l2x_update_geometry(l2x_handle h, const double* coords, void* stream);
+
+/* Velocity transfer (Step 1 of the FSI algorithm, Sec. 3): for every velocity
+ * grid g, u_s[g] = M_s^{-1} B_g u_f[g] by Jacobi-preconditioned CG.
+ * u_f: n_grids device arrays of n_fluid[g] entries; u_s: n_grids arrays of
+ * n_nodes entries (written).  Returns ENOTCONVERGED if cg_rtol was not met. */
+l2x_status l2x_transfer_velocity(l2x_handle h, const void* const* u_f, void* const* u_s,
+                                 void* stream);
+
+/* Force transfer by the transpose (Step 4 of Sec. 3): for every grid g,
+ *   DUAL : f_f[g] += s * B_g^T M_s^{-1} f_s[g]   (= s T_g^T f_s[g])
+ *   NODAL: f_f[g] += s * B_g^T f_s[g]
+ * f_s: n_grids arrays of n_nodes entries; f_f: n_grids fluid arrays, accumulated. */
+l2x_status l2x_transfer_force(l2x_handle h, const void* const* f_s, void* const* f_f,
+                              void* stream);
+
+/* Building blocks of the two transfers (used by the autograd binding):
+ * y_s[g] = B_g x_f[g];  f_f[g] += scale * B_g^T z_s[g];  w_s[g] = M_s^{-1} y_s[g]. */
+l2x_status l2x_apply_B(l2x_handle h, const void* const* x_f, void* const* y_s, void* stream);
+l2x_status l2x_apply_BT(l2x_handle h, const void* const* z_s, void* const* f_f, double scale,
+                        void* stream);
+l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s, void* stream);
+
+/* Sizes and solver statistics of a coupling (host struct). */
+l2x_status l2x_query(l2x_handle h, l2x_info* info);
+
+/* Copies of internal data for tests, into caller-owned device buffers sized from
+ * l2x_query().  Pairs of grid g: element index and linear cell index (cell
+ * (i0,i1,i2) of grid g at i0 + ncell0*(i1 + ncell1*i2)), element-major with
+ * cells in z, y, x order.  Pair blocks (fused path only): blocks[p*(d+1)*2^d +
+ * a*2^d + b] = ∫_{E∩C} lambda_a psi_b, corner b = bits (x, y, z); vols[p] =
+ * |E∩C|.  CSR (which = L2X_MAT_B0..B2 or L2X_MAT_M): row_ptr (n_rows+1, int64),
+ * cols (int32, ascending within a row), vals (double). */
+l2x_status l2x_export_pairs(l2x_handle h, int32_t grid, int32_t* elem, int32_t* cell, void* stream);
+l2x_status l2x_export_pair_blocks(l2x_handle h, int32_t grid, double* blocks, double* vols,
+                                  void* stream);
+l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t* cols,
+                          double* vals, void* stream);
+
+/* Releases every device allocation of the handle (stream-ordered on the stream
+ * of the last call).  NULL is accepted. */
+l2x_status l2x_destroy(l2x_handle h);
+
+const char* l2x_status_string(l2x_status s);
+/* Description of the most recent error on this host thread ("" if none). */
+const char* l2x_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* L2XFER_H */

@@ -1,0 +1,344 @@
+"""GB300 L2-projection transfer between a staggered Q1 fluid grid and a P1 solid mesh.
+
+A thin ctypes binding of ``libl2xfer.so`` (C ABI declared in ``include/l2xfer.h``):
+argument marshalling only, every step of the transfer runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current CUDA stream.
+
+The method is the variational transfer of Sec. 2.3 of the paper (mortar
+integrals ``B_ij = ∫ psi_j phi_i``, ``S = M_s``, ``w_s = S^-1 B v_f``, forces by
+``T^T``), assembled by the four steps given there.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+__all__ = ["Coupling", "Grid", "VelocityTransfer", "ForceTransfer", "L2XError", "library_path", "load_library",
+           "PLAIN", "FUSED", "FP64", "MIXED", "NODAL", "DUAL"]
+
+PLAIN, FUSED = 0, 1
+FP64, MIXED = 0, 1
+NODAL, DUAL = 0, 1
+MAT_M = 3
+
+
+class L2XError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"l2xfer status {status}: {msg}")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("staggered", ctypes.c_int32), ("ncell", ctypes.c_int32 * 3),
+                ("origin", ctypes.c_double * 3), ("h", ctypes.c_double * 3)]
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_nodes", ctypes.c_int64),
+                ("n_elems", ctypes.c_int64), ("coords", ctypes.c_void_p), ("elems", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("precision", ctypes.c_int32), ("cg_rtol", ctypes.c_double),
+                ("cg_max_iter", ctypes.c_int32), ("force_mode", ctypes.c_int32), ("force_scale", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n_grids", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("n_elems", ctypes.c_int64),
+                ("n_pairs", ctypes.c_int64 * 3), ("n_pairs_total", ctypes.c_int64), ("nnz_B", ctypes.c_int64 * 3),
+                ("nnz_M", ctypes.c_int64), ("n_fluid", ctypes.c_int64 * 3), ("nnode", (ctypes.c_int32 * 3) * 3),
+                ("cg_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cg_residual", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libl2xfer.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libl2xfer.so not found at {_build.LIB}; run paper_1810_13046_gb300.build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.c_void_p
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "l2x_default_opts": ([ctypes.POINTER(_Opts)], None),
+        "l2x_build_coupling": ([ctypes.POINTER(_Grid), ctypes.POINTER(_Mesh), ctypes.POINTER(_Opts), P,
+                                ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "l2x_update_geometry": ([P, P, P], ctypes.c_int),
+        "l2x_transfer_velocity": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_transfer_force": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_apply_B": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_apply_BT": ([P, PP, PP, ctypes.c_double, P], ctypes.c_int),
+        "l2x_solve_mass": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_query": ([P, ctypes.POINTER(_Info)], ctypes.c_int),
+        "l2x_export_pairs": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
+        "l2x_export_pair_blocks": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
+        "l2x_export_csr": ([P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
+        "l2x_destroy": ([P], ctypes.c_int),
+        "l2x_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "l2x_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        lib = load_library()
+        msg = lib.l2x_last_error().decode() or lib.l2x_status_string(status).decode()
+        raise L2XError(status, msg)
+
+
+def _stream_ptr(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptrs(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = t.data_ptr()
+    return arr
+
+
+@dataclass
+class Grid:
+    """Base (pressure) grid: ``ncell`` cells of width ``h`` from ``origin``.
+
+    ``staggered=True`` gives one Q1 velocity grid per axis (Sec. 2.2's staggered
+    arrangement); ``False`` gives one nodal Q1 grid."""
+    dim: int
+    ncell: tuple
+    h: tuple
+    origin: tuple
+    staggered: bool
+
+
+def _as_cgrid(grid) -> _Grid:
+    g = _Grid()
+    g.dim = int(grid.dim)
+    g.staggered = int(bool(grid.staggered))
+    for k in range(3):
+        g.ncell[k] = int(grid.ncell[k]) if k < grid.dim else 1
+        g.origin[k] = float(grid.origin[k]) if k < grid.dim else 0.0
+        g.h[k] = float(grid.h[k]) if k < grid.dim else 1.0
+    return g
+
+
+class Coupling:
+    """B_g (one per velocity grid) and M_s of a P1 mesh in its current configuration.
+
+    ``coords``: (n_nodes, dim) float64 CUDA tensor; ``elems``: (n_elems, dim+1)
+    int32 CUDA tensor.  Fields are float64 tensors (``precision=FP64``) or float32
+    tensors (``precision=MIXED``)."""
+
+    def __init__(self, grid, coords: torch.Tensor, elems: torch.Tensor, path: int = FUSED,
+                 precision: int = FP64, cg_rtol: float | None = None, cg_max_iter: int = 200,
+                 force_mode: int = DUAL, force_scale: float = 1.0):
+        lib = load_library()
+        if not coords.is_cuda or not elems.is_cuda:
+            raise ValueError("coords and elems must be CUDA tensors")
+        self.device = coords.device
+        self.coords = coords.to(torch.float64).contiguous()
+        self.elems = elems.to(torch.int32).contiguous()
+        self.grid = grid
+        self.dim = int(grid.dim)
+        self.n_grids = self.dim if grid.staggered else 1
+        self.precision = precision
+        self.dtype = torch.float32 if precision == MIXED else torch.float64
+        opts = _Opts()
+        lib.l2x_default_opts(ctypes.byref(opts))
+        opts.path = path
+        opts.precision = precision
+        opts.cg_rtol = cg_rtol if cg_rtol is not None else (1e-13 if precision == FP64 else 1e-9)
+        opts.cg_max_iter = cg_max_iter
+        opts.force_mode = force_mode
+        opts.force_scale = force_scale
+        self.force_mode = force_mode
+        self.force_scale = force_scale
+        mesh = _Mesh()
+        mesh.dim = self.dim
+        mesh.n_nodes = self.coords.shape[0]
+        mesh.n_elems = self.elems.shape[0]
+        mesh.coords = self.coords.data_ptr()
+        mesh.elems = self.elems.data_ptr()
+        self._grid_c = _as_cgrid(grid)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.l2x_build_coupling(ctypes.byref(self._grid_c), ctypes.byref(mesh), ctypes.byref(opts),
+                                          _stream_ptr(self.device), ctypes.byref(h)))
+        self._h = h
+        self.n_nodes = int(mesh.n_nodes)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.l2x_destroy(h)
+            self._h = None
+
+    # ------------------------------------------------------------------ info
+    def info(self) -> dict:
+        inf = _Info()
+        _check(load_library().l2x_query(self._h, ctypes.byref(inf)))
+        G = inf.n_grids
+        return dict(dim=inf.dim, n_grids=G, n_nodes=inf.n_nodes, n_elems=inf.n_elems,
+                    n_pairs=[inf.n_pairs[g] for g in range(G)], n_pairs_total=inf.n_pairs_total,
+                    nnz_B=[inf.nnz_B[g] for g in range(G)], nnz_M=inf.nnz_M,
+                    n_fluid=[inf.n_fluid[g] for g in range(G)],
+                    nnode=[tuple(inf.nnode[g][k] for k in range(3)) for g in range(G)],
+                    cg_iters=inf.cg_iters, cg_residual=inf.cg_residual)
+
+    def fluid_sizes(self):
+        return self.info()["n_fluid"]
+
+    # ------------------------------------------------------------------ geometry
+    def update_geometry(self, coords: torch.Tensor):
+        c = coords.to(device=self.device, dtype=torch.float64).contiguous()
+        if c.shape != self.coords.shape:
+            raise ValueError("update_geometry needs the same number of nodes")
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_update_geometry(self._h, ctypes.c_void_p(c.data_ptr()),
+                                                      _stream_ptr(self.device)))
+        self.coords = c
+
+    # ------------------------------------------------------------------ apply
+    def _solid(self):
+        return [torch.empty(self.n_nodes, dtype=self.dtype, device=self.device) for _ in range(self.n_grids)]
+
+    def _fields(self, xs, n):
+        xs = list(xs)
+        if len(xs) != self.n_grids:
+            raise ValueError(f"expected {self.n_grids} arrays")
+        out = []
+        for x, m in zip(xs, n):
+            if x.dtype != self.dtype or not x.is_cuda or x.numel() != m:
+                raise ValueError(f"field must be a CUDA {self.dtype} tensor with {m} entries")
+            out.append(x.contiguous())
+        return out
+
+    def transfer_velocity(self, u_f, out=None):
+        """u_s[g] = M_s^-1 B_g u_f[g] for every velocity grid g."""
+        u_f = self._fields(u_f, self.fluid_sizes())
+        u_s = out if out is not None else self._solid()
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_transfer_velocity(self._h, _ptrs(u_f), _ptrs(u_s), _stream_ptr(self.device)))
+        return u_s
+
+    def transfer_force(self, f_s, f_f=None):
+        """f_f[g] += s B_g^T M_s^-1 f_s[g] (DUAL) or s B_g^T f_s[g] (NODAL); returns f_f."""
+        f_s = self._fields(f_s, [self.n_nodes] * self.n_grids)
+        if f_f is None:
+            f_f = [torch.zeros(n, dtype=self.dtype, device=self.device) for n in self.fluid_sizes()]
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_transfer_force(self._h, _ptrs(f_s), _ptrs(f_f), _stream_ptr(self.device)))
+        return f_f
+
+    def apply_B(self, x_f, out=None):
+        x_f = self._fields(x_f, self.fluid_sizes())
+        y = out if out is not None else self._solid()
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_apply_B(self._h, _ptrs(x_f), _ptrs(y), _stream_ptr(self.device)))
+        return y
+
+    def apply_BT(self, z_s, f_f=None, scale: float = 1.0):
+        z_s = self._fields(z_s, [self.n_nodes] * self.n_grids)
+        if f_f is None:
+            f_f = [torch.zeros(n, dtype=self.dtype, device=self.device) for n in self.fluid_sizes()]
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_apply_BT(self._h, _ptrs(z_s), _ptrs(f_f), float(scale), _stream_ptr(self.device)))
+        return f_f
+
+    def solve_mass(self, y_s, out=None):
+        y_s = self._fields(y_s, [self.n_nodes] * self.n_grids)
+        w = out if out is not None else self._solid()
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_solve_mass(self._h, _ptrs(y_s), _ptrs(w), _stream_ptr(self.device)))
+        return w
+
+    # ------------------------------------------------------------------ exports (tests)
+    def export_pairs(self, g: int):
+        n = self.info()["n_pairs"][g]
+        e = torch.empty(n, dtype=torch.int32, device=self.device)
+        c = torch.empty(n, dtype=torch.int32, device=self.device)
+        _check(load_library().l2x_export_pairs(self._h, g, ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                               _stream_ptr(self.device)))
+        return e, c
+
+    def export_pair_blocks(self, g: int):
+        n = self.info()["n_pairs"][g]
+        d = self.dim
+        b = torch.empty((n, d + 1, 1 << d), dtype=torch.float64, device=self.device)
+        v = torch.empty(n, dtype=torch.float64, device=self.device)
+        _check(load_library().l2x_export_pair_blocks(self._h, g, ctypes.c_void_p(b.data_ptr()),
+                                                     ctypes.c_void_p(v.data_ptr()), _stream_ptr(self.device)))
+        return b, v
+
+    def export_csr(self, which: int):
+        """(row_ptr int64, cols int32, vals float64) of B_which (0..n_grids-1) or M_s (which=3)."""
+        inf = self.info()
+        nnz = inf["nnz_M"] if which == MAT_M else inf["nnz_B"][which]
+        rp = torch.empty(self.n_nodes + 1, dtype=torch.int64, device=self.device)
+        cols = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.device)
+        vals = torch.empty(max(nnz, 1), dtype=torch.float64, device=self.device)
+        _check(load_library().l2x_export_csr(self._h, which, ctypes.c_void_p(rp.data_ptr()),
+                                             ctypes.c_void_p(cols.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+                                             _stream_ptr(self.device)))
+        return rp, cols[:nnz], vals[:nnz]
+
+
+# ---------------------------------------------------------------------- autograd
+
+class VelocityTransfer(torch.autograd.Function):
+    """u_s = M_s^-1 B u_f per grid; backward: grad_u_f = B^T M_s^-1 grad_u_s (the exact adjoint)."""
+
+    @staticmethod
+    def forward(ctx, coupling: Coupling, *u_f):
+        ctx.coupling = coupling
+        return tuple(coupling.transfer_velocity([u.detach() for u in u_f]))
+
+    @staticmethod
+    def backward(ctx, *grad_u_s):
+        c = ctx.coupling
+        gs = [(g if g is not None else torch.zeros(c.n_nodes, dtype=c.dtype, device=c.device)).contiguous()
+              for g in grad_u_s]
+        z = c.solve_mass(gs)
+        gf = c.apply_BT(z, scale=1.0)
+        return (None, *gf)
+
+
+class ForceTransfer(torch.autograd.Function):
+    """f_f = s B^T M_s^-1 f_s (DUAL) or s B^T f_s (NODAL) per grid; backward applies
+    the adjoint s M_s^-1 B (DUAL) or s B (NODAL) to grad_f_f."""
+
+    @staticmethod
+    def forward(ctx, coupling: Coupling, *f_s):
+        ctx.coupling = coupling
+        return tuple(coupling.transfer_force([f.detach() for f in f_s]))
+
+    @staticmethod
+    def backward(ctx, *grad_f_f):
+        c = ctx.coupling
+        gf = [(g if g is not None else torch.zeros(n, dtype=c.dtype, device=c.device)).contiguous()
+              for g, n in zip(grad_f_f, c.fluid_sizes())]
+        y = c.apply_B(gf)
+        if c.force_mode == DUAL:
+            y = c.solve_mass(y)
+        return (None, *[c.force_scale * v for v in y])

@@ -1,0 +1,604 @@
+// C-ABI entry points of l2xfer: handle management and the orchestration of the
+// assembly (steps I-IV of Sec. 2.3) and of the two transfers.
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "l2x_internal.cuh"
+
+using namespace l2x;
+
+struct l2x_coupling {
+    int dim = 0, n_grids = 0;
+    int64_t n_nodes = 0, n_elems = 0;
+    l2x_grid grid{};
+    l2x_opts opts{};
+    SubGrid sg[kMaxGrids]{};
+    cudaStream_t stream = nullptr;
+    // own copies of the mesh
+    double* X = nullptr;
+    int32_t* E = nullptr;
+    // topology
+    int64_t* adj_ptr = nullptr;
+    int32_t* adj = nullptr;
+    int32_t* cursor = nullptr;
+    // per element
+    double* elem_vol = nullptr;
+    ElemBox* boxes = nullptr;
+    int64_t* counts = nullptr;
+    int64_t* offsets = nullptr;      // n_grids*m + 1
+    int32_t* node_box = nullptr;     // n_grids * 6
+    int64_t pair_begin[kMaxGrids + 1]{};
+    // pairs
+    int64_t n_pairs = 0, pair_cap = 0;
+    int32_t* pair_elem = nullptr;
+    int32_t* pair_cell = nullptr;
+    double* blocks = nullptr;
+    double* vols = nullptr;
+    // matrices
+    Csr B[kMaxGrids];
+    int64_t B_cap[kMaxGrids]{};
+    CsrT T[kMaxGrids];
+    int64_t T_cap[kMaxGrids]{}, T_rows_cap[kMaxGrids]{};
+    Csr M;
+    double* M_dinv = nullptr;
+    float* M_dinv32 = nullptr;
+    // scratch
+    void* scan_tmp = nullptr;
+    size_t scan_tmp_cap = 0;
+    int64_t* row_count = nullptr;    // n_nodes + 1
+    void* pcg_ws = nullptr;
+    void* vec_tmp = nullptr;         // n_grids * n_nodes doubles
+    DevStatus* st = nullptr;
+    DevStatus* st_host = nullptr;    // pinned
+    // last solve
+    int cg_iters = 0;
+    double cg_residual = 0.0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+l2x_status fail(l2x_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+l2x_status cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return L2X_ECUDA;
+}
+
+#define L2X_CUDA(call)                                            \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+#define L2X_TRY(call)                     \
+    do {                                  \
+        l2x_status s_ = (call);           \
+        if (s_ != L2X_OK) return s_;      \
+    } while (0)
+
+template <typename T>
+l2x_status dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        g_last_error = "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed";
+        return L2X_ENOMEM;
+    }
+    return L2X_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+l2x_status ensure_scan(l2x_coupling* h, int64_t n) {
+    size_t need = scan_tmp_bytes(n);
+    if (need <= h->scan_tmp_cap && h->scan_tmp) return L2X_OK;
+    if (h->scan_tmp) cudaFree(h->scan_tmp);
+    h->scan_tmp = nullptr;
+    if (cudaMalloc(&h->scan_tmp, need) != cudaSuccess) return fail(L2X_ENOMEM, "scan scratch");
+    h->scan_tmp_cap = need;
+    return L2X_OK;
+}
+
+l2x_status flags_to_status(const DevStatus& s) {
+    if (s.flags & FLAG_NONFINITE) return fail(L2X_ENONFINITE, "non-finite coordinate in element " + std::to_string(s.bad_elem));
+    if (s.flags & FLAG_DEGENERATE) return fail(L2X_EDEGENERATE, "zero-volume element " + std::to_string(s.bad_elem));
+    if (s.flags & FLAG_OUTOFGRID)
+        return fail(L2X_EOUTOFGRID, "element " + std::to_string(s.bad_elem) + " leaves the cells of a velocity grid");
+    if (s.flags & FLAG_CAPACITY) return fail(L2X_ECAPACITY, "fixed-capacity buffer overflow (element box > 1023 cells or node degree too high)");
+    if (s.flags & FLAG_TIMEOUT) return fail(L2X_ETIMEOUT, "device wait timed out");
+    return L2X_OK;
+}
+
+l2x_status read_status(l2x_coupling* h, cudaStream_t s) {
+    L2X_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    L2X_CUDA(cudaGetLastError());
+    return flags_to_status(*h->st_host);
+}
+
+l2x_status reset_status(l2x_coupling* h, cudaStream_t s) {
+    DevStatus z{};
+    z.bad_elem = INT_MAX;
+    *h->st_host = z;
+    L2X_CUDA(cudaMemcpyAsync(h->st, h->st_host, sizeof(DevStatus), cudaMemcpyHostToDevice, s));
+    return L2X_OK;
+}
+
+void make_subgrids(l2x_coupling* h) {
+    const l2x_grid& G = h->grid;
+    for (int g = 0; g < h->n_grids; ++g) {
+        SubGrid& s = h->sg[g];
+        for (int k = 0; k < 3; ++k) {
+            if (k < G.dim) {
+                bool shifted = G.staggered && k != g;
+                s.ncell[k] = shifted ? G.ncell[k] - 1 : G.ncell[k];
+                s.origin[k] = shifted ? G.origin[k] + 0.5 * G.h[k] : G.origin[k];
+                s.h[k] = G.h[k];
+                s.inv_h[k] = 1.0 / G.h[k];
+            } else {
+                s.ncell[k] = 1;
+                s.origin[k] = 0.0;
+                s.h[k] = 1.0;
+                s.inv_h[k] = 1.0;
+            }
+            s.nnode[k] = k < G.dim ? s.ncell[k] + 1 : 1;
+        }
+    }
+}
+
+// Topology-only structures: node adjacency and the sparsity of M_s.
+l2x_status build_topology(l2x_coupling* h, cudaStream_t s) {
+    const int64_t n = h->n_nodes, m = h->n_elems;
+    const int NA = h->dim + 1;
+    L2X_TRY(dalloc(&h->adj_ptr, n + 1));
+    L2X_TRY(dalloc(&h->adj, (size_t)(m * NA)));
+    L2X_TRY(dalloc(&h->cursor, n));
+    L2X_TRY(dalloc(&h->row_count, n + 1));
+    L2X_TRY(ensure_scan(h, n));
+    launch_node_adjacency(h->dim, n, m, h->E, h->adj_ptr, h->adj, h->cursor, h->scan_tmp, s);
+    // mass structure
+    launch_mass_structure(0, h->dim, n, h->E, h->adj_ptr, h->adj, h->row_count, nullptr, nullptr, h->st, s);
+    L2X_TRY(dalloc(&h->M.ptr, n + 1));
+    launch_scan_i64(h->row_count, h->M.ptr, n, h->scan_tmp, s);
+    int64_t nnz = 0;
+    L2X_CUDA(cudaMemcpyAsync(&nnz, h->M.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    L2X_TRY(read_status(h, s));
+    h->M.n_rows = n;
+    h->M.nnz = nnz;
+    L2X_TRY(dalloc(&h->M.col, nnz));
+    L2X_TRY(dalloc(&h->M.val, nnz));
+    L2X_TRY(dalloc(&h->M.val32, nnz));
+    L2X_TRY(dalloc(&h->M_dinv, n));
+    L2X_TRY(dalloc(&h->M_dinv32, n));
+    launch_mass_structure(1, h->dim, n, h->E, h->adj_ptr, h->adj, nullptr, h->M.ptr, h->M.col, h->st, s);
+    return L2X_OK;
+}
+
+// Everything that depends on the node positions.
+l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
+    const int64_t n = h->n_nodes, m = h->n_elems;
+    const int G = h->n_grids, d = h->dim;
+    const int NS = (d + 1) << d;
+    L2X_TRY(reset_status(h, s));
+    int32_t nb_init[kMaxGrids * 6];
+    for (int g = 0; g < G; ++g)
+        for (int k = 0; k < 3; ++k) {
+            nb_init[g * 6 + k] = INT_MAX;
+            nb_init[g * 6 + 3 + k] = INT_MIN;
+        }
+    L2X_CUDA(cudaMemcpyAsync(h->node_box, nb_init, sizeof(int32_t) * 6 * G, cudaMemcpyHostToDevice, s));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    // (I) candidate boxes, counts, offsets
+    launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->node_box, h->elem_vol, h->st, s);
+    launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
+    std::vector<int64_t> gb(G + 1);
+    for (int g = 0; g <= G; ++g)
+        L2X_CUDA(cudaMemcpyAsync(&gb[g], h->offsets + (int64_t)g * m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int32_t nbh[kMaxGrids * 6];
+    L2X_CUDA(cudaMemcpyAsync(nbh, h->node_box, sizeof(int32_t) * 6 * G, cudaMemcpyDeviceToHost, s));
+    L2X_TRY(read_status(h, s));
+    for (int g = 0; g <= G; ++g) h->pair_begin[g] = gb[g];
+    h->n_pairs = gb[G];
+    const int64_t NP = h->n_pairs;
+    if (NP > h->pair_cap || !h->pair_elem) {
+        dfree(h->pair_elem);
+        dfree(h->pair_cell);
+        dfree(h->blocks);
+        dfree(h->vols);
+        h->pair_cap = 0;
+        const int64_t cap = NP + NP / 4 + 128;
+        L2X_TRY(dalloc(&h->pair_elem, cap));
+        L2X_TRY(dalloc(&h->pair_cell, cap));
+        L2X_TRY(dalloc(&h->blocks, (size_t)cap * NS));
+        L2X_TRY(dalloc(&h->vols, cap));
+        h->pair_cap = cap;
+    }
+    launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, s);
+    // (II)-(III) clip + quadrature
+    const bool plain = h->opts.path == L2X_PATH_PLAIN;
+    for (int g = 0; g < G; ++g) {
+        if (plain)
+            launch_clip_plain(d, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks,
+                              h->vols, h->st, s);
+        else
+            launch_clip_fused(d, h->opts.precision, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem,
+                              h->pair_cell, h->blocks, h->pair_cap, h->vols, h->st, s);
+    }
+    // (IV) B_g by rows
+    for (int g = 0; g < G; ++g) {
+        Csr& B = h->B[g];
+        const ElemBox* bx = h->boxes + (int64_t)g * m;
+        const int64_t* off = h->offsets + (int64_t)g * m;
+        launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, h->row_count,
+                      nullptr, nullptr, nullptr, h->st, s);
+        if (!B.ptr) L2X_TRY(dalloc(&B.ptr, n + 1));
+        launch_scan_i64(h->row_count, B.ptr, n, h->scan_tmp, s);
+        int64_t nnz = 0;
+        L2X_CUDA(cudaMemcpyAsync(&nnz, B.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        L2X_TRY(read_status(h, s));
+        B.n_rows = n;
+        B.nnz = nnz;
+        if (nnz > h->B_cap[g] || !B.col) {
+            dfree(B.col);
+            dfree(B.val);
+            dfree(B.val32);
+            int64_t c = nnz + nnz / 4 + 16;
+            L2X_TRY(dalloc(&B.col, c));
+            L2X_TRY(dalloc(&B.val, c));
+            L2X_TRY(dalloc(&B.val32, c));
+            h->B_cap[g] = c;
+        }
+        if (plain) {
+            launch_b_rows(2, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, nullptr,
+                          B.ptr, B.col, B.val, h->st, s);
+            launch_scatter_plain(d, h->sg[g], h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks, h->vols,
+                                 B, s);
+        } else {
+            launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, nullptr,
+                          B.ptr, B.col, B.val, h->st, s);
+            if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, nnz, s);
+            // B_g^T over the box of touched fluid nodes
+            CsrT& T = h->T[g];
+            int64_t rows = 1;
+            for (int k = 0; k < 3; ++k) {
+                if (k < d && nbh[g * 6 + k] <= nbh[g * 6 + 3 + k]) {
+                    T.lo[k] = nbh[g * 6 + k];
+                    T.n[k] = nbh[g * 6 + 3 + k] - nbh[g * 6 + k] + 1;
+                } else {
+                    T.lo[k] = 0;
+                    T.n[k] = 1;
+                }
+                rows *= T.n[k];
+            }
+            T.n_rows = rows;
+            if (rows + 1 > h->T_rows_cap[g] || !T.ptr) {
+                dfree(T.ptr);
+                L2X_TRY(dalloc(&T.ptr, rows + 1));
+                h->T_rows_cap[g] = rows + 1;
+            }
+            if (nnz > h->T_cap[g] || !T.col) {
+                dfree(T.col);
+                dfree(T.val);
+                dfree(T.val32);
+                int64_t c = nnz + nnz / 4 + 16;
+                L2X_TRY(dalloc(&T.col, c));
+                L2X_TRY(dalloc(&T.val, c));
+                L2X_TRY(dalloc(&T.val32, c));
+                h->T_cap[g] = c;
+            }
+            L2X_TRY(ensure_scan(h, rows));
+            int32_t* tcursor = nullptr;
+            L2X_TRY(dalloc(&tcursor, rows));
+            launch_transpose_count(B, h->sg[g], T, T.ptr, s);
+            launch_scan_i64(T.ptr, T.ptr, rows, h->scan_tmp, s);
+            launch_transpose_fill(B, h->sg[g], T, tcursor, s);
+            launch_transpose_sort(T, s);
+            if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, nnz, s);
+            L2X_CUDA(cudaStreamSynchronize(s));
+            cudaFree(tcursor);
+        }
+    }
+    // mass matrix values
+    launch_mass_values(d, n, h->E, h->adj_ptr, h->adj, h->elem_vol, h->M.ptr, h->M.col, h->M.val, h->M_dinv, s);
+    launch_to_f32(h->M.val, h->M.val32, h->M.nnz, s);
+    launch_to_f32(h->M_dinv, h->M_dinv32, n, s);
+    return read_status(h, s);
+}
+
+l2x_status validate(const l2x_grid* grid, const l2x_mesh* mesh, const l2x_opts* o) {
+    if (!grid || !mesh) return fail(L2X_EINVAL, "grid and mesh must not be NULL");
+    if (grid->dim != 2 && grid->dim != 3) return fail(L2X_EINVAL, "grid dim must be 2 or 3");
+    if (mesh->dim != grid->dim) return fail(L2X_EINVAL, "mesh dim differs from grid dim");
+    if (mesh->n_nodes <= 0 || mesh->n_elems <= 0) return fail(L2X_EINVAL, "empty mesh");
+    if (mesh->n_nodes >= INT_MAX || mesh->n_elems >= (INT_MAX >> 2)) return fail(L2X_EINVAL, "mesh too large for int32 indices");
+    if (!mesh->coords || !mesh->elems) return fail(L2X_EINVAL, "mesh arrays must not be NULL");
+    for (int k = 0; k < grid->dim; ++k) {
+        if (grid->ncell[k] < (grid->staggered ? 2 : 1)) return fail(L2X_EINVAL, "ncell too small");
+        if (!(grid->h[k] > 0.0)) return fail(L2X_EINVAL, "h must be positive");
+    }
+    int64_t nodes = 1;
+    for (int k = 0; k < grid->dim; ++k) nodes *= (int64_t)grid->ncell[k] + 1;
+    if (nodes >= INT_MAX) return fail(L2X_EINVAL, "grid too large for int32 node indices");
+    if (o) {
+        if (o->path != L2X_PATH_PLAIN && o->path != L2X_PATH_FUSED) return fail(L2X_EINVAL, "bad path");
+        if (o->precision != L2X_FP64 && o->precision != L2X_MIXED) return fail(L2X_EINVAL, "bad precision");
+        if (o->path == L2X_PATH_PLAIN && o->precision != L2X_FP64) return fail(L2X_EINVAL, "the plain path is FP64 only");
+        if (!(o->cg_rtol > 0.0) || o->cg_max_iter <= 0) return fail(L2X_EINVAL, "bad CG settings");
+        if (o->force_mode != L2X_FORCE_NODAL && o->force_mode != L2X_FORCE_DUAL) return fail(L2X_EINVAL, "bad force mode");
+    }
+    return L2X_OK;
+}
+
+l2x_status check_ptrs(const void* const* a, int n, const char* what) {
+    if (!a) return fail(L2X_EINVAL, std::string(what) + " must not be NULL");
+    for (int i = 0; i < n; ++i)
+        if (!a[i]) return fail(L2X_EINVAL, std::string(what) + " has a NULL component");
+    return L2X_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void l2x_default_opts(l2x_opts* o) {
+    if (!o) return;
+    o->path = L2X_PATH_FUSED;
+    o->precision = L2X_FP64;
+    o->cg_rtol = 1e-13;
+    o->cg_max_iter = 200;
+    o->force_mode = L2X_FORCE_DUAL;
+    o->force_scale = 1.0;
+}
+
+const char* l2x_status_string(l2x_status s) {
+    switch (s) {
+        case L2X_OK: return "ok";
+        case L2X_EINVAL: return "invalid argument";
+        case L2X_ENOMEM: return "out of device memory";
+        case L2X_ECAPACITY: return "capacity exceeded";
+        case L2X_EOUTOFGRID: return "solid element outside the fluid grid";
+        case L2X_EDEGENERATE: return "degenerate solid element";
+        case L2X_ENOTCONVERGED: return "mass-matrix solve did not converge";
+        case L2X_ETIMEOUT: return "device wait timed out";
+        case L2X_ECUDA: return "CUDA error";
+        case L2X_ENONFINITE: return "non-finite input";
+    }
+    return "unknown status";
+}
+
+const char* l2x_last_error(void) { return g_last_error.c_str(); }
+
+l2x_status l2x_destroy(l2x_handle h) {
+    if (!h) return L2X_OK;
+    cudaStreamSynchronize(h->stream);
+    dfree(h->X); dfree(h->E); dfree(h->adj_ptr); dfree(h->adj); dfree(h->cursor); dfree(h->elem_vol);
+    dfree(h->boxes); dfree(h->counts); dfree(h->offsets); dfree(h->node_box); dfree(h->pair_elem);
+    dfree(h->pair_cell); dfree(h->blocks); dfree(h->vols);
+    for (int g = 0; g < kMaxGrids; ++g) {
+        dfree(h->B[g].ptr); dfree(h->B[g].col); dfree(h->B[g].val); dfree(h->B[g].val32);
+        dfree(h->T[g].ptr); dfree(h->T[g].col); dfree(h->T[g].val); dfree(h->T[g].val32);
+    }
+    dfree(h->M.ptr); dfree(h->M.col); dfree(h->M.val); dfree(h->M.val32); dfree(h->M_dinv); dfree(h->M_dinv32);
+    if (h->scan_tmp) cudaFree(h->scan_tmp);
+    dfree(h->row_count);
+    if (h->pcg_ws) cudaFree(h->pcg_ws);
+    if (h->vec_tmp) cudaFree(h->vec_tmp);
+    dfree(h->st);
+    if (h->st_host) cudaFreeHost(h->st_host);
+    delete h;
+    return L2X_OK;
+}
+
+l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const l2x_opts* opts, void* stream,
+                              l2x_handle* out) {
+    g_last_error.clear();
+    if (!out) return fail(L2X_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    l2x_opts o;
+    l2x_default_opts(&o);
+    if (opts) o = *opts;
+    L2X_TRY(validate(grid, mesh, &o));
+    cudaStream_t s = (cudaStream_t)stream;
+    l2x_coupling* h = new l2x_coupling();
+    h->dim = grid->dim;
+    h->n_grids = grid->staggered ? grid->dim : 1;
+    h->n_nodes = mesh->n_nodes;
+    h->n_elems = mesh->n_elems;
+    h->grid = *grid;
+    h->opts = o;
+    h->stream = s;
+    make_subgrids(h);
+    auto body = [&]() -> l2x_status {
+        const int64_t n = h->n_nodes, m = h->n_elems;
+        const int d = h->dim, G = h->n_grids;
+        if (cudaMallocHost((void**)&h->st_host, sizeof(DevStatus)) != cudaSuccess) return fail(L2X_ENOMEM, "pinned status");
+        L2X_TRY(dalloc(&h->st, 1));
+        L2X_TRY(dalloc(&h->X, (size_t)(n * d)));
+        L2X_TRY(dalloc(&h->E, (size_t)(m * (d + 1))));
+        L2X_CUDA(cudaMemcpyAsync(h->X, mesh->coords, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
+        L2X_CUDA(cudaMemcpyAsync(h->E, mesh->elems, sizeof(int32_t) * m * (d + 1), cudaMemcpyDeviceToDevice, s));
+        L2X_TRY(dalloc(&h->elem_vol, m));
+        L2X_TRY(dalloc(&h->boxes, (size_t)(G * m)));
+        L2X_TRY(dalloc(&h->counts, (size_t)(G * m)));
+        L2X_TRY(dalloc(&h->offsets, (size_t)(G * m + 1)));
+        L2X_TRY(dalloc(&h->node_box, (size_t)(6 * G)));
+        L2X_TRY(ensure_scan(h, (int64_t)G * m > n ? (int64_t)G * m : n));
+        L2X_TRY(reset_status(h, s));
+        // element indices must be valid node numbers: checked on the host copy-free path by the
+        // adjacency kernel's atomics would fault otherwise, so verify here.
+        {
+            std::vector<int32_t> eh((size_t)(m * (d + 1)));
+            L2X_CUDA(cudaMemcpyAsync(eh.data(), h->E, sizeof(int32_t) * eh.size(), cudaMemcpyDeviceToHost, s));
+            L2X_CUDA(cudaStreamSynchronize(s));
+            for (int32_t v : eh)
+                if (v < 0 || v >= n) return fail(L2X_EINVAL, "element references a node outside [0, n_nodes)");
+        }
+        L2X_TRY(build_topology(h, s));
+        size_t ws = pcg_ws_bytes(n, G, pcg_max_blocks());
+        if (cudaMalloc(&h->pcg_ws, ws) != cudaSuccess) return fail(L2X_ENOMEM, "CG workspace");
+        if (cudaMalloc(&h->vec_tmp, sizeof(double) * n * G) != cudaSuccess) return fail(L2X_ENOMEM, "vector scratch");
+        return build_geometry(h, s);
+    };
+    l2x_status st = body();
+    if (st != L2X_OK) {
+        std::string keep = g_last_error;
+        l2x_destroy(h);
+        g_last_error = keep;
+        return st;
+    }
+    *out = h;
+    return L2X_OK;
+}
+
+l2x_status l2x_update_geometry(l2x_handle h, const double* coords, void* stream) {
+    g_last_error.clear();
+    if (!h || !coords) return fail(L2X_EINVAL, "NULL handle or coordinates");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->stream = s;
+    L2X_CUDA(cudaMemcpyAsync(h->X, coords, sizeof(double) * h->n_nodes * h->dim, cudaMemcpyDeviceToDevice, s));
+    return build_geometry(h, s);
+}
+
+l2x_status l2x_apply_B(l2x_handle h, const void* const* x_f, void* const* y_s, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    L2X_TRY(check_ptrs(x_f, h->n_grids, "x_f"));
+    L2X_TRY(check_ptrs((const void* const*)y_s, h->n_grids, "y_s"));
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_spmv_B(h->opts.path, h->opts.precision, h->n_grids, h->B, x_f, y_s, s);
+    L2X_CUDA(cudaGetLastError());
+    return L2X_OK;
+}
+
+l2x_status l2x_apply_BT(l2x_handle h, const void* const* z_s, void* const* f_f, double scale, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    L2X_TRY(check_ptrs(z_s, h->n_grids, "z_s"));
+    L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_spmv_BT(h->opts.path, h->opts.precision, h->n_grids, h->B, h->T, h->sg, z_s, f_f, scale, s);
+    L2X_CUDA(cudaGetLastError());
+    return L2X_OK;
+}
+
+l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    L2X_TRY(check_ptrs(y_s, h->n_grids, "y_s"));
+    L2X_TRY(check_ptrs((const void* const*)w_s, h->n_grids, "w_s"));
+    cudaStream_t s = (cudaStream_t)stream;
+    PcgResult r;
+    l2x_status st = solve_mass_pcg(h->opts.path, h->opts.precision, h->M, h->M_dinv, h->M_dinv32, h->n_grids, y_s,
+                                   w_s, h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, h->st_host, s, &r);
+    h->cg_iters = r.iters;
+    h->cg_residual = r.residual;
+    if (st == L2X_ECUDA) return cuda_fail(cudaGetLastError(), "mass-matrix solve");
+    if (st == L2X_ENOTCONVERGED)
+        return fail(st, "CG reached relative residual " + std::to_string(r.residual) + " after " + std::to_string(r.iters) + " iterations");
+    return st;
+}
+
+l2x_status l2x_transfer_velocity(l2x_handle h, const void* const* u_f, void* const* u_s, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    L2X_TRY(check_ptrs(u_f, h->n_grids, "u_f"));
+    L2X_TRY(check_ptrs((const void* const*)u_s, h->n_grids, "u_s"));
+    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+    void* y[kMaxGrids];
+    for (int g = 0; g < h->n_grids; ++g) y[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
+    L2X_TRY(l2x_apply_B(h, u_f, y, stream));
+    return l2x_solve_mass(h, (const void* const*)y, u_s, stream);
+}
+
+l2x_status l2x_transfer_force(l2x_handle h, const void* const* f_s, void* const* f_f, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    L2X_TRY(check_ptrs(f_s, h->n_grids, "f_s"));
+    L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
+    if (h->opts.force_mode == L2X_FORCE_NODAL) return l2x_apply_BT(h, f_s, f_f, h->opts.force_scale, stream);
+    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+    void* z[kMaxGrids];
+    for (int g = 0; g < h->n_grids; ++g) z[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
+    L2X_TRY(l2x_solve_mass(h, f_s, z, stream));
+    return l2x_apply_BT(h, (const void* const*)z, f_f, h->opts.force_scale, stream);
+}
+
+l2x_status l2x_query(l2x_handle h, l2x_info* info) {
+    if (!h || !info) return fail(L2X_EINVAL, "NULL handle or info");
+    memset(info, 0, sizeof(*info));
+    info->dim = h->dim;
+    info->n_grids = h->n_grids;
+    info->path = h->opts.path;
+    info->precision = h->opts.precision;
+    info->n_nodes = h->n_nodes;
+    info->n_elems = h->n_elems;
+    for (int g = 0; g < h->n_grids; ++g) {
+        info->n_pairs[g] = h->pair_begin[g + 1] - h->pair_begin[g];
+        info->nnz_B[g] = h->B[g].nnz;
+        int64_t nf = 1;
+        for (int k = 0; k < 3; ++k) {
+            info->nnode[g][k] = h->sg[g].nnode[k];
+            nf *= h->sg[g].nnode[k];
+        }
+        info->n_fluid[g] = nf;
+    }
+    info->n_pairs_total = h->n_pairs;
+    info->nnz_M = h->M.nnz;
+    info->cg_iters = h->cg_iters;
+    info->cg_residual = h->cg_residual;
+    return L2X_OK;
+}
+
+l2x_status l2x_export_pairs(l2x_handle h, int32_t grid, int32_t* elem, int32_t* cell, void* stream) {
+    if (!h || !elem || !cell || grid < 0 || grid >= h->n_grids) return fail(L2X_EINVAL, "bad export_pairs arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t p0 = h->pair_begin[grid], np = h->pair_begin[grid + 1] - p0;
+    L2X_CUDA(cudaMemcpyAsync(elem, h->pair_elem + p0, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, s));
+    L2X_CUDA(cudaMemcpyAsync(cell, h->pair_cell + p0, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, s));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    return L2X_OK;
+}
+
+l2x_status l2x_export_pair_blocks(l2x_handle h, int32_t grid, double* blocks, double* vols, void* stream) {
+    if (!h || !blocks || !vols || grid < 0 || grid >= h->n_grids) return fail(L2X_EINVAL, "bad export arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int NS = (h->dim + 1) << h->dim;
+    int64_t p0 = h->pair_begin[grid], np = h->pair_begin[grid + 1] - p0;
+    L2X_CUDA(cudaMemcpyAsync(vols, h->vols + p0, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
+    if (h->opts.path == L2X_PATH_PLAIN) {
+        L2X_CUDA(cudaMemcpyAsync(blocks, h->blocks + p0 * NS, sizeof(double) * np * NS, cudaMemcpyDeviceToDevice, s));
+    } else {
+        // structure-of-arrays -> pair-major
+        for (int slot = 0; slot < NS; ++slot)
+            L2X_CUDA(cudaMemcpy2DAsync(blocks + slot, sizeof(double) * NS, h->blocks + slot * h->pair_cap + p0,
+                                       sizeof(double), sizeof(double), np, cudaMemcpyDeviceToDevice, s));
+    }
+    L2X_CUDA(cudaStreamSynchronize(s));
+    return L2X_OK;
+}
+
+l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t* cols, double* vals, void* stream) {
+    if (!h || !row_ptr || !cols || !vals) return fail(L2X_EINVAL, "bad export_csr arguments");
+    const Csr* A = nullptr;
+    if (which == L2X_MAT_M) A = &h->M;
+    else if (which >= 0 && which < h->n_grids) A = &h->B[which];
+    else return fail(L2X_EINVAL, "bad matrix id");
+    cudaStream_t s = (cudaStream_t)stream;
+    L2X_CUDA(cudaMemcpyAsync(row_ptr, A->ptr, sizeof(int64_t) * (A->n_rows + 1), cudaMemcpyDeviceToDevice, s));
+    L2X_CUDA(cudaMemcpyAsync(cols, A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToDevice, s));
+    L2X_CUDA(cudaMemcpyAsync(vals, A->val, sizeof(double) * A->nnz, cudaMemcpyDeviceToDevice, s));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    return L2X_OK;
+}
+
+}  // extern "C"

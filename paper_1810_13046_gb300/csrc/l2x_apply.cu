@@ -1,0 +1,677 @@
+// Velocity and force transfer (Sec. 2.3, algebraic form B v_f = S w_s,
+// w_s = S^-1 B v_f = T v_f, forces by T^T; Steps 1 and 4 of the FSI algorithm,
+// Sec. 3): sparse products with B_g and B_g^T and the Jacobi-preconditioned
+// conjugate-gradient solve with S = M_s.
+#include <cooperative_groups.h>
+
+#include <cmath>
+
+#include "l2x_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace l2x {
+
+namespace {
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------ B x
+template <typename TV, typename TM>
+struct SpmvPack {
+    const int64_t* ptr[kMaxGrids];
+    const int32_t* col[kMaxGrids];
+    const TM* val[kMaxGrids];
+    const TV* x[kMaxGrids];
+    TV* y[kMaxGrids];
+};
+
+// 8 lanes per row; accumulation in the vector type.
+template <typename TV, typename TM>
+__global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM> P) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t grp = tid >> 3;
+    const int l8 = threadIdx.x & 7;
+    const bool active = grp < n_rows * n_grids;
+    const int g = active ? (int)(grp / n_rows) : 0;
+    const int64_t row = active ? grp - g * n_rows : 0;
+    TV acc = TV(0);
+    if (active) {
+        const int64_t lo = P.ptr[g][row], hi = P.ptr[g][row + 1];
+        const int32_t* __restrict__ col = P.col[g];
+        const TM* __restrict__ val = P.val[g];
+        const TV* __restrict__ x = P.x[g];
+        for (int64_t q = lo + l8; q < hi; q += 8) acc += (TV)__ldg(val + q) * __ldg(x + __ldg(col + q));
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (active && l8 == 0) P.y[g][row] = acc;
+}
+
+__global__ void spmv_B_plain_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                    const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    double s = 0.0;
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) s += val[q] * x[col[q]];
+    y[i] = s;
+}
+
+// ------------------------------------------------------------------ B^T z
+template <typename TV, typename TM>
+struct SpmvTPack {
+    const int64_t* ptr[kMaxGrids];
+    const int32_t* col[kMaxGrids];
+    const TM* val[kMaxGrids];
+    int32_t lo[kMaxGrids][3];
+    int32_t n[kMaxGrids][3];
+    int32_t nnode[kMaxGrids][3];
+    int64_t n_rows[kMaxGrids];
+    int64_t row_base[kMaxGrids + 1];
+    const TV* z[kMaxGrids];
+    TV* f[kMaxGrids];
+};
+
+// One thread per row of B_g^T (fluid node of the touched box): gather, no atomics.
+template <typename TV, typename TM>
+__global__ void spmv_BT_fused_kernel(int n_grids, SpmvTPack<TV, TM> P, TV scale) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= P.row_base[n_grids]) return;
+    int g = 0;
+    while (g + 1 < n_grids && t >= P.row_base[g + 1]) ++g;
+    const int64_t r = t - P.row_base[g];
+    const int64_t lo = P.ptr[g][r], hi = P.ptr[g][r + 1];
+    if (lo == hi) return;
+    TV acc = TV(0);
+    const TV* __restrict__ z = P.z[g];
+    for (int64_t q = lo; q < hi; ++q) acc += (TV)__ldg(P.val[g] + q) * __ldg(z + __ldg(P.col[g] + q));
+    const int x = (int)(r % P.n[g][0]);
+    const int64_t rr = r / P.n[g][0];
+    const int y = (int)(rr % P.n[g][1]);
+    const int zz = (int)(rr / P.n[g][1]);
+    const int64_t node = (x + P.lo[g][0]) + (int64_t)P.nnode[g][0] * ((y + P.lo[g][1]) + (int64_t)P.nnode[g][1] * (zz + P.lo[g][2]));
+    P.f[g][node] += scale * acc;
+}
+
+__global__ void spmv_BT_plain_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                     const double* __restrict__ val, const double* __restrict__ z, double* f,
+                                     double scale) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    double zi = scale * z[i];
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) atomicAdd(f + col[q], val[q] * zi);
+}
+
+// ------------------------------------------------------------------ PCG (fused, cooperative)
+constexpr int kPcgThreads = 256;
+constexpr int kMaxRhs = 3;
+
+// Dot-product accumulator: exact double for FP64 vectors; for FP32 vectors the
+// product is split exactly (fma) and summed with an error-compensated pair of
+// floats, converted to double once per thread.
+template <typename TV>
+struct DotAcc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(TV a, TV b) { s = fma((double)a, (double)b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        float p = __fmul_rn(a, b);
+        float e = __fmaf_rn(a, b, -p);
+        float s = __fadd_rn(hi, p);
+        float bb = __fsub_rn(s, hi);
+        float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <typename TV>
+struct PcgArgs {
+    int64_t n;
+    int nrhs;
+    const int64_t* ptr;
+    const int32_t* col;
+    const TV* val;
+    const TV* dinv;
+    const TV* y[kMaxRhs];
+    TV* x[kMaxRhs];
+    TV* r;   // n * nrhs each, component-major
+    TV* u;
+    TV* p;
+    TV* s;
+    TV* w;
+    double* partial;  // gridDim.x * 3 * kMaxRhs
+    double rtol;
+    int max_iter;
+    DevStatus* st;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// Chronopoulos-Gear form of Jacobi-PCG: one global reduction and one vector
+// exchange per iteration (two grid barriers), all right-hand sides together.
+template <typename TV>
+__global__ void __launch_bounds__(kPcgThreads) pcg_fused_kernel(PcgArgs<TV> A) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ double sh[32];
+    __shared__ double tot[3 * kMaxRhs];
+    const int nr = A.nrhs;
+    const int64_t n = A.n;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = min(n, (int64_t)blockIdx.x * per), r1 = min(n, r0 + per);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const TV di = A.dinv[i];
+        for (int k = 0; k < nr; ++k) {
+            TV yi = A.y[k][i];
+            A.x[k][i] = TV(0);
+            A.r[k * n + i] = yi;
+            A.u[k * n + i] = di * yi;
+        }
+    }
+    grid.sync();
+    double alpha[kMaxRhs], gamma_old[kMaxRhs], rho0[kMaxRhs], rho[kMaxRhs];
+    bool conv[kMaxRhs];
+    for (int k = 0; k < kMaxRhs; ++k) { alpha[k] = 0.0; gamma_old[k] = 0.0; rho0[k] = 0.0; rho[k] = 0.0; conv[k] = true; }
+    int it = 0;
+    bool all_conv = false;
+    for (;;) {
+        DotAcc<TV> dg[kMaxRhs], dd[kMaxRhs], dr[kMaxRhs];
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const int64_t lo = A.ptr[i], hi = A.ptr[i + 1];
+            TV acc[kMaxRhs];
+            for (int k = 0; k < kMaxRhs; ++k) acc[k] = TV(0);
+            for (int64_t q = lo; q < hi; ++q) {
+                const TV v = A.val[q];
+                const int32_t j = A.col[q];
+                for (int k = 0; k < nr; ++k) acc[k] += v * A.u[k * n + j];
+            }
+            for (int k = 0; k < nr; ++k) {
+                const TV ri = A.r[k * n + i], ui = A.u[k * n + i];
+                A.w[k * n + i] = acc[k];
+                dg[k].add(ri, ui);
+                dd[k].add(acc[k], ui);
+                dr[k].add(ri, ri);
+            }
+        }
+        for (int k = 0; k < nr; ++k) {
+            double a = block_sum(dg[k].value(), sh);
+            double b = block_sum(dd[k].value(), sh);
+            double c = block_sum(dr[k].value(), sh);
+            if (threadIdx.x == 0) {
+                A.partial[(int64_t)blockIdx.x * 3 * kMaxRhs + 3 * k + 0] = a;
+                A.partial[(int64_t)blockIdx.x * 3 * kMaxRhs + 3 * k + 1] = b;
+                A.partial[(int64_t)blockIdx.x * 3 * kMaxRhs + 3 * k + 2] = c;
+            }
+        }
+        grid.sync();
+        for (int j = 0; j < 3 * nr; ++j) {
+            double v = 0.0;
+            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += A.partial[(int64_t)b * 3 * kMaxRhs + j];
+            v = block_sum(v, sh);
+            if (threadIdx.x == 0) tot[j] = v;
+        }
+        __syncthreads();
+        double beta[kMaxRhs];
+        all_conv = true;
+        for (int k = 0; k < nr; ++k) {
+            const double gam = tot[3 * k], del = tot[3 * k + 1];
+            rho[k] = tot[3 * k + 2];
+            if (it == 0) rho0[k] = rho[k];
+            conv[k] = rho[k] <= A.rtol * A.rtol * rho0[k];
+            all_conv = all_conv && conv[k];
+            beta[k] = 0.0;
+            if (!conv[k]) {
+                if (it == 0) {
+                    alpha[k] = gam / del;
+                } else {
+                    beta[k] = gam / gamma_old[k];
+                    alpha[k] = gam / (del - beta[k] * gam / alpha[k]);
+                }
+                gamma_old[k] = gam;
+            }
+        }
+        if (all_conv || it >= A.max_iter) break;
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const TV di = A.dinv[i];
+            for (int k = 0; k < nr; ++k) {
+                if (conv[k]) continue;
+                const int64_t o = k * n + i;
+                const TV b = (TV)beta[k], a = (TV)alpha[k];
+                const TV pn = it == 0 ? A.u[o] : A.u[o] + b * A.p[o];
+                const TV sn = it == 0 ? A.w[o] : A.w[o] + b * A.s[o];
+                A.p[o] = pn;
+                A.s[o] = sn;
+                A.x[k][i] += a * pn;
+                const TV rn = A.r[o] - a * sn;
+                A.r[o] = rn;
+                A.u[o] = di * rn;
+            }
+        }
+        grid.sync();
+        ++it;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double worst = 0.0;
+        for (int k = 0; k < nr; ++k) worst = fmax(worst, rho0[k] > 0.0 ? sqrt(rho[k] / rho0[k]) : 0.0);
+        A.st->cg_iters = it;
+        A.st->cg_residual = worst;
+        if (!all_conv) atomicOr(&A.st->flags, FLAG_NOTCONVERGED);
+    }
+}
+
+// ------------------------------------------------------------------ PCG (plain, unfused, FP64)
+__global__ void plain_init_kernel(int64_t n, int nr, const double* y0, const double* y1, const double* y2,
+                                  double* x0, double* x1, double* x2, const double* dinv, double* r, double* z,
+                                  double* p) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* y[3] = {y0, y1, y2};
+    double* x[3] = {x0, x1, x2};
+    for (int k = 0; k < nr; ++k) {
+        double yi = y[k][i];
+        x[k][i] = 0.0;
+        r[k * n + i] = yi;
+        z[k * n + i] = dinv[i] * yi;
+        p[k * n + i] = dinv[i] * yi;
+    }
+}
+
+__global__ void plain_spmv_kernel(int64_t n, int nr, const int64_t* ptr, const int32_t* col, const double* val,
+                                  const double* p, double* q) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < nr; ++k) {
+        double s = 0.0;
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e] * p[k * n + col[e]];
+        q[k * n + i] = s;
+    }
+}
+
+// out[k] += sum_i a[k*n+i] * b[k*n+i]
+__global__ void plain_dot_kernel(int64_t n, int nr, const double* a, const double* b, double* out) {
+    __shared__ double sh[32];
+    for (int k = 0; k < nr; ++k) {
+        double v = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            v += a[k * n + i] * b[k * n + i];
+        v = block_sum(v, sh);
+        if (threadIdx.x == 0) atomicAdd(out + k, v);
+    }
+}
+
+// scal: [0..2] rz, [3..5] pq, [6..8] rz_new, [9..11] rr, [12..14] active flag
+__global__ void plain_update_x_kernel(int64_t n, int nr, const double* scal, double* x0, double* x1, double* x2,
+                                      double* r, double* z, const double* p, const double* q, const double* dinv) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double* x[3] = {x0, x1, x2};
+    for (int k = 0; k < nr; ++k) {
+        if (scal[12 + k] == 0.0) continue;
+        double alpha = scal[k] / scal[3 + k];
+        x[k][i] += alpha * p[k * n + i];
+        double rn = r[k * n + i] - alpha * q[k * n + i];
+        r[k * n + i] = rn;
+        z[k * n + i] = dinv[i] * rn;
+    }
+}
+
+__global__ void plain_update_p_kernel(int64_t n, int nr, const double* scal, const double* z, double* p) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < nr; ++k) {
+        if (scal[12 + k] == 0.0) continue;
+        double beta = scal[6 + k] / scal[k];
+        p[k * n + i] = z[k * n + i] + beta * p[k * n + i];
+    }
+}
+
+__global__ void plain_scalars_kernel(int nr, double* scal, const double* rr0, double rtol) {
+    // after an iteration: rz <- rz_new, clear accumulators, freeze converged components
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < nr; ++k) {
+        if (scal[12 + k] != 0.0) scal[k] = scal[6 + k];
+        if (scal[9 + k] <= rtol * rtol * rr0[k]) scal[12 + k] = 0.0;
+        scal[3 + k] = 0.0;
+        scal[6 + k] = 0.0;
+        scal[9 + k] = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ mixed-precision refinement
+// r64 = y - M x64 (FP64), norms[k] += |r64|^2
+__global__ void residual_f64_kernel(int64_t n, int nr, const int64_t* ptr, const int32_t* col, const double* val,
+                                    const float* y0, const float* y1, const float* y2, const double* x64,
+                                    double* r64, float* r32, double* norms) {
+    __shared__ double sh[32];
+    const float* y[3] = {y0, y1, y2};
+    for (int k = 0; k < nr; ++k) {
+        double acc = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            double s = 0.0;
+            for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], x64[k * n + col[e]], s);
+            double ri = (double)y[k][i] - s;
+            r64[k * n + i] = ri;
+            r32[k * n + i] = (float)ri;
+            acc = fma(ri, ri, acc);
+        }
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) atomicAdd(norms + k, acc);
+    }
+}
+
+__global__ void add_correction_kernel(int64_t n, int nr, double* x64, const float* d0, const float* d1,
+                                      const float* d2, int first) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* d[3] = {d0, d1, d2};
+    for (int k = 0; k < nr; ++k) x64[k * n + i] = (first ? 0.0 : x64[k * n + i]) + (double)d[k][i];
+}
+
+__global__ void norm2_f32_kernel(int64_t n, int nr, const float* y0, const float* y1, const float* y2,
+                                 double* out) {
+    __shared__ double sh[32];
+    const float* y[3] = {y0, y1, y2};
+    for (int k = 0; k < nr; ++k) {
+        double acc = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            acc = fma((double)y[k][i], (double)y[k][i], acc);
+        acc = block_sum(acc, sh);
+        if (threadIdx.x == 0) atomicAdd(out + k, acc);
+    }
+}
+
+__global__ void store_f32_kernel(int64_t n, int nr, const double* x64, float* w0, float* w1, float* w2) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float* w[3] = {w0, w1, w2};
+    for (int k = 0; k < nr; ++k) w[k][i] = (float)x64[k * n + i];
+}
+
+template <typename TV>
+int pcg_blocks_for(int64_t n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_fused_kernel<TV>, kPcgThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t want = (n + 2 * kPcgThreads - 1) / (2 * kPcgThreads);  // >= 2 rows per thread
+    int64_t cap = (int64_t)sms * per_sm;
+    int64_t b = want < cap ? want : cap;
+    if (b > (int64_t)sms * 8) b = (int64_t)sms * 8;  // partial-sum buffer holds sms * 8 blocks
+    return b < 1 ? 1 : (int)b;
+}
+
+template <typename TV>
+cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val, const TV* dinv, int64_t n,
+                          int nr, const TV* const* y, TV* const* x, TV* vecs, double* partial, double rtol,
+                          int max_iter, DevStatus* st, cudaStream_t s) {
+    PcgArgs<TV> A{};
+    A.n = n;
+    A.nrhs = nr;
+    A.ptr = ptr;
+    A.col = col;
+    A.val = val;
+    A.dinv = dinv;
+    for (int k = 0; k < kMaxRhs; ++k) {
+        A.y[k] = k < nr ? y[k] : nullptr;
+        A.x[k] = k < nr ? x[k] : nullptr;
+    }
+    int64_t stride = n * nr;
+    A.r = vecs;
+    A.u = vecs + stride;
+    A.p = vecs + 2 * stride;
+    A.s = vecs + 3 * stride;
+    A.w = vecs + 4 * stride;
+    A.partial = partial;
+    A.rtol = rtol;
+    A.max_iter = max_iter;
+    A.st = st;
+    int blocks = pcg_blocks_for<TV>(n);
+    void* args[] = {&A};
+    return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV>, dim3(blocks), dim3(kPcgThreads), args, 0, s);
+}
+
+}  // namespace
+
+int pcg_max_blocks() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * 8;
+}
+
+size_t pcg_ws_bytes(int64_t n, int n_rhs, int max_blocks) {
+    // 5 vectors (double upper bound) + mixed: x64, r64 (double), r32, d (float) + partials + plain scalars
+    size_t v = (size_t)n * n_rhs;
+    return 5 * v * sizeof(double) + 2 * v * sizeof(double) + 2 * v * sizeof(float) +
+           (size_t)max_blocks * 3 * kMaxRhs * sizeof(double) + 64 * sizeof(double) + 16384;
+}
+
+void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const void* const* x, void* const* y,
+                   cudaStream_t s) {
+    const int64_t n = B[0].n_rows;
+    if (n <= 0) return;
+    if (path == L2X_PATH_PLAIN) {
+        for (int g = 0; g < n_grids; ++g)
+            spmv_B_plain_kernel<<<nblk(n, 256), 256, 0, s>>>(n, B[g].ptr, B[g].col, B[g].val, (const double*)x[g],
+                                                             (double*)y[g]);
+        return;
+    }
+    const int64_t threads = n * n_grids * 8;
+    if (precision == L2X_MIXED) {
+        SpmvPack<float, float> P{};
+        for (int g = 0; g < n_grids; ++g) {
+            P.ptr[g] = B[g].ptr; P.col[g] = B[g].col; P.val[g] = B[g].val32;
+            P.x[g] = (const float*)x[g]; P.y[g] = (float*)y[g];
+        }
+        spmv_B_fused_kernel<float, float><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P);
+    } else {
+        SpmvPack<double, double> P{};
+        for (int g = 0; g < n_grids; ++g) {
+            P.ptr[g] = B[g].ptr; P.col[g] = B[g].col; P.val[g] = B[g].val;
+            P.x[g] = (const double*)x[g]; P.y[g] = (double*)y[g];
+        }
+        spmv_B_fused_kernel<double, double><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P);
+    }
+}
+
+void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const CsrT* T, const SubGrid* sg,
+                    const void* const* z, void* const* f, double scale, cudaStream_t s) {
+    if (path == L2X_PATH_PLAIN) {
+        for (int g = 0; g < n_grids; ++g)
+            if (B[g].n_rows > 0)
+                spmv_BT_plain_kernel<<<nblk(B[g].n_rows, 256), 256, 0, s>>>(B[g].n_rows, B[g].ptr, B[g].col, B[g].val,
+                                                                            (const double*)z[g], (double*)f[g], scale);
+        return;
+    }
+    auto fill = [&](auto& P, bool f32) {
+        int64_t base = 0;
+        for (int g = 0; g < n_grids; ++g) {
+            P.ptr[g] = T[g].ptr;
+            P.col[g] = T[g].col;
+            for (int k = 0; k < 3; ++k) {
+                P.lo[g][k] = T[g].lo[k];
+                P.n[g][k] = T[g].n[k];
+                P.nnode[g][k] = sg[g].nnode[k];
+            }
+            P.n_rows[g] = T[g].n_rows;
+            P.row_base[g] = base;
+            base += T[g].n_rows;
+        }
+        P.row_base[n_grids] = base;
+        (void)f32;
+        return base;
+    };
+    if (precision == L2X_MIXED) {
+        SpmvTPack<float, float> P{};
+        int64_t total = fill(P, true);
+        for (int g = 0; g < n_grids; ++g) {
+            P.val[g] = T[g].val32;
+            P.z[g] = (const float*)z[g];
+            P.f[g] = (float*)f[g];
+        }
+        if (total > 0) spmv_BT_fused_kernel<float, float><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, (float)scale);
+    } else {
+        SpmvTPack<double, double> P{};
+        int64_t total = fill(P, false);
+        for (int g = 0; g < n_grids; ++g) {
+            P.val[g] = T[g].val;
+            P.z[g] = (const double*)z[g];
+            P.f[g] = (double*)f[g];
+        }
+        if (total > 0) spmv_BT_fused_kernel<double, double><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, scale);
+    }
+}
+
+l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv, const float* diag_inv32,
+                          int nr, const void* const* y, void* const* w, double rtol, int max_iter, void* ws,
+                          DevStatus* st, DevStatus* st_host, cudaStream_t s, PcgResult* res) {
+    const int64_t n = M.n_rows;
+    res->iters = 0;
+    res->residual = 0.0;
+    res->converged = true;
+    if (n <= 0 || nr <= 0) return L2X_OK;
+    const int64_t v = n * nr;
+    char* base = (char*)ws;
+    auto take = [&](size_t bytes) {
+        void* p = base;
+        base += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    cudaError_t ce;
+    if (path == L2X_PATH_PLAIN) {
+        double* r = (double*)take(v * 8);
+        double* z = (double*)take(v * 8);
+        double* p = (double*)take(v * 8);
+        double* q = (double*)take(v * 8);
+        double* scal = (double*)take(16 * 8);
+        double* rr0 = (double*)take(4 * 8);
+        double hs[16];
+        const double* yy[3] = {(const double*)y[0], nr > 1 ? (const double*)y[1] : nullptr, nr > 2 ? (const double*)y[2] : nullptr};
+        double* xx[3] = {(double*)w[0], nr > 1 ? (double*)w[1] : nullptr, nr > 2 ? (double*)w[2] : nullptr};
+        unsigned nb = nblk(n, 256);
+        unsigned nbd = nb < 1024 ? nb : 1024;
+        plain_init_kernel<<<nb, 256, 0, s>>>(n, nr, yy[0], yy[1], yy[2], xx[0], xx[1], xx[2], diag_inv, r, z, p);
+        cudaMemsetAsync(scal, 0, 16 * 8, s);
+        cudaMemsetAsync(rr0, 0, 4 * 8, s);
+        plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, z, scal);      // rz
+        plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, r, rr0);       // |y|^2
+        double ones[3] = {1.0, 1.0, 1.0};
+        cudaMemcpyAsync(scal + 12, ones, sizeof(double) * nr, cudaMemcpyHostToDevice, s);
+        double rr0h[3] = {0, 0, 0};
+        int it = 0;
+        bool done = false;
+        double worst = 0.0;
+        for (; it < max_iter && !done; ++it) {
+            plain_spmv_kernel<<<nb, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, p, q);
+            plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, p, q, scal + 3);
+            plain_update_x_kernel<<<nb, 256, 0, s>>>(n, nr, scal, xx[0], xx[1], xx[2], r, z, p, q, diag_inv);
+            plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, z, scal + 6);
+            plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, r, scal + 9);
+            plain_update_p_kernel<<<nb, 256, 0, s>>>(n, nr, scal, z, p);
+            // host convergence check (read the residual norms every iteration)
+            if ((ce = cudaMemcpyAsync(hs, scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+            if (it == 0 && (ce = cudaMemcpyAsync(rr0h, rr0, sizeof(double) * nr, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+            if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) break;
+            plain_scalars_kernel<<<1, 32, 0, s>>>(nr, scal, rr0, rtol);
+            done = true;
+            worst = 0.0;
+            for (int k = 0; k < nr; ++k) {
+                double rel = rr0h[k] > 0.0 ? sqrt(hs[9 + k] / rr0h[k]) : 0.0;
+                worst = fmax(worst, rel);
+                if (!(rel <= rtol)) done = false;
+            }
+        }
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) return L2X_ECUDA;
+        res->iters = it;
+        res->residual = worst;
+        res->converged = done;
+        return done ? L2X_OK : L2X_ENOTCONVERGED;
+    }
+    double* partial = (double*)take((size_t)pcg_max_blocks() * 3 * kMaxRhs * 8);
+    if (precision == L2X_FP64) {
+        double* vecs = (double*)take(5 * v * 8);
+        cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s);
+        ce = run_pcg_fused<double>(M.ptr, M.col, M.val, diag_inv, n, nr, (const double* const*)y, (double* const*)w,
+                                   vecs, partial, rtol, max_iter, st, s);
+        if (ce != cudaSuccess) return L2X_ECUDA;
+        if (cudaMemcpyAsync(st_host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return L2X_ECUDA;
+        res->iters = st_host->cg_iters;
+        res->residual = st_host->cg_residual;
+        res->converged = !(st_host->flags & FLAG_NOTCONVERGED);
+        return res->converged ? L2X_OK : L2X_ENOTCONVERGED;
+    }
+    // mixed: FP32 PCG, then FP64 residual refinement (x accumulated in FP64,
+    // residual y - M x in FP64) until rtol, at most 3 corrections
+    float* vecs = (float*)take(5 * v * 4);
+    double* x64 = (double*)take(v * 8);
+    double* r64 = (double*)take(v * 8);
+    float* r32 = (float*)take(v * 4);
+    float* d32 = (float*)take(v * 4);
+    double* norms = (double*)take(8 * 8);
+    const float* yf[3] = {(const float*)y[0], nr > 1 ? (const float*)y[1] : nullptr, nr > 2 ? (const float*)y[2] : nullptr};
+    float* wf[3] = {(float*)w[0], nr > 1 ? (float*)w[1] : nullptr, nr > 2 ? (float*)w[2] : nullptr};
+    unsigned nb = nblk(n, 256);
+    unsigned nbd = nb < 1024 ? nb : 1024;
+    const double inner = rtol > 1e-6 ? rtol : 1e-6;
+    cudaMemsetAsync(norms, 0, 8 * 8, s);
+    norm2_f32_kernel<<<nbd, 256, 0, s>>>(n, nr, yf[0], yf[1], yf[2], norms + 4);
+    int total_it = 0;
+    double worst = 0.0;
+    bool ok = false;
+    double hn[8];
+    for (int ref = 0; ref < 4 && !ok; ++ref) {
+        const float* rhs[3];
+        float* dst[3];
+        for (int k = 0; k < nr; ++k) {
+            rhs[k] = ref == 0 ? yf[k] : r32 + k * n;
+            dst[k] = d32 + k * n;
+        }
+        cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s);
+        ce = run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner,
+                                  max_iter, st, s);
+        if (ce != cudaSuccess) return L2X_ECUDA;
+        add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr,
+                                                 nr > 2 ? dst[2] : nullptr, ref == 0);
+        cudaMemsetAsync(norms, 0, 4 * 8, s);
+        residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf[0], yf[1], yf[2], x64, r64, r32, norms);
+        if (cudaMemcpyAsync(st_host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
+        if (cudaMemcpyAsync(hn, norms, 8 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return L2X_ECUDA;
+        total_it += st_host->cg_iters;
+        worst = 0.0;
+        for (int k = 0; k < nr; ++k) worst = fmax(worst, hn[4 + k] > 0.0 ? sqrt(hn[k] / hn[4 + k]) : 0.0);
+        ok = worst <= rtol;
+    }
+    store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf[0], wf[1], wf[2]);
+    if (cudaGetLastError() != cudaSuccess) return L2X_ECUDA;
+    res->iters = total_it;
+    res->residual = worst;
+    res->converged = ok;
+    return ok ? L2X_OK : L2X_ENOTCONVERGED;
+}
+
+}  // namespace l2x

@@ -1,0 +1,340 @@
+// Step (IV) of Sec. 2.3: assembly of the mortar matrices B_g (one per velocity
+// grid) and S = M_s (P1 mass matrix, Sec. 2.1 "Spatial Discretization") into
+// CSR, and the transpose of B_g used by the force transfer.
+#include <climits>
+
+#include "l2x_internal.cuh"
+
+namespace l2x {
+
+namespace {
+
+constexpr int kRowWarps = 4;
+constexpr int kRowMax = 1024;   // dense row box held in shared memory per warp
+constexpr int kMassMaxCand = 256;
+
+__global__ void adj_count_kernel(int NA, int64_t total, const int32_t* __restrict__ E, int64_t* cnt) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    atomicAdd((unsigned long long*)(cnt + E[t]), 1ull);
+}
+
+__global__ void adj_fill_kernel(int NA, int64_t total, const int32_t* __restrict__ E,
+                                const int64_t* __restrict__ ptr, int32_t* cursor, int32_t* adj) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int64_t e = t / NA;
+    int a = (int)(t - e * NA);
+    int32_t node = E[t];
+    int64_t pos = ptr[node] + atomicAdd(cursor + node, 1);
+    adj[pos] = (int32_t)(e * 4 + a);
+}
+
+// insertion sort of every segment [ptr[i], ptr[i+1]) (short segments)
+template <typename V>
+__global__ void segment_sort_kernel(int64_t n, const int64_t* __restrict__ ptr, int32_t* key, V* val) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t lo = ptr[i], hi = ptr[i + 1];
+    for (int64_t a = lo + 1; a < hi; ++a) {
+        int32_t k = key[a];
+        V v = val ? val[a] : V(0);
+        int64_t b = a - 1;
+        while (b >= lo && key[b] > k) {
+            key[b + 1] = key[b];
+            if (val) val[b + 1] = val[b];
+            --b;
+        }
+        key[b + 1] = k;
+        if (val) val[b + 1] = v;
+    }
+}
+
+// One warp per solid node (row of B_g).  The row's columns are the nodes of the
+// union of the candidate boxes of the incident elements; the warp accumulates
+// the rows of the incident elements' pair blocks into a dense box in shared
+// memory (in a fixed order: adjacency order, pair order, then slot order, so
+// the sums are reproducible) and emits the touched columns in ascending order.
+template <int D>
+__global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
+    int pass, SubGrid sg, int64_t n_nodes, const int64_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+    const ElemBox* __restrict__ boxes, const int64_t* __restrict__ offsets, const double* __restrict__ blocks,
+    int64_t slot_stride, const double* __restrict__ vols, int64_t* __restrict__ row_count,
+    const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols, double* __restrict__ vals, DevStatus* st) {
+    constexpr int NB = 1 << D;
+    constexpr int SLOTS = 32 / NB;
+    __shared__ double s_acc[kRowWarps][kRowMax];
+    __shared__ unsigned char s_flag[kRowWarps][kRowMax];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = blockIdx.x * (int64_t)kRowWarps + w;
+    if (i >= n_nodes) return;
+    const int64_t a0 = adj_ptr[i], a1 = adj_ptr[i + 1];
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    for (int64_t t = a0 + lane; t < a1; t += 32) {
+        int32_t e = adj[t] >> 2;
+        ElemBox b = boxes[e];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            lo[k] = min(lo[k], b.lo[k]);
+            hi[k] = max(hi[k], b.lo[k] + box_ext(b, k));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    int64_t cnt = 0;
+    const int64_t out0 = pass >= 1 ? row_ptr[i] : 0;
+    const bool too_wide = a0 < a1 && hi[0] - lo[0] + 1 > kRowMax;
+    if (too_wide && lane == 0) atomicOr(&st->flags, FLAG_CAPACITY);
+    if (a0 < a1 && !too_wide) {
+        const int nx = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1;
+        const int nz = D == 3 ? hi[2] - lo[2] + 1 : 1;
+        if (D == 2) { lo[2] = 0; }
+        // tiles: whole (x,y) planes over a z-range, or single planes over a y-range
+        const int plane = nx * ny;
+        const int tz = plane <= kRowMax ? max(1, kRowMax / plane) : 1;
+        const int ty = plane <= kRowMax ? ny : max(1, kRowMax / nx);
+        for (int zb = 0; zb < nz; zb += tz) {
+            const int ze = min(nz, zb + tz);
+            for (int yb = 0; yb < ny; yb += ty) {
+                const int ye = min(ny, yb + ty);
+                const int tyn = ye - yb;
+                const int tsz = nx * tyn * (ze - zb);
+                for (int t = lane; t < tsz; t += 32) {
+                    s_acc[w][t] = 0.0;
+                    s_flag[w][t] = 0;
+                }
+                __syncwarp();
+                for (int64_t t = a0; t < a1; ++t) {
+                    const int32_t ea = adj[t];
+                    const int32_t e = ea >> 2;
+                    const int a = ea & 3;
+                    const ElemBox b = boxes[e];
+                    const int ex = box_ext(b, 0), ey = box_ext(b, 1);
+                    const int npairs = ex * ey * box_ext(b, 2);
+                    const int64_t q0 = offsets[e];
+                    for (int base = 0; base < npairs; base += SLOTS) {
+                        const int slot = lane / NB, cb = lane % NB;
+                        const int k = base + slot;
+                        int idx = -1;
+                        double v = 0.0;
+                        if (k < npairs) {
+                            const int64_t q = q0 + k;
+                            if (vols[q] > 0.0) {
+                                const int kx = k % ex, ky = (k / ex) % ey, kz = k / (ex * ey);
+                                const int bx = b.lo[0] + kx + (cb & 1) - lo[0];
+                                const int by = b.lo[1] + ky + ((cb >> 1) & 1) - lo[1];
+                                const int bz = D == 3 ? b.lo[2] + kz + ((cb >> 2) & 1) - lo[2] : 0;
+                                if (by >= yb && by < ye && bz >= zb && bz < ze) {
+                                    idx = bx + nx * ((by - yb) + tyn * (bz - zb));
+                                    if (pass == 1) v = blocks[(int64_t)(a * NB + cb) * slot_stride + q];
+                                }
+                            }
+                        }
+                        for (int st = 0; st < SLOTS; ++st) {
+                            if (slot == st && idx >= 0) {
+                                s_acc[w][idx] += v;
+                                s_flag[w][idx] = 1;
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
+                for (int base = 0; base < tsz; base += 32) {
+                    const int idx = base + lane;
+                    const bool f = idx < tsz && s_flag[w][idx];
+                    const unsigned bal = __ballot_sync(0xffffffffu, f);
+                    if (pass >= 1 && f) {
+                        const int pos = __popc(bal & ((1u << lane) - 1u));
+                        const int bx = idx % nx;
+                        const int r = idx / nx;
+                        const int by = r % tyn + yb, bz = r / tyn + zb;
+                        const int32_t node = (lo[0] + bx) + sg.nnode[0] * ((lo[1] + by) + sg.nnode[1] * (lo[2] + bz));
+                        cols[out0 + cnt + pos] = node;
+                        vals[out0 + cnt + pos] = pass == 1 ? s_acc[w][idx] : 0.0;
+                    }
+                    cnt += __popc(bal);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (pass == 0 && lane == 0) row_count[i] = cnt;
+}
+
+template <int D>
+__global__ void mass_structure_kernel(int pass, int64_t n_nodes, const int32_t* __restrict__ E,
+                                      const int64_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
+                                      int64_t* row_count, const int64_t* __restrict__ row_ptr, int32_t* cols,
+                                      DevStatus* st) {
+    constexpr int NA = D + 1;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_nodes) return;
+    int32_t cand[kMassMaxCand];
+    int n = 0;
+    bool overflow = false;
+    for (int64_t t = adj_ptr[i]; t < adj_ptr[i + 1]; ++t) {
+        int32_t e = adj[t] >> 2;
+        for (int v = 0; v < NA; ++v) {
+            int32_t j = E[(int64_t)e * NA + v];
+            // insert keeping cand sorted and unique
+            int p = n;
+            bool dup = false;
+            while (p > 0 && cand[p - 1] >= j) {
+                if (cand[p - 1] == j) { dup = true; break; }
+                --p;
+            }
+            if (dup) continue;
+            if (n == kMassMaxCand) { overflow = true; continue; }
+            for (int q = n; q > p; --q) cand[q] = cand[q - 1];
+            cand[p] = j;
+            ++n;
+        }
+    }
+    if (overflow) atomicOr(&st->flags, FLAG_CAPACITY);
+    if (pass == 0) {
+        row_count[i] = n;
+    } else {
+        int64_t o = row_ptr[i];
+        for (int q = 0; q < n; ++q) cols[o + q] = cand[q];
+    }
+}
+
+template <int D>
+__global__ void mass_values_kernel(int64_t n_nodes, const int32_t* __restrict__ E, const int64_t* __restrict__ adj_ptr,
+                                   const int32_t* __restrict__ adj, const double* __restrict__ elem_vol,
+                                   const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cols,
+                                   double* vals, double* diag_inv) {
+    constexpr int NA = D + 1;
+    const double w = 1.0 / ((D + 1) * (D + 2));
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_nodes) return;
+    const int64_t lo = row_ptr[i], hi = row_ptr[i + 1];
+    for (int64_t q = lo; q < hi; ++q) vals[q] = 0.0;
+    for (int64_t t = adj_ptr[i]; t < adj_ptr[i + 1]; ++t) {
+        const int32_t e = adj[t] >> 2;
+        const int a = adj[t] & 3;
+        const double ve = elem_vol[e] * w;
+        for (int v = 0; v < NA; ++v) {
+            const int32_t j = E[(int64_t)e * NA + v];
+            int64_t l = lo, r = hi;
+            while (l < r) {
+                int64_t mid = (l + r) >> 1;
+                if (cols[mid] < j) l = mid + 1; else r = mid;
+            }
+            if (l < hi && cols[l] == j) vals[l] += v == a ? 2.0 * ve : ve;
+        }
+    }
+    double dgl = 0.0;
+    for (int64_t q = lo; q < hi; ++q)
+        if (cols[q] == (int32_t)i) dgl = vals[q];
+    diag_inv[i] = dgl > 0.0 ? 1.0 / dgl : 0.0;
+}
+
+__device__ __forceinline__ int64_t tbox_index(const SubGrid& sg, const CsrT& T, int32_t j) {
+    int x = j % sg.nnode[0];
+    int r = j / sg.nnode[0];
+    int y = r % sg.nnode[1];
+    int z = r / sg.nnode[1];
+    return (x - T.lo[0]) + (int64_t)T.n[0] * ((y - T.lo[1]) + (int64_t)T.n[1] * (z - T.lo[2]));
+}
+
+__global__ void transpose_count_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                       SubGrid sg, CsrT T, int64_t* cnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q)
+        atomicAdd((unsigned long long*)(cnt + tbox_index(sg, T, col[q])), 1ull);
+}
+
+__global__ void transpose_fill_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                      const double* __restrict__ val, SubGrid sg, CsrT T, int32_t* cursor) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
+        int64_t r = tbox_index(sg, T, col[q]);
+        int64_t pos = T.ptr[r] + atomicAdd(cursor + r, 1);
+        T.col[pos] = (int32_t)i;
+        T.val[pos] = val[q];
+    }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E, int64_t* adj_ptr,
+                           int32_t* adj, int32_t* cursor, void* scan_tmp, cudaStream_t s) {
+    const int NA = dim + 1;
+    const int64_t total = m * NA;
+    cudaMemsetAsync(adj_ptr, 0, sizeof(int64_t) * (n_nodes + 1), s);
+    cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n_nodes, s);
+    if (total > 0) adj_count_kernel<<<nblk(total, 256), 256, 0, s>>>(NA, total, E, adj_ptr);
+    launch_scan_i64(adj_ptr, adj_ptr, n_nodes, scan_tmp, s);
+    if (total > 0) adj_fill_kernel<<<nblk(total, 256), 256, 0, s>>>(NA, total, E, adj_ptr, cursor, adj);
+    segment_sort_kernel<double><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, adj_ptr, adj, nullptr);
+}
+
+void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const int64_t* adj_ptr,
+                   const int32_t* adj, const ElemBox* boxes_g, const int64_t* offsets_g,
+                   const double* blocks, int64_t slot_stride, const double* vols, int64_t* row_count,
+                   const int64_t* row_ptr, int32_t* cols, double* vals, DevStatus* st, cudaStream_t s) {
+    if (n_nodes <= 0) return;
+    unsigned nb = nblk(n_nodes, kRowWarps);
+    if (dim == 2)
+        b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, offsets_g, blocks,
+                                                      slot_stride, vols, row_count, row_ptr, cols, vals, st);
+    else
+        b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, offsets_g, blocks,
+                                                      slot_stride, vols, row_count, row_ptr, cols, vals, st);
+}
+
+void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
+                           const int32_t* adj, int64_t* row_count, const int64_t* row_ptr, int32_t* cols,
+                           DevStatus* st, cudaStream_t s) {
+    if (n_nodes <= 0) return;
+    if (dim == 2)
+        mass_structure_kernel<2><<<nblk(n_nodes, 128), 128, 0, s>>>(pass, n_nodes, E, adj_ptr, adj, row_count, row_ptr, cols, st);
+    else
+        mass_structure_kernel<3><<<nblk(n_nodes, 128), 128, 0, s>>>(pass, n_nodes, E, adj_ptr, adj, row_count, row_ptr, cols, st);
+}
+
+void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
+                        const int32_t* adj, const double* elem_vol, const int64_t* row_ptr,
+                        const int32_t* cols, double* vals, double* diag_inv, cudaStream_t s) {
+    if (n_nodes <= 0) return;
+    if (dim == 2)
+        mass_values_kernel<2><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv);
+    else
+        mass_values_kernel<3><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv);
+}
+
+void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, cudaStream_t s) {
+    cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (T.n_rows + 1), s);
+    if (B.n_rows > 0) transpose_count_kernel<<<nblk(B.n_rows, 128), 128, 0, s>>>(B.n_rows, B.ptr, B.col, sg, T, cnt);
+}
+
+void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, cudaStream_t s) {
+    cudaMemsetAsync(cursor, 0, sizeof(int32_t) * T.n_rows, s);
+    if (B.n_rows > 0)
+        transpose_fill_kernel<<<nblk(B.n_rows, 128), 128, 0, s>>>(B.n_rows, B.ptr, B.col, B.val, sg, T, cursor);
+}
+
+void launch_transpose_sort(const CsrT& T, cudaStream_t s) {
+    if (T.n_rows > 0) segment_sort_kernel<double><<<nblk(T.n_rows, 128), 128, 0, s>>>(T.n_rows, T.ptr, T.col, T.val);
+}
+
+void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {
+    if (n > 0) to_f32_kernel<<<nblk(n, 256), 256, 0, s>>>(in, out, n);
+}
+
+}  // namespace l2x

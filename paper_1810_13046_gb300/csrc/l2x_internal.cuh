@@ -1,0 +1,145 @@
+// Internal declarations shared by the l2xfer translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "l2xfer.h"
+
+namespace l2x {
+
+constexpr int kMaxGrids = 3;
+
+// Device status word, written with atomics by kernels, read by the host after
+// the call's stream is synchronised.
+enum : int32_t {
+    FLAG_OUTOFGRID = 1,
+    FLAG_DEGENERATE = 2,
+    FLAG_CAPACITY = 4,
+    FLAG_NONFINITE = 8,
+    FLAG_NOTCONVERGED = 16,
+    FLAG_TIMEOUT = 32,
+};
+
+struct DevStatus {
+    int32_t flags;
+    int32_t bad_elem;     // first element that raised OUTOFGRID / DEGENERATE (min)
+    int32_t cg_iters;
+    int32_t pad;
+    double cg_residual;
+};
+
+// One Q1 velocity grid.
+struct SubGrid {
+    int32_t ncell[3];   // Q1 cells per axis (1 on unused axes)
+    int32_t nnode[3];   // ncell + 1 (1 on unused axes)
+    double origin[3];
+    double h[3];
+    double inv_h[3];
+};
+
+// Per-element candidate box on one grid: lowest cell index and extent per axis.
+struct ElemBox {
+    int32_t lo[3];
+    int32_t ext;        // packed extents: ex | ey << 10 | ez << 20 (each <= 1023)
+};
+
+__host__ __device__ inline int box_ext(const ElemBox& b, int k) { return (b.ext >> (10 * k)) & 1023; }
+
+// CSR matrix (int64 row pointers, int32 columns).
+struct Csr {
+    int64_t n_rows = 0;
+    int64_t nnz = 0;
+    int64_t* ptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    float* val32 = nullptr;  // mixed-precision copy
+};
+
+// Transposed coupling matrix restricted to the box of fluid nodes the mesh touches.
+struct CsrT {
+    int32_t lo[3] = {0, 0, 0};   // first node of the box per axis
+    int32_t n[3] = {1, 1, 1};    // box nodes per axis
+    int64_t n_rows = 0;          // n[0]*n[1]*n[2]
+    int64_t* ptr = nullptr;
+    int32_t* col = nullptr;      // solid node
+    double* val = nullptr;
+    float* val32 = nullptr;
+};
+
+// Stream-ordered scratch allocation helpers (l2x_api.cu).
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// ---------------------------------------------------------------- launchers
+// pairs (l2x_pairs.cu)
+void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const double* X,
+                       const int32_t* E, ElemBox* boxes, int64_t* counts, int32_t* node_box,
+                       double* elem_vol, DevStatus* st, cudaStream_t s);
+void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
+size_t scan_tmp_bytes(int64_t n);
+void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const ElemBox* boxes,
+                       const int64_t* offsets, int32_t* pair_elem, int32_t* pair_cell, cudaStream_t s);
+
+// clipping + quadrature (l2x_clip.cu).  Pair blocks are stored at
+// blocks[slot * slot_stride + p * pair_stride], slot = a * 2^d + b.
+void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* X, const int32_t* E,
+                       int64_t p_begin, int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell,
+                       double* blocks, int64_t slot_stride, double* vols, DevStatus* st, cudaStream_t s);
+void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
+                       int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, double* blocks,
+                       double* vols, DevStatus* st, cudaStream_t s);
+// plain assembly: atomicAdd of every pair block into the pre-built CSR of B_g
+void launch_scatter_plain(int dim, const SubGrid& sg, const int32_t* E, int64_t p_begin, int64_t p_end,
+                          const int32_t* pair_elem, const int32_t* pair_cell, const double* blocks,
+                          const double* vols, const Csr& B, cudaStream_t s);
+
+// assembly (l2x_assemble.cu)
+// node -> (element, local vertex) adjacency, entries e*4 + a sorted per node.
+// adj_ptr must hold n_nodes + 1 entries; cursor n_nodes int32 (scratch).
+void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E, int64_t* adj_ptr,
+                           int32_t* adj, int32_t* cursor, void* scan_tmp, cudaStream_t s);
+// Row-wise assembly of B_g.  pass 0: row_count[i] = nonzeros of row i;
+// pass 1: cols + vals (fused, from SoA blocks); pass 2: cols only, vals zeroed (plain).
+void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const int64_t* adj_ptr,
+                   const int32_t* adj, const ElemBox* boxes_g, const int64_t* offsets_g,
+                   const double* blocks, int64_t slot_stride, const double* vols, int64_t* row_count,
+                   const int64_t* row_ptr, int32_t* cols, double* vals, DevStatus* st, cudaStream_t s);
+// P1 mass matrix structure (pass 0 counts, pass 1 columns) and values.
+void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
+                           const int32_t* adj, int64_t* row_count, const int64_t* row_ptr, int32_t* cols,
+                           DevStatus* st, cudaStream_t s);
+void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
+                        const int32_t* adj, const double* elem_vol, const int64_t* row_ptr,
+                        const int32_t* cols, double* vals, double* diag_inv, cudaStream_t s);
+// B_g^T over the box of touched fluid nodes.
+void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, cudaStream_t s);
+void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, cudaStream_t s);
+void launch_transpose_sort(const CsrT& T, cudaStream_t s);
+void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+
+// apply (l2x_apply.cu)
+// y[g] = B_g x[g] (n_rows = solid nodes).  Fused: 8 lanes per row, all grids in
+// one launch; plain: one thread per row, FP64 only.
+void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const void* const* x,
+                   void* const* y, cudaStream_t s);
+// f[g] += scale * B_g^T z[g].  Fused: gather over the rows of B_g^T (no atomics);
+// plain: scatter with atomics from the rows of B_g.
+void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const CsrT* T,
+                    const SubGrid* sg, const void* const* z, void* const* f, double scale,
+                    cudaStream_t s);
+// Jacobi-preconditioned CG on M for n_rhs right-hand sides (FP64, or FP32 with
+// compensated dot products and FP64 residual refinement in mixed mode).
+struct PcgResult {
+    int iters = 0;
+    double residual = 0.0;
+    bool converged = false;
+};
+l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv,
+                          const float* diag_inv32, int n_rhs, const void* const* y, void* const* w,
+                          double rtol, int max_iter, void* ws, DevStatus* st, DevStatus* st_host,
+                          cudaStream_t s, PcgResult* res);
+size_t pcg_ws_bytes(int64_t n, int n_rhs, int max_blocks);
+int pcg_max_blocks();
+
+}  // namespace l2x

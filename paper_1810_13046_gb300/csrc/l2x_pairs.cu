@@ -1,0 +1,242 @@
+// Step (I) of the assembly (Sec. 2.3): overlap detection between solid elements
+// and the cells of every velocity grid.  The uniform grid replaces the tree
+// search: the candidate cells of an element are the cells of its bounding box,
+//   i_lo = floor((lo - o) / h),   i_hi = ceil((hi - o) / h) - 1,
+// with one IEEE-rounded subtraction and one correctly rounded division (the
+// intrinsics below are never contracted into a fused multiply-add), so the pair
+// list is reproducible bit for bit on any IEEE machine.
+#include <climits>
+
+#include "l2x_internal.cuh"
+
+namespace l2x {
+
+namespace {
+
+struct SubGridSet {
+    SubGrid g[kMaxGrids];
+};
+
+__device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
+
+template <int D>
+__global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const double* __restrict__ X,
+                                  const int32_t* __restrict__ E, ElemBox* __restrict__ boxes,
+                                  int64_t* __restrict__ counts, int32_t* __restrict__ node_box,
+                                  double* __restrict__ elem_vol, DevStatus* st) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    double V[D + 1][D];
+    bool finite = true;
+    for (int a = 0; a <= D; ++a) {
+        int32_t v = __ldg(E + e * (D + 1) + a);
+        for (int k = 0; k < D; ++k) {
+            V[a][k] = ldg(X + (int64_t)v * D + k);
+            finite = finite && isfinite(V[a][k]);
+        }
+    }
+    double det;
+    if (D == 2) {
+        det = (V[1][0] - V[0][0]) * (V[2][1] - V[0][1]) - (V[1][1] - V[0][1]) * (V[2][0] - V[0][0]);
+    } else {
+        double a0 = V[1][0] - V[0][0], a1 = V[1][1 % D] - V[0][1 % D], a2 = V[1][2 % D] - V[0][2 % D];
+        double b0 = V[2][0] - V[0][0], b1 = V[2][1 % D] - V[0][1 % D], b2 = V[2][2 % D] - V[0][2 % D];
+        double c0 = V[D][0] - V[0][0], c1 = V[D][1 % D] - V[0][1 % D], c2 = V[D][2 % D] - V[0][2 % D];
+        det = a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0);
+    }
+    elem_vol[e] = fabs(det) / (D == 2 ? 2.0 : 6.0);
+    int32_t flags = 0;
+    if (!finite) flags |= FLAG_NONFINITE;
+    else if (det == 0.0) flags |= FLAG_DEGENERATE;
+    double lo[D], hi[D];
+    for (int k = 0; k < D; ++k) {
+        lo[k] = V[0][k];
+        hi[k] = V[0][k];
+        for (int a = 1; a <= D; ++a) {
+            lo[k] = fmin(lo[k], V[a][k]);
+            hi[k] = fmax(hi[k], V[a][k]);
+        }
+    }
+    for (int g = 0; g < n_grids; ++g) {
+        const SubGrid& sg = sgs.g[g];
+        ElemBox b;
+        b.lo[0] = b.lo[1] = b.lo[2] = 0;
+        int ext[3] = {1, 1, 1};
+        int64_t count = 1;
+        bool ok = finite;
+        for (int k = 0; k < D; ++k) {
+            double qlo = __ddiv_rn(__dsub_rn(lo[k], sg.origin[k]), sg.h[k]);
+            double qhi = __ddiv_rn(__dsub_rn(hi[k], sg.origin[k]), sg.h[k]);
+            double flo = floor(qlo), chi = ceil(qhi) - 1.0;
+            if (!(flo >= 0.0) || !(chi < (double)sg.ncell[k])) { ok = false; break; }
+            int il = (int)flo, ih = (int)chi;
+            if (ih < il) ih = il;
+            ext[k] = ih - il + 1;
+            b.lo[k] = il;
+            if (ext[k] > 1023) { flags |= FLAG_CAPACITY; ok = false; break; }
+            count *= ext[k];
+        }
+        if (!ok && finite && !(flags & FLAG_CAPACITY)) flags |= FLAG_OUTOFGRID;
+        if (!ok || (flags & FLAG_DEGENERATE)) count = 0;
+        b.ext = ext[0] | (ext[1] << 10) | (ext[2] << 20);
+        boxes[g * m + e] = b;
+        counts[g * m + e] = count;
+        if (count > 0) {
+            for (int k = 0; k < D; ++k) {
+                atomicMin(node_box + g * 6 + k, b.lo[k]);
+                atomicMax(node_box + g * 6 + 3 + k, b.lo[k] + ext[k]);
+            }
+        }
+    }
+    if (flags) {
+        atomicOr(&st->flags, flags);
+        atomicMin(&st->bad_elem, (int32_t)e);
+    }
+}
+
+template <int D>
+__global__ void emit_pairs_kernel(int n_grids, SubGridSet sgs, int64_t m, const ElemBox* __restrict__ boxes,
+                                  const int64_t* __restrict__ offsets, int32_t* __restrict__ pair_elem,
+                                  int32_t* __restrict__ pair_cell) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= m * n_grids) return;
+    int g = (int)(t / m);
+    int64_t e = t - g * m;
+    const SubGrid& sg = sgs.g[g];
+    ElemBox b = boxes[t];
+    int64_t p = offsets[t], p1 = offsets[t + 1];
+    if (p == p1) return;
+    int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = box_ext(b, 2);
+    for (int kz = 0; kz < ez; ++kz)
+        for (int ky = 0; ky < ey; ++ky)
+            for (int kx = 0; kx < ex; ++kx) {
+                int32_t cell = (b.lo[0] + kx) + sg.ncell[0] * ((b.lo[1] + ky) + sg.ncell[1] * (b.lo[2] + kz));
+                pair_elem[p] = (int32_t)e;
+                pair_cell[p] = cell;
+                ++p;
+            }
+}
+
+// ------------------------------------------------------------------ scan
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* total) {
+    __shared__ int64_t warp_sums[kScanThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanThreads / 32) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int64_t warp_prefix = wid > 0 ? warp_sums[wid - 1] : 0;
+    *total = warp_sums[kScanThreads / 32 - 1];
+    __syncthreads();
+    return warp_prefix + x - v;
+}
+
+__global__ void scan_reduce_kernel(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ partial) {
+    int64_t base = blockIdx.x * (int64_t)kScanTile;
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
+        if (idx < n) s += in[idx];
+    }
+    int64_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void scan_partials_kernel(int64_t* partial, int64_t nb) {
+    // single block: exclusive scan of the block totals in place; partial[nb] = grand total
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanThreads) {
+        int64_t idx = base + threadIdx.x;
+        int64_t v = idx < nb ? partial[idx] : 0;
+        int64_t tot;
+        int64_t ex = block_exclusive_scan(v, &tot);
+        if (idx < nb) partial[idx] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) partial[nb] = carry;
+}
+
+__global__ void scan_apply_kernel(const int64_t* __restrict__ in, int64_t n, const int64_t* __restrict__ partial,
+                                  int64_t* __restrict__ out, int64_t nb) {
+    int64_t base = blockIdx.x * (int64_t)kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        s += v[i];
+    }
+    int64_t tot;
+    int64_t ex = block_exclusive_scan(s, &tot) + partial[blockIdx.x];
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = ex;
+        ex += v[i];
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = partial[nb];
+}
+
+}  // namespace
+
+void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const double* X,
+                       const int32_t* E, ElemBox* boxes, int64_t* counts, int32_t* node_box,
+                       double* elem_vol, DevStatus* st, cudaStream_t s) {
+    SubGridSet sgs{};
+    for (int g = 0; g < n_grids; ++g) sgs.g[g] = sg_host[g];
+    int threads = 256;
+    int64_t blocks = (m + threads - 1) / threads;
+    if (blocks == 0) return;
+    if (dim == 2)
+        elem_boxes_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, st);
+    else
+        elem_boxes_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, st);
+}
+
+size_t scan_tmp_bytes(int64_t n) {
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb < 1) nb = 1;
+    return (size_t)(nb + 1) * sizeof(int64_t);
+}
+
+// out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total.  n >= 1.
+void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s) {
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb < 1) nb = 1;
+    int64_t* partial = (int64_t*)tmp;
+    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
+    scan_partials_kernel<<<1, kScanThreads, 0, s>>>(partial, nb);
+    scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial, out, nb);
+}
+
+void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const ElemBox* boxes,
+                       const int64_t* offsets, int32_t* pair_elem, int32_t* pair_cell, cudaStream_t s) {
+    SubGridSet sgs{};
+    for (int g = 0; g < n_grids; ++g) sgs.g[g] = sg_host[g];
+    int threads = 256;
+    int64_t total = m * n_grids;
+    int64_t blocks = (total + threads - 1) / threads;
+    if (blocks == 0) return;
+    if (dim == 2)
+        emit_pairs_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell);
+    else
+        emit_pairs_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell);
+}
+
+}  // namespace l2x

@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/l2xfer.h with struct layouts that match the binding.
+(No compute calls: these run without a GPU.)"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1810_13046_gb300 as l2x
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "l2xfer.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(l2x_[A-Za-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = l2x.load_library()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", l2x.library_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (l2x_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "sizes.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "l2xfer.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(l2x_grid), sizeof(l2x_mesh),"
+        " sizeof(l2x_opts), sizeof(l2x_info), offsetof(l2x_info, cg_residual), offsetof(l2x_opts, force_scale));"
+        "return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    vals = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert vals == [ctypes.sizeof(l2x._Grid), ctypes.sizeof(l2x._Mesh), ctypes.sizeof(l2x._Opts),
+                    ctypes.sizeof(l2x._Info), l2x._Info.cg_residual.offset, l2x._Opts.force_scale.offset]
+
+
+def test_status_strings_and_defaults():
+    lib = l2x.load_library()
+    for s in range(10):
+        assert lib.l2x_status_string(s)
+    o = l2x._Opts()
+    lib.l2x_default_opts(ctypes.byref(o))
+    assert (o.path, o.precision, o.cg_max_iter, o.force_mode) == (l2x.FUSED, l2x.FP64, 200, l2x.DUAL)
+    assert o.cg_rtol == 1e-13 and o.force_scale == 1.0
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu():
+    """Argument validation happens on the host before any CUDA call."""
+    lib = l2x.load_library()
+    g = l2x._Grid()
+    g.dim = 4
+    m = l2x._Mesh()
+    m.dim = 4
+    h = ctypes.c_void_p()
+    st = lib.l2x_build_coupling(ctypes.byref(g), ctypes.byref(m), None, None, ctypes.byref(h))
+    assert st == 1 and not h.value
+    assert b"dim" in lib.l2x_last_error()
+    assert lib.l2x_destroy(None) == 0
