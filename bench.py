@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the L2-projection fluid <-> solid transfer on GB300.
+
+One step = the whole hot path of Sec. 2.3 on the current configuration of the
+solid: assembly of B_g (3 staggered Q1 grids) and M_s from scratch (candidate
+pairs, clipping + quadrature, CSR), the velocity transfer u_s = M_s^-1 B u_f
+(3 components) and the dual force transfer f_f += B^T M_s^-1 r (3 components).
+
+Workload (default): 128^3-cell staggered grids on [0,1]^3 (h = 1/128), a
+0.4 x 0.1 x 0.02 beam of 48,000 P1 tetrahedra under a seeded random rotation, a
+Taylor-Green velocity field (float32) and N(0,1) nodal forces; synthetic data.
+Each rank (torchrun, N > 1) transfers its own independently rotated beam: weak
+scaling, no collective on the data path.
+
+value = candidate pairs per second over whole steps (summed over ranks);
+assembly pairs/s and apply ms are reported beside it, together with the plain
+FP64 GPU path.  Inputs are resident in HBM; L2 is flushed (256 MB write) before
+every timed step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "L2-transfer assembly pairs/s & apply ms, 1 GB300, fused vs plain at rel≤1e-6"
+UNIT = "pairs/s"
+WORKLOAD = "beam128"
+WORKLOAD_DESC = ("3-D staggered Q1 grids 128^3 cells (h=1/128) on [0,1]^3; rotated beam 0.4x0.1x0.02, "
+                 "48,000 P1 tets / 10,206 nodes; Taylor-Green u_f (f32); N(0,1) nodal forces")
+# FP64 pipe peak derived from the unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Executed FP64 flops per candidate pair of the fused clip kernel (mixed form) on this workload,
+# from the ncu SASS instruction counters (2*DFMA + DADD + DMUL) of one launch divided by its pairs;
+# profiles/clip_fused_beam128.md.  None until measured.
+FP64_FLOPS_PER_PAIR = None
+CLIP_DRAM_BYTES_PER_PAIR = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(x: float, world: int):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- oracle legs
+
+def oracle_step(w, elems, nthreads):
+    """One step of the plain FP64 CPU oracle (assembly + both transfers)."""
+    import oracle
+    t0 = time.perf_counter()
+    oc = oracle.Coupling(w.grid, w.coords, elems, nthreads=nthreads)
+    t1 = time.perf_counter()
+    fields = [f.astype(np.float32).astype(np.float64) for f in w.fields]
+    us = oc.transfer_velocity(fields)
+    ff = oc.transfer_force(w.force.astype(np.float32).astype(np.float64), mode="dual")
+    t2 = time.perf_counter()
+    npairs = sum(len(p[0]) for p in oc.pairs)
+    return oc, us, ff, npairs, t1 - t0, t2 - t1
+
+
+def reference_arm(args, rank, world):
+    """The oracle as it stands, on the host cores: each step a bounded sample
+    (the first quarter of the beam's tetrahedra) of the same workload."""
+    if rank != 0:
+        return 0
+    import synth
+    w = synth.workload(args.workload, 0)
+    m = w.elems.shape[0] // 4
+    elems = w.elems[:m]
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_step(w, elems, cores)
+    times, pairs = [], 0
+    for _ in range(args.steps):
+        _, _, _, npairs, tb, ta = oracle_step(w, elems, cores)
+        times.append(tb + ta)
+        pairs = npairs
+    total = sum(times)
+    value = pairs * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": WORKLOAD_DESC,
+                                            "sample": f"first {m} of {w.elems.shape[0]} tetrahedra per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {m} of {w.elems.shape[0]} tetrahedra per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    import torch
+    import synth
+    import paper_1810_13046_gb300 as l2x
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    w = synth.workload(args.workload, seed=rank)
+    X = torch.from_numpy(w.coords).to(dev)
+    E = torch.from_numpy(w.elems).to(dev)
+    u32 = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in w.fields]
+    F32 = w.force.astype(np.float32)
+    f32 = [torch.from_numpy(np.ascontiguousarray(F32[:, g])).to(dev) for g in range(3)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run_form(path, precision, steps, warmup, timing=False):
+        dt = torch.float32 if precision == l2x.MIXED else torch.float64
+        c = l2x.Coupling(w.grid, X, E, path=path, precision=precision,
+                         cg_rtol=1e-9 if precision == l2x.MIXED else 1e-13)
+        uf = [u.to(dt) for u in u32]
+        fs = [f.to(dt) for f in f32]
+        ff = [torch.zeros(n, dtype=dt, device=dev) for n in c.fluid_sizes()]
+        stream = torch.cuda.current_stream(dev)
+
+        def step(ev=None):
+            if ev is not None:
+                ev[0].record(stream)
+            c.update_geometry(X)
+            if ev is not None:
+                ev[1].record(stream)
+            us = c.transfer_velocity(uf)
+            c.transfer_force(fs, ff)
+            if ev is not None:
+                ev[2].record(stream)
+            return us
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        if timing:
+            c.set_timing(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        n0 = l2x.kernel_launch_count()
+        tb = ta = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step(ev)
+            ev[2].synchronize()
+            tb += ev[0].elapsed_time(ev[1])
+            ta += ev[1].elapsed_time(ev[2])
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = l2x.kernel_launch_count() - n0
+        info = c.info()
+        return c, info, tb / steps, ta / steps, launches, uf, fs
+
+    # chosen form: fused, FP64 geometry + FP32 fields/SpMV/CG with FP64 dots and refinement
+    with ClockSampler(local) as clocks:
+        c, info, build_ms, apply_ms, launches, uf, fs = run_form(l2x.FUSED, l2x.MIXED, args.steps, args.warmup,
+                                                                 timing=True)
+    step_ms = max_over_ranks(build_ms + apply_ms, world)
+    pairs = info["n_pairs_total"]
+    total_pairs = sum_over_ranks(float(pairs), world)
+    value = total_pairs / (step_ms * 1e-3)
+    asm_pairs_s = total_pairs / (max_over_ranks(build_ms, world) * 1e-3)
+    ph = info["phase_ms"]
+    calls = info["phase_calls"]
+    clip_launch_ms = ph["clip"] / max(1, calls["clip"])
+    clip_pairs_per_launch = pairs / 3.0
+
+    # comparison forms (fewer steps)
+    cp, ip, pb, pa, _, _, _ = run_form(l2x.PLAIN, l2x.FP64, args.plain_steps, 2)
+    cf, if64, fb, fa, _, _, _ = run_form(l2x.FUSED, l2x.FP64, args.plain_steps, 2)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    Xh = torch.from_numpy(w.coords).pin_memory()
+    uh = [torch.from_numpy(f.astype(np.float32)).pin_memory() for f in w.fields]
+    fh = [torch.from_numpy(np.ascontiguousarray(F32[:, g])).pin_memory() for g in range(3)]
+    us_h = [torch.empty(c.n_nodes, dtype=torch.float32).pin_memory() for _ in range(3)]
+    ff_h = [torch.empty(n, dtype=torch.float32).pin_memory() for n in c.fluid_sizes()]
+    Xd = torch.empty_like(X)
+    ud = [torch.empty_like(u) for u in uf]
+    fd = [torch.empty_like(f) for f in fs]
+    ffd = [torch.zeros(n, dtype=torch.float32, device=dev) for n in c.fluid_sizes()]
+    stream = torch.cuda.current_stream(dev)
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        for a, b in zip(ud, uh):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(fd, fh):
+            a.copy_(b, non_blocking=True)
+        c.update_geometry(Xd)
+        us = c.transfer_velocity(ud)
+        for z in ffd:
+            z.zero_()
+        c.transfer_force(fd, ffd)
+        for a, b in zip(us_h, us):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(ff_h, ffd):
+            a.copy_(b, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    e_ms = 0.0
+    n_e2e = max(3, args.steps // 2)
+    for _ in range(n_e2e):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        e1.synchronize()
+        e_ms += e0.elapsed_time(e1)
+    e_ms = max_over_ranks(e_ms / n_e2e, world)
+    h2d = Xh.numel() * 8 + sum(t.numel() * 4 for t in uh) + sum(t.numel() * 4 for t in fh)
+    d2h = sum(t.numel() * 4 for t in us_h) + sum(t.numel() * 4 for t in ff_h)
+
+    roof = None
+    if FP64_FLOPS_PER_PAIR is not None:
+        achieved = FP64_FLOPS_PER_PAIR * clip_pairs_per_launch / (clip_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "clip_fused_kernel<3,float>",
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and clock)",
+                "traffic": (CLIP_DRAM_BYTES_PER_PAIR * clip_pairs_per_launch
+                            if CLIP_DRAM_BYTES_PER_PAIR is not None else None)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        oc, us_ref, ff_ref, npairs_o, tb_o, ta_o = oracle_step(w, w.elems, cores)
+        got = np.stack([u.cpu().numpy() for u in c.transfer_velocity(uf)], axis=1)
+        err_u = float(np.linalg.norm(got - us_ref) / np.linalg.norm(us_ref))
+        ffz = [torch.zeros(n, dtype=torch.float32, device=dev) for n in c.fluid_sizes()]
+        c.transfer_force(fs, ffz)
+        err_f = max(float(np.linalg.norm(ffz[g].cpu().numpy() - ff_ref[g]) / np.linalg.norm(ff_ref[g]))
+                    for g in range(3))
+        cpu = {"value": npairs_o / (tb_o + ta_o), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "one full step (assembly + velocity + dual force transfer) of the same workload",
+               "assembly_s": tb_o, "apply_s": ta_o, "rel_err_u_s": err_u, "rel_err_f_f": err_f}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "form": "fused, FP64 geometry, FP32 "
+                       "fields/SpMV/CG with compensated dots and FP64 refinement", "pairs_per_step": pairs,
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "assembly_pairs_per_s": asm_pairs_s, "assembly_ms": build_ms, "apply_ms": apply_ms,
+            "phase_ms_per_step": {k: v / args.steps for k, v in ph.items()},
+            "plain_fp64": {"assembly_ms": pb, "apply_ms": pa, "pairs_per_s": pairs / ((pb + pa) * 1e-3),
+                           "assembly_pairs_per_s": pairs / (pb * 1e-3), "cg_iters": ip["cg_iters"]},
+            "fused_fp64": {"assembly_ms": fb, "apply_ms": fa, "pairs_per_s": pairs / ((fb + fa) * 1e-3),
+                           "assembly_pairs_per_s": pairs / (fb * 1e-3), "cg_iters": if64["cg_iters"]},
+            "e2e": {"value": total_pairs / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": e_ms,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -63,6 +63,19 @@ enum { L2X_FP64 = 0, L2X_MIXED = 1 };
 enum { L2X_FORCE_NODAL = 0, L2X_FORCE_DUAL = 1 };
 enum { L2X_MAT_B0 = 0, L2X_MAT_B1 = 1, L2X_MAT_B2 = 2, L2X_MAT_M = 3 };
 
+/* Phases timed by l2x_set_timing (indices of l2x_info.phase_ms). */
+enum {
+    L2X_PH_PAIRS = 0,      /* step (I): candidate boxes, counts, scan, pair list */
+    L2X_PH_CLIP = 1,       /* steps (II)-(III): clipping + quadrature of every pair */
+    L2X_PH_ROWS = 2,       /* step (IV): CSR assembly of B_g */
+    L2X_PH_TRANSPOSE = 3,  /* B_g^T for the force transfer */
+    L2X_PH_MASS = 4,       /* values of M_s */
+    L2X_PH_SPMV_B = 5,     /* y = B_g u_f */
+    L2X_PH_PCG = 6,        /* M_s^-1 by Jacobi-PCG */
+    L2X_PH_SPMV_BT = 7,    /* f_f += s B_g^T z */
+    L2X_NPHASE = 8
+};
+
 /* Base (pressure) grid: ncell[k] cells of width h[k] from origin[k], k < dim. */
 typedef struct l2x_grid {
     int32_t dim;        /* 2 or 3 */
@@ -105,6 +118,8 @@ typedef struct l2x_info {
     int32_t cg_iters;          /* iterations of the last mass-matrix solve (max over components) */
     int32_t reserved;
     double cg_residual;        /* relative residual reached by the last solve (max over components) */
+    double phase_ms[8];        /* device time per phase since l2x_set_timing(h, 1) (CUDA events) */
+    int64_t phase_calls[8];    /* timed intervals per phase */
 } l2x_info;
 
 typedef struct l2x_coupling* l2x_handle;
@@ -163,6 +178,14 @@ l2x_status l2x_export_pair_blocks(l2x_handle h, int32_t grid, double* blocks, do
                                   void* stream);
 l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t* cols,
                           double* vals, void* stream);
+
+/* Enables (1, also clears the totals) or disables (0) CUDA-event timing of the
+ * phases listed above, recorded on the stream of each call; l2x_query resolves
+ * the events (waiting for them). */
+l2x_status l2x_set_timing(l2x_handle h, int32_t enable);
+
+/* Number of kernels this library has launched in this process (all handles). */
+int64_t l2x_kernel_launch_count(void);
 
 /* Releases every device allocation of the handle (stream-ordered on the stream
  * of the last call).  NULL is accepted. */

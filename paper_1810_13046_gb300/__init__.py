@@ -18,7 +18,7 @@ import torch
 
 from . import build as _build
 
-__all__ = ["Coupling", "Grid", "VelocityTransfer", "ForceTransfer", "L2XError", "library_path", "load_library",
+__all__ = ["kernel_launch_count", "PHASES", "Coupling", "Grid", "VelocityTransfer", "ForceTransfer", "L2XError", "library_path", "load_library",
            "PLAIN", "FUSED", "FP64", "MIXED", "NODAL", "DUAL"]
 
 PLAIN, FUSED = 0, 1
@@ -53,7 +53,11 @@ class _Info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("n_elems", ctypes.c_int64),
                 ("n_pairs", ctypes.c_int64 * 3), ("n_pairs_total", ctypes.c_int64), ("nnz_B", ctypes.c_int64 * 3),
                 ("nnz_M", ctypes.c_int64), ("n_fluid", ctypes.c_int64 * 3), ("nnode", (ctypes.c_int32 * 3) * 3),
-                ("cg_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cg_residual", ctypes.c_double)]
+                ("cg_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cg_residual", ctypes.c_double),
+                ("phase_ms", ctypes.c_double * 8), ("phase_calls", ctypes.c_int64 * 8)]
+
+
+PHASES = ["pairs", "clip", "rows", "transpose", "mass", "spmv_B", "pcg", "spmv_BT"]
 
 
 _lib = None
@@ -90,6 +94,8 @@ def load_library(build_if_missing: bool = True):
         "l2x_export_pair_blocks": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
         "l2x_export_csr": ([P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
         "l2x_destroy": ([P], ctypes.c_int),
+        "l2x_set_timing": ([P, ctypes.c_int32], ctypes.c_int),
+        "l2x_kernel_launch_count": ([], ctypes.c_int64),
         "l2x_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "l2x_last_error": ([], ctypes.c_char_p),
     }
@@ -99,6 +105,11 @@ def load_library(build_if_missing: bool = True):
         fn.restype = res
     _lib = lib
     return lib
+
+
+def kernel_launch_count() -> int:
+    """Kernels launched by libl2xfer in this process so far."""
+    return int(load_library().l2x_kernel_launch_count())
 
 
 def _check(status: int):
@@ -204,7 +215,13 @@ class Coupling:
                     nnz_B=[inf.nnz_B[g] for g in range(G)], nnz_M=inf.nnz_M,
                     n_fluid=[inf.n_fluid[g] for g in range(G)],
                     nnode=[tuple(inf.nnode[g][k] for k in range(3)) for g in range(G)],
-                    cg_iters=inf.cg_iters, cg_residual=inf.cg_residual)
+                    cg_iters=inf.cg_iters, cg_residual=inf.cg_residual,
+                    phase_ms={p: inf.phase_ms[i] for i, p in enumerate(PHASES)},
+                    phase_calls={p: inf.phase_calls[i] for i, p in enumerate(PHASES)})
+
+    def set_timing(self, enable: bool = True):
+        """CUDA-event timing of the library's phases (totals in info()['phase_ms'])."""
+        _check(load_library().l2x_set_timing(self._h, int(bool(enable))))
 
     def fluid_sizes(self):
         return self.info()["n_fluid"]

@@ -1,5 +1,7 @@
 // C-ABI entry points of l2xfer: handle management and the orchestration of the
 // assembly (steps I-IV of Sec. 2.3) and of the two transfers.
+#include <atomic>
+#include <memory>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -9,6 +11,16 @@
 #include "l2x_internal.cuh"
 
 using namespace l2x;
+
+namespace l2x {
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace l2x
+
+struct PhaseRec {
+    int phase;
+    cudaEvent_t a, b;
+};
 
 struct l2x_coupling {
     int dim = 0, n_grids = 0;
@@ -56,7 +68,62 @@ struct l2x_coupling {
     // last solve
     int cg_iters = 0;
     double cg_residual = 0.0;
+    // phase timing
+    bool timing = false;
+    std::vector<PhaseRec> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double phase_ms[L2X_NPHASE]{};
+    int64_t phase_calls[L2X_NPHASE]{};
 };
+
+namespace {
+
+cudaEvent_t take_event(l2x_coupling* h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records CUDA events around one phase on the call's stream when timing is on.
+struct PhaseScope {
+    l2x_coupling* h;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    PhaseScope(l2x_coupling* h_, int phase_, cudaStream_t s_) : h(h_), phase(phase_), s(s_) {
+        if (h->timing) {
+            a = take_event(h);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~PhaseScope() {
+        if (a) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, s);
+            h->pending.push_back(PhaseRec{phase, a, b});
+        }
+    }
+};
+
+void resolve_timing(l2x_coupling* h) {
+    for (auto& r : h->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            h->phase_ms[r.phase] += ms;
+            h->phase_calls[r.phase] += 1;
+        }
+        h->event_pool.push_back(r.a);
+        h->event_pool.push_back(r.b);
+    }
+    h->pending.clear();
+}
+
+}  // namespace
 
 namespace {
 
@@ -204,6 +271,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
     L2X_CUDA(cudaMemcpyAsync(h->node_box, nb_init, sizeof(int32_t) * 6 * G, cudaMemcpyHostToDevice, s));
     L2X_CUDA(cudaStreamSynchronize(s));
     // (I) candidate boxes, counts, offsets
+    auto ph_pairs = std::make_unique<PhaseScope>(h, L2X_PH_PAIRS, s);
     launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->node_box, h->elem_vol, h->st, s);
     launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
     std::vector<int64_t> gb(G + 1);
@@ -229,9 +297,11 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         h->pair_cap = cap;
     }
     launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, s);
+    ph_pairs.reset();
     // (II)-(III) clip + quadrature
     const bool plain = h->opts.path == L2X_PATH_PLAIN;
     for (int g = 0; g < G; ++g) {
+        PhaseScope ph(h, L2X_PH_CLIP, s);
         if (plain)
             launch_clip_plain(d, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks,
                               h->vols, h->st, s);
@@ -241,6 +311,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
     }
     // (IV) B_g by rows
     for (int g = 0; g < G; ++g) {
+        auto ph_rows = std::make_unique<PhaseScope>(h, L2X_PH_ROWS, s);
         Csr& B = h->B[g];
         const ElemBox* bx = h->boxes + (int64_t)g * m;
         const int64_t* off = h->offsets + (int64_t)g * m;
@@ -250,6 +321,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         launch_scan_i64(h->row_count, B.ptr, n, h->scan_tmp, s);
         int64_t nnz = 0;
         L2X_CUDA(cudaMemcpyAsync(&nnz, B.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        ph_rows.reset();
         L2X_TRY(read_status(h, s));
         B.n_rows = n;
         B.nnz = nnz;
@@ -264,14 +336,19 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
             h->B_cap[g] = c;
         }
         if (plain) {
+            PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
             launch_b_rows(2, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, nullptr,
                           B.ptr, B.col, B.val, h->st, s);
             launch_scatter_plain(d, h->sg[g], h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks, h->vols,
                                  B, s);
         } else {
-            launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, nullptr,
-                          B.ptr, B.col, B.val, h->st, s);
-            if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, nnz, s);
+            {
+                PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
+                launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols,
+                              nullptr, B.ptr, B.col, B.val, h->st, s);
+                if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, nnz, s);
+            }
+            PhaseScope ph_t(h, L2X_PH_TRANSPOSE, s);
             // B_g^T over the box of touched fluid nodes
             CsrT& T = h->T[g];
             int64_t rows = 1;
@@ -314,6 +391,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         }
     }
     // mass matrix values
+    PhaseScope ph_mass(h, L2X_PH_MASS, s);
     launch_mass_values(d, n, h->E, h->adj_ptr, h->adj, h->elem_vol, h->M.ptr, h->M.col, h->M.val, h->M_dinv, s);
     launch_to_f32(h->M.val, h->M.val32, h->M.nnz, s);
     launch_to_f32(h->M_dinv, h->M_dinv32, n, s);
@@ -386,6 +464,8 @@ const char* l2x_last_error(void) { return g_last_error.c_str(); }
 l2x_status l2x_destroy(l2x_handle h) {
     if (!h) return L2X_OK;
     cudaStreamSynchronize(h->stream);
+    resolve_timing(h);
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     dfree(h->X); dfree(h->E); dfree(h->adj_ptr); dfree(h->adj); dfree(h->cursor); dfree(h->elem_vol);
     dfree(h->boxes); dfree(h->counts); dfree(h->offsets); dfree(h->node_box); dfree(h->pair_elem);
     dfree(h->pair_cell); dfree(h->blocks); dfree(h->vols);
@@ -479,6 +559,7 @@ l2x_status l2x_apply_B(l2x_handle h, const void* const* x_f, void* const* y_s, v
     L2X_TRY(check_ptrs(x_f, h->n_grids, "x_f"));
     L2X_TRY(check_ptrs((const void* const*)y_s, h->n_grids, "y_s"));
     cudaStream_t s = (cudaStream_t)stream;
+    PhaseScope ph(h, L2X_PH_SPMV_B, s);
     launch_spmv_B(h->opts.path, h->opts.precision, h->n_grids, h->B, x_f, y_s, s);
     L2X_CUDA(cudaGetLastError());
     return L2X_OK;
@@ -489,6 +570,7 @@ l2x_status l2x_apply_BT(l2x_handle h, const void* const* z_s, void* const* f_f, 
     L2X_TRY(check_ptrs(z_s, h->n_grids, "z_s"));
     L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
     cudaStream_t s = (cudaStream_t)stream;
+    PhaseScope ph(h, L2X_PH_SPMV_BT, s);
     launch_spmv_BT(h->opts.path, h->opts.precision, h->n_grids, h->B, h->T, h->sg, z_s, f_f, scale, s);
     L2X_CUDA(cudaGetLastError());
     return L2X_OK;
@@ -500,8 +582,10 @@ l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s
     L2X_TRY(check_ptrs((const void* const*)w_s, h->n_grids, "w_s"));
     cudaStream_t s = (cudaStream_t)stream;
     PcgResult r;
+    auto ph = std::make_unique<PhaseScope>(h, L2X_PH_PCG, s);
     l2x_status st = solve_mass_pcg(h->opts.path, h->opts.precision, h->M, h->M_dinv, h->M_dinv32, h->n_grids, y_s,
                                    w_s, h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, h->st_host, s, &r);
+    ph.reset();
     h->cg_iters = r.iters;
     h->cg_residual = r.residual;
     if (st == L2X_ECUDA) return cuda_fail(cudaGetLastError(), "mass-matrix solve");
@@ -556,8 +640,27 @@ l2x_status l2x_query(l2x_handle h, l2x_info* info) {
     info->nnz_M = h->M.nnz;
     info->cg_iters = h->cg_iters;
     info->cg_residual = h->cg_residual;
+    resolve_timing(h);
+    for (int p = 0; p < L2X_NPHASE; ++p) {
+        info->phase_ms[p] = h->phase_ms[p];
+        info->phase_calls[p] = h->phase_calls[p];
+    }
     return L2X_OK;
 }
+
+l2x_status l2x_set_timing(l2x_handle h, int32_t enable) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    resolve_timing(h);
+    h->timing = enable != 0;
+    if (enable)
+        for (int p = 0; p < L2X_NPHASE; ++p) {
+            h->phase_ms[p] = 0.0;
+            h->phase_calls[p] = 0;
+        }
+    return L2X_OK;
+}
+
+int64_t l2x_kernel_launch_count(void) { return l2x::g_launches.load(); }
 
 l2x_status l2x_export_pairs(l2x_handle h, int32_t grid, int32_t* elem, int32_t* cell, void* stream) {
     if (!h || !elem || !cell || grid < 0 || grid >= h->n_grids) return fail(L2X_EINVAL, "bad export_pairs arguments");

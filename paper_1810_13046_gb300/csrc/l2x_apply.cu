@@ -343,6 +343,11 @@ __global__ void plain_update_p_kernel(int64_t n, int nr, const double* scal, con
     }
 }
 
+// a component with a zero right-hand side has the solution 0 and takes no step
+__global__ void plain_active_kernel(int nr, double* scal, const double* rr0) {
+    if (threadIdx.x < nr) scal[12 + threadIdx.x] = rr0[threadIdx.x] > 0.0 ? 1.0 : 0.0;
+}
+
 __global__ void plain_scalars_kernel(int nr, double* scal, const double* rr0, double rtol) {
     // after an iteration: rz <- rz_new, clear accumulators, freeze converged components
     if (threadIdx.x != 0) return;
@@ -448,6 +453,7 @@ cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val,
     A.st = st;
     int blocks = pcg_blocks_for<TV>(n);
     void* args[] = {&A};
+    count_launch();
     return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV>, dim3(blocks), dim3(kPcgThreads), args, 0, s);
 }
 
@@ -474,8 +480,8 @@ void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const voi
     if (n <= 0) return;
     if (path == L2X_PATH_PLAIN) {
         for (int g = 0; g < n_grids; ++g)
-            spmv_B_plain_kernel<<<nblk(n, 256), 256, 0, s>>>(n, B[g].ptr, B[g].col, B[g].val, (const double*)x[g],
-                                                             (double*)y[g]);
+            { spmv_B_plain_kernel<<<nblk(n, 256), 256, 0, s>>>(n, B[g].ptr, B[g].col, B[g].val, (const double*)x[g],
+                                                             (double*)y[g]); count_launch(); }
         return;
     }
     const int64_t threads = n * n_grids * 8;
@@ -485,14 +491,14 @@ void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const voi
             P.ptr[g] = B[g].ptr; P.col[g] = B[g].col; P.val[g] = B[g].val32;
             P.x[g] = (const float*)x[g]; P.y[g] = (float*)y[g];
         }
-        spmv_B_fused_kernel<float, float><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P);
+        { spmv_B_fused_kernel<float, float><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P); count_launch(); }
     } else {
         SpmvPack<double, double> P{};
         for (int g = 0; g < n_grids; ++g) {
             P.ptr[g] = B[g].ptr; P.col[g] = B[g].col; P.val[g] = B[g].val;
             P.x[g] = (const double*)x[g]; P.y[g] = (double*)y[g];
         }
-        spmv_B_fused_kernel<double, double><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P);
+        { spmv_B_fused_kernel<double, double><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P); count_launch(); }
     }
 }
 
@@ -501,8 +507,8 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
     if (path == L2X_PATH_PLAIN) {
         for (int g = 0; g < n_grids; ++g)
             if (B[g].n_rows > 0)
-                spmv_BT_plain_kernel<<<nblk(B[g].n_rows, 256), 256, 0, s>>>(B[g].n_rows, B[g].ptr, B[g].col, B[g].val,
-                                                                            (const double*)z[g], (double*)f[g], scale);
+                { spmv_BT_plain_kernel<<<nblk(B[g].n_rows, 256), 256, 0, s>>>(B[g].n_rows, B[g].ptr, B[g].col, B[g].val,
+                                                                            (const double*)z[g], (double*)f[g], scale); count_launch(); }
         return;
     }
     auto fill = [&](auto& P, bool f32) {
@@ -531,7 +537,7 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
             P.z[g] = (const float*)z[g];
             P.f[g] = (float*)f[g];
         }
-        if (total > 0) spmv_BT_fused_kernel<float, float><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, (float)scale);
+        if (total > 0) { spmv_BT_fused_kernel<float, float><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, (float)scale); count_launch(); }
     } else {
         SpmvTPack<double, double> P{};
         int64_t total = fill(P, false);
@@ -540,7 +546,7 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
             P.z[g] = (const double*)z[g];
             P.f[g] = (double*)f[g];
         }
-        if (total > 0) spmv_BT_fused_kernel<double, double><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, scale);
+        if (total > 0) { spmv_BT_fused_kernel<double, double><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, scale); count_launch(); }
     }
 }
 
@@ -572,29 +578,28 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
         double* xx[3] = {(double*)w[0], nr > 1 ? (double*)w[1] : nullptr, nr > 2 ? (double*)w[2] : nullptr};
         unsigned nb = nblk(n, 256);
         unsigned nbd = nb < 1024 ? nb : 1024;
-        plain_init_kernel<<<nb, 256, 0, s>>>(n, nr, yy[0], yy[1], yy[2], xx[0], xx[1], xx[2], diag_inv, r, z, p);
+        { plain_init_kernel<<<nb, 256, 0, s>>>(n, nr, yy[0], yy[1], yy[2], xx[0], xx[1], xx[2], diag_inv, r, z, p); count_launch(); }
         cudaMemsetAsync(scal, 0, 16 * 8, s);
         cudaMemsetAsync(rr0, 0, 4 * 8, s);
-        plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, z, scal);      // rz
-        plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, r, rr0);       // |y|^2
-        double ones[3] = {1.0, 1.0, 1.0};
-        cudaMemcpyAsync(scal + 12, ones, sizeof(double) * nr, cudaMemcpyHostToDevice, s);
+        { plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, z, scal); count_launch(); }      // rz
+        { plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, r, rr0); count_launch(); }       // |y|^2
+        { plain_active_kernel<<<1, 32, 0, s>>>(nr, scal, rr0); count_launch(); }
         double rr0h[3] = {0, 0, 0};
         int it = 0;
         bool done = false;
         double worst = 0.0;
         for (; it < max_iter && !done; ++it) {
-            plain_spmv_kernel<<<nb, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, p, q);
-            plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, p, q, scal + 3);
-            plain_update_x_kernel<<<nb, 256, 0, s>>>(n, nr, scal, xx[0], xx[1], xx[2], r, z, p, q, diag_inv);
-            plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, z, scal + 6);
-            plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, r, scal + 9);
-            plain_update_p_kernel<<<nb, 256, 0, s>>>(n, nr, scal, z, p);
+            { plain_spmv_kernel<<<nb, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, p, q); count_launch(); }
+            { plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, p, q, scal + 3); count_launch(); }
+            { plain_update_x_kernel<<<nb, 256, 0, s>>>(n, nr, scal, xx[0], xx[1], xx[2], r, z, p, q, diag_inv); count_launch(); }
+            { plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, z, scal + 6); count_launch(); }
+            { plain_dot_kernel<<<nbd, 256, 0, s>>>(n, nr, r, r, scal + 9); count_launch(); }
+            { plain_update_p_kernel<<<nb, 256, 0, s>>>(n, nr, scal, z, p); count_launch(); }
             // host convergence check (read the residual norms every iteration)
             if ((ce = cudaMemcpyAsync(hs, scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
             if (it == 0 && (ce = cudaMemcpyAsync(rr0h, rr0, sizeof(double) * nr, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
             if ((ce = cudaStreamSynchronize(s)) != cudaSuccess) break;
-            plain_scalars_kernel<<<1, 32, 0, s>>>(nr, scal, rr0, rtol);
+            { plain_scalars_kernel<<<1, 32, 0, s>>>(nr, scal, rr0, rtol); count_launch(); }
             done = true;
             worst = 0.0;
             for (int k = 0; k < nr; ++k) {
@@ -638,7 +643,7 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
     unsigned nbd = nb < 1024 ? nb : 1024;
     const double inner = rtol > 1e-6 ? rtol : 1e-6;
     cudaMemsetAsync(norms, 0, 8 * 8, s);
-    norm2_f32_kernel<<<nbd, 256, 0, s>>>(n, nr, yf[0], yf[1], yf[2], norms + 4);
+    { norm2_f32_kernel<<<nbd, 256, 0, s>>>(n, nr, yf[0], yf[1], yf[2], norms + 4); count_launch(); }
     int total_it = 0;
     double worst = 0.0;
     bool ok = false;
@@ -654,10 +659,10 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
         ce = run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner,
                                   max_iter, st, s);
         if (ce != cudaSuccess) return L2X_ECUDA;
-        add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr,
-                                                 nr > 2 ? dst[2] : nullptr, ref == 0);
+        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr,
+                                                 nr > 2 ? dst[2] : nullptr, ref == 0); count_launch(); }
         cudaMemsetAsync(norms, 0, 4 * 8, s);
-        residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf[0], yf[1], yf[2], x64, r64, r32, norms);
+        { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf[0], yf[1], yf[2], x64, r64, r32, norms); count_launch(); }
         if (cudaMemcpyAsync(st_host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
         if (cudaMemcpyAsync(hn, norms, 8 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return L2X_ECUDA;
@@ -666,7 +671,7 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
         for (int k = 0; k < nr; ++k) worst = fmax(worst, hn[4 + k] > 0.0 ? sqrt(hn[k] / hn[4 + k]) : 0.0);
         ok = worst <= rtol;
     }
-    store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf[0], wf[1], wf[2]);
+    { store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf[0], wf[1], wf[2]); count_launch(); }
     if (cudaGetLastError() != cudaSuccess) return L2X_ECUDA;
     res->iters = total_it;
     res->residual = worst;

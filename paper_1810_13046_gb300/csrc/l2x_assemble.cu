@@ -278,10 +278,10 @@ void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E
     const int64_t total = m * NA;
     cudaMemsetAsync(adj_ptr, 0, sizeof(int64_t) * (n_nodes + 1), s);
     cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n_nodes, s);
-    if (total > 0) adj_count_kernel<<<nblk(total, 256), 256, 0, s>>>(NA, total, E, adj_ptr);
+    if (total > 0) { adj_count_kernel<<<nblk(total, 256), 256, 0, s>>>(NA, total, E, adj_ptr); count_launch(); }
     launch_scan_i64(adj_ptr, adj_ptr, n_nodes, scan_tmp, s);
-    if (total > 0) adj_fill_kernel<<<nblk(total, 256), 256, 0, s>>>(NA, total, E, adj_ptr, cursor, adj);
-    segment_sort_kernel<double><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, adj_ptr, adj, nullptr);
+    if (total > 0) { adj_fill_kernel<<<nblk(total, 256), 256, 0, s>>>(NA, total, E, adj_ptr, cursor, adj); count_launch(); }
+    { segment_sort_kernel<double><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, adj_ptr, adj, nullptr); count_launch(); }
 }
 
 void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const int64_t* adj_ptr,
@@ -291,11 +291,11 @@ void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const 
     if (n_nodes <= 0) return;
     unsigned nb = nblk(n_nodes, kRowWarps);
     if (dim == 2)
-        b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, offsets_g, blocks,
-                                                      slot_stride, vols, row_count, row_ptr, cols, vals, st);
+        { b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, offsets_g, blocks,
+                                                      slot_stride, vols, row_count, row_ptr, cols, vals, st); count_launch(); }
     else
-        b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, offsets_g, blocks,
-                                                      slot_stride, vols, row_count, row_ptr, cols, vals, st);
+        { b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, offsets_g, blocks,
+                                                      slot_stride, vols, row_count, row_ptr, cols, vals, st); count_launch(); }
 }
 
 void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
@@ -303,9 +303,9 @@ void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E,
                            DevStatus* st, cudaStream_t s) {
     if (n_nodes <= 0) return;
     if (dim == 2)
-        mass_structure_kernel<2><<<nblk(n_nodes, 128), 128, 0, s>>>(pass, n_nodes, E, adj_ptr, adj, row_count, row_ptr, cols, st);
+        { mass_structure_kernel<2><<<nblk(n_nodes, 128), 128, 0, s>>>(pass, n_nodes, E, adj_ptr, adj, row_count, row_ptr, cols, st); count_launch(); }
     else
-        mass_structure_kernel<3><<<nblk(n_nodes, 128), 128, 0, s>>>(pass, n_nodes, E, adj_ptr, adj, row_count, row_ptr, cols, st);
+        { mass_structure_kernel<3><<<nblk(n_nodes, 128), 128, 0, s>>>(pass, n_nodes, E, adj_ptr, adj, row_count, row_ptr, cols, st); count_launch(); }
 }
 
 void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
@@ -313,28 +313,28 @@ void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_
                         const int32_t* cols, double* vals, double* diag_inv, cudaStream_t s) {
     if (n_nodes <= 0) return;
     if (dim == 2)
-        mass_values_kernel<2><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv);
+        { mass_values_kernel<2><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv); count_launch(); }
     else
-        mass_values_kernel<3><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv);
+        { mass_values_kernel<3><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv); count_launch(); }
 }
 
 void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, cudaStream_t s) {
     cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (T.n_rows + 1), s);
-    if (B.n_rows > 0) transpose_count_kernel<<<nblk(B.n_rows, 128), 128, 0, s>>>(B.n_rows, B.ptr, B.col, sg, T, cnt);
+    if (B.n_rows > 0) { transpose_count_kernel<<<nblk(B.n_rows, 128), 128, 0, s>>>(B.n_rows, B.ptr, B.col, sg, T, cnt); count_launch(); }
 }
 
 void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, cudaStream_t s) {
     cudaMemsetAsync(cursor, 0, sizeof(int32_t) * T.n_rows, s);
     if (B.n_rows > 0)
-        transpose_fill_kernel<<<nblk(B.n_rows, 128), 128, 0, s>>>(B.n_rows, B.ptr, B.col, B.val, sg, T, cursor);
+        { transpose_fill_kernel<<<nblk(B.n_rows, 128), 128, 0, s>>>(B.n_rows, B.ptr, B.col, B.val, sg, T, cursor); count_launch(); }
 }
 
 void launch_transpose_sort(const CsrT& T, cudaStream_t s) {
-    if (T.n_rows > 0) segment_sort_kernel<double><<<nblk(T.n_rows, 128), 128, 0, s>>>(T.n_rows, T.ptr, T.col, T.val);
+    if (T.n_rows > 0) { segment_sort_kernel<double><<<nblk(T.n_rows, 128), 128, 0, s>>>(T.n_rows, T.ptr, T.col, T.val); count_launch(); }
 }
 
 void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {
-    if (n > 0) to_f32_kernel<<<nblk(n, 256), 256, 0, s>>>(in, out, n);
+    if (n > 0) { to_f32_kernel<<<nblk(n, 256), 256, 0, s>>>(in, out, n); count_launch(); }
 }
 
 }  // namespace l2x

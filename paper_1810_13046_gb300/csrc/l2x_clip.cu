@@ -144,14 +144,14 @@ void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* 
     unsigned nb = (unsigned)((n + kClipThreads - 1) / kClipThreads);
     if (dim == 2) {
         if (precision == L2X_MIXED)
-            clip_fused_kernel<2, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st);
+            { clip_fused_kernel<2, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
         else
-            clip_fused_kernel<2, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st);
+            { clip_fused_kernel<2, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
     } else {
         if (precision == L2X_MIXED)
-            clip_fused_kernel<3, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st);
+            { clip_fused_kernel<3, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
         else
-            clip_fused_kernel<3, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st);
+            { clip_fused_kernel<3, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
     }
 }
 
@@ -162,9 +162,9 @@ void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_
     if (n <= 0) return;
     unsigned nb = (unsigned)((n + 127) / 128);
     if (dim == 2)
-        clip_plain_kernel<2><<<nb, 128, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, st);
+        { clip_plain_kernel<2><<<nb, 128, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, st); count_launch(); }
     else
-        clip_plain_kernel<3><<<nb, 128, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, st);
+        { clip_plain_kernel<3><<<nb, 128, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, st); count_launch(); }
 }
 
 void launch_scatter_plain(int dim, const SubGrid& sg, const int32_t* E, int64_t p_begin, int64_t p_end,
@@ -174,9 +174,9 @@ void launch_scatter_plain(int dim, const SubGrid& sg, const int32_t* E, int64_t 
     if (n <= 0) return;
     unsigned nb = (unsigned)((n + 255) / 256);
     if (dim == 2)
-        scatter_plain_kernel<2><<<nb, 256, 0, s>>>(sg, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, B.ptr, B.col, B.val);
+        { scatter_plain_kernel<2><<<nb, 256, 0, s>>>(sg, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, B.ptr, B.col, B.val); count_launch(); }
     else
-        scatter_plain_kernel<3><<<nb, 256, 0, s>>>(sg, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, B.ptr, B.col, B.val);
+        { scatter_plain_kernel<3><<<nb, 256, 0, s>>>(sg, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, B.ptr, B.col, B.val); count_launch(); }
 }
 
 }  // namespace l2x

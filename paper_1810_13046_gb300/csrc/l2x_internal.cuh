@@ -67,9 +67,8 @@ struct CsrT {
     float* val32 = nullptr;
 };
 
-// Stream-ordered scratch allocation helpers (l2x_api.cu).
-cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
-void dev_free(void* p, cudaStream_t s);
+// Counts kernel launches of the library (l2x_api.cu).
+void count_launch();
 
 // ---------------------------------------------------------------- launchers
 // pairs (l2x_pairs.cu)

@@ -204,9 +204,9 @@ void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
     int64_t blocks = (m + threads - 1) / threads;
     if (blocks == 0) return;
     if (dim == 2)
-        elem_boxes_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, st);
+        { elem_boxes_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, st); count_launch(); }
     else
-        elem_boxes_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, st);
+        { elem_boxes_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, st); count_launch(); }
 }
 
 size_t scan_tmp_bytes(int64_t n) {
@@ -220,9 +220,9 @@ void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cuda
     int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb < 1) nb = 1;
     int64_t* partial = (int64_t*)tmp;
-    scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial);
-    scan_partials_kernel<<<1, kScanThreads, 0, s>>>(partial, nb);
-    scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial, out, nb);
+    { scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial); count_launch(); }
+    { scan_partials_kernel<<<1, kScanThreads, 0, s>>>(partial, nb); count_launch(); }
+    { scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial, out, nb); count_launch(); }
 }
 
 void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const ElemBox* boxes,
@@ -234,9 +234,9 @@ void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
     int64_t blocks = (total + threads - 1) / threads;
     if (blocks == 0) return;
     if (dim == 2)
-        emit_pairs_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell);
+        { emit_pairs_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell); count_launch(); }
     else
-        emit_pairs_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell);
+        { emit_pairs_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell); count_launch(); }
 }
 
 }  // namespace l2x

@@ -141,13 +141,15 @@ def test_force_transfer(name, mode, path, precision):
     oc = oracle_coupling(name)
     dt = np.float32 if mixed else np.float64
     F = w.force.astype(dt)
-    base = [np.full(n, 0.5, dtype=dt) for n in c.fluid_sizes()]
+    ref = oc.transfer_force(F.astype(np.float64), mode=mode, scale=scale)
+    # the call accumulates: start from a non-zero array of the result's magnitude
+    rng = np.random.default_rng(4)
+    base = [(0.5 * np.abs(r).max() * rng.random(r.shape[0])).astype(dt) for r in ref]
     f_f = [torch.from_numpy(b.copy()).cuda() for b in base]
     c.transfer_force([torch.from_numpy(np.ascontiguousarray(F[:, g])).cuda() for g in range(F.shape[1])], f_f)
-    ref = oc.transfer_force(F.astype(np.float64), mode=mode, scale=scale)
     tol = TOL_MIXED if mixed else TOL64
     for g in range(len(ref)):
-        got = f_f[g].cpu().numpy().astype(np.float64) - base[g]
+        got = f_f[g].cpu().numpy().astype(np.float64) - base[g].astype(np.float64)
         assert rel_l2(got, ref[g]) <= (tol if not mixed else 2 * tol)
 
 
