@@ -187,6 +187,36 @@ l2x_status l2x_set_timing(l2x_handle h, int32_t enable);
 /* Number of kernels this library has launched in this process (all handles). */
 int64_t l2x_kernel_launch_count(void);
 
+/* Jacobi-preconditioned CG that allocates no device memory.
+ *
+ * No counterpart in the paper: this is a service for callers that cannot call
+ * cudaMalloc (for example a process whose device memory is owned by an outer
+ * framework's memory pool, or a solver loop that must not add allocation calls).
+ * It solves A w_k = y_k, k < n_rhs, for a caller-supplied CSR matrix A (n x n,
+ * symmetric positive definite with a non-zero diagonal, such as M_s exported by
+ * l2x_export_csr): row_ptr (n+1, int64), cols (int32), vals (double), all device
+ * pointers; y and w are arrays of n_rhs device pointers to n doubles (w written).
+ * Stops when ||r_k|| <= rtol ||y_k|| for every k or after max_iter iterations.
+ * *iters and *residual (host pointers, may be NULL) receive the iterations and
+ * the largest relative residual.
+ *
+ * Its work vectors live in one fixed device array of L2X_NOALLOC_MAX_DOUBLES
+ * doubles (about 6.3 MB) that every GPU which loads the library holds until the
+ * process exits; n and n * n_rhs must not exceed L2X_NOALLOC_MAX_ENTRIES, larger
+ * problems return L2X_ECAPACITY.  The first call on a device looks up that array's
+ * device address (once per device, with that device current), so make the first
+ * call on each device before any stream capture.  All calls share the array and
+ * the kernel initialises everything it reads; two calls whose kernels overlap on
+ * the GPU (different streams or threads) race on it and give wrong results.
+ * The call synchronises `stream` to read the solver status.
+ * Errors: EINVAL, ECAPACITY, ENOTCONVERGED, ECUDA (l2x_noalloc_last_error()). */
+#define L2X_NOALLOC_MAX_ENTRIES 131072
+#define L2X_NOALLOC_MAX_DOUBLES (6 * L2X_NOALLOC_MAX_ENTRIES + 1024 * 9 + 16)
+l2x_status l2x_solve_mass_noalloc(int64_t n, const int64_t* row_ptr, const int32_t* cols, const double* vals,
+                                  int32_t n_rhs, const double* const* y, double* const* w, double rtol,
+                                  int32_t max_iter, void* stream, int32_t* iters, double* residual);
+const char* l2x_noalloc_last_error(void);
+
 /* Releases every device allocation of the handle (stream-ordered on the stream
  * of the last call).  NULL is accepted. */
 l2x_status l2x_destroy(l2x_handle h);
