@@ -61,6 +61,8 @@ struct l2x_coupling {
     void* scan_tmp = nullptr;
     size_t scan_tmp_cap = 0;
     int64_t* row_count = nullptr;    // n_nodes + 1
+    int32_t* tcursor = nullptr;      // fill cursors of the B^T rows
+    int64_t tcursor_cap = 0;
     void* pcg_ws = nullptr;
     void* vec_tmp = nullptr;         // n_grids * n_nodes doubles
     DevStatus* st = nullptr;
@@ -379,15 +381,16 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
                 h->T_cap[g] = c;
             }
             L2X_TRY(ensure_scan(h, rows));
-            int32_t* tcursor = nullptr;
-            L2X_TRY(dalloc(&tcursor, rows));
+            if (rows > h->tcursor_cap || !h->tcursor) {
+                dfree(h->tcursor);
+                L2X_TRY(dalloc(&h->tcursor, rows + rows / 4 + 16));
+                h->tcursor_cap = rows + rows / 4 + 16;
+            }
             launch_transpose_count(B, h->sg[g], T, T.ptr, s);
             launch_scan_i64(T.ptr, T.ptr, rows, h->scan_tmp, s);
-            launch_transpose_fill(B, h->sg[g], T, tcursor, s);
+            launch_transpose_fill(B, h->sg[g], T, h->tcursor, s);
             launch_transpose_sort(T, s);
             if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, nnz, s);
-            L2X_CUDA(cudaStreamSynchronize(s));
-            cudaFree(tcursor);
         }
     }
     // mass matrix values
@@ -476,6 +479,7 @@ l2x_status l2x_destroy(l2x_handle h) {
     dfree(h->M.ptr); dfree(h->M.col); dfree(h->M.val); dfree(h->M.val32); dfree(h->M_dinv); dfree(h->M_dinv32);
     if (h->scan_tmp) cudaFree(h->scan_tmp);
     dfree(h->row_count);
+    dfree(h->tcursor);
     if (h->pcg_ws) cudaFree(h->pcg_ws);
     if (h->vec_tmp) cudaFree(h->vec_tmp);
     dfree(h->st);

@@ -6,6 +6,7 @@
 
 #include <cmath>
 
+#include "l2x_fp.cuh"
 #include "l2x_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -115,6 +116,7 @@ struct DotAcc {
     double s = 0.0;
     __device__ __forceinline__ void add(TV a, TV b) { s = fma((double)a, (double)b, s); }
     __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ DF df(int e) const { return df_from_double(ldexp_d_int(s, e)); }
 };
 template <>
 struct DotAcc<float> {
@@ -129,6 +131,7 @@ struct DotAcc<float> {
         lo = __fadd_rn(lo, __fadd_rn(err, e));
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ DF df(int e) const { return df_scale(DF{hi, lo}, e); }
 };
 
 template <typename TV>
@@ -152,6 +155,31 @@ struct PcgArgs {
     DevStatus* st;
 };
 
+// Block-wide sums of N values at once (result valid in thread 0 and, through
+// `out`, in every thread after the final barrier).
+template <int N>
+__device__ __forceinline__ void block_sum_n(double (&v)[N], double* sh, double* out) {
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < N; ++j) sh[j * 32 + wid] = v[j];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            double t = lane < nw ? sh[j * 32 + lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) out[j] = t;
+        }
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -168,95 +196,270 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // Chronopoulos-Gear form of Jacobi-PCG: one global reduction and one vector
 // exchange per iteration (two grid barriers), all right-hand sides together.
-template <typename TV>
-__global__ void __launch_bounds__(kPcgThreads) pcg_fused_kernel(PcgArgs<TV> A) {
+// Rows are split evenly over small blocks (2 warps) so that every SM takes part
+// even for small systems; the product w = M u uses kRowLanes lanes per row.
+// GB300 runs FP64 instructions on a narrow unit, so the per-iteration
+// reductions run in double-float single-precision arithmetic (about 48 bits)
+// and the scalars alpha, beta of right-hand side k are formed by thread k only.
+constexpr int kRowLanes = 4;
+constexpr int kPcgBlock = 256;
+
+template <typename TV, int NR>
+__global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ double sh[32];
-    __shared__ double tot[3 * kMaxRhs];
-    const int nr = A.nrhs;
+    constexpr int NV = 3 * NR;                  // gamma, delta, rho per right-hand side
+    constexpr int NW = kPcgBlock / 32;
+    __shared__ DF sh[NV][NW];
+    __shared__ double s_red[NV * 32];
+    __shared__ double s_tot[NV];
+    __shared__ double s_alpha[NR], s_beta[NR];
+    __shared__ int s_conv[NR], s_all;
+    __shared__ int s_exp[NV];
     const int64_t n = A.n;
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = min(n, (int64_t)blockIdx.x * per), r1 = min(n, r0 + per);
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const int glane = threadIdx.x % kRowLanes;
+    const int grow = threadIdx.x / kRowLanes;
+    constexpr int kRowsPerPass = kPcgBlock / kRowLanes;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    DF* partial = reinterpret_cast<DF*>(A.partial);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += kPcgBlock) {
         const TV di = A.dinv[i];
-        for (int k = 0; k < nr; ++k) {
-            TV yi = A.y[k][i];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const TV yi = A.y[k][i];
             A.x[k][i] = TV(0);
             A.r[k * n + i] = yi;
             A.u[k * n + i] = di * yi;
         }
     }
+    // per-rhs state kept by thread k of every block (identical in all blocks)
+    double alpha = 0.0, gamma_old = 0.0, rho0 = 0.0, rho = 0.0;
+    if (threadIdx.x < NR) s_conv[threadIdx.x] = 0;
     grid.sync();
-    double alpha[kMaxRhs], gamma_old[kMaxRhs], rho0[kMaxRhs], rho[kMaxRhs];
-    bool conv[kMaxRhs];
-    for (int k = 0; k < kMaxRhs; ++k) { alpha[k] = 0.0; gamma_old[k] = 0.0; rho0[k] = 0.0; rho[k] = 0.0; conv[k] = true; }
-    int it = 0;
-    bool all_conv = false;
+    int it = 0, it_local = 0, restarts = 0;
     for (;;) {
-        DotAcc<TV> dg[kMaxRhs], dd[kMaxRhs], dr[kMaxRhs];
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            const int64_t lo = A.ptr[i], hi = A.ptr[i + 1];
-            TV acc[kMaxRhs];
-            for (int k = 0; k < kMaxRhs; ++k) acc[k] = TV(0);
-            for (int64_t q = lo; q < hi; ++q) {
-                const TV v = A.val[q];
-                const int32_t j = A.col[q];
-                for (int k = 0; k < nr; ++k) acc[k] += v * A.u[k * n + j];
+        DotAcc<TV> dg[NR], dd[NR], dr[NR];
+        for (int64_t base = r0; base < r1; base += kRowsPerPass) {
+            const int64_t i = base + grow;
+            const bool live = i < r1;
+            TV acc[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) acc[k] = TV(0);
+            if (live) {
+                const int64_t hi = A.ptr[i + 1];
+                for (int64_t q = A.ptr[i] + glane; q < hi; q += kRowLanes) {
+                    const TV v = A.val[q];
+                    const int32_t j = A.col[q];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc[k] += v * A.u[k * n + j];
+                }
             }
-            for (int k = 0; k < nr; ++k) {
-                const TV ri = A.r[k * n + i], ui = A.u[k * n + i];
-                A.w[k * n + i] = acc[k];
-                dg[k].add(ri, ui);
-                dd[k].add(acc[k], ui);
-                dr[k].add(ri, ri);
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+#pragma unroll
+                for (int o = kRowLanes / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            }
+            if (live && glane == 0) {
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const TV ri = A.r[k * n + i], ui = A.u[k * n + i];
+                    A.w[k * n + i] = acc[k];
+                    dg[k].add(ri, ui);
+                    dd[k].add(acc[k], ui);
+                    dr[k].add(ri, ri);
+                }
             }
         }
-        for (int k = 0; k < nr; ++k) {
-            double a = block_sum(dg[k].value(), sh);
-            double b = block_sum(dd[k].value(), sh);
-            double c = block_sum(dr[k].value(), sh);
-            if (threadIdx.x == 0) {
-                A.partial[(int64_t)blockIdx.x * 3 * kMaxRhs + 3 * k + 0] = a;
-                A.partial[(int64_t)blockIdx.x * 3 * kMaxRhs + 3 * k + 1] = b;
-                A.partial[(int64_t)blockIdx.x * 3 * kMaxRhs + 3 * k + 2] = c;
+        // Reduction of (gamma, delta, rho) per right-hand side.  After a (re)start
+        // the sums are formed once in FP64, which also fixes a power-of-two shift
+        // per sum (about 2^100 at that point); later iterations sum the shifted
+        // values in double-float single precision, whose exponent range then
+        // covers the decrease by rtol^2.
+        const bool exact = it_local == 0;
+        {
+            if (exact) {
+                double v[NV];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    v[3 * k + 0] = dg[k].value();
+                    v[3 * k + 1] = dd[k].value();
+                    v[3 * k + 2] = dr[k].value();
+                }
+                block_sum_n<NV>(v, s_red, s_tot);
+                if (threadIdx.x < NV) A.partial[(int64_t)blockIdx.x * NV + threadIdx.x] = s_tot[threadIdx.x];
+            } else {
+                DF v[NV];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    v[3 * k + 0] = dg[k].df(s_exp[3 * k + 0]);
+                    v[3 * k + 1] = dd[k].df(s_exp[3 * k + 1]);
+                    v[3 * k + 2] = dr[k].df(s_exp[3 * k + 2]);
+                }
+#pragma unroll
+                for (int j = 0; j < NV; ++j)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v[j] = df_add(v[j], df_shfl_xor(v[j], o));
+                __syncthreads();
+                if (lane == 0)
+#pragma unroll
+                    for (int j = 0; j < NV; ++j) sh[j][wid] = v[j];
+                __syncthreads();
+                if (threadIdx.x < NV) {
+                    DF t = sh[threadIdx.x][0];
+#pragma unroll
+                    for (int ww = 1; ww < NW; ++ww) t = df_add(t, sh[threadIdx.x][ww]);
+                    partial[(int64_t)blockIdx.x * NV + threadIdx.x] = t;
+                }
             }
         }
         grid.sync();
-        for (int j = 0; j < 3 * nr; ++j) {
-            double v = 0.0;
-            for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += A.partial[(int64_t)b * 3 * kMaxRhs + j];
-            v = block_sum(v, sh);
-            if (threadIdx.x == 0) tot[j] = v;
-        }
-        __syncthreads();
-        double beta[kMaxRhs];
-        all_conv = true;
-        for (int k = 0; k < nr; ++k) {
-            const double gam = tot[3 * k], del = tot[3 * k + 1];
-            rho[k] = tot[3 * k + 2];
-            if (it == 0) rho0[k] = rho[k];
-            conv[k] = rho[k] <= A.rtol * A.rtol * rho0[k];
-            all_conv = all_conv && conv[k];
-            beta[k] = 0.0;
-            if (!conv[k]) {
-                if (it == 0) {
-                    alpha[k] = gam / del;
-                } else {
-                    beta[k] = gam / gamma_old[k];
-                    alpha[k] = gam / (del - beta[k] * gam / alpha[k]);
+        // every block sums the partials of all blocks in the same order
+        {
+            if (exact) {
+                double v[NV];
+#pragma unroll
+                for (int j = 0; j < NV; ++j) v[j] = 0.0;
+                for (int b = threadIdx.x; b < (int)gridDim.x; b += kPcgBlock) {
+#pragma unroll
+                    for (int j = 0; j < NV; ++j) v[j] += A.partial[(int64_t)b * NV + j];
                 }
-                gamma_old[k] = gam;
+                block_sum_n<NV>(v, s_red, s_tot);
+                if (threadIdx.x < NV) {
+                    const double t = s_tot[threadIdx.x];
+                    s_exp[threadIdx.x] = t > 0.0 ? 100 - ilogb_int(t) : 0;
+                }
+                __syncthreads();
+            } else {
+                DF v[NV];
+#pragma unroll
+                for (int j = 0; j < NV; ++j) v[j] = DF{0.f, 0.f};
+                for (int b = threadIdx.x; b < (int)gridDim.x; b += kPcgBlock) {
+#pragma unroll
+                    for (int j = 0; j < NV; ++j) v[j] = df_add(v[j], partial[(int64_t)b * NV + j]);
+                }
+#pragma unroll
+                for (int j = 0; j < NV; ++j)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v[j] = df_add(v[j], df_shfl_xor(v[j], o));
+                __syncthreads();
+                if (lane == 0)
+#pragma unroll
+                    for (int j = 0; j < NV; ++j) sh[j][wid] = v[j];
+                __syncthreads();
+                if (threadIdx.x < NV) {
+                    DF t = sh[threadIdx.x][0];
+#pragma unroll
+                    for (int ww = 1; ww < NW; ++ww) t = df_add(t, sh[threadIdx.x][ww]);
+                    s_tot[threadIdx.x] = ldexp_d_int(df_to_double(t), -s_exp[threadIdx.x]);
+                }
+                __syncthreads();
             }
+            if (threadIdx.x < NR) {
+                const int k = threadIdx.x;
+                const double gam = s_tot[3 * k], del = s_tot[3 * k + 1];
+                rho = s_tot[3 * k + 2];
+                if (it == 0) rho0 = rho;
+                const bool conv = rho <= A.rtol * A.rtol * rho0;
+                double beta = 0.0;
+                if (!conv) {
+                    if (it_local == 0) {
+                        alpha = div_nr(gam, del);
+                    } else {
+                        beta = div_nr(gam, gamma_old);
+                        alpha = div_nr(gam, del - beta * div_nr(gam, alpha));
+                    }
+                    gamma_old = gam;
+                }
+                s_alpha[k] = alpha;
+                s_beta[k] = beta;
+                s_conv[k] = conv ? 1 : 0;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int all = 1;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) all &= s_conv[k];
+                s_all = all;
+            }
+            __syncthreads();
         }
-        if (all_conv || it >= A.max_iter) break;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        if (s_all && sizeof(TV) == 8 && restarts < 2) {
+            // FP64: check the true residual y - M x and restart from it if the
+            // recurrence has drifted (Chronopoulos-Gear keeps an extra recurrence)
+            grid.sync();
+            DotAcc<TV> dt[NR];
+            for (int64_t i = r0 + threadIdx.x; i < r1; i += kPcgBlock) {
+                const int64_t hi = A.ptr[i + 1];
+                TV acc[NR];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) acc[k] = TV(0);
+                for (int64_t q = A.ptr[i]; q < hi; ++q) {
+                    const TV v = A.val[q];
+                    const int32_t j = A.col[q];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc[k] += v * A.x[k][j];
+                }
+                const TV di = A.dinv[i];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const TV rt = A.y[k][i] - acc[k];
+                    A.r[k * n + i] = rt;
+                    A.u[k * n + i] = di * rt;
+                    dt[k].add(rt, rt);
+                }
+            }
+            {
+                double v[NV];
+#pragma unroll
+                for (int j = 0; j < NV; ++j) v[j] = 0.0;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) v[k] = dt[k].value();
+                block_sum_n<NV>(v, s_red, s_tot);
+                if (threadIdx.x < NV) A.partial[(int64_t)blockIdx.x * NV + threadIdx.x] = s_tot[threadIdx.x];
+            }
+            grid.sync();
+            {
+                double v[NV];
+#pragma unroll
+                for (int j = 0; j < NV; ++j) v[j] = 0.0;
+                for (int b = threadIdx.x; b < (int)gridDim.x; b += kPcgBlock) {
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) v[k] += A.partial[(int64_t)b * NV + k];
+                }
+                block_sum_n<NV>(v, s_red, s_tot);
+                if (threadIdx.x < NR) {
+                    const double rt = s_tot[threadIdx.x];
+                    const bool ok = rt <= A.rtol * A.rtol * rho0;
+                    s_conv[threadIdx.x] = ok ? 1 : 0;
+                    if (!ok) rho = rt;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int all = 1;
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) all &= s_conv[k];
+                    s_all = all;
+                }
+                __syncthreads();
+            }
+            if (s_all) break;
+            // restart the recurrences from the true residual (r, u already written)
+            ++restarts;
+            it_local = 0;
+            grid.sync();
+            continue;
+        }
+        if (s_all || it >= A.max_iter) break;
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += kPcgBlock) {
             const TV di = A.dinv[i];
-            for (int k = 0; k < nr; ++k) {
-                if (conv[k]) continue;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                if (s_conv[k]) continue;
                 const int64_t o = k * n + i;
-                const TV b = (TV)beta[k], a = (TV)alpha[k];
-                const TV pn = it == 0 ? A.u[o] : A.u[o] + b * A.p[o];
-                const TV sn = it == 0 ? A.w[o] : A.w[o] + b * A.s[o];
+                const TV b = (TV)s_beta[k], a = (TV)s_alpha[k];
+                const TV pn = it_local == 0 ? A.u[o] : A.u[o] + b * A.p[o];
+                const TV sn = it_local == 0 ? A.w[o] : A.w[o] + b * A.s[o];
                 A.p[o] = pn;
                 A.s[o] = sn;
                 A.x[k][i] += a * pn;
@@ -267,13 +470,17 @@ __global__ void __launch_bounds__(kPcgThreads) pcg_fused_kernel(PcgArgs<TV> A) {
         }
         grid.sync();
         ++it;
+        ++it_local;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double worst = 0.0;
-        for (int k = 0; k < nr; ++k) worst = fmax(worst, rho0[k] > 0.0 ? sqrt(rho[k] / rho0[k]) : 0.0);
-        A.st->cg_iters = it;
-        A.st->cg_residual = worst;
-        if (!all_conv) atomicOr(&A.st->flags, FLAG_NOTCONVERGED);
+    if (blockIdx.x == 0) {
+        // residual of every rhs: thread k holds rho, rho0
+        double rel = threadIdx.x < NR && rho0 > 0.0 ? sqrt(rho / rho0) : 0.0;
+        for (int o = 16; o > 0; o >>= 1) rel = fmax(rel, __shfl_xor_sync(0xffffffffu, rel, o));
+        if (threadIdx.x == 0) {
+            A.st->cg_iters = it;
+            A.st->cg_residual = rel;
+            if (!s_all) atomicOr(&A.st->flags, FLAG_NOTCONVERGED);
+        }
     }
 }
 
@@ -410,16 +617,18 @@ __global__ void store_f32_kernel(int64_t n, int nr, const double* x64, float* w0
     for (int k = 0; k < nr; ++k) w[k][i] = (float)x64[k * n + i];
 }
 
-template <typename TV>
+template <typename TV, int NR>
 int pcg_blocks_for(int64_t n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_fused_kernel<TV>, kPcgThreads, 0);
-    if (per_sm < 1) per_sm = 1;
-    int64_t want = (n + 2 * kPcgThreads - 1) / (2 * kPcgThreads);  // >= 2 rows per thread
+    static int sms = 0, per_sm = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_fused_kernel<TV, NR>, kPcgBlock, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int64_t rows_per_block = kPcgBlock / kRowLanes;  // one pass of the product per block
+    int64_t want = (n + rows_per_block - 1) / rows_per_block;
     int64_t cap = (int64_t)sms * per_sm;
     int64_t b = want < cap ? want : cap;
     if (b > (int64_t)sms * 8) b = (int64_t)sms * 8;  // partial-sum buffer holds sms * 8 blocks
@@ -451,10 +660,19 @@ cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val,
     A.rtol = rtol;
     A.max_iter = max_iter;
     A.st = st;
-    int blocks = pcg_blocks_for<TV>(n);
     void* args[] = {&A};
     count_launch();
-    return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV>, dim3(blocks), dim3(kPcgThreads), args, 0, s);
+    switch (nr) {
+        case 1:
+            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 1>, dim3(pcg_blocks_for<TV, 1>(n)),
+                                               dim3(kPcgBlock), args, 0, s);
+        case 2:
+            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 2>, dim3(pcg_blocks_for<TV, 2>(n)),
+                                               dim3(kPcgBlock), args, 0, s);
+        default:
+            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 3>, dim3(pcg_blocks_for<TV, 3>(n)),
+                                               dim3(kPcgBlock), args, 0, s);
+    }
 }
 
 }  // namespace
@@ -641,7 +859,7 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
     float* wf[3] = {(float*)w[0], nr > 1 ? (float*)w[1] : nullptr, nr > 2 ? (float*)w[2] : nullptr};
     unsigned nb = nblk(n, 256);
     unsigned nbd = nb < 1024 ? nb : 1024;
-    const double inner = rtol > 1e-6 ? rtol : 1e-6;
+    const double inner = rtol > 1e-7 ? rtol : 1e-7;
     cudaMemsetAsync(norms, 0, 8 * 8, s);
     { norm2_f32_kernel<<<nbd, 256, 0, s>>>(n, nr, yf[0], yf[1], yf[2], norms + 4); count_launch(); }
     int total_it = 0;

@@ -10,7 +10,7 @@ namespace l2x {
 namespace {
 
 constexpr int kRowWarps = 4;
-constexpr int kRowMax = 1024;   // dense row box held in shared memory per warp
+constexpr int kRowAdj = 64;     // incident elements staged in shared memory per warp
 constexpr int kMassMaxCand = 256;
 
 __global__ void adj_count_kernel(int NA, int64_t total, const int32_t* __restrict__ E, int64_t* cnt) {
@@ -50,11 +50,15 @@ __global__ void segment_sort_kernel(int64_t n, const int64_t* __restrict__ ptr, 
     }
 }
 
-// One warp per solid node (row of B_g).  The row's columns are the nodes of the
-// union of the candidate boxes of the incident elements; the warp accumulates
-// the rows of the incident elements' pair blocks into a dense box in shared
-// memory (in a fixed order: adjacency order, pair order, then slot order, so
-// the sums are reproducible) and emits the touched columns in ascending order.
+// One warp per solid node i (row of B_g).  The row's columns lie in the union of
+// the node boxes of the incident elements' candidate cells.  Every lane owns box
+// nodes j and gathers, in a fixed order (adjacency order, then the element's
+// cells around j in z, y, x order), the entries block[a][b] of the pairs
+// (element with local vertex a, cell with corner b at j) whose intersection
+// volume is positive; sums stay in registers, so the result is reproducible and
+// needs no atomics.  Touched columns are emitted in ascending order.
+// pass 0: row_count[i] = number of touched columns; pass 1: columns and values;
+// pass 2: columns only, values zeroed (the plain path adds them with atomics).
 template <int D>
 __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
     int pass, SubGrid sg, int64_t n_nodes, const int64_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
@@ -62,23 +66,31 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
     int64_t slot_stride, const double* __restrict__ vols, int64_t* __restrict__ row_count,
     const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols, double* __restrict__ vals, DevStatus* st) {
     constexpr int NB = 1 << D;
-    constexpr int SLOTS = 32 / NB;
-    __shared__ double s_acc[kRowWarps][kRowMax];
-    __shared__ unsigned char s_flag[kRowWarps][kRowMax];
+    __shared__ ElemBox s_box[kRowWarps][kRowAdj];
+    __shared__ int64_t s_off[kRowWarps][kRowAdj];
+    __shared__ int32_t s_ea[kRowWarps][kRowAdj];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i = blockIdx.x * (int64_t)kRowWarps + w;
     if (i >= n_nodes) return;
     const int64_t a0 = adj_ptr[i], a1 = adj_ptr[i + 1];
+    const bool staged = a1 - a0 <= kRowAdj;
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
     for (int64_t t = a0 + lane; t < a1; t += 32) {
-        int32_t e = adj[t] >> 2;
-        ElemBox b = boxes[e];
+        const int32_t ea = adj[t];
+        const int32_t e = ea >> 2;
+        const ElemBox b = boxes[e];
+        if (staged) {
+            s_box[w][t - a0] = b;
+            s_off[w][t - a0] = offsets[e];
+            s_ea[w][t - a0] = ea;
+        }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             lo[k] = min(lo[k], b.lo[k]);
             hi[k] = max(hi[k], b.lo[k] + box_ext(b, k));
         }
     }
+    __syncwarp();
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -86,84 +98,61 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
             hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
         }
     }
+    if (D == 2) {
+        lo[2] = 0;
+        hi[2] = 0;
+    }
     int64_t cnt = 0;
     const int64_t out0 = pass >= 1 ? row_ptr[i] : 0;
-    const bool too_wide = a0 < a1 && hi[0] - lo[0] + 1 > kRowMax;
-    if (too_wide && lane == 0) atomicOr(&st->flags, FLAG_CAPACITY);
-    if (a0 < a1 && !too_wide) {
-        const int nx = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1;
-        const int nz = D == 3 ? hi[2] - lo[2] + 1 : 1;
-        if (D == 2) { lo[2] = 0; }
-        // tiles: whole (x,y) planes over a z-range, or single planes over a y-range
-        const int plane = nx * ny;
-        const int tz = plane <= kRowMax ? max(1, kRowMax / plane) : 1;
-        const int ty = plane <= kRowMax ? ny : max(1, kRowMax / nx);
-        for (int zb = 0; zb < nz; zb += tz) {
-            const int ze = min(nz, zb + tz);
-            for (int yb = 0; yb < ny; yb += ty) {
-                const int ye = min(ny, yb + ty);
-                const int tyn = ye - yb;
-                const int tsz = nx * tyn * (ze - zb);
-                for (int t = lane; t < tsz; t += 32) {
-                    s_acc[w][t] = 0.0;
-                    s_flag[w][t] = 0;
-                }
-                __syncwarp();
+    if (a0 < a1) {
+        const int nx = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1, nz = hi[2] - lo[2] + 1;
+        const int64_t total = (int64_t)nx * ny * nz;
+        for (int64_t base = 0; base < total; base += 32) {
+            const int64_t idx = base + lane;
+            bool touched = false;
+            double acc = 0.0;
+            int jx = 0, jy = 0, jz = 0;
+            if (idx < total) {
+                jx = lo[0] + (int)(idx % nx);
+                const int64_t r = idx / nx;
+                jy = lo[1] + (int)(r % ny);
+                jz = lo[2] + (int)(r / ny);
                 for (int64_t t = a0; t < a1; ++t) {
-                    const int32_t ea = adj[t];
-                    const int32_t e = ea >> 2;
+                    const int32_t ea = staged ? s_ea[w][t - a0] : adj[t];
+                    const ElemBox b = staged ? s_box[w][t - a0] : boxes[ea >> 2];
+                    const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = box_ext(b, 2);
+                    // cells c of the element's box with c_k in {j_k - 1, j_k}
+                    const int cx0 = max(jx - 1, b.lo[0]), cx1 = min(jx, b.lo[0] + ex - 1);
+                    const int cy0 = max(jy - 1, b.lo[1]), cy1 = min(jy, b.lo[1] + ey - 1);
+                    const int cz0 = D == 3 ? max(jz - 1, b.lo[2]) : 0, cz1 = D == 3 ? min(jz, b.lo[2] + ez - 1) : 0;
+                    if (cx0 > cx1 || cy0 > cy1 || cz0 > cz1) continue;
+                    const int64_t q0 = staged ? s_off[w][t - a0] : offsets[ea >> 2];
                     const int a = ea & 3;
-                    const ElemBox b = boxes[e];
-                    const int ex = box_ext(b, 0), ey = box_ext(b, 1);
-                    const int npairs = ex * ey * box_ext(b, 2);
-                    const int64_t q0 = offsets[e];
-                    for (int base = 0; base < npairs; base += SLOTS) {
-                        const int slot = lane / NB, cb = lane % NB;
-                        const int k = base + slot;
-                        int idx = -1;
-                        double v = 0.0;
-                        if (k < npairs) {
-                            const int64_t q = q0 + k;
-                            if (vols[q] > 0.0) {
-                                const int kx = k % ex, ky = (k / ex) % ey, kz = k / (ex * ey);
-                                const int bx = b.lo[0] + kx + (cb & 1) - lo[0];
-                                const int by = b.lo[1] + ky + ((cb >> 1) & 1) - lo[1];
-                                const int bz = D == 3 ? b.lo[2] + kz + ((cb >> 2) & 1) - lo[2] : 0;
-                                if (by >= yb && by < ye && bz >= zb && bz < ze) {
-                                    idx = bx + nx * ((by - yb) + tyn * (bz - zb));
-                                    if (pass == 1) v = blocks[(int64_t)(a * NB + cb) * slot_stride + q];
+                    for (int cz = cz0; cz <= cz1; ++cz)
+                        for (int cy = cy0; cy <= cy1; ++cy)
+                            for (int cx = cx0; cx <= cx1; ++cx) {
+                                const int64_t q = q0 + (cx - b.lo[0]) + (int64_t)ex * ((cy - b.lo[1]) + (int64_t)ey * (cz - b.lo[2]));
+                                if (__double_as_longlong(vols[q]) > 0) {  // volume > 0
+                                    touched = true;
+                                    if (pass == 1) {
+                                        const int cb = (jx - cx) | ((jy - cy) << 1) | (D == 3 ? (jz - cz) << 2 : 0);
+                                        acc += blocks[(int64_t)(a * NB + cb) * slot_stride + q];
+                                    }
                                 }
                             }
-                        }
-                        for (int st = 0; st < SLOTS; ++st) {
-                            if (slot == st && idx >= 0) {
-                                s_acc[w][idx] += v;
-                                s_flag[w][idx] = 1;
-                            }
-                            __syncwarp();
-                        }
-                    }
                 }
-                for (int base = 0; base < tsz; base += 32) {
-                    const int idx = base + lane;
-                    const bool f = idx < tsz && s_flag[w][idx];
-                    const unsigned bal = __ballot_sync(0xffffffffu, f);
-                    if (pass >= 1 && f) {
-                        const int pos = __popc(bal & ((1u << lane) - 1u));
-                        const int bx = idx % nx;
-                        const int r = idx / nx;
-                        const int by = r % tyn + yb, bz = r / tyn + zb;
-                        const int32_t node = (lo[0] + bx) + sg.nnode[0] * ((lo[1] + by) + sg.nnode[1] * (lo[2] + bz));
-                        cols[out0 + cnt + pos] = node;
-                        vals[out0 + cnt + pos] = pass == 1 ? s_acc[w][idx] : 0.0;
-                    }
-                    cnt += __popc(bal);
-                }
-                __syncwarp();
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, touched);
+            if (pass >= 1 && touched) {
+                const int pos = __popc(bal & ((1u << lane) - 1u));
+                cols[out0 + cnt + pos] = jx + sg.nnode[0] * (jy + sg.nnode[1] * jz);
+                vals[out0 + cnt + pos] = pass == 1 ? acc : 0.0;
+            }
+            cnt += __popc(bal);
         }
     }
     if (pass == 0 && lane == 0) row_count[i] = cnt;
+    (void)st;
 }
 
 template <int D>
@@ -243,23 +232,73 @@ __device__ __forceinline__ int64_t tbox_index(const SubGrid& sg, const CsrT& T, 
     return (x - T.lo[0]) + (int64_t)T.n[0] * ((y - T.lo[1]) + (int64_t)T.n[1] * (z - T.lo[2]));
 }
 
+// Warp per row of B_g: count the entries of every B_g^T row.
 __global__ void transpose_count_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                        SubGrid sg, CsrT T, int64_t* cnt) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n_rows) return;
-    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q)
+    for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
         atomicAdd((unsigned long long*)(cnt + tbox_index(sg, T, col[q])), 1ull);
 }
 
+// Warp per row of B_g: scatter (row, value) into the B_g^T rows (order fixed later).
 __global__ void transpose_fill_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                       const double* __restrict__ val, SubGrid sg, CsrT T, int32_t* cursor) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= n_rows) return;
-    for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
-        int64_t r = tbox_index(sg, T, col[q]);
-        int64_t pos = T.ptr[r] + atomicAdd(cursor + r, 1);
+    for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32) {
+        const int64_t r = tbox_index(sg, T, col[q]);
+        const int64_t pos = T.ptr[r] + atomicAdd(cursor + r, 1);
         T.col[pos] = (int32_t)i;
         T.val[pos] = val[q];
+    }
+}
+
+// Warp per B_g^T row: the keys (solid nodes) of a row are distinct, so every
+// entry's final position is its rank, counted against the row staged in shared
+// memory.  Rows longer than the staging area are sorted in place by one lane.
+constexpr int kSortWarps = 4;
+constexpr int kSortMax = 512;
+
+__global__ void __launch_bounds__(kSortWarps * 32) transpose_sort_kernel(int64_t n, const int64_t* __restrict__ ptr,
+                                                                        int32_t* key, double* val) {
+    __shared__ int32_t sk[kSortWarps][kSortMax];
+    __shared__ double sv[kSortWarps][kSortMax];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = blockIdx.x * (int64_t)kSortWarps + w;
+    if (i >= n) return;
+    const int64_t lo = ptr[i], hi = ptr[i + 1];
+    const int len = (int)(hi - lo);
+    if (len <= 1) return;
+    if (len <= kSortMax) {
+        for (int a = lane; a < len; a += 32) {
+            sk[w][a] = key[lo + a];
+            sv[w][a] = val[lo + a];
+        }
+        __syncwarp();
+        for (int a = lane; a < len; a += 32) {
+            const int32_t k = sk[w][a];
+            int rank = 0;
+            for (int b = 0; b < len; ++b) rank += sk[w][b] < k;
+            key[lo + rank] = k;
+            val[lo + rank] = sv[w][a];
+        }
+        return;
+    }
+    if (lane != 0) return;
+    for (int64_t a = lo + 1; a < hi; ++a) {
+        const int32_t kk = key[a];
+        const double vv = val[a];
+        int64_t b = a - 1;
+        while (b >= lo && key[b] > kk) {
+            key[b + 1] = key[b];
+            val[b + 1] = val[b];
+            --b;
+        }
+        key[b + 1] = kk;
+        val[b + 1] = vv;
     }
 }
 
@@ -320,17 +359,17 @@ void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_
 
 void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, cudaStream_t s) {
     cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (T.n_rows + 1), s);
-    if (B.n_rows > 0) { transpose_count_kernel<<<nblk(B.n_rows, 128), 128, 0, s>>>(B.n_rows, B.ptr, B.col, sg, T, cnt); count_launch(); }
+    if (B.n_rows > 0) { transpose_count_kernel<<<nblk(B.n_rows * 32, 256), 256, 0, s>>>(B.n_rows, B.ptr, B.col, sg, T, cnt); count_launch(); }
 }
 
 void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, cudaStream_t s) {
     cudaMemsetAsync(cursor, 0, sizeof(int32_t) * T.n_rows, s);
     if (B.n_rows > 0)
-        { transpose_fill_kernel<<<nblk(B.n_rows, 128), 128, 0, s>>>(B.n_rows, B.ptr, B.col, B.val, sg, T, cursor); count_launch(); }
+        { transpose_fill_kernel<<<nblk(B.n_rows * 32, 256), 256, 0, s>>>(B.n_rows, B.ptr, B.col, B.val, sg, T, cursor); count_launch(); }
 }
 
 void launch_transpose_sort(const CsrT& T, cudaStream_t s) {
-    if (T.n_rows > 0) { segment_sort_kernel<double><<<nblk(T.n_rows, 128), 128, 0, s>>>(T.n_rows, T.ptr, T.col, T.val); count_launch(); }
+    if (T.n_rows > 0) { transpose_sort_kernel<<<nblk(T.n_rows, kSortWarps), kSortWarps * 32, 0, s>>>(T.n_rows, T.ptr, T.col, T.val); count_launch(); }
 }
 
 void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {

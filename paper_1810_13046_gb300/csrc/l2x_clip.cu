@@ -18,9 +18,10 @@ __device__ __forceinline__ void cell_lower(const SubGrid& sg, int dim, int32_t c
     for (int k = 0; k < dim; ++k) clo[k] = __dadd_rn(sg.origin[k], __dmul_rn((double)ci[k], sg.h[k]));
 }
 
-// Fused: one thread per pair; the block stages the vertex coordinates of the
-// (consecutive) elements of its 128 pairs in shared memory once.  Blocks are
-// written structure-of-arrays so that every store instruction is coalesced.
+// Fused: one thread per pair; the block stages the vertex coordinates and the
+// barycentric gradients of the (consecutive) elements of its 128 pairs in shared
+// memory once.  Blocks are written structure-of-arrays so that every store
+// instruction is coalesced.
 template <int D, typename R>
 __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(SubGrid sg, const double* __restrict__ X,
                                                                   const int32_t* __restrict__ E, int64_t p_begin,
@@ -30,15 +31,32 @@ __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(SubGrid sg, co
                                                                   double* __restrict__ vols, DevStatus* st) {
     constexpr int NA = D + 1, NB = 1 << D;
     __shared__ double sV[kClipThreads][NA][D];
+    __shared__ double sG[kClipThreads][NA][D];
+    __shared__ int sPos[kClipThreads];
     const int64_t p0 = p_begin + (int64_t)blockIdx.x * kClipThreads;
     const int64_t plast = min(p0 + kClipThreads - 1, p_end - 1);
     const int32_t e_first = pair_elem[p0];
     const int n_e = min(pair_elem[plast] - e_first + 1, kClipThreads);
-    for (int i = threadIdx.x; i < n_e * NA; i += kClipThreads) {
-        int le = i / NA, a = i - le * NA;
-        int32_t v = __ldg(E + (int64_t)(e_first + le) * NA + a);
+    if (threadIdx.x < n_e) {
+        const int le = threadIdx.x;
+        double Xe[NA][D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) sV[le][a][k] = __ldg(X + (int64_t)v * D + k);
+        for (int a = 0; a < NA; ++a) {
+            const int32_t v = __ldg(E + (int64_t)(e_first + le) * NA + a);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                Xe[a][k] = __ldg(X + (int64_t)v * D + k);
+                sV[le][a][k] = Xe[a][k];
+            }
+        }
+        double ge[NA][D];
+        bool pos = true;
+        const bool ok = elem_gradients<D>(Xe, sg.inv_h, ge, pos);
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int k = 0; k < D; ++k) sG[le][a][k] = ok ? ge[a][k] : 0.0;
+        sPos[le] = ok ? (pos ? 1 : 0) : -1;
     }
     __syncthreads();
     const int64_t p = p0 + threadIdx.x;
@@ -48,22 +66,42 @@ __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(SubGrid sg, co
     int ci[3];
     cell_lower(sg, D, pair_cell[p], clo, ci);
     const int le = e - e_first;
-    double T[NA][D];
+    double Xe[NA][D], ge[NA][D];
+    int posflag;
+    if (le < kClipThreads) {
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-        int32_t v = le < kClipThreads ? 0 : __ldg(E + (int64_t)e * NA + a);
+        for (int a = 0; a < NA; ++a)
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            double x = le < kClipThreads ? sV[le][a][k] : __ldg(X + (int64_t)v * D + k);
-            T[a][k] = (x - clo[k]) * sg.inv_h[k];
+            for (int k = 0; k < D; ++k) {
+                Xe[a][k] = sV[le][a][k];
+                ge[a][k] = sG[le][a][k];
+            }
+        posflag = sPos[le];
+    } else {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const int32_t v = __ldg(E + (int64_t)e * NA + a);
+#pragma unroll
+            for (int k = 0; k < D; ++k) Xe[a][k] = __ldg(X + (int64_t)v * D + k);
         }
+        bool pos = true;
+        posflag = elem_gradients<D>(Xe, sg.inv_h, ge, pos) ? (pos ? 1 : 0) : -1;
     }
-    double scale = sg.h[0] * sg.h[1] * (D == 3 ? sg.h[2] : 1.0);
     double blk[NA * NB];
-    double vol;
-    if (!pair_integrals<D, R>(T, scale, blk, &vol)) {
+    double vol = 0.0;
+    if (posflag < 0) {
         atomicOr(&st->flags, FLAG_DEGENERATE);
         atomicMin(&st->bad_elem, e);
+#pragma unroll
+        for (int i = 0; i < NA * NB; ++i) blk[i] = 0.0;
+    } else {
+        double T[NA][D];
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int k = 0; k < D; ++k) T[a][k] = (Xe[a][k] - clo[k]) * sg.inv_h[k];
+        const double scale = sg.h[0] * sg.h[1] * (D == 3 ? sg.h[2] : 1.0);
+        pair_integrals<D, R>(T, ge, posflag == 1, scale, blk, &vol);
     }
 #pragma unroll
     for (int i = 0; i < NA * NB; ++i) blocks[i * slot_stride + p] = blk[i];
@@ -84,17 +122,24 @@ __global__ void clip_plain_kernel(SubGrid sg, const double* __restrict__ X, cons
     double clo[3];
     int ci[3];
     cell_lower(sg, D, pair_cell[p], clo, ci);
-    double T[NA][D];
+    double Xe[NA][D], T[NA][D], ge[NA][D];
     for (int a = 0; a < NA; ++a) {
-        int32_t v = E[(int64_t)e * NA + a];
-        for (int k = 0; k < D; ++k) T[a][k] = (X[(int64_t)v * D + k] - clo[k]) * sg.inv_h[k];
+        const int32_t v = E[(int64_t)e * NA + a];
+        for (int k = 0; k < D; ++k) {
+            Xe[a][k] = X[(int64_t)v * D + k];
+            T[a][k] = (Xe[a][k] - clo[k]) * sg.inv_h[k];
+        }
     }
-    double scale = sg.h[0] * sg.h[1] * (D == 3 ? sg.h[2] : 1.0);
     double blk[NA * NB];
-    double vol;
-    if (!pair_integrals<D, double>(T, scale, blk, &vol)) {
+    double vol = 0.0;
+    bool pos = true;
+    if (!elem_gradients<D>(Xe, sg.inv_h, ge, pos)) {
         atomicOr(&st->flags, FLAG_DEGENERATE);
         atomicMin(&st->bad_elem, e);
+        for (int i = 0; i < NA * NB; ++i) blk[i] = 0.0;
+    } else {
+        const double scale = sg.h[0] * sg.h[1] * (D == 3 ? sg.h[2] : 1.0);
+        pair_integrals<D, double>(T, ge, pos, scale, blk, &vol);
     }
     for (int i = 0; i < NA * NB; ++i) blocks[p * (NA * NB) + i] = blk[i];
     vols[p] = vol;

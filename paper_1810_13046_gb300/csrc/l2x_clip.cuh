@@ -24,6 +24,9 @@
 //    arithmetic runs in R = double (FP64 mode) or R = float (mixed mode).
 #pragma once
 
+#include <climits>
+
+#include "l2x_fp.cuh"
 #include "l2x_internal.cuh"
 
 namespace l2x {
@@ -35,30 +38,36 @@ struct ElemT {
     double T[D + 1][D];   // vertices in cell-local coordinates
 };
 
-// Sutherland-Hodgman step against an axis plane: keep v[k] >= c (upper=false)
-// or v[k] <= c (upper=true).  Intersection points are put on the plane exactly.
+// Sutherland-Hodgman step against an axis plane at coordinate c: keep v[k] >= c
+// (upper = false) or v[k] <= c (upper = true).  Crossing points lie on the plane
+// exactly.  Inside tests are integer comparisons; FP64 arithmetic only at crossings.
 template <int D>
 __device__ __forceinline__ int clip_axis(const double (*in)[D], int n, double (*out)[D], int k, double c,
                                          bool upper) {
     int m = 0;
+    const long long kc = order_key(c);
+    long long kp = order_key(in[0][k]);
+    const long long k0 = kp;
     for (int i = 0; i < n; ++i) {
         const double* p = in[i];
         const double* q = in[i + 1 == n ? 0 : i + 1];
-        double sp = upper ? c - p[k] : p[k] - c;
-        double sq = upper ? c - q[k] : q[k] - c;
-        bool ip = sp >= 0.0, iq = sq >= 0.0;
+        const long long kq = i + 1 == n ? k0 : order_key(q[k]);
+        const bool ip = upper ? kp <= kc : kp >= kc;
+        const bool iq = upper ? kq <= kc : kq >= kc;
         if (ip) {
 #pragma unroll
             for (int j = 0; j < D; ++j) out[m][j] = p[j];
             ++m;
         }
         if (ip != iq) {
-            double t = sp / (sp - sq);
+            const double sp = p[k] - c, sq = q[k] - c;
+            const double t = div_nr(sp, sp - sq);
 #pragma unroll
             for (int j = 0; j < D; ++j) out[m][j] = fma(t, q[j] - p[j], p[j]);
             out[m][k] = c;
             ++m;
         }
+        kp = kq;
     }
     return m;
 }
@@ -83,14 +92,14 @@ __device__ __forceinline__ int clip_plane(const double (*in)[D], int n, double (
 #pragma unroll
             for (int j = 0; j < D; ++j) sq = fma(g[j], q[j], sq);
         }
-        bool ip = sp >= 0.0, iq = sq >= 0.0;
+        const bool ip = nonneg_d(sp), iq = nonneg_d(sq);
         if (ip) {
 #pragma unroll
             for (int j = 0; j < D; ++j) out[m][j] = p[j];
             ++m;
         }
         if (ip != iq) {
-            double t = sp / (sp - sq);
+            const double t = div_nr(sp, sp - sq);
 #pragma unroll
             for (int j = 0; j < D; ++j) out[m][j] = fma(t, q[j] - p[j], p[j]);
             ++m;
@@ -216,95 +225,71 @@ __device__ __forceinline__ R moment_nu(const R* acc, int j, int S) {
     return acc[S | (1 << j)];
 }
 
-// Fan a polygon (in t-space) into cone simplices with apex A and accumulate.
+// Fan a polygon given in apex coordinates (apex at the origin) into cone
+// simplices and accumulate their moments.  2-D: cone triangles (0, v_i, v_i+1);
+// 3-D: cone tetrahedra (0, v_0, v_i, v_i+1).
 template <int D, typename R>
-__device__ __forceinline__ void accum_polygon(const double (*poly)[D], int n, const double* A, R* acc) {
+__device__ __forceinline__ void accum_polygon(const double (*poly)[D], int n, R* acc) {
     if constexpr (D == 2) {
-        // 2-D: the polygon is P itself; apex = its vertex 0 (A is ignored).
         R q[2], r[2];
-        for (int i = 1; i + 1 < n; ++i) {
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                q[k] = (R)(poly[i][k] - poly[0][k]);
-                r[k] = (R)(poly[i + 1][k] - poly[0][k]);
-            }
+        q[0] = to_r<R>(poly[0][0]);
+        q[1] = to_r<R>(poly[0][1]);
+        for (int i = 0; i < n; ++i) {
+            const int j = i + 1 == n ? 0 : i + 1;
+            r[0] = to_r<R>(poly[j][0]);
+            r[1] = to_r<R>(poly[j][1]);
             cone_accum2<R>(q, r, acc);
+            q[0] = r[0];
+            q[1] = r[1];
         }
     } else {
         if (n < 3) return;
         R p[3], q[3], r[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) p[k] = (R)(poly[0][k] - A[k]);
+        for (int k = 0; k < 3; ++k) {
+            p[k] = to_r<R>(poly[0][k]);
+            q[k] = to_r<R>(poly[1][k]);
+        }
         for (int i = 1; i + 1 < n; ++i) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                q[k] = (R)(poly[i][k] - A[k]);
-                r[k] = (R)(poly[i + 1][k] - A[k]);
-            }
+            for (int k = 0; k < 3; ++k) r[k] = to_r<R>(poly[i + 1][k]);
             cone_accum3<R>(p, q, r, acc);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) q[k] = r[k];
         }
     }
 }
 
-// Clip + integrate one pair.  T: element vertices in cell-local coordinates.
-// scale = h0*h1(*h2) (volume of the cell).  Writes (d+1)*2^d block entries and
-// the intersection volume.  Returns false if the element is degenerate.
-template <int D, typename R>
-__device__ bool pair_integrals(const double (&T)[D + 1][D], double scale, double* block, double* vol) {
-    constexpr int NB = 1 << D;
-    constexpr int NA = D + 1;
-    using L = MomentLayout<D>;
-    // crossing mask and bounds
-    double mn[D], mx[D];
+// Barycentric coordinates of an element in cell-local coordinates t = (x - c)/h:
+// lambda_a(t) = c_a + g[a] . t, with g independent of the cell.  Edges
+// (X_i - X_0) / h, adjugate over determinant.  Returns false for a zero volume.
+template <int D>
+__device__ __forceinline__ bool elem_gradients(const double (&X)[D + 1][D], const double* inv_h,
+                                               double (&g)[D + 1][D], bool& positive) {
+    double e[D][D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        mn[k] = T[0][k];
-        mx[k] = T[0][k];
+    for (int i = 0; i < D; ++i)
 #pragma unroll
-        for (int a = 1; a < NA; ++a) {
-            mn[k] = fmin(mn[k], T[a][k]);
-            mx[k] = fmax(mx[k], T[a][k]);
-        }
-    }
-    *vol = 0.0;
-#pragma unroll
-    for (int i = 0; i < NA * NB; ++i) block[i] = 0.0;
-#pragma unroll
-    for (int k = 0; k < D; ++k)
-        if (mx[k] <= 0.0 || mn[k] >= 1.0) return true;  // no overlap of positive measure
-    int lower_mask = 0, upper_mask = 0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if (mn[k] < 0.0) lower_mask |= 1 << k;
-        if (mx[k] > 1.0) upper_mask |= 1 << k;
-    }
-    // barycentric coordinates in t-space: lambda_a(t) = c[a] + g[a] . t
-    double g[NA][D], c[NA];
+        for (int k = 0; k < D; ++k) e[i][k] = (X[i + 1][k] - X[0][k]) * inv_h[k];
     double det;
     if constexpr (D == 2) {
-        double e1x = T[1][0] - T[0][0], e1y = T[1][1] - T[0][1];
-        double e2x = T[2][0] - T[0][0], e2y = T[2][1] - T[0][1];
-        det = e1x * e2y - e1y * e2x;
+        det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
         if (det == 0.0) return false;
-        double id = 1.0 / det;
-        g[1][0] = e2y * id; g[1][1] = -e2x * id;
-        g[2][0] = -e1y * id; g[2][1] = e1x * id;
+        const double id = 1.0 / det;
+        g[1][0] = e[1][1] * id;
+        g[1][1] = -e[1][0] * id;
+        g[2][0] = -e[0][1] * id;
+        g[2][1] = e[0][0] * id;
     } else {
-        double e[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) e[i][k] = T[i + 1][k] - T[0][k];
-        // rows of the inverse edge matrix: (e1 x e2, e2 x e0, e0 x e1) / det
-        double c0[3] = {e[1][1] * e[2][2] - e[1][2] * e[2][1], e[1][2] * e[2][0] - e[1][0] * e[2][2],
-                        e[1][0] * e[2][1] - e[1][1] * e[2][0]};
+        const double c0[3] = {e[1][1] * e[2][2] - e[1][2] * e[2][1], e[1][2] * e[2][0] - e[1][0] * e[2][2],
+                              e[1][0] * e[2][1] - e[1][1] * e[2][0]};
         det = e[0][0] * c0[0] + e[0][1] * c0[1] + e[0][2] * c0[2];
         if (det == 0.0) return false;
-        double id = 1.0 / det;
-        double c1[3] = {e[2][1] * e[0][2] - e[2][2] * e[0][1], e[2][2] * e[0][0] - e[2][0] * e[0][2],
-                        e[2][0] * e[0][1] - e[2][1] * e[0][0]};
-        double c2[3] = {e[0][1] * e[1][2] - e[0][2] * e[1][1], e[0][2] * e[1][0] - e[0][0] * e[1][2],
-                        e[0][0] * e[1][1] - e[0][1] * e[1][0]};
+        const double id = 1.0 / det;
+        const double c1[3] = {e[2][1] * e[0][2] - e[2][2] * e[0][1], e[2][2] * e[0][0] - e[2][0] * e[0][2],
+                              e[2][0] * e[0][1] - e[2][1] * e[0][0]};
+        const double c2[3] = {e[0][1] * e[1][2] - e[0][2] * e[1][1], e[0][2] * e[1][0] - e[0][0] * e[1][2],
+                              e[0][0] * e[1][1] - e[0][1] * e[1][0]};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             g[1][k] = c0[k] * id;
@@ -314,49 +299,86 @@ __device__ bool pair_integrals(const double (&T)[D + 1][D], double scale, double
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        double sgk = 0.0;
+        double s = 0.0;
 #pragma unroll
-        for (int a = 1; a < NA; ++a) sgk += g[a][k];
-        g[0][k] = -sgk;
+        for (int a = 1; a <= D; ++a) s += g[a][k];
+        g[0][k] = -s;
     }
+    positive = det > 0.0;
+    return true;
+}
+
+// Clip + integrate one pair.  T: element vertices in cell-local coordinates;
+// g, positive: from elem_gradients; scale = volume of the cell.  Writes the
+// (d+1)*2^d block and the intersection volume.
+template <int D, typename R>
+__device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D + 1][D], bool positive,
+                               double scale, double* block, double* vol) {
+    constexpr int NB = 1 << D;
+    constexpr int NA = D + 1;
+    using L = MomentLayout<D>;
+    constexpr long long K1 = 0x3ff0000000000000LL;  // order key of 1.0 (key of +0.0 is 0)
+    *vol = 0.0;
+#pragma unroll
+    for (int i = 0; i < NA * NB; ++i) block[i] = 0.0;
+    // classification of the vertices against the cell, by integer keys
+    long long kmin[D], kmax[D];
+    int lower_mask = 0, upper_mask = 0, inside_mask = (1 << NA) - 1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        kmin[k] = LLONG_MAX;
+        kmax[k] = LLONG_MIN;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const long long kk = order_key(T[a][k]);
+            kmin[k] = min(kmin[k], kk);
+            kmax[k] = max(kmax[k], kk);
+            if (kk < 0 || kk > K1) inside_mask &= ~(1 << a);
+        }
+        if (kmax[k] <= 0 || kmin[k] >= K1) return;  // no overlap of positive measure
+        if (kmin[k] < 0) lower_mask |= 1 << k;
+        if (kmax[k] > K1) upper_mask |= 1 << k;
+    }
+    const int apex_v = inside_mask ? __ffs(inside_mask) - 1 : -1;
+    double A[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (apex_v >= 0) {
+            A[k] = T[apex_v][k];
+        } else {
+            const double lo = from_order_key(max(kmin[k], 0LL));
+            const double hi = from_order_key(min(kmax[k], K1));
+            A[k] = 0.5 * (lo + hi);
+        }
+    }
+    // lambda_a at the apex: c'_a = -g_a . (T_0 - A) for a >= 1, c'_0 = 1 - sum
+    double cA[NA];
     {
+        double u0[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) u0[k] = T[0][k] - A[k];
         double csum = 0.0;
 #pragma unroll
         for (int a = 1; a < NA; ++a) {
             double v = 0.0;
 #pragma unroll
-            for (int k = 0; k < D; ++k) v = fma(-g[a][k], T[0][k], v);
-            c[a] = v;
+            for (int k = 0; k < D; ++k) v = fma(-g[a][k], u0[k], v);
+            cA[a] = v;
             csum += v;
         }
-        c[0] = 1.0 - csum;
+        cA[0] = 1.0 - csum;
     }
-    // apex: an element vertex inside the closed cell, else the centre of bbox ∩ cell
-    int apex_v = -1;
-#pragma unroll
-    for (int a = NA - 1; a >= 0; --a) {
-        bool in = true;
-#pragma unroll
-        for (int k = 0; k < D; ++k) in = in && T[a][k] >= 0.0 && T[a][k] <= 1.0;
-        if (in) apex_v = a;
-    }
-    double A[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k)
-        A[k] = apex_v >= 0 ? T[apex_v][k] : 0.5 * (fmax(mn[k], 0.0) + fmin(mx[k], 1.0));
-
     R acc[L::kN];
 #pragma unroll
     for (int i = 0; i < L::kN; ++i) acc[i] = R(0);
-
     double bufA[kMaxPoly][D], bufB[kMaxPoly][D];
-    const bool positive = det > 0.0;
     if constexpr (D == 2) {
-        // P = triangle clipped by the crossed cell lines; oriented counter-clockwise
+        // P = triangle clipped by the crossed cell lines (counter-clockwise), then
+        // re-centred on its first vertex, which becomes the apex.
         int n = 3;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            int v = positive ? i : 2 - i;
+            const int v = positive ? i : 2 - i;
 #pragma unroll
             for (int k = 0; k < D; ++k) bufA[i][k] = T[v][k];
         }
@@ -368,13 +390,38 @@ __device__ bool pair_integrals(const double (&T)[D + 1][D], double scale, double
             if ((upper_mask >> k) & 1) { n = clip_axis<D>(cur, n, nxt, k, 1.0, true); double (*t)[D] = cur; cur = nxt; nxt = t; }
         }
         if (n >= 3) {
-            // 2-D apex: vertex 0 of P (the fan below cones every triangle to it)
+            double P0[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) A[k] = cur[0][k];
-            accum_polygon<D, R>(cur, n, A, acc);
+            for (int k = 0; k < D; ++k) P0[k] = cur[0][k];
+            for (int i = 0; i < n; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) cur[i][k] -= P0[k];
+            // lambda at the new apex
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                double v = cA[a];
+#pragma unroll
+                for (int k = 0; k < D; ++k) v = fma(g[a][k], P0[k] - A[k], v);
+                cA[a] = v;
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) A[k] = P0[k];
+            accum_polygon<D, R>(cur, n, acc);
         }
         finish_moments2<R>(acc);
     } else {
+        // apex coordinates u = t - A: element vertices, cell planes
+        double U[NA][3];
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) U[a][k] = T[a][k] - A[k];
+        double clo[3], chi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            clo[k] = -A[k];
+            chi[k] = 1.0 - A[k];
+        }
         // element faces: face opposite vertex f, outward for a positive element
         const int faces[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
 #pragma unroll 1
@@ -383,34 +430,36 @@ __device__ bool pair_integrals(const double (&T)[D + 1][D], double scale, double
             int n = 3;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                int v = faces[f][positive ? i : 2 - i];
+                const int v = faces[f][positive ? i : 2 - i];
 #pragma unroll
-                for (int k = 0; k < D; ++k) bufA[i][k] = T[v][k];
+                for (int k = 0; k < 3; ++k) bufA[i][k] = U[v][k];
             }
             double (*cur)[D] = bufA;
             double (*nxt)[D] = bufB;
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                if (n > 0 && ((lower_mask >> k) & 1)) { n = clip_axis<D>(cur, n, nxt, k, 0.0, false); double (*t)[D] = cur; cur = nxt; nxt = t; }
-                if (n > 0 && ((upper_mask >> k) & 1)) { n = clip_axis<D>(cur, n, nxt, k, 1.0, true); double (*t)[D] = cur; cur = nxt; nxt = t; }
+            for (int k = 0; k < 3; ++k) {
+                if (n > 0 && ((lower_mask >> k) & 1)) { n = clip_axis<D>(cur, n, nxt, k, clo[k], false); double (*t)[D] = cur; cur = nxt; nxt = t; }
+                if (n > 0 && ((upper_mask >> k) & 1)) { n = clip_axis<D>(cur, n, nxt, k, chi[k], true); double (*t)[D] = cur; cur = nxt; nxt = t; }
             }
-            accum_polygon<D, R>(cur, n, A, acc);
+            accum_polygon<D, R>(cur, n, acc);
         }
         // cell faces the element crosses, clipped to the element
 #pragma unroll 1
         for (int side = 0; side < 2; ++side) {
-            int mask = side == 0 ? lower_mask : upper_mask;
+            const int mask = side == 0 ? lower_mask : upper_mask;
 #pragma unroll 1
             for (int k = 0; k < 3; ++k) {
                 if (!((mask >> k) & 1)) continue;
                 const int i1 = (k + 1) % 3, i2 = (k + 2) % 3;
-                const double sq[4][2] = {{0.0, 0.0}, {1.0, 0.0}, {1.0, 1.0}, {0.0, 1.0}};
+                const double ck = side == 1 ? chi[k] : clo[k];
+                const double a1[4] = {clo[i1], chi[i1], chi[i1], clo[i1]};
+                const double a2[4] = {clo[i2], clo[i2], chi[i2], chi[i2]};
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    int s = side == 1 ? v : 3 - v;  // outward: +e_k on t_k = 1, -e_k on t_k = 0
-                    bufA[v][k] = side == 1 ? 1.0 : 0.0;
-                    bufA[v][i1] = sq[s][0];
-                    bufA[v][i2] = sq[s][1];
+                    const int s = side == 1 ? v : 3 - v;  // outward: +e_k on t_k = 1, -e_k on t_k = 0
+                    bufA[v][k] = ck;
+                    bufA[v][i1] = a1[s];
+                    bufA[v][i2] = a2[s];
                 }
                 int n = 4;
                 double (*cur)[D] = bufA;
@@ -418,17 +467,25 @@ __device__ bool pair_integrals(const double (&T)[D + 1][D], double scale, double
 #pragma unroll
                 for (int a = 0; a < NA; ++a) {
                     if (n == 0) break;
-                    n = clip_plane<D>(cur, n, nxt, g[a], c[a]);
+                    n = clip_plane<D>(cur, n, nxt, g[a], cA[a]);
                     double (*t)[D] = cur; cur = nxt; nxt = t;
                 }
-                accum_polygon<D, R>(cur, n, A, acc);
+                accum_polygon<D, R>(cur, n, acc);
             }
         }
         finish_moments3<R>(acc);
     }
-    // lambda and psi around the apex: lambda_a = cA[a] + g[a].u, psi_b = prod_k (alpha_bk + sigma_bk u_k)
-    *vol = (double)acc[0] * scale;
+    // lambda_a = cA[a] + g[a].u and psi_b = prod_k (alpha_bk + sigma_bk u_k) around the apex
+    const R scale_r = to_r<R>(scale);
+    if constexpr (sizeof(R) == 4) *vol = f2d_int(acc[0] * scale_r);
+    else *vol = (double)acc[0] * scale;
     R W[NB], Wj[NB][D];
+    R Ar[D], A1r[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        Ar[k] = to_r<R>(A[k]);
+        A1r[k] = to_r<R>(1.0 - A[k]);
+    }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         R coef[NB];
@@ -437,9 +494,9 @@ __device__ bool pair_integrals(const double (&T)[D + 1][D], double scale, double
             R cf = R(1);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                bool bk = (b >> k) & 1;
-                if ((S >> k) & 1) cf *= bk ? R(1) : R(-1);
-                else cf *= bk ? (R)A[k] : (R)(1.0 - A[k]);
+                const bool bk = (b >> k) & 1;
+                if ((S >> k) & 1) cf = bk ? cf : -cf;
+                else cf *= bk ? Ar[k] : A1r[k];
             }
             coef[S] = cf;
         }
@@ -457,22 +514,19 @@ __device__ bool pair_integrals(const double (&T)[D + 1][D], double scale, double
     }
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
-        double cA = c[a];
-#pragma unroll
-        for (int k = 0; k < D; ++k) cA = fma(g[a][k], A[k], cA);
-        R ca = (R)cA;
+        const R ca = to_r<R>(cA[a]);
         R ga[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) ga[k] = (R)g[a][k];
+        for (int k = 0; k < D; ++k) ga[k] = to_r<R>(g[a][k]);
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             R v = ca * W[b];
 #pragma unroll
             for (int j = 0; j < D; ++j) v += ga[j] * Wj[b][j];
-            block[a * NB + b] = (double)v * scale;
+            if constexpr (sizeof(R) == 4) block[a * NB + b] = f2d_int(v * scale_r);
+            else block[a * NB + b] = (double)v * scale;
         }
     }
-    return true;
 }
 
 }  // namespace l2x

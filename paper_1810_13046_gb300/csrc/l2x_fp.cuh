@@ -1,0 +1,127 @@
+// Bit-level helpers for IEEE doubles on GB300 (sm_103a).
+//
+// On this part every FP64 instruction -- arithmetic, compares, min/max and
+// conversions alike -- issues to a narrow FP64 unit (2 thread-operations per
+// clock per SM), so these helpers do compares, conversions and the reciprocal
+// seed with integer and single-precision instructions instead.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace l2x {
+
+// ---------------------------------------------------------------- bit-level helpers
+// On GB300 every FP64 instruction (compare, min/max and conversion included) runs
+// on the narrow FP64 unit; these helpers do the same jobs with integer
+// instructions on the bit patterns of IEEE doubles (finite inputs only).
+
+// Signed-integer key with the same order as the doubles it encodes.
+__device__ __forceinline__ long long order_key(double x) {
+    long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+// x >= y (with -0.0 < +0.0, a consistent tie rule for both sides of every plane)
+__device__ __forceinline__ bool ge_d(double x, double y) { return order_key(x) >= order_key(y); }
+__device__ __forceinline__ bool le_d(double x, double y) { return order_key(x) <= order_key(y); }
+// sign bit clear: x >= +0.0
+__device__ __forceinline__ bool nonneg_d(double x) { return __double2hiint(x) >= 0; }
+
+// double -> float, rounding half away from zero in magnitude, flushing magnitudes
+// below 2^-126 to zero (the moment arithmetic never needs subnormals).
+__device__ __forceinline__ float d2f_int(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x) + 0x10000000ull;
+    unsigned int hi = (unsigned int)(b >> 32);
+    int e = (int)((hi >> 20) & 0x7ff) - 896;
+    unsigned int sign = hi & 0x80000000u;
+    if (e <= 0) return __uint_as_float(sign);
+    unsigned int m = (unsigned int)(b >> 29) & 0x7fffffu;
+    return __uint_as_float(sign | ((unsigned int)e << 23) | m);
+}
+// float -> double, exact (normal floats; zero maps to zero).
+__device__ __forceinline__ double f2d_int(float f) {
+    unsigned int u = __float_as_uint(f);
+    unsigned int e = (u >> 23) & 0xff;
+    if (e == 0) return __longlong_as_double((long long)(u & 0x80000000u) << 32);
+    unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                           ((unsigned long long)(e + 896) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+template <typename R>
+__device__ __forceinline__ R to_r(double x);
+template <>
+__device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_r<float>(double x) { return d2f_int(x); }
+
+// a / b by Newton-Raphson on the reciprocal (seed: single-precision reciprocal),
+// two refinements and one residual correction of the quotient.  Used for the
+// edge parameters of plane crossings, where |b| > 0 and a / b lies in [0, 1].
+__device__ __forceinline__ double div_nr(double a, double b) {
+    const int eb = (__double2hiint(b) >> 20) & 0x7ff;
+    if (eb < 1023 - 120 || eb > 1023 + 120) return a / b;
+    double r = f2d_int(__frcp_rn(d2f_int(b)));
+    double e = fma(-b, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-b, r, 1.0);
+    r = fma(r, e, r);
+    double q = a * r;
+    double rem = fma(-b, q, a);
+    return fma(rem, r, q);
+}
+
+
+// Double-float value (hi + lo) and its sum with a second one (Knuth's two-sum,
+// renormalised); single-precision instructions only.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
+    const float h = __fadd_rn(s, lo);
+    return DF{h, __fsub_rn(lo, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ DF df_from_double(double x) {
+    const float hi = d2f_int(x);
+    return DF{hi, d2f_int(x - f2d_int(hi))};
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return f2d_int(a.hi) + f2d_int(a.lo); }
+
+// x * 2^e by integer arithmetic on the exponent field (finite x; results below
+// the normal range become zero of the same sign).
+__device__ __forceinline__ float ldexp_f_int(float x, int e) {
+    const unsigned int u = __float_as_uint(x);
+    const int ex = (int)((u >> 23) & 0xff);
+    if (ex == 0) return __uint_as_float(u & 0x80000000u);
+    const int en = ex + e;
+    if (en <= 0) return __uint_as_float(u & 0x80000000u);
+    return __uint_as_float((u & 0x807fffffu) | ((unsigned int)en << 23));
+}
+__device__ __forceinline__ double ldexp_d_int(double x, int e) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((u >> 52) & 0x7ff);
+    if (ex == 0) return __longlong_as_double((long long)(u & 0x8000000000000000ull));
+    const int en = ex + e;
+    if (en <= 0) return __longlong_as_double((long long)(u & 0x8000000000000000ull));
+    return __longlong_as_double((long long)((u & 0x800fffffffffffffull) | ((unsigned long long)en << 52)));
+}
+// binary exponent of a positive finite double (floor(log2 x))
+__device__ __forceinline__ int ilogb_int(double x) {
+    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+}
+__device__ __forceinline__ DF df_scale(DF a, int e) { return DF{ldexp_f_int(a.hi, e), ldexp_f_int(a.lo, e)}; }
+
+__device__ __forceinline__ DF df_shfl_xor(DF a, int o) {
+    return DF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+}  // namespace l2x
