@@ -38,6 +38,8 @@ struct l2x_coupling {
     int32_t* cursor = nullptr;
     // per element
     double* elem_vol = nullptr;
+    double* elem_grad = nullptr;     // per element: barycentric gradients in cell-local coordinates
+    int8_t* elem_flag = nullptr;     // 1 positive, 0 negative orientation, -1 degenerate
     ElemBox* boxes = nullptr;
     int64_t* counts = nullptr;
     int64_t* offsets = nullptr;      // n_grids*m + 1
@@ -49,6 +51,9 @@ struct l2x_coupling {
     int32_t* pair_cell = nullptr;
     double* blocks = nullptr;
     double* vols = nullptr;
+    uint8_t* pair_key = nullptr;     // scheduling class per pair (fused path)
+    int32_t* pair_perm = nullptr;    // pairs in class order (fused path)
+    int32_t* buckets = nullptr;      // class counts and cursors
     // matrices
     Csr B[kMaxGrids];
     int64_t B_cap[kMaxGrids]{};
@@ -274,7 +279,8 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
     L2X_CUDA(cudaStreamSynchronize(s));
     // (I) candidate boxes, counts, offsets
     auto ph_pairs = std::make_unique<PhaseScope>(h, L2X_PH_PAIRS, s);
-    launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->node_box, h->elem_vol, h->st, s);
+    launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->node_box, h->elem_vol, h->elem_grad,
+                      h->elem_flag, h->st, s);
     launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
     std::vector<int64_t> gb(G + 1);
     for (int g = 0; g <= G; ++g)
@@ -290,12 +296,16 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         dfree(h->pair_cell);
         dfree(h->blocks);
         dfree(h->vols);
+        dfree(h->pair_key);
+        dfree(h->pair_perm);
         h->pair_cap = 0;
         const int64_t cap = NP + NP / 4 + 128;
         L2X_TRY(dalloc(&h->pair_elem, cap));
         L2X_TRY(dalloc(&h->pair_cell, cap));
         L2X_TRY(dalloc(&h->blocks, (size_t)cap * NS));
         L2X_TRY(dalloc(&h->vols, cap));
+        L2X_TRY(dalloc(&h->pair_key, cap));
+        L2X_TRY(dalloc(&h->pair_perm, cap));
         h->pair_cap = cap;
     }
     launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, s);
@@ -308,8 +318,9 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
             launch_clip_plain(d, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks,
                               h->vols, h->st, s);
         else
-            launch_clip_fused(d, h->opts.precision, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem,
-                              h->pair_cell, h->blocks, h->pair_cap, h->vols, h->st, s);
+            launch_clip_fused(d, h->opts.precision, h->sg[g], h->X, h->E, h->elem_grad, h->elem_flag, gb[g],
+                              gb[g + 1], h->pair_elem, h->pair_cell, h->pair_key, h->pair_perm, h->buckets,
+                              h->blocks, h->pair_cap, h->vols, h->st, s);
     }
     // (IV) B_g by rows
     for (int g = 0; g < G; ++g) {
@@ -470,6 +481,7 @@ l2x_status l2x_destroy(l2x_handle h) {
     resolve_timing(h);
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     dfree(h->X); dfree(h->E); dfree(h->adj_ptr); dfree(h->adj); dfree(h->cursor); dfree(h->elem_vol);
+    dfree(h->elem_grad); dfree(h->elem_flag); dfree(h->buckets); dfree(h->pair_key); dfree(h->pair_perm);
     dfree(h->boxes); dfree(h->counts); dfree(h->offsets); dfree(h->node_box); dfree(h->pair_elem);
     dfree(h->pair_cell); dfree(h->blocks); dfree(h->vols);
     for (int g = 0; g < kMaxGrids; ++g) {
@@ -517,6 +529,9 @@ l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const 
         L2X_CUDA(cudaMemcpyAsync(h->X, mesh->coords, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
         L2X_CUDA(cudaMemcpyAsync(h->E, mesh->elems, sizeof(int32_t) * m * (d + 1), cudaMemcpyDeviceToDevice, s));
         L2X_TRY(dalloc(&h->elem_vol, m));
+        L2X_TRY(dalloc(&h->elem_grad, (size_t)(m * (d + 1) * d)));
+        L2X_TRY(dalloc(&h->elem_flag, m));
+        L2X_TRY(dalloc(&h->buckets, 2 * kClasses));
         L2X_TRY(dalloc(&h->boxes, (size_t)(G * m)));
         L2X_TRY(dalloc(&h->counts, (size_t)(G * m)));
         L2X_TRY(dalloc(&h->offsets, (size_t)(G * m + 1)));

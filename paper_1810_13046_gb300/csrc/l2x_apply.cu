@@ -204,12 +204,35 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 constexpr int kRowLanes = 4;
 constexpr int kPcgBlock = 256;
 
+// Sum of NV double-float values over the kPcgBlock threads of a block: staged in
+// shared memory, value j summed by warp j % NW (8 per lane, then 5 shuffle
+// levels), result in out[j] after the final barrier.
+template <int NV>
+__device__ __forceinline__ void block_df_sum(const DF (&v)[NV], DF (*stage)[kPcgBlock], DF* out) {
+    constexpr int NW = kPcgBlock / 32;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) stage[j][threadIdx.x] = v[j];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = wid; j < NV; j += NW) {
+        DF t = stage[j][lane];
+#pragma unroll
+        for (int q = 1; q < kPcgBlock / 32; ++q) t = df_add(t, stage[j][lane + 32 * q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = df_add(t, df_shfl_xor(t, o));
+        if (lane == 0) out[j] = t;
+    }
+    __syncthreads();
+}
+
 template <typename TV, int NR>
 __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
     cg::grid_group grid = cg::this_grid();
     constexpr int NV = 3 * NR;                  // gamma, delta, rho per right-hand side
     constexpr int NW = kPcgBlock / 32;
-    __shared__ DF sh[NV][NW];
+    __shared__ DF s_stage[NV][kPcgBlock];
+    __shared__ DF s_dfo[NV];
     __shared__ double s_red[NV * 32];
     __shared__ double s_tot[NV];
     __shared__ double s_alpha[NR], s_beta[NR];
@@ -287,7 +310,7 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
                     v[3 * k + 2] = dr[k].value();
                 }
                 block_sum_n<NV>(v, s_red, s_tot);
-                if (threadIdx.x < NV) A.partial[(int64_t)blockIdx.x * NV + threadIdx.x] = s_tot[threadIdx.x];
+                if (threadIdx.x < NV) A.partial[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = s_tot[threadIdx.x];
             } else {
                 DF v[NV];
 #pragma unroll
@@ -296,21 +319,8 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
                     v[3 * k + 1] = dd[k].df(s_exp[3 * k + 1]);
                     v[3 * k + 2] = dr[k].df(s_exp[3 * k + 2]);
                 }
-#pragma unroll
-                for (int j = 0; j < NV; ++j)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v[j] = df_add(v[j], df_shfl_xor(v[j], o));
-                __syncthreads();
-                if (lane == 0)
-#pragma unroll
-                    for (int j = 0; j < NV; ++j) sh[j][wid] = v[j];
-                __syncthreads();
-                if (threadIdx.x < NV) {
-                    DF t = sh[threadIdx.x][0];
-#pragma unroll
-                    for (int ww = 1; ww < NW; ++ww) t = df_add(t, sh[threadIdx.x][ww]);
-                    partial[(int64_t)blockIdx.x * NV + threadIdx.x] = t;
-                }
+                block_df_sum<NV>(v, s_stage, s_dfo);
+                if (threadIdx.x < NV) partial[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = s_dfo[threadIdx.x];
             }
         }
         grid.sync();
@@ -322,7 +332,7 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
                 for (int j = 0; j < NV; ++j) v[j] = 0.0;
                 for (int b = threadIdx.x; b < (int)gridDim.x; b += kPcgBlock) {
 #pragma unroll
-                    for (int j = 0; j < NV; ++j) v[j] += A.partial[(int64_t)b * NV + j];
+                    for (int j = 0; j < NV; ++j) v[j] += A.partial[(int64_t)j * gridDim.x + b];
                 }
                 block_sum_n<NV>(v, s_red, s_tot);
                 if (threadIdx.x < NV) {
@@ -336,23 +346,10 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
                 for (int j = 0; j < NV; ++j) v[j] = DF{0.f, 0.f};
                 for (int b = threadIdx.x; b < (int)gridDim.x; b += kPcgBlock) {
 #pragma unroll
-                    for (int j = 0; j < NV; ++j) v[j] = df_add(v[j], partial[(int64_t)b * NV + j]);
+                    for (int j = 0; j < NV; ++j) v[j] = df_add(v[j], partial[(int64_t)j * gridDim.x + b]);
                 }
-#pragma unroll
-                for (int j = 0; j < NV; ++j)
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v[j] = df_add(v[j], df_shfl_xor(v[j], o));
-                __syncthreads();
-                if (lane == 0)
-#pragma unroll
-                    for (int j = 0; j < NV; ++j) sh[j][wid] = v[j];
-                __syncthreads();
-                if (threadIdx.x < NV) {
-                    DF t = sh[threadIdx.x][0];
-#pragma unroll
-                    for (int ww = 1; ww < NW; ++ww) t = df_add(t, sh[threadIdx.x][ww]);
-                    s_tot[threadIdx.x] = ldexp_d_int(df_to_double(t), -s_exp[threadIdx.x]);
-                }
+                block_df_sum<NV>(v, s_stage, s_dfo);
+                if (threadIdx.x < NV) s_tot[threadIdx.x] = ldexp_d_int(df_to_double(s_dfo[threadIdx.x]), -s_exp[threadIdx.x]);
                 __syncthreads();
             }
             if (threadIdx.x < NR) {
@@ -416,7 +413,7 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
 #pragma unroll
                 for (int k = 0; k < NR; ++k) v[k] = dt[k].value();
                 block_sum_n<NV>(v, s_red, s_tot);
-                if (threadIdx.x < NV) A.partial[(int64_t)blockIdx.x * NV + threadIdx.x] = s_tot[threadIdx.x];
+                if (threadIdx.x < NV) A.partial[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = s_tot[threadIdx.x];
             }
             grid.sync();
             {
@@ -425,7 +422,7 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
                 for (int j = 0; j < NV; ++j) v[j] = 0.0;
                 for (int b = threadIdx.x; b < (int)gridDim.x; b += kPcgBlock) {
 #pragma unroll
-                    for (int k = 0; k < NR; ++k) v[k] += A.partial[(int64_t)b * NV + k];
+                    for (int k = 0; k < NR; ++k) v[k] += A.partial[(int64_t)k * gridDim.x + b];
                 }
                 block_sum_n<NV>(v, s_red, s_tot);
                 if (threadIdx.x < NR) {

@@ -18,93 +18,107 @@ __device__ __forceinline__ void cell_lower(const SubGrid& sg, int dim, int32_t c
     for (int k = 0; k < dim; ++k) clo[k] = __dadd_rn(sg.origin[k], __dmul_rn((double)ci[k], sg.h[k]));
 }
 
-// Fused: one thread per pair; the block stages the vertex coordinates and the
-// barycentric gradients of the (consecutive) elements of its 128 pairs in shared
-// memory once.  Blocks are written structure-of-arrays so that every store
-// instruction is coalesced.
+// Element vertices of pair p in cell-local coordinates.
+template <int D>
+__device__ __forceinline__ void pair_vertices(const SubGrid& sg, const double* __restrict__ X, const int32_t* __restrict__ E,
+                                              int32_t e, int32_t cell, double (&T)[D + 1][D]) {
+    double clo[3];
+    int ci[3];
+    cell_lower(sg, D, cell, clo, ci);
+#pragma unroll
+    for (int a = 0; a <= D; ++a) {
+        const int32_t v = __ldg(E + (int64_t)e * (D + 1) + a);
+#pragma unroll
+        for (int k = 0; k < D; ++k) T[a][k] = (__ldg(X + (int64_t)v * D + k) - clo[k]) * sg.inv_h[k];
+    }
+}
+
+// Fused, step 1: scheduling class of every pair and per-class counts.
+template <int D>
+__global__ void pair_class_kernel(SubGrid sg, const double* __restrict__ X, const int32_t* __restrict__ E,
+                                  int64_t p_begin, int64_t p_end, const int32_t* __restrict__ pair_elem,
+                                  const int32_t* __restrict__ pair_cell, uint8_t* __restrict__ keys, int32_t* counts) {
+    __shared__ int hist[kClasses];
+    if (threadIdx.x < kClasses) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t p = p_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < p_end) {
+        double T[D + 1][D];
+        pair_vertices<D>(sg, X, E, pair_elem[p], pair_cell[p], T);
+        const int key = min(pair_class<D>(T), kClasses - 1);
+        keys[p - p_begin] = (uint8_t)key;
+        atomicAdd(&hist[key], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses && hist[threadIdx.x]) atomicAdd(counts + threadIdx.x, hist[threadIdx.x]);
+}
+
+// Fused, step 2: exclusive scan of the class counts into bucket cursors.
+__global__ void class_scan_kernel(int32_t* counts, int32_t* cursors) {
+    if (threadIdx.x != 0) return;
+    int32_t acc = 0;
+    for (int k = 0; k < kClasses; ++k) {
+        cursors[k] = acc;
+        acc += counts[k];
+    }
+}
+
+// Fused, step 3: permutation listing the pairs class by class.  Each block
+// reserves one range per class, so runs of consecutive pairs stay together.
+__global__ void pair_scatter_kernel(int64_t n, const uint8_t* __restrict__ keys, int32_t* cursors, int32_t* perm) {
+    __shared__ int hist[kClasses];
+    __shared__ int base[kClasses];
+    if (threadIdx.x < kClasses) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int key = 0, rank = 0;
+    if (i < n) {
+        key = keys[i];
+        rank = atomicAdd(&hist[key], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kClasses && hist[threadIdx.x]) base[threadIdx.x] = atomicAdd(cursors + threadIdx.x, hist[threadIdx.x]);
+    __syncthreads();
+    if (i < n) perm[base[key] + rank] = (int32_t)i;
+}
+
+// Fused, step 4: one thread per pair, in class order.  Gradients come from the
+// element pass; blocks are written structure-of-arrays at the pair's index.
 template <int D, typename R>
 __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(SubGrid sg, const double* __restrict__ X,
-                                                                  const int32_t* __restrict__ E, int64_t p_begin,
-                                                                  int64_t p_end, const int32_t* __restrict__ pair_elem,
+                                                                  const int32_t* __restrict__ E,
+                                                                  const double* __restrict__ elem_grad,
+                                                                  const int8_t* __restrict__ elem_flag, int64_t p_begin,
+                                                                  int64_t n, const int32_t* __restrict__ perm,
+                                                                  const int32_t* __restrict__ pair_elem,
                                                                   const int32_t* __restrict__ pair_cell,
                                                                   double* __restrict__ blocks, int64_t slot_stride,
                                                                   double* __restrict__ vols, DevStatus* st) {
     constexpr int NA = D + 1, NB = 1 << D;
-    __shared__ double sV[kClipThreads][NA][D];
-    __shared__ double sG[kClipThreads][NA][D];
-    __shared__ int sPos[kClipThreads];
-    const int64_t p0 = p_begin + (int64_t)blockIdx.x * kClipThreads;
-    const int64_t plast = min(p0 + kClipThreads - 1, p_end - 1);
-    const int32_t e_first = pair_elem[p0];
-    const int n_e = min(pair_elem[plast] - e_first + 1, kClipThreads);
-    if (threadIdx.x < n_e) {
-        const int le = threadIdx.x;
-        double Xe[NA][D];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            const int32_t v = __ldg(E + (int64_t)(e_first + le) * NA + a);
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                Xe[a][k] = __ldg(X + (int64_t)v * D + k);
-                sV[le][a][k] = Xe[a][k];
-            }
-        }
-        double ge[NA][D];
-        bool pos = true;
-        const bool ok = elem_gradients<D>(Xe, sg.inv_h, ge, pos);
-#pragma unroll
-        for (int a = 0; a < NA; ++a)
-#pragma unroll
-            for (int k = 0; k < D; ++k) sG[le][a][k] = ok ? ge[a][k] : 0.0;
-        sPos[le] = ok ? (pos ? 1 : 0) : -1;
-    }
-    __syncthreads();
-    const int64_t p = p0 + threadIdx.x;
-    if (p >= p_end) return;
+    const int64_t i = blockIdx.x * (int64_t)kClipThreads + threadIdx.x;
+    if (i >= n) return;
+    const int64_t p = p_begin + perm[i];
     const int32_t e = pair_elem[p];
-    double clo[3];
-    int ci[3];
-    cell_lower(sg, D, pair_cell[p], clo, ci);
-    const int le = e - e_first;
-    double Xe[NA][D], ge[NA][D];
-    int posflag;
-    if (le < kClipThreads) {
-#pragma unroll
-        for (int a = 0; a < NA; ++a)
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                Xe[a][k] = sV[le][a][k];
-                ge[a][k] = sG[le][a][k];
-            }
-        posflag = sPos[le];
-    } else {
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            const int32_t v = __ldg(E + (int64_t)e * NA + a);
-#pragma unroll
-            for (int k = 0; k < D; ++k) Xe[a][k] = __ldg(X + (int64_t)v * D + k);
-        }
-        bool pos = true;
-        posflag = elem_gradients<D>(Xe, sg.inv_h, ge, pos) ? (pos ? 1 : 0) : -1;
-    }
     double blk[NA * NB];
     double vol = 0.0;
-    if (posflag < 0) {
+    const int flag = elem_flag[e];
+    if (flag < 0) {
         atomicOr(&st->flags, FLAG_DEGENERATE);
         atomicMin(&st->bad_elem, e);
 #pragma unroll
-        for (int i = 0; i < NA * NB; ++i) blk[i] = 0.0;
+        for (int j = 0; j < NA * NB; ++j) blk[j] = 0.0;
     } else {
-        double T[NA][D];
+        double T[NA][D], g[NA][D];
+        pair_vertices<D>(sg, X, E, e, pair_cell[p], T);
 #pragma unroll
         for (int a = 0; a < NA; ++a)
 #pragma unroll
-            for (int k = 0; k < D; ++k) T[a][k] = (Xe[a][k] - clo[k]) * sg.inv_h[k];
+            for (int k = 0; k < D; ++k) g[a][k] = __ldg(elem_grad + ((int64_t)e * NA + a) * D + k);
         const double scale = sg.h[0] * sg.h[1] * (D == 3 ? sg.h[2] : 1.0);
-        pair_integrals<D, R>(T, ge, posflag == 1, scale, blk, &vol);
+        pair_integrals<D, R>(T, g, flag == 1, scale, blk, &vol);
     }
 #pragma unroll
-    for (int i = 0; i < NA * NB; ++i) blocks[i * slot_stride + p] = blk[i];
+    for (int j = 0; j < NA * NB; ++j) blocks[j * slot_stride + p] = blk[j];
     vols[p] = vol;
 }
 
@@ -182,21 +196,29 @@ __global__ void scatter_plain_kernel(SubGrid sg, const int32_t* __restrict__ E, 
 }  // namespace
 
 void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* X, const int32_t* E,
-                       int64_t p_begin, int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell,
-                       double* blocks, int64_t slot_stride, double* vols, DevStatus* st, cudaStream_t s) {
-    int64_t n = p_end - p_begin;
+                       const double* elem_grad, const int8_t* elem_flag, int64_t p_begin, int64_t p_end,
+                       const int32_t* pair_elem, const int32_t* pair_cell, uint8_t* keys, int32_t* perm,
+                       int32_t* buckets, double* blocks, int64_t slot_stride, double* vols, DevStatus* st,
+                       cudaStream_t s) {
+    const int64_t n = p_end - p_begin;
     if (n <= 0) return;
-    unsigned nb = (unsigned)((n + kClipThreads - 1) / kClipThreads);
+    cudaMemsetAsync(buckets, 0, sizeof(int32_t) * 2 * kClasses, s);
+    const unsigned nb256 = (unsigned)((n + 255) / 256);
+    if (dim == 2) { pair_class_kernel<2><<<nb256, 256, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, keys, buckets); count_launch(); }
+    else { pair_class_kernel<3><<<nb256, 256, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, keys, buckets); count_launch(); }
+    { class_scan_kernel<<<1, 32, 0, s>>>(buckets, buckets + kClasses); count_launch(); }
+    { pair_scatter_kernel<<<nb256, 256, 0, s>>>(n, keys, buckets + kClasses, perm); count_launch(); }
+    const unsigned nb = (unsigned)((n + kClipThreads - 1) / kClipThreads);
     if (dim == 2) {
         if (precision == L2X_MIXED)
-            { clip_fused_kernel<2, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
+            { clip_fused_kernel<2, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, elem_grad, elem_flag, p_begin, n, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
         else
-            { clip_fused_kernel<2, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
+            { clip_fused_kernel<2, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, elem_grad, elem_flag, p_begin, n, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
     } else {
         if (precision == L2X_MIXED)
-            { clip_fused_kernel<3, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
+            { clip_fused_kernel<3, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, elem_grad, elem_flag, p_begin, n, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
         else
-            { clip_fused_kernel<3, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
+            { clip_fused_kernel<3, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, elem_grad, elem_flag, p_begin, n, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
     }
 }
 

@@ -308,6 +308,45 @@ __device__ __forceinline__ bool elem_gradients(const double (&X)[D + 1][D], cons
     return true;
 }
 
+// Classification of a pair from the element's vertices in cell-local
+// coordinates: returns false if the overlap has zero measure; sets the masks of
+// crossed lower / upper cell planes and of vertices inside the closed cell.
+template <int D>
+__device__ __forceinline__ bool classify_pair(const double (&T)[D + 1][D], long long (&kmin)[D], long long (&kmax)[D],
+                                              int& lower_mask, int& upper_mask, int& inside_mask) {
+    constexpr int NA = D + 1;
+    constexpr long long K1 = 0x3ff0000000000000LL;  // order key of 1.0 (key of +0.0 is 0)
+    lower_mask = upper_mask = 0;
+    inside_mask = (1 << NA) - 1;
+    bool live = true;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        kmin[k] = LLONG_MAX;
+        kmax[k] = LLONG_MIN;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const long long kk = order_key(T[a][k]);
+            kmin[k] = min(kmin[k], kk);
+            kmax[k] = max(kmax[k], kk);
+            if (kk < 0 || kk > K1) inside_mask &= ~(1 << a);
+        }
+        if (kmax[k] <= 0 || kmin[k] >= K1) live = false;
+        if (kmin[k] < 0) lower_mask |= 1 << k;
+        if (kmax[k] > K1) upper_mask |= 1 << k;
+    }
+    return live;
+}
+
+// Scheduling class of a pair (pairs of one class run similar code paths):
+// 0 = no overlap, else 1 + 2 * (crossed cell planes) + (a vertex inside the cell).
+template <int D>
+__device__ __forceinline__ int pair_class(const double (&T)[D + 1][D]) {
+    long long kmin[D], kmax[D];
+    int lo, up, in;
+    if (!classify_pair<D>(T, kmin, kmax, lo, up, in)) return 0;
+    return 1 + 2 * (__popc(lo) + __popc(up)) + (in ? 1 : 0);
+}
+
 // Clip + integrate one pair.  T: element vertices in cell-local coordinates;
 // g, positive: from elem_gradients; scale = volume of the cell.  Writes the
 // (d+1)*2^d block and the intersection volume.
@@ -321,24 +360,9 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     *vol = 0.0;
 #pragma unroll
     for (int i = 0; i < NA * NB; ++i) block[i] = 0.0;
-    // classification of the vertices against the cell, by integer keys
     long long kmin[D], kmax[D];
-    int lower_mask = 0, upper_mask = 0, inside_mask = (1 << NA) - 1;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        kmin[k] = LLONG_MAX;
-        kmax[k] = LLONG_MIN;
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            const long long kk = order_key(T[a][k]);
-            kmin[k] = min(kmin[k], kk);
-            kmax[k] = max(kmax[k], kk);
-            if (kk < 0 || kk > K1) inside_mask &= ~(1 << a);
-        }
-        if (kmax[k] <= 0 || kmin[k] >= K1) return;  // no overlap of positive measure
-        if (kmin[k] < 0) lower_mask |= 1 << k;
-        if (kmax[k] > K1) upper_mask |= 1 << k;
-    }
+    int lower_mask, upper_mask, inside_mask;
+    if (!classify_pair<D>(T, kmin, kmax, lower_mask, upper_mask, inside_mask)) return;  // no overlap of positive measure
     const int apex_v = inside_mask ? __ffs(inside_mask) - 1 : -1;
     double A[D];
 #pragma unroll
@@ -422,11 +446,23 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
             clo[k] = -A[k];
             chi[k] = 1.0 - A[k];
         }
-        // element faces: face opposite vertex f, outward for a positive element
+        // crossed cell planes as a compact list (its length is the same for every
+        // pair of a scheduling class, so the loops below stay converged)
+        int plane_k[6], plane_up[6];
+        double plane_c[6];
+        int n_planes = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if ((lower_mask >> k) & 1) { plane_k[n_planes] = k; plane_up[n_planes] = 0; plane_c[n_planes] = clo[k]; ++n_planes; }
+            if ((upper_mask >> k) & 1) { plane_k[n_planes] = k; plane_up[n_planes] = 1; plane_c[n_planes] = chi[k]; ++n_planes; }
+        }
+        // element faces: face opposite vertex f, outward for a positive element;
+        // with an element vertex as apex only the face opposite it has a cone
         const int faces[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+        const int n_faces = apex_v >= 0 ? 1 : 4;
 #pragma unroll 1
-        for (int f = 0; f < 4; ++f) {
-            if (apex_v >= 0 && apex_v != f) continue;  // face contains the apex: zero cone
+        for (int jf = 0; jf < n_faces; ++jf) {
+            const int f = apex_v >= 0 ? apex_v : jf;
             int n = 3;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -436,42 +472,38 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
             }
             double (*cur)[D] = bufA;
             double (*nxt)[D] = bufB;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (n > 0 && ((lower_mask >> k) & 1)) { n = clip_axis<D>(cur, n, nxt, k, clo[k], false); double (*t)[D] = cur; cur = nxt; nxt = t; }
-                if (n > 0 && ((upper_mask >> k) & 1)) { n = clip_axis<D>(cur, n, nxt, k, chi[k], true); double (*t)[D] = cur; cur = nxt; nxt = t; }
+#pragma unroll 1
+            for (int jp = 0; jp < n_planes; ++jp) {
+                n = clip_axis<D>(cur, n, nxt, plane_k[jp], plane_c[jp], plane_up[jp] != 0);
+                double (*t)[D] = cur; cur = nxt; nxt = t;
             }
             accum_polygon<D, R>(cur, n, acc);
         }
         // cell faces the element crosses, clipped to the element
 #pragma unroll 1
-        for (int side = 0; side < 2; ++side) {
-            const int mask = side == 0 ? lower_mask : upper_mask;
-#pragma unroll 1
-            for (int k = 0; k < 3; ++k) {
-                if (!((mask >> k) & 1)) continue;
-                const int i1 = (k + 1) % 3, i2 = (k + 2) % 3;
-                const double ck = side == 1 ? chi[k] : clo[k];
-                const double a1[4] = {clo[i1], chi[i1], chi[i1], clo[i1]};
-                const double a2[4] = {clo[i2], clo[i2], chi[i2], chi[i2]};
+        for (int jp = 0; jp < n_planes; ++jp) {
+            const int k = plane_k[jp];
+            const int side = plane_up[jp];
+            const int j1 = (k + 1) % 3, j2 = (k + 2) % 3;
+            const double ck = plane_c[jp];
+            const double a1[4] = {clo[j1], chi[j1], chi[j1], clo[j1]};
+            const double a2[4] = {clo[j2], clo[j2], chi[j2], chi[j2]};
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int s = side == 1 ? v : 3 - v;  // outward: +e_k on t_k = 1, -e_k on t_k = 0
-                    bufA[v][k] = ck;
-                    bufA[v][i1] = a1[s];
-                    bufA[v][i2] = a2[s];
-                }
-                int n = 4;
-                double (*cur)[D] = bufA;
-                double (*nxt)[D] = bufB;
-#pragma unroll
-                for (int a = 0; a < NA; ++a) {
-                    if (n == 0) break;
-                    n = clip_plane<D>(cur, n, nxt, g[a], cA[a]);
-                    double (*t)[D] = cur; cur = nxt; nxt = t;
-                }
-                accum_polygon<D, R>(cur, n, acc);
+            for (int v = 0; v < 4; ++v) {
+                const int sidx = side == 1 ? v : 3 - v;  // outward: +e_k on t_k = 1, -e_k on t_k = 0
+                bufA[v][k] = ck;
+                bufA[v][j1] = a1[sidx];
+                bufA[v][j2] = a2[sidx];
             }
+            int n = 4;
+            double (*cur)[D] = bufA;
+            double (*nxt)[D] = bufB;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                n = clip_plane<D>(cur, n, nxt, g[a], cA[a]);
+                double (*t)[D] = cur; cur = nxt; nxt = t;
+            }
+            accum_polygon<D, R>(cur, n, acc);
         }
         finish_moments3<R>(acc);
     }

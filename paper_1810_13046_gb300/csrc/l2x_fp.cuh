@@ -76,7 +76,7 @@ __device__ __forceinline__ double div_nr(double a, double b) {
 
 // Double-float value (hi + lo) and its sum with a second one (Knuth's two-sum,
 // renormalised); single-precision instructions only.
-struct DF {
+struct __align__(8) DF {
     float hi, lo;
 };
 

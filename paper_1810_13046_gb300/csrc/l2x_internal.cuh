@@ -74,7 +74,7 @@ void count_launch();
 // pairs (l2x_pairs.cu)
 void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const double* X,
                        const int32_t* E, ElemBox* boxes, int64_t* counts, int32_t* node_box,
-                       double* elem_vol, DevStatus* st, cudaStream_t s);
+                       double* elem_vol, double* elem_grad, int8_t* elem_flag, DevStatus* st, cudaStream_t s);
 void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
 size_t scan_tmp_bytes(int64_t n);
 void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const ElemBox* boxes,
@@ -82,9 +82,15 @@ void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
 
 // clipping + quadrature (l2x_clip.cu).  Pair blocks are stored at
 // blocks[slot * slot_stride + p * pair_stride], slot = a * 2^d + b.
+// Fused: pairs are first bucketed by scheduling class (similar control flow per
+// warp), then clipped in bucket order.  keys: uint8 per pair; perm: int32 per
+// pair (offsets from p_begin); buckets: 2 * kClasses int32 scratch.
+constexpr int kClasses = 16;
 void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* X, const int32_t* E,
-                       int64_t p_begin, int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell,
-                       double* blocks, int64_t slot_stride, double* vols, DevStatus* st, cudaStream_t s);
+                       const double* elem_grad, const int8_t* elem_flag, int64_t p_begin, int64_t p_end,
+                       const int32_t* pair_elem, const int32_t* pair_cell, uint8_t* keys, int32_t* perm,
+                       int32_t* buckets, double* blocks, int64_t slot_stride, double* vols, DevStatus* st,
+                       cudaStream_t s);
 void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
                        int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, double* blocks,
                        double* vols, DevStatus* st, cudaStream_t s);

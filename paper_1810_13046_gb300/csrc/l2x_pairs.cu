@@ -7,6 +7,7 @@
 // list is reproducible bit for bit on any IEEE machine.
 #include <climits>
 
+#include "l2x_clip.cuh"
 #include "l2x_internal.cuh"
 
 namespace l2x {
@@ -23,7 +24,8 @@ template <int D>
 __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const double* __restrict__ X,
                                   const int32_t* __restrict__ E, ElemBox* __restrict__ boxes,
                                   int64_t* __restrict__ counts, int32_t* __restrict__ node_box,
-                                  double* __restrict__ elem_vol, DevStatus* st) {
+                                  double* __restrict__ elem_vol, double* __restrict__ elem_grad,
+                                  int8_t* __restrict__ elem_flag, DevStatus* st) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= m) return;
     double V[D + 1][D];
@@ -45,6 +47,17 @@ __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const 
         det = a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0);
     }
     elem_vol[e] = fabs(det) / (D == 2 ? 2.0 : 6.0);
+    if (elem_grad) {
+        // barycentric gradients in cell-local coordinates (the same for every grid)
+        double g[D + 1][D];
+        bool pos = true;
+        const bool ok = finite && elem_gradients<D>(V, sgs.g[0].inv_h, g, pos);
+#pragma unroll
+        for (int a = 0; a <= D; ++a)
+#pragma unroll
+            for (int k = 0; k < D; ++k) elem_grad[(e * (D + 1) + a) * D + k] = ok ? g[a][k] : 0.0;
+        elem_flag[e] = ok ? (pos ? 1 : 0) : -1;
+    }
     int32_t flags = 0;
     if (!finite) flags |= FLAG_NONFINITE;
     else if (det == 0.0) flags |= FLAG_DEGENERATE;
@@ -197,16 +210,16 @@ __global__ void scan_apply_kernel(const int64_t* __restrict__ in, int64_t n, con
 
 void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const double* X,
                        const int32_t* E, ElemBox* boxes, int64_t* counts, int32_t* node_box,
-                       double* elem_vol, DevStatus* st, cudaStream_t s) {
+                       double* elem_vol, double* elem_grad, int8_t* elem_flag, DevStatus* st, cudaStream_t s) {
     SubGridSet sgs{};
     for (int g = 0; g < n_grids; ++g) sgs.g[g] = sg_host[g];
     int threads = 256;
     int64_t blocks = (m + threads - 1) / threads;
     if (blocks == 0) return;
     if (dim == 2)
-        { elem_boxes_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, st); count_launch(); }
+        { elem_boxes_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, elem_grad, elem_flag, st); count_launch(); }
     else
-        { elem_boxes_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, st); count_launch(); }
+        { elem_boxes_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, elem_grad, elem_flag, st); count_launch(); }
 }
 
 size_t scan_tmp_bytes(int64_t n) {
