@@ -41,21 +41,21 @@ WORKLOAD_DESC = ("3-D staggered Q1 grids 128^3 cells (h=1/128) on [0,1]^3; rotat
                  "48,000 P1 tets / 10,206 nodes; Taylor-Green u_f (f32); N(0,1) nodal forces")
 # FP64 pipe peak derived from the unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# Executed FP64 flops per candidate pair of the fused clip kernel (mixed form) on this workload,
-# from the ncu SASS instruction counters (2*DFMA + DADD + DMUL) of one launch divided by its pairs;
-# profiles/clip_fused_beam128.md.  None until measured.
-FP64_FLOPS_PER_PAIR = None
-CLIP_DRAM_BYTES_PER_PAIR = None
+# FP64 flops per candidate pair executed by the fused clip kernel (mixed form) on this workload:
+# ncu SASS instruction counters of one launch, (2*DFMA + DADD + DMUL) / pairs = 169.3e6 / 238254;
+# DRAM bytes per pair from the same capture (read + write).  profiles/clip_fused_beam128.md.
+FP64_FLOPS_PER_PAIR = 711.0
+CLIP_DRAM_BYTES_PER_PAIR = 823.6
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -275,7 +275,7 @@ def main():
     ph = info["phase_ms"]
     calls = info["phase_calls"]
     clip_launch_ms = ph["clip"] / max(1, calls["clip"])
-    clip_pairs_per_launch = pairs / 3.0
+    clip_pairs_per_launch = pairs / max(1, calls["clip"] // args.steps)
 
     # comparison forms (fewer steps)
     cp, ip, pb, pa, _, _, _ = run_form(l2x.PLAIN, l2x.FP64, args.plain_steps, 2)
@@ -332,6 +332,8 @@ def main():
         achieved = FP64_FLOPS_PER_PAIR * clip_pairs_per_launch / (clip_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "clip_fused_kernel<3,float>",
+                "launch_ms": clip_launch_ms, "pairs_per_launch": clip_pairs_per_launch,
+                "flops_per_pair": FP64_FLOPS_PER_PAIR,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and clock)",
                 "traffic": (CLIP_DRAM_BYTES_PER_PAIR * clip_pairs_per_launch
                             if CLIP_DRAM_BYTES_PER_PAIR is not None else None)}

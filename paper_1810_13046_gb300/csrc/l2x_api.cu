@@ -313,14 +313,19 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
     // (II)-(III) clip + quadrature
     const bool plain = h->opts.path == L2X_PATH_PLAIN;
     for (int g = 0; g < G; ++g) {
+        if (!plain) {
+            PhaseScope ph_cls(h, L2X_PH_PAIRS, s);
+            launch_pair_classes(d, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->pair_key,
+                                h->pair_perm, h->buckets, s);
+        }
         PhaseScope ph(h, L2X_PH_CLIP, s);
         if (plain)
             launch_clip_plain(d, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks,
                               h->vols, h->st, s);
         else
             launch_clip_fused(d, h->opts.precision, h->sg[g], h->X, h->E, h->elem_grad, h->elem_flag, gb[g],
-                              gb[g + 1], h->pair_elem, h->pair_cell, h->pair_key, h->pair_perm, h->buckets,
-                              h->blocks, h->pair_cap, h->vols, h->st, s);
+                              gb[g + 1], h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->pair_cap, h->vols,
+                              h->st, s);
     }
     // (IV) B_g by rows
     for (int g = 0; g < G; ++g) {

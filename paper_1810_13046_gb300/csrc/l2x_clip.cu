@@ -195,11 +195,9 @@ __global__ void scatter_plain_kernel(SubGrid sg, const int32_t* __restrict__ E, 
 
 }  // namespace
 
-void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* X, const int32_t* E,
-                       const double* elem_grad, const int8_t* elem_flag, int64_t p_begin, int64_t p_end,
-                       const int32_t* pair_elem, const int32_t* pair_cell, uint8_t* keys, int32_t* perm,
-                       int32_t* buckets, double* blocks, int64_t slot_stride, double* vols, DevStatus* st,
-                       cudaStream_t s) {
+void launch_pair_classes(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
+                         int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, uint8_t* keys,
+                         int32_t* perm, int32_t* buckets, cudaStream_t s) {
     const int64_t n = p_end - p_begin;
     if (n <= 0) return;
     cudaMemsetAsync(buckets, 0, sizeof(int32_t) * 2 * kClasses, s);
@@ -208,6 +206,14 @@ void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* 
     else { pair_class_kernel<3><<<nb256, 256, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, keys, buckets); count_launch(); }
     { class_scan_kernel<<<1, 32, 0, s>>>(buckets, buckets + kClasses); count_launch(); }
     { pair_scatter_kernel<<<nb256, 256, 0, s>>>(n, keys, buckets + kClasses, perm); count_launch(); }
+}
+
+void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* X, const int32_t* E,
+                       const double* elem_grad, const int8_t* elem_flag, int64_t p_begin, int64_t p_end,
+                       const int32_t* pair_elem, const int32_t* pair_cell, const int32_t* perm, double* blocks,
+                       int64_t slot_stride, double* vols, DevStatus* st, cudaStream_t s) {
+    const int64_t n = p_end - p_begin;
+    if (n <= 0) return;
     const unsigned nb = (unsigned)((n + kClipThreads - 1) / kClipThreads);
     if (dim == 2) {
         if (precision == L2X_MIXED)

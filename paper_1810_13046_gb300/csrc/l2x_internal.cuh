@@ -83,14 +83,16 @@ void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
 // clipping + quadrature (l2x_clip.cu).  Pair blocks are stored at
 // blocks[slot * slot_stride + p * pair_stride], slot = a * 2^d + b.
 // Fused: pairs are first bucketed by scheduling class (similar control flow per
-// warp), then clipped in bucket order.  keys: uint8 per pair; perm: int32 per
-// pair (offsets from p_begin); buckets: 2 * kClasses int32 scratch.
+// warp, launch_pair_classes), then clipped in bucket order.  keys: uint8 per
+// pair; perm: int32 per pair (offsets from p_begin); buckets: 2 * kClasses int32.
 constexpr int kClasses = 16;
+void launch_pair_classes(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
+                         int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, uint8_t* keys,
+                         int32_t* perm, int32_t* buckets, cudaStream_t s);
 void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* X, const int32_t* E,
                        const double* elem_grad, const int8_t* elem_flag, int64_t p_begin, int64_t p_end,
-                       const int32_t* pair_elem, const int32_t* pair_cell, uint8_t* keys, int32_t* perm,
-                       int32_t* buckets, double* blocks, int64_t slot_stride, double* vols, DevStatus* st,
-                       cudaStream_t s);
+                       const int32_t* pair_elem, const int32_t* pair_cell, const int32_t* perm, double* blocks,
+                       int64_t slot_stride, double* vols, DevStatus* st, cudaStream_t s);
 void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
                        int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, double* blocks,
                        double* vols, DevStatus* st, cudaStream_t s);
