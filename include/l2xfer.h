@@ -176,6 +176,12 @@ l2x_status l2x_query(l2x_handle h, l2x_info* info);
 l2x_status l2x_export_pairs(l2x_handle h, int32_t grid, int32_t* elem, int32_t* cell, void* stream);
 l2x_status l2x_export_pair_blocks(l2x_handle h, int32_t grid, double* blocks, double* vols,
                                   void* stream);
+/* The same for the pairs of elements [e_first, e_first + n_elems) of grid g only
+ * (contiguous in the element-major list).  *first_pair and *n_pairs (host) receive
+ * the range; pass NULL arrays to query the range alone. */
+l2x_status l2x_export_pair_range(l2x_handle h, int32_t grid, int64_t e_first, int64_t n_elems,
+                                 int64_t* first_pair, int64_t* n_pairs, int32_t* elem, int32_t* cell,
+                                 double* blocks, double* vols, void* stream);
 l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t* cols,
                           double* vals, void* stream);
 

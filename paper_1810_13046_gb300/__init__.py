@@ -93,6 +93,8 @@ def load_library(build_if_missing: bool = True):
         "l2x_export_pairs": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
         "l2x_export_pair_blocks": ([P, ctypes.c_int32, P, P, P], ctypes.c_int),
         "l2x_export_csr": ([P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
+        "l2x_export_pair_range": ([P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64), P, P, P, P, P], ctypes.c_int),
         "l2x_destroy": ([P], ctypes.c_int),
         "l2x_set_timing": ([P, ctypes.c_int32], ctypes.c_int),
         "l2x_kernel_launch_count": ([], ctypes.c_int64),
@@ -307,6 +309,24 @@ class Coupling:
         _check(load_library().l2x_export_pair_blocks(self._h, g, ctypes.c_void_p(b.data_ptr()),
                                                      ctypes.c_void_p(v.data_ptr()), _stream_ptr(self.device)))
         return b, v
+
+    def export_pair_range(self, g: int, e_first: int, n_elems: int):
+        """Pairs, blocks and volumes of the elements [e_first, e_first + n_elems) on grid g."""
+        lib = load_library()
+        p0, npairs = ctypes.c_int64(0), ctypes.c_int64(0)
+        st = _stream_ptr(self.device)
+        _check(lib.l2x_export_pair_range(self._h, g, e_first, n_elems, ctypes.byref(p0), ctypes.byref(npairs),
+                                         None, None, None, None, st))
+        n = npairs.value
+        d = self.dim
+        e = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        c = torch.empty(max(n, 1), dtype=torch.int32, device=self.device)
+        b = torch.empty((max(n, 1), d + 1, 1 << d), dtype=torch.float64, device=self.device)
+        v = torch.empty(max(n, 1), dtype=torch.float64, device=self.device)
+        _check(lib.l2x_export_pair_range(self._h, g, e_first, n_elems, None, None, ctypes.c_void_p(e.data_ptr()),
+                                         ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                         ctypes.c_void_p(v.data_ptr()), st))
+        return e[:n], c[:n], b[:n], v[:n]
 
     def export_csr(self, which: int):
         """(row_ptr int64, cols int32, vals float64) of B_which (0..n_grids-1) or M_s (which=3)."""

@@ -714,6 +714,38 @@ l2x_status l2x_export_pair_blocks(l2x_handle h, int32_t grid, double* blocks, do
     return L2X_OK;
 }
 
+l2x_status l2x_export_pair_range(l2x_handle h, int32_t grid, int64_t e_first, int64_t n_elems,
+                                 int64_t* first_pair, int64_t* n_pairs, int32_t* elem, int32_t* cell,
+                                 double* blocks, double* vols, void* stream) {
+    if (!h || grid < 0 || grid >= h->n_grids || e_first < 0 || n_elems < 0 || e_first + n_elems > h->n_elems)
+        return fail(L2X_EINVAL, "bad export_pair_range arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t m = h->n_elems;
+    int64_t p0 = 0, p1 = 0;
+    L2X_CUDA(cudaMemcpyAsync(&p0, h->offsets + (int64_t)grid * m + e_first, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    L2X_CUDA(cudaMemcpyAsync(&p1, h->offsets + (int64_t)grid * m + e_first + n_elems, sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, s));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    const int64_t np = p1 - p0;
+    if (first_pair) *first_pair = p0 - h->pair_begin[grid];
+    if (n_pairs) *n_pairs = np;
+    const int NS = (h->dim + 1) << h->dim;
+    if (elem) L2X_CUDA(cudaMemcpyAsync(elem, h->pair_elem + p0, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, s));
+    if (cell) L2X_CUDA(cudaMemcpyAsync(cell, h->pair_cell + p0, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, s));
+    if (vols) L2X_CUDA(cudaMemcpyAsync(vols, h->vols + p0, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
+    if (blocks) {
+        if (h->opts.path == L2X_PATH_PLAIN) {
+            L2X_CUDA(cudaMemcpyAsync(blocks, h->blocks + p0 * NS, sizeof(double) * np * NS, cudaMemcpyDeviceToDevice, s));
+        } else {
+            for (int slot = 0; slot < NS; ++slot)
+                L2X_CUDA(cudaMemcpy2DAsync(blocks + slot, sizeof(double) * NS, h->blocks + slot * h->pair_cap + p0,
+                                           sizeof(double), sizeof(double), np, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    L2X_CUDA(cudaStreamSynchronize(s));
+    return L2X_OK;
+}
+
 l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t* cols, double* vals, void* stream) {
     if (!h || !row_ptr || !cols || !vals) return fail(L2X_EINVAL, "bad export_csr arguments");
     const Csr* A = nullptr;

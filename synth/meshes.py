@@ -180,15 +180,18 @@ def _signed_volumes(X, E):
 
 def deformed_beam_mesh(nx=320, ny=80, nz=26, size=(0.4, 0.1, 0.02), sigma_rel=0.02,
                        sweeps=10, seed=0, max_tries=8):
-    """Beam with node displacements N(0, sigma_rel*width), then Laplacian-smoothed.
+    """Beam with node displacements N(0, sigma_rel * thickness), then smoothed.
 
-    Smoothing averages each node with its 6 lattice neighbours ``sweeps`` times.
+    The beam's smallest dimension (its thickness, 0.02) is read as the "width"
+    the displacement amplitude is relative to; relative to the 0.1 side the
+    unsmoothed noise would be larger than the elements.  Smoothing replaces each
+    node's displacement by the mean of its 6 lattice neighbours ``sweeps`` times.
     A sample whose tetrahedra change orientation is rejected and redrawn.
     """
     rng = np.random.default_rng(seed)
     X0, E = beam_mesh(nx, ny, nz, size)
     sign0 = np.sign(_signed_volumes(X0, E))
-    sigma = sigma_rel * size[1]
+    sigma = sigma_rel * min(size)
     shape = (nx + 1, ny + 1, nz + 1)
     for _ in range(max_tries):
         D = rng.normal(0.0, sigma, size=X0.shape).reshape(shape[2], shape[1], shape[0], 3)
