@@ -123,6 +123,7 @@ typedef struct l2x_info {
 } l2x_info;
 
 typedef struct l2x_coupling* l2x_handle;
+typedef struct l2x_step_graph* l2x_graph;
 
 /* Fills *opts with the defaults: fused path, FP64, cg_rtol 1e-13, 200 iterations,
  * DUAL force mode, scale 1. */
@@ -162,6 +163,26 @@ l2x_status l2x_apply_B(l2x_handle h, const void* const* x_f, void* const* y_s, v
 l2x_status l2x_apply_BT(l2x_handle h, const void* const* z_s, void* const* f_f, double scale,
                         void* stream);
 l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s, void* stream);
+
+/* One time step as a CUDA graph (the batched moving-bodies pattern): a mesh made
+ * of many bodies (disjoint node sets in one l2x_mesh) is re-assembled in its
+ * current configuration and both transfers run, with no host synchronisation,
+ * by one cudaGraphLaunch per step.  Each replay copies the node positions from
+ * coords_src (device, n_nodes x dim, read at replay time), rebuilds B_g, B_g^T
+ * and M_s, writes u_s = M_s^-1 B u_f and f_f (+)= s B^T (M_s^-1) f_s (zeroed first
+ * if zero_force != 0); all pointers are fixed at creation.  Pair and entry
+ * capacities are the current sizes times capacity_margin (>= 1); a replay that
+ * needs more sets a flag and skips its work, reported by l2x_graph_sync_status
+ * as L2X_ECAPACITY (create the graph again).  Fused path only; `stream` must
+ * not be the legacy default stream.  While a graph exists, use the handle only
+ * through it.  l2x_graph_sync_status waits for the stream and returns the
+ * status of the last replay (capacity, degenerate or out-of-grid elements, CG). */
+l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* const* u_f, void* const* u_s,
+                            const void* const* f_s, void* const* f_f, double capacity_margin, int32_t zero_force,
+                            void* stream, l2x_graph* out);
+l2x_status l2x_graph_launch(l2x_graph g, void* stream);
+l2x_status l2x_graph_sync_status(l2x_graph g, void* stream);
+l2x_status l2x_graph_destroy(l2x_graph g);
 
 /* Sizes and solver statistics of a coupling (host struct). */
 l2x_status l2x_query(l2x_handle h, l2x_info* info);

@@ -18,7 +18,7 @@ import torch
 
 from . import build as _build
 
-__all__ = ["kernel_launch_count", "PHASES", "Coupling", "Grid", "VelocityTransfer", "ForceTransfer", "L2XError", "library_path", "load_library",
+__all__ = ["kernel_launch_count", "PHASES", "StepGraph", "Coupling", "Grid", "VelocityTransfer", "ForceTransfer", "L2XError", "library_path", "load_library",
            "PLAIN", "FUSED", "FP64", "MIXED", "NODAL", "DUAL"]
 
 PLAIN, FUSED = 0, 1
@@ -97,6 +97,11 @@ def load_library(build_if_missing: bool = True):
                                    ctypes.POINTER(ctypes.c_int64), P, P, P, P, P], ctypes.c_int),
         "l2x_destroy": ([P], ctypes.c_int),
         "l2x_set_timing": ([P, ctypes.c_int32], ctypes.c_int),
+        "l2x_graph_create": ([P, P, PP, PP, PP, PP, ctypes.c_double, ctypes.c_int32, P,
+                              ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "l2x_graph_launch": ([P, P], ctypes.c_int),
+        "l2x_graph_sync_status": ([P, P], ctypes.c_int),
+        "l2x_graph_destroy": ([P], ctypes.c_int),
         "l2x_kernel_launch_count": ([], ctypes.c_int64),
         "l2x_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "l2x_last_error": ([], ctypes.c_char_p),
@@ -292,6 +297,13 @@ class Coupling:
             _check(load_library().l2x_solve_mass(self._h, _ptrs(y_s), _ptrs(w), _stream_ptr(self.device)))
         return w
 
+    # ------------------------------------------------------------------ captured steps
+    def capture_step(self, coords_src, u_f, u_s, f_s, f_f, margin: float = 1.5, zero_force: bool = True,
+                     stream=None):
+        """A CUDA graph that re-assembles the coupling for the positions in
+        ``coords_src`` and runs both transfers; see :class:`StepGraph`."""
+        return StepGraph(self, coords_src, u_f, u_s, f_s, f_f, margin, zero_force, stream)
+
     # ------------------------------------------------------------------ exports (tests)
     def export_pairs(self, g: int):
         n = self.info()["n_pairs"][g]
@@ -339,6 +351,48 @@ class Coupling:
                                              ctypes.c_void_p(cols.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
                                              _stream_ptr(self.device)))
         return rp, cols[:nnz], vals[:nnz]
+
+
+class StepGraph:
+    """One time step of a (multi-body) coupling captured as a CUDA graph.
+
+    Every :meth:`launch` copies the node positions from ``coords_src``, rebuilds
+    B_g, B_g^T and M_s and runs the velocity and force transfers into the arrays
+    given at capture time, without host synchronisation.  :meth:`status` waits
+    and raises :class:`L2XError` if the last replay overflowed the capacities
+    (create a new graph with a larger margin) or CG did not converge."""
+
+    def __init__(self, c: Coupling, coords_src, u_f, u_s, f_s, f_f, margin, zero_force, stream):
+        lib = load_library()
+        self.c = c
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=c.device)
+        # keep the buffers alive as long as the graph
+        self.buffers = (coords_src, list(u_f), list(u_s), list(f_s), list(f_f))
+        g = ctypes.c_void_p()
+        torch.cuda.current_stream(c.device).synchronize()
+        with torch.cuda.device(c.device):
+            _check(lib.l2x_graph_create(c._h, ctypes.c_void_p(coords_src.data_ptr()), _ptrs(u_f), _ptrs(u_s),
+                                        _ptrs(f_s), _ptrs(f_f), float(margin), int(bool(zero_force)),
+                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(g)))
+        self._g = g
+
+    def launch(self):
+        """Replay one step, ordered after the work already queued on the current
+        stream (e.g. the copy of new positions into coords_src) and before
+        anything queued on it afterwards."""
+        cur = torch.cuda.current_stream(self.c.device)
+        self.stream.wait_stream(cur)
+        _check(load_library().l2x_graph_launch(self._g, ctypes.c_void_p(self.stream.cuda_stream)))
+        cur.wait_stream(self.stream)
+
+    def status(self):
+        _check(load_library().l2x_graph_sync_status(self._g, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def __del__(self):
+        g = getattr(self, "_g", None)
+        if g is not None and g.value and _lib is not None:
+            _lib.l2x_graph_destroy(g)
+            self._g = None
 
 
 # ---------------------------------------------------------------------- autograd

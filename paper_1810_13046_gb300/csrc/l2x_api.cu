@@ -308,24 +308,26 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         L2X_TRY(dalloc(&h->pair_perm, cap));
         h->pair_cap = cap;
     }
-    launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, s);
+    launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, h->pair_cap, h->st, s);
     ph_pairs.reset();
     // (II)-(III) clip + quadrature
     const bool plain = h->opts.path == L2X_PATH_PLAIN;
-    for (int g = 0; g < G; ++g) {
-        if (!plain) {
-            PhaseScope ph_cls(h, L2X_PH_PAIRS, s);
-            launch_pair_classes(d, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->pair_key,
-                                h->pair_perm, h->buckets, s);
-        }
-        PhaseScope ph(h, L2X_PH_CLIP, s);
-        if (plain)
+    if (plain) {
+        for (int g = 0; g < G; ++g) {
+            PhaseScope ph(h, L2X_PH_CLIP, s);
             launch_clip_plain(d, h->sg[g], h->X, h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks,
                               h->vols, h->st, s);
-        else
-            launch_clip_fused(d, h->opts.precision, h->sg[g], h->X, h->E, h->elem_grad, h->elem_flag, gb[g],
-                              gb[g + 1], h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->pair_cap, h->vols,
-                              h->st, s);
+        }
+    } else {
+        {
+            PhaseScope ph_cls(h, L2X_PH_PAIRS, s);
+            launch_pair_classes(d, G, h->sg, m, h->offsets, NP, h->pair_cap, h->X, h->E, h->pair_elem, h->pair_cell,
+                                h->pair_key, h->pair_perm, h->buckets, s);
+        }
+        PhaseScope ph(h, L2X_PH_CLIP, s);
+        launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, NP, h->pair_cap, h->X, h->E, h->elem_grad,
+                          h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->pair_cap, h->vols,
+                          h->st, s);
     }
     // (IV) B_g by rows
     for (int g = 0; g < G; ++g) {
@@ -402,10 +404,10 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
                 L2X_TRY(dalloc(&h->tcursor, rows + rows / 4 + 16));
                 h->tcursor_cap = rows + rows / 4 + 16;
             }
-            launch_transpose_count(B, h->sg[g], T, T.ptr, s);
+            launch_transpose_count(B, h->sg[g], T, T.ptr, h->st, s);
             launch_scan_i64(T.ptr, T.ptr, rows, h->scan_tmp, s);
-            launch_transpose_fill(B, h->sg[g], T, h->tcursor, s);
-            launch_transpose_sort(T, s);
+            launch_transpose_fill(B, h->sg[g], T, h->tcursor, h->st, s);
+            launch_transpose_sort(T, h->st, s);
             if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, nnz, s);
         }
     }
@@ -448,7 +450,75 @@ l2x_status check_ptrs(const void* const* a, int n, const char* what) {
     return L2X_OK;
 }
 
+// Enqueues one whole time step without host synchronisation: copy of the new
+// node positions, re-assembly with the capacities of the handle (overflow sets
+// FLAG_CAPACITY and later kernels skip their work), velocity transfer and dual
+// or nodal force transfer.  Used under stream capture by l2x_graph_create.
+l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* const* u_f, void* const* u_s,
+                       const void* const* f_s, void* const* f_f, bool zero_force, cudaStream_t s) {
+    const int64_t n = h->n_nodes, m = h->n_elems;
+    const int G = h->n_grids, d = h->dim;
+    L2X_CUDA(cudaMemcpyAsync(h->X, coords_src, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
+    launch_reset_status(h->st, s);
+    launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->node_box, h->elem_vol, h->elem_grad,
+                      h->elem_flag, h->st, s);
+    launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
+    launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, h->pair_cap, h->st, s);
+    launch_pair_classes(d, G, h->sg, m, h->offsets, h->pair_cap, h->pair_cap, h->X, h->E, h->pair_elem, h->pair_cell,
+                        h->pair_key, h->pair_perm, h->buckets, s);
+    launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, h->pair_cap, h->pair_cap, h->X, h->E,
+                      h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->pair_cap,
+                      h->vols, h->st, s);
+    for (int g = 0; g < G; ++g) {
+        Csr& B = h->B[g];
+        const ElemBox* bx = h->boxes + (int64_t)g * m;
+        const int64_t* off = h->offsets + (int64_t)g * m;
+        launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, h->row_count,
+                      nullptr, nullptr, nullptr, h->st, s);
+        launch_scan_i64(h->row_count, B.ptr, n, h->scan_tmp, s);
+        launch_check_capacity(B.ptr + n, h->B_cap[g], h->st, s);
+        launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, nullptr,
+                      B.ptr, B.col, B.val, h->st, s);
+        B.n_rows = n;
+        B.nnz = h->B_cap[g];  // an upper bound: the row pointers hold the actual count
+        if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, h->B_cap[g], s);
+        CsrT& T = h->T[g];
+        launch_transpose_count(B, h->sg[g], T, T.ptr, h->st, s);
+        launch_scan_i64(T.ptr, T.ptr, T.n_rows, h->scan_tmp, s);
+        launch_transpose_fill(B, h->sg[g], T, h->tcursor, h->st, s);
+        launch_transpose_sort(T, h->st, s);
+        if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, h->T_cap[g], s);
+    }
+    launch_mass_values(d, n, h->E, h->adj_ptr, h->adj, h->elem_vol, h->M.ptr, h->M.col, h->M.val, h->M_dinv, s);
+    launch_to_f32(h->M.val, h->M.val32, h->M.nnz, s);
+    launch_to_f32(h->M_dinv, h->M_dinv32, n, s);
+    // transfers
+    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+    void* tmp[kMaxGrids];
+    for (int g = 0; g < G; ++g) tmp[g] = (char*)h->vec_tmp + es * n * g;
+    launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, tmp, h->st, s);
+    solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)tmp, u_s,
+                         h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s);
+    if (zero_force)
+        for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
+    if (h->opts.force_mode == L2X_FORCE_DUAL) {
+        solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, f_s, tmp, h->opts.cg_rtol,
+                             h->opts.cg_max_iter, h->pcg_ws, h->st, s);
+        launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)tmp, f_f,
+                       h->opts.force_scale, h->st, s);
+    } else {
+        launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, f_s, f_f, h->opts.force_scale, h->st, s);
+    }
+    return L2X_OK;
+}
+
 }  // namespace
+
+struct l2x_step_graph {
+    l2x_coupling* h = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 
 extern "C" {
 
@@ -584,7 +654,7 @@ l2x_status l2x_apply_B(l2x_handle h, const void* const* x_f, void* const* y_s, v
     L2X_TRY(check_ptrs((const void* const*)y_s, h->n_grids, "y_s"));
     cudaStream_t s = (cudaStream_t)stream;
     PhaseScope ph(h, L2X_PH_SPMV_B, s);
-    launch_spmv_B(h->opts.path, h->opts.precision, h->n_grids, h->B, x_f, y_s, s);
+    launch_spmv_B(h->opts.path, h->opts.precision, h->n_grids, h->B, x_f, y_s, h->st, s);
     L2X_CUDA(cudaGetLastError());
     return L2X_OK;
 }
@@ -595,7 +665,7 @@ l2x_status l2x_apply_BT(l2x_handle h, const void* const* z_s, void* const* f_f, 
     L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
     cudaStream_t s = (cudaStream_t)stream;
     PhaseScope ph(h, L2X_PH_SPMV_BT, s);
-    launch_spmv_BT(h->opts.path, h->opts.precision, h->n_grids, h->B, h->T, h->sg, z_s, f_f, scale, s);
+    launch_spmv_BT(h->opts.path, h->opts.precision, h->n_grids, h->B, h->T, h->sg, z_s, f_f, scale, h->st, s);
     L2X_CUDA(cudaGetLastError());
     return L2X_OK;
 }
@@ -639,6 +709,139 @@ l2x_status l2x_transfer_force(l2x_handle h, const void* const* f_s, void* const*
     for (int g = 0; g < h->n_grids; ++g) z[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
     L2X_TRY(l2x_solve_mass(h, f_s, z, stream));
     return l2x_apply_BT(h, (const void* const*)z, f_f, h->opts.force_scale, stream);
+}
+
+l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* const* u_f, void* const* u_s,
+                            const void* const* f_s, void* const* f_f, double capacity_margin, int32_t zero_force,
+                            void* stream, l2x_graph* out) {
+    g_last_error.clear();
+    if (!h || !out || !coords_src) return fail(L2X_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (h->opts.path != L2X_PATH_FUSED) return fail(L2X_EINVAL, "step graphs need the fused path");
+    if (!(capacity_margin >= 1.0)) return fail(L2X_EINVAL, "capacity_margin must be >= 1");
+    L2X_TRY(check_ptrs(u_f, h->n_grids, "u_f"));
+    L2X_TRY(check_ptrs((const void* const*)u_s, h->n_grids, "u_s"));
+    L2X_TRY(check_ptrs(f_s, h->n_grids, "f_s"));
+    L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
+    cudaStream_t s = (cudaStream_t)stream;
+    h->stream = s;
+    const int G = h->n_grids, d = h->dim;
+    const int NS = (d + 1) << d;
+    // capacities with margin (pairs and B entries), B^T over every fluid node
+    const int64_t pcap = (int64_t)(capacity_margin * (double)h->n_pairs) + 1024;
+    if (pcap > h->pair_cap) {
+        dfree(h->pair_elem); dfree(h->pair_cell); dfree(h->blocks); dfree(h->vols); dfree(h->pair_key);
+        dfree(h->pair_perm);
+        h->pair_cap = 0;
+        L2X_TRY(dalloc(&h->pair_elem, pcap));
+        L2X_TRY(dalloc(&h->pair_cell, pcap));
+        L2X_TRY(dalloc(&h->blocks, (size_t)pcap * NS));
+        L2X_TRY(dalloc(&h->vols, pcap));
+        L2X_TRY(dalloc(&h->pair_key, pcap));
+        L2X_TRY(dalloc(&h->pair_perm, pcap));
+        h->pair_cap = pcap;
+    }
+    int64_t max_rows = 0;
+    for (int g = 0; g < G; ++g) {
+        Csr& B = h->B[g];
+        const int64_t bcap = (int64_t)(capacity_margin * (double)B.nnz) + 1024;
+        if (bcap > h->B_cap[g]) {
+            dfree(B.col); dfree(B.val); dfree(B.val32);
+            L2X_TRY(dalloc(&B.col, bcap));
+            L2X_TRY(dalloc(&B.val, bcap));
+            L2X_TRY(dalloc(&B.val32, bcap));
+            h->B_cap[g] = bcap;
+        }
+        CsrT& T = h->T[g];
+        if (h->B_cap[g] > h->T_cap[g]) {
+            dfree(T.col); dfree(T.val); dfree(T.val32);
+            L2X_TRY(dalloc(&T.col, h->B_cap[g]));
+            L2X_TRY(dalloc(&T.val, h->B_cap[g]));
+            L2X_TRY(dalloc(&T.val32, h->B_cap[g]));
+            h->T_cap[g] = h->B_cap[g];
+        }
+        int64_t rows = 1;
+        for (int k = 0; k < 3; ++k) {
+            T.lo[k] = 0;
+            T.n[k] = h->sg[g].nnode[k];
+            rows *= T.n[k];
+        }
+        T.n_rows = rows;
+        if (rows + 1 > h->T_rows_cap[g]) {
+            dfree(T.ptr);
+            L2X_TRY(dalloc(&T.ptr, rows + 1));
+            h->T_rows_cap[g] = rows + 1;
+        }
+        if (rows > max_rows) max_rows = rows;
+    }
+    if (max_rows > h->tcursor_cap) {
+        dfree(h->tcursor);
+        L2X_TRY(dalloc(&h->tcursor, max_rows));
+        h->tcursor_cap = max_rows;
+    }
+    L2X_TRY(ensure_scan(h, max_rows));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    // capture one step
+    l2x_step_graph* gr = new l2x_step_graph();
+    gr->h = h;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        delete gr;
+        return cuda_fail(e, "cudaStreamBeginCapture (use a non-default stream)");
+    }
+    l2x_status st = record_step(h, coords_src, u_f, u_s, f_s, f_f, zero_force != 0, s);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    if (st != L2X_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        delete gr;
+        cudaGetLastError();
+        return st != L2X_OK ? st : cuda_fail(e, "cudaStreamEndCapture");
+    }
+    gr->graph = graph;
+    e = cudaGraphInstantiate(&gr->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        delete gr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    *out = gr;
+    return L2X_OK;
+}
+
+l2x_status l2x_graph_launch(l2x_graph g, void* stream) {
+    if (!g) return fail(L2X_EINVAL, "NULL graph");
+    L2X_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return L2X_OK;
+}
+
+l2x_status l2x_graph_sync_status(l2x_graph g, void* stream) {
+    if (!g) return fail(L2X_EINVAL, "NULL graph");
+    l2x_coupling* h = g->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t np = 0;
+    L2X_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    L2X_CUDA(cudaMemcpyAsync(&np, h->offsets + (int64_t)h->n_grids * h->n_elems, sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, s));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    h->n_pairs = np;  // candidate pairs of the last replay (l2x_query's n_pairs_total)
+    const DevStatus& ds = *h->st_host;
+    h->cg_iters = ds.cg_iters;
+    h->cg_residual = ds.cg_residual;
+    if (ds.flags & FLAG_CAPACITY)
+        return fail(L2X_ECAPACITY, "the step needed more pairs or matrix entries than the graph's capacity; "
+                                   "create the graph again (larger margin)");
+    L2X_TRY(flags_to_status(ds));
+    if (ds.flags & FLAG_NOTCONVERGED) return fail(L2X_ENOTCONVERGED, "CG did not reach cg_rtol in a captured step");
+    return L2X_OK;
+}
+
+l2x_status l2x_graph_destroy(l2x_graph g) {
+    if (!g) return L2X_OK;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return L2X_OK;
 }
 
 l2x_status l2x_query(l2x_handle h, l2x_info* info) {

@@ -29,7 +29,8 @@ struct SpmvPack {
 
 // 8 lanes per row; accumulation in the vector type.
 template <typename TV, typename TM>
-__global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM> P) {
+__global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM> P, const DevStatus* st) {
+    if (st->flags & FLAG_CAPACITY) return;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t grp = tid >> 3;
     const int l8 = threadIdx.x & 7;
@@ -76,7 +77,8 @@ struct SpmvTPack {
 
 // One thread per row of B_g^T (fluid node of the touched box): gather, no atomics.
 template <typename TV, typename TM>
-__global__ void spmv_BT_fused_kernel(int n_grids, SpmvTPack<TV, TM> P, TV scale) {
+__global__ void spmv_BT_fused_kernel(int n_grids, SpmvTPack<TV, TM> P, TV scale, const DevStatus* st) {
+    if (st->flags & FLAG_CAPACITY) return;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= P.row_base[n_grids]) return;
     int g = 0;
@@ -690,7 +692,7 @@ size_t pcg_ws_bytes(int64_t n, int n_rhs, int max_blocks) {
 }
 
 void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const void* const* x, void* const* y,
-                   cudaStream_t s) {
+                   const DevStatus* st, cudaStream_t s) {
     const int64_t n = B[0].n_rows;
     if (n <= 0) return;
     if (path == L2X_PATH_PLAIN) {
@@ -706,19 +708,19 @@ void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const voi
             P.ptr[g] = B[g].ptr; P.col[g] = B[g].col; P.val[g] = B[g].val32;
             P.x[g] = (const float*)x[g]; P.y[g] = (float*)y[g];
         }
-        { spmv_B_fused_kernel<float, float><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P); count_launch(); }
+        { spmv_B_fused_kernel<float, float><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P, st); count_launch(); }
     } else {
         SpmvPack<double, double> P{};
         for (int g = 0; g < n_grids; ++g) {
             P.ptr[g] = B[g].ptr; P.col[g] = B[g].col; P.val[g] = B[g].val;
             P.x[g] = (const double*)x[g]; P.y[g] = (double*)y[g];
         }
-        { spmv_B_fused_kernel<double, double><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P); count_launch(); }
+        { spmv_B_fused_kernel<double, double><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P, st); count_launch(); }
     }
 }
 
 void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const CsrT* T, const SubGrid* sg,
-                    const void* const* z, void* const* f, double scale, cudaStream_t s) {
+                    const void* const* z, void* const* f, double scale, const DevStatus* st, cudaStream_t s) {
     if (path == L2X_PATH_PLAIN) {
         for (int g = 0; g < n_grids; ++g)
             if (B[g].n_rows > 0)
@@ -752,7 +754,7 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
             P.z[g] = (const float*)z[g];
             P.f[g] = (float*)f[g];
         }
-        if (total > 0) { spmv_BT_fused_kernel<float, float><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, (float)scale); count_launch(); }
+        if (total > 0) { spmv_BT_fused_kernel<float, float><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, (float)scale, st); count_launch(); }
     } else {
         SpmvTPack<double, double> P{};
         int64_t total = fill(P, false);
@@ -761,8 +763,56 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
             P.z[g] = (const double*)z[g];
             P.f[g] = (double*)f[g];
         }
-        if (total > 0) { spmv_BT_fused_kernel<double, double><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, scale); count_launch(); }
+        if (total > 0) { spmv_BT_fused_kernel<double, double><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, scale, st); count_launch(); }
     }
+}
+
+void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, const float* diag_inv32, int nr,
+                          const void* const* y, void* const* w, double rtol, int max_iter, void* ws, DevStatus* st,
+                          cudaStream_t s) {
+    const int64_t n = M.n_rows;
+    if (n <= 0 || nr <= 0) return;
+    const int64_t v = n * nr;
+    char* base = (char*)ws;
+    auto take = [&](size_t bytes) {
+        void* p = base;
+        base += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    double* partial = (double*)take((size_t)pcg_max_blocks() * 3 * kMaxRhs * 8);
+    if (precision == L2X_FP64) {
+        double* vecs = (double*)take(5 * v * 8);
+        run_pcg_fused<double>(M.ptr, M.col, M.val, diag_inv, n, nr, (const double* const*)y, (double* const*)w, vecs,
+                              partial, rtol, max_iter, st, s);
+        return;
+    }
+    float* vecs = (float*)take(5 * v * 4);
+    double* x64 = (double*)take(v * 8);
+    double* r64 = (double*)take(v * 8);
+    float* r32 = (float*)take(v * 4);
+    float* d32 = (float*)take(v * 4);
+    double* norms = (double*)take(8 * 8);
+    const float* yf[3] = {(const float*)y[0], nr > 1 ? (const float*)y[1] : nullptr, nr > 2 ? (const float*)y[2] : nullptr};
+    float* wf[3] = {(float*)w[0], nr > 1 ? (float*)w[1] : nullptr, nr > 2 ? (float*)w[2] : nullptr};
+    const unsigned nb = nblk(n, 256);
+    const unsigned nbd = nb < 1024 ? nb : 1024;
+    const double inner = rtol > 1e-7 ? rtol : 1e-7;
+    // one FP32 solve and one FP64 residual correction, fixed (no host decisions)
+    for (int ref = 0; ref < 2; ++ref) {
+        const float* rhs[3];
+        float* dst[3];
+        for (int k = 0; k < nr; ++k) {
+            rhs[k] = ref == 0 ? yf[k] : r32 + k * n;
+            dst[k] = d32 + k * n;
+        }
+        run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s);
+        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr, nr > 2 ? dst[2] : nullptr, ref == 0); count_launch(); }
+        if (ref == 0) {
+            cudaMemsetAsync(norms, 0, 4 * 8, s);
+            { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf[0], yf[1], yf[2], x64, r64, r32, norms); count_launch(); }
+        }
+    }
+    { store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf[0], wf[1], wf[2]); count_launch(); }
 }
 
 l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv, const float* diag_inv32,

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i = blockIdx.x * (int64_t)kRowWarps + w;
     if (i >= n_nodes) return;
+    if (st->flags & FLAG_CAPACITY) return;  // a captured step whose pairs or entries did not fit
     const int64_t a0 = adj_ptr[i], a1 = adj_ptr[i + 1];
     const bool staged = a1 - a0 <= kRowAdj;
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
@@ -152,7 +153,6 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
         }
     }
     if (pass == 0 && lane == 0) row_count[i] = cnt;
-    (void)st;
 }
 
 template <int D>
@@ -234,20 +234,21 @@ __device__ __forceinline__ int64_t tbox_index(const SubGrid& sg, const CsrT& T, 
 
 // Warp per row of B_g: count the entries of every B_g^T row.
 __global__ void transpose_count_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                       SubGrid sg, CsrT T, int64_t* cnt) {
+                                       SubGrid sg, CsrT T, int64_t* cnt, const DevStatus* st) {
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= n_rows) return;
+    if (i >= n_rows || (st->flags & FLAG_CAPACITY)) return;
     for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
         atomicAdd((unsigned long long*)(cnt + tbox_index(sg, T, col[q])), 1ull);
 }
 
 // Warp per row of B_g: scatter (row, value) into the B_g^T rows (order fixed later).
 __global__ void transpose_fill_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                      const double* __restrict__ val, SubGrid sg, CsrT T, int32_t* cursor) {
+                                      const double* __restrict__ val, SubGrid sg, CsrT T, int32_t* cursor,
+                                      const DevStatus* st) {
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= n_rows) return;
+    if (i >= n_rows || (st->flags & FLAG_CAPACITY)) return;
     for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32) {
         const int64_t r = tbox_index(sg, T, col[q]);
         const int64_t pos = T.ptr[r] + atomicAdd(cursor + r, 1);
@@ -263,12 +264,12 @@ constexpr int kSortWarps = 4;
 constexpr int kSortMax = 512;
 
 __global__ void __launch_bounds__(kSortWarps * 32) transpose_sort_kernel(int64_t n, const int64_t* __restrict__ ptr,
-                                                                        int32_t* key, double* val) {
+                                                                        int32_t* key, double* val, const DevStatus* st) {
     __shared__ int32_t sk[kSortWarps][kSortMax];
     __shared__ double sv[kSortWarps][kSortMax];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = blockIdx.x * (int64_t)kSortWarps + w;
-    if (i >= n) return;
+    if (i >= n || (st->flags & FLAG_CAPACITY)) return;
     const int64_t lo = ptr[i], hi = ptr[i + 1];
     const int len = (int)(hi - lo);
     if (len <= 1) return;
@@ -357,19 +358,21 @@ void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_
         { mass_values_kernel<3><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv); count_launch(); }
 }
 
-void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, cudaStream_t s) {
+void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, const DevStatus* st,
+                            cudaStream_t s) {
     cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (T.n_rows + 1), s);
-    if (B.n_rows > 0) { transpose_count_kernel<<<nblk(B.n_rows * 32, 256), 256, 0, s>>>(B.n_rows, B.ptr, B.col, sg, T, cnt); count_launch(); }
+    if (B.n_rows > 0) { transpose_count_kernel<<<nblk(B.n_rows * 32, 256), 256, 0, s>>>(B.n_rows, B.ptr, B.col, sg, T, cnt, st); count_launch(); }
 }
 
-void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, cudaStream_t s) {
+void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, const DevStatus* st,
+                           cudaStream_t s) {
     cudaMemsetAsync(cursor, 0, sizeof(int32_t) * T.n_rows, s);
     if (B.n_rows > 0)
-        { transpose_fill_kernel<<<nblk(B.n_rows * 32, 256), 256, 0, s>>>(B.n_rows, B.ptr, B.col, B.val, sg, T, cursor); count_launch(); }
+        { transpose_fill_kernel<<<nblk(B.n_rows * 32, 256), 256, 0, s>>>(B.n_rows, B.ptr, B.col, B.val, sg, T, cursor, st); count_launch(); }
 }
 
-void launch_transpose_sort(const CsrT& T, cudaStream_t s) {
-    if (T.n_rows > 0) { transpose_sort_kernel<<<nblk(T.n_rows, kSortWarps), kSortWarps * 32, 0, s>>>(T.n_rows, T.ptr, T.col, T.val); count_launch(); }
+void launch_transpose_sort(const CsrT& T, const DevStatus* st, cudaStream_t s) {
+    if (T.n_rows > 0) { transpose_sort_kernel<<<nblk(T.n_rows, kSortWarps), kSortWarps * 32, 0, s>>>(T.n_rows, T.ptr, T.col, T.val, st); count_launch(); }
 }
 
 void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {

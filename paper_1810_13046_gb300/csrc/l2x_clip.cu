@@ -33,20 +33,36 @@ __device__ __forceinline__ void pair_vertices(const SubGrid& sg, const double* _
     }
 }
 
+struct SubGridSet {
+    SubGrid g[kMaxGrids];
+};
+
+// Pairs of all grids are listed grid by grid; offsets[g * m] is the first pair
+// of grid g and offsets[G * m] the total (device values, so that the same
+// kernels run inside a captured CUDA graph).  n_cap bounds every index.
+__device__ __forceinline__ int grid_of_pair(int64_t p, int G, int64_t m, const int64_t* __restrict__ offsets) {
+    int g = 0;
+    while (g + 1 < G && p >= offsets[(int64_t)(g + 1) * m]) ++g;
+    return g;
+}
+
 // Fused, step 1: scheduling class of every pair and per-class counts.
 template <int D>
-__global__ void pair_class_kernel(SubGrid sg, const double* __restrict__ X, const int32_t* __restrict__ E,
-                                  int64_t p_begin, int64_t p_end, const int32_t* __restrict__ pair_elem,
-                                  const int32_t* __restrict__ pair_cell, uint8_t* __restrict__ keys, int32_t* counts) {
+__global__ void pair_class_kernel(int G, SubGridSet sgs, int64_t m, const int64_t* __restrict__ offsets, int64_t n_cap,
+                                  const double* __restrict__ X, const int32_t* __restrict__ E,
+                                  const int32_t* __restrict__ pair_elem, const int32_t* __restrict__ pair_cell,
+                                  uint8_t* __restrict__ keys, int32_t* counts) {
     __shared__ int hist[kClasses];
     if (threadIdx.x < kClasses) hist[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t p = p_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p < p_end) {
+    const int64_t n = min(offsets[(int64_t)G * m], n_cap);
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) {
+        const int g = grid_of_pair(p, G, m, offsets);
         double T[D + 1][D];
-        pair_vertices<D>(sg, X, E, pair_elem[p], pair_cell[p], T);
+        pair_vertices<D>(sgs.g[g], X, E, pair_elem[p], pair_cell[p], T);
         const int key = min(pair_class<D>(T), kClasses - 1);
-        keys[p - p_begin] = (uint8_t)key;
+        keys[p] = (uint8_t)key;
         atomicAdd(&hist[key], 1);
     }
     __syncthreads();
@@ -65,11 +81,13 @@ __global__ void class_scan_kernel(int32_t* counts, int32_t* cursors) {
 
 // Fused, step 3: permutation listing the pairs class by class.  Each block
 // reserves one range per class, so runs of consecutive pairs stay together.
-__global__ void pair_scatter_kernel(int64_t n, const uint8_t* __restrict__ keys, int32_t* cursors, int32_t* perm) {
+__global__ void pair_scatter_kernel(int G, int64_t m, const int64_t* __restrict__ offsets, int64_t n_cap,
+                                    const uint8_t* __restrict__ keys, int32_t* cursors, int32_t* perm) {
     __shared__ int hist[kClasses];
     __shared__ int base[kClasses];
     if (threadIdx.x < kClasses) hist[threadIdx.x] = 0;
     __syncthreads();
+    const int64_t n = min(offsets[(int64_t)G * m], n_cap);
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int key = 0, rank = 0;
     if (i < n) {
@@ -85,19 +103,24 @@ __global__ void pair_scatter_kernel(int64_t n, const uint8_t* __restrict__ keys,
 // Fused, step 4: one thread per pair, in class order.  Gradients come from the
 // element pass; blocks are written structure-of-arrays at the pair's index.
 template <int D, typename R>
-__global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(SubGrid sg, const double* __restrict__ X,
+__global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(int G, SubGridSet sgs, int64_t m,
+                                                                  const int64_t* __restrict__ offsets, int64_t n_cap,
+                                                                  const double* __restrict__ X,
                                                                   const int32_t* __restrict__ E,
                                                                   const double* __restrict__ elem_grad,
-                                                                  const int8_t* __restrict__ elem_flag, int64_t p_begin,
-                                                                  int64_t n, const int32_t* __restrict__ perm,
+                                                                  const int8_t* __restrict__ elem_flag,
+                                                                  const int32_t* __restrict__ perm,
                                                                   const int32_t* __restrict__ pair_elem,
                                                                   const int32_t* __restrict__ pair_cell,
                                                                   double* __restrict__ blocks, int64_t slot_stride,
                                                                   double* __restrict__ vols, DevStatus* st) {
     constexpr int NA = D + 1, NB = 1 << D;
+    const int64_t n = min(offsets[(int64_t)G * m], n_cap);
     const int64_t i = blockIdx.x * (int64_t)kClipThreads + threadIdx.x;
     if (i >= n) return;
-    const int64_t p = p_begin + perm[i];
+    const int64_t p = perm[i];
+    const int g = grid_of_pair(p, G, m, offsets);
+    const SubGrid& sg = sgs.g[g];
     const int32_t e = pair_elem[p];
     double blk[NA * NB];
     double vol = 0.0;
@@ -108,14 +131,14 @@ __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(SubGrid sg, co
 #pragma unroll
         for (int j = 0; j < NA * NB; ++j) blk[j] = 0.0;
     } else {
-        double T[NA][D], g[NA][D];
+        double T[NA][D], gr[NA][D];
         pair_vertices<D>(sg, X, E, e, pair_cell[p], T);
 #pragma unroll
         for (int a = 0; a < NA; ++a)
 #pragma unroll
-            for (int k = 0; k < D; ++k) g[a][k] = __ldg(elem_grad + ((int64_t)e * NA + a) * D + k);
+            for (int k = 0; k < D; ++k) gr[a][k] = __ldg(elem_grad + ((int64_t)e * NA + a) * D + k);
         const double scale = sg.h[0] * sg.h[1] * (D == 3 ? sg.h[2] : 1.0);
-        pair_integrals<D, R>(T, g, flag == 1, scale, blk, &vol);
+        pair_integrals<D, R>(T, gr, flag == 1, scale, blk, &vol);
     }
 #pragma unroll
     for (int j = 0; j < NA * NB; ++j) blocks[j * slot_stride + p] = blk[j];
@@ -195,37 +218,38 @@ __global__ void scatter_plain_kernel(SubGrid sg, const int32_t* __restrict__ E, 
 
 }  // namespace
 
-void launch_pair_classes(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
-                         int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, uint8_t* keys,
-                         int32_t* perm, int32_t* buckets, cudaStream_t s) {
-    const int64_t n = p_end - p_begin;
-    if (n <= 0) return;
+void launch_pair_classes(int dim, int G, const SubGrid* sg, int64_t m, const int64_t* offsets, int64_t n_launch,
+                         int64_t n_cap, const double* X, const int32_t* E, const int32_t* pair_elem,
+                         const int32_t* pair_cell, uint8_t* keys, int32_t* perm, int32_t* buckets, cudaStream_t s) {
+    if (n_launch <= 0) return;
+    SubGridSet sgs{};
+    for (int g = 0; g < G; ++g) sgs.g[g] = sg[g];
     cudaMemsetAsync(buckets, 0, sizeof(int32_t) * 2 * kClasses, s);
-    const unsigned nb256 = (unsigned)((n + 255) / 256);
-    if (dim == 2) { pair_class_kernel<2><<<nb256, 256, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, keys, buckets); count_launch(); }
-    else { pair_class_kernel<3><<<nb256, 256, 0, s>>>(sg, X, E, p_begin, p_end, pair_elem, pair_cell, keys, buckets); count_launch(); }
+    const unsigned nb256 = (unsigned)((n_launch + 255) / 256);
+    if (dim == 2) { pair_class_kernel<2><<<nb256, 256, 0, s>>>(G, sgs, m, offsets, n_cap, X, E, pair_elem, pair_cell, keys, buckets); count_launch(); }
+    else { pair_class_kernel<3><<<nb256, 256, 0, s>>>(G, sgs, m, offsets, n_cap, X, E, pair_elem, pair_cell, keys, buckets); count_launch(); }
     { class_scan_kernel<<<1, 32, 0, s>>>(buckets, buckets + kClasses); count_launch(); }
-    { pair_scatter_kernel<<<nb256, 256, 0, s>>>(n, keys, buckets + kClasses, perm); count_launch(); }
+    { pair_scatter_kernel<<<nb256, 256, 0, s>>>(G, m, offsets, n_cap, keys, buckets + kClasses, perm); count_launch(); }
 }
 
-void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* X, const int32_t* E,
-                       const double* elem_grad, const int8_t* elem_flag, int64_t p_begin, int64_t p_end,
-                       const int32_t* pair_elem, const int32_t* pair_cell, const int32_t* perm, double* blocks,
-                       int64_t slot_stride, double* vols, DevStatus* st, cudaStream_t s) {
-    const int64_t n = p_end - p_begin;
-    if (n <= 0) return;
-    const unsigned nb = (unsigned)((n + kClipThreads - 1) / kClipThreads);
+void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t m, const int64_t* offsets,
+                       int64_t n_launch, int64_t n_cap, const double* X, const int32_t* E, const double* elem_grad,
+                       const int8_t* elem_flag, const int32_t* pair_elem, const int32_t* pair_cell,
+                       const int32_t* perm, double* blocks, int64_t slot_stride, double* vols, DevStatus* st,
+                       cudaStream_t s) {
+    if (n_launch <= 0) return;
+    SubGridSet sgs{};
+    for (int g = 0; g < G; ++g) sgs.g[g] = sg[g];
+    const unsigned nb = (unsigned)((n_launch + kClipThreads - 1) / kClipThreads);
+#define L2X_CLIP_ARGS G, sgs, m, offsets, n_cap, X, E, elem_grad, elem_flag, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st
     if (dim == 2) {
-        if (precision == L2X_MIXED)
-            { clip_fused_kernel<2, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, elem_grad, elem_flag, p_begin, n, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
-        else
-            { clip_fused_kernel<2, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, elem_grad, elem_flag, p_begin, n, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
+        if (precision == L2X_MIXED) { clip_fused_kernel<2, float><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        else { clip_fused_kernel<2, double><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
     } else {
-        if (precision == L2X_MIXED)
-            { clip_fused_kernel<3, float><<<nb, kClipThreads, 0, s>>>(sg, X, E, elem_grad, elem_flag, p_begin, n, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
-        else
-            { clip_fused_kernel<3, double><<<nb, kClipThreads, 0, s>>>(sg, X, E, elem_grad, elem_flag, p_begin, n, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st); count_launch(); }
+        if (precision == L2X_MIXED) { clip_fused_kernel<3, float><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        else { clip_fused_kernel<3, double><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
     }
+#undef L2X_CLIP_ARGS
 }
 
 void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,

@@ -78,21 +78,29 @@ void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
 void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
 size_t scan_tmp_bytes(int64_t n);
 void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const ElemBox* boxes,
-                       const int64_t* offsets, int32_t* pair_elem, int32_t* pair_cell, cudaStream_t s);
+                       const int64_t* offsets, int32_t* pair_elem, int32_t* pair_cell, int64_t cap, DevStatus* st,
+                       cudaStream_t s);
+void launch_reset_status(DevStatus* st, cudaStream_t s);
+// FLAG_CAPACITY if *total > cap (device value); kernels after it skip their work
+void launch_check_capacity(const int64_t* total, int64_t cap, DevStatus* st, cudaStream_t s);
 
 // clipping + quadrature (l2x_clip.cu).  Pair blocks are stored at
 // blocks[slot * slot_stride + p * pair_stride], slot = a * 2^d + b.
-// Fused: pairs are first bucketed by scheduling class (similar control flow per
-// warp, launch_pair_classes), then clipped in bucket order.  keys: uint8 per
-// pair; perm: int32 per pair (offsets from p_begin); buckets: 2 * kClasses int32.
+// Fused: pairs of all grids are first bucketed by scheduling class (similar
+// control flow per warp, launch_pair_classes), then clipped in bucket order.
+// Sizes are read on the device from offsets[G * m] (bounded by n_cap); n_launch
+// is the number of threads launched (exact pair count, or the capacity when the
+// count is not known on the host).  keys: uint8 per pair; perm: int32 per pair;
+// buckets: 2 * kClasses int32.
 constexpr int kClasses = 16;
-void launch_pair_classes(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
-                         int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, uint8_t* keys,
-                         int32_t* perm, int32_t* buckets, cudaStream_t s);
-void launch_clip_fused(int dim, int precision, const SubGrid& sg, const double* X, const int32_t* E,
-                       const double* elem_grad, const int8_t* elem_flag, int64_t p_begin, int64_t p_end,
-                       const int32_t* pair_elem, const int32_t* pair_cell, const int32_t* perm, double* blocks,
-                       int64_t slot_stride, double* vols, DevStatus* st, cudaStream_t s);
+void launch_pair_classes(int dim, int G, const SubGrid* sg, int64_t m, const int64_t* offsets, int64_t n_launch,
+                         int64_t n_cap, const double* X, const int32_t* E, const int32_t* pair_elem,
+                         const int32_t* pair_cell, uint8_t* keys, int32_t* perm, int32_t* buckets, cudaStream_t s);
+void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t m, const int64_t* offsets,
+                       int64_t n_launch, int64_t n_cap, const double* X, const int32_t* E, const double* elem_grad,
+                       const int8_t* elem_flag, const int32_t* pair_elem, const int32_t* pair_cell,
+                       const int32_t* perm, double* blocks, int64_t slot_stride, double* vols, DevStatus* st,
+                       cudaStream_t s);
 void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
                        int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, double* blocks,
                        double* vols, DevStatus* st, cudaStream_t s);
@@ -120,21 +128,23 @@ void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_
                         const int32_t* adj, const double* elem_vol, const int64_t* row_ptr,
                         const int32_t* cols, double* vals, double* diag_inv, cudaStream_t s);
 // B_g^T over the box of touched fluid nodes.
-void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, cudaStream_t s);
-void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, cudaStream_t s);
-void launch_transpose_sort(const CsrT& T, cudaStream_t s);
+void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, const DevStatus* st,
+                            cudaStream_t s);
+void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, const DevStatus* st,
+                           cudaStream_t s);
+void launch_transpose_sort(const CsrT& T, const DevStatus* st, cudaStream_t s);
 void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 
 // apply (l2x_apply.cu)
 // y[g] = B_g x[g] (n_rows = solid nodes).  Fused: 8 lanes per row, all grids in
 // one launch; plain: one thread per row, FP64 only.
 void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const void* const* x,
-                   void* const* y, cudaStream_t s);
+                   void* const* y, const DevStatus* st, cudaStream_t s);
 // f[g] += scale * B_g^T z[g].  Fused: gather over the rows of B_g^T (no atomics);
 // plain: scatter with atomics from the rows of B_g.
 void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const CsrT* T,
                     const SubGrid* sg, const void* const* z, void* const* f, double scale,
-                    cudaStream_t s);
+                    const DevStatus* st, cudaStream_t s);
 // Jacobi-preconditioned CG on M for n_rhs right-hand sides (FP64, or FP32 with
 // compensated dot products and FP64 residual refinement in mixed mode).
 struct PcgResult {
@@ -142,6 +152,12 @@ struct PcgResult {
     double residual = 0.0;
     bool converged = false;
 };
+// The same without any host synchronisation (capturable in a CUDA graph): FP64
+// runs the cooperative PCG once; mixed runs the FP32 PCG and one FP64 residual
+// refinement.  Convergence is reported through the device status word.
+void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, const float* diag_inv32, int n_rhs,
+                          const void* const* y, void* const* w, double rtol, int max_iter, void* ws, DevStatus* st,
+                          cudaStream_t s);
 l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv,
                           const float* diag_inv32, int n_rhs, const void* const* y, void* const* w,
                           double rtol, int max_iter, void* ws, DevStatus* st, DevStatus* st_host,

@@ -110,7 +110,7 @@ __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const 
 template <int D>
 __global__ void emit_pairs_kernel(int n_grids, SubGridSet sgs, int64_t m, const ElemBox* __restrict__ boxes,
                                   const int64_t* __restrict__ offsets, int32_t* __restrict__ pair_elem,
-                                  int32_t* __restrict__ pair_cell) {
+                                  int32_t* __restrict__ pair_cell, int64_t cap, DevStatus* st) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= m * n_grids) return;
     int g = (int)(t / m);
@@ -119,6 +119,10 @@ __global__ void emit_pairs_kernel(int n_grids, SubGridSet sgs, int64_t m, const 
     ElemBox b = boxes[t];
     int64_t p = offsets[t], p1 = offsets[t + 1];
     if (p == p1) return;
+    if (p1 > cap) {  // the pair list does not fit the capacity fixed for a captured step
+        atomicOr(&st->flags, FLAG_CAPACITY);
+        return;
+    }
     int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = box_ext(b, 2);
     for (int kz = 0; kz < ez; ++kz)
         for (int ky = 0; ky < ey; ++ky)
@@ -206,7 +210,28 @@ __global__ void scan_apply_kernel(const int64_t* __restrict__ in, int64_t n, con
     if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = partial[nb];
 }
 
+__global__ void reset_status_kernel(DevStatus* st) {
+    if (threadIdx.x == 0) {
+        st->flags = 0;
+        st->bad_elem = INT_MAX;
+        st->cg_iters = 0;
+        st->cg_residual = 0.0;
+    }
+}
+
+__global__ void check_capacity_kernel(const int64_t* total, int64_t cap, DevStatus* st) {
+    if (threadIdx.x == 0 && *total > cap) atomicOr(&st->flags, FLAG_CAPACITY);
+}
+
 }  // namespace
+
+void launch_reset_status(DevStatus* st, cudaStream_t s) {
+    { reset_status_kernel<<<1, 32, 0, s>>>(st); count_launch(); }
+}
+
+void launch_check_capacity(const int64_t* total, int64_t cap, DevStatus* st, cudaStream_t s) {
+    { check_capacity_kernel<<<1, 32, 0, s>>>(total, cap, st); count_launch(); }
+}
 
 void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const double* X,
                        const int32_t* E, ElemBox* boxes, int64_t* counts, int32_t* node_box,
@@ -239,7 +264,8 @@ void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cuda
 }
 
 void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const ElemBox* boxes,
-                       const int64_t* offsets, int32_t* pair_elem, int32_t* pair_cell, cudaStream_t s) {
+                       const int64_t* offsets, int32_t* pair_elem, int32_t* pair_cell, int64_t cap, DevStatus* st,
+                       cudaStream_t s) {
     SubGridSet sgs{};
     for (int g = 0; g < n_grids; ++g) sgs.g[g] = sg_host[g];
     int threads = 256;
@@ -247,9 +273,9 @@ void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
     int64_t blocks = (total + threads - 1) / threads;
     if (blocks == 0) return;
     if (dim == 2)
-        { emit_pairs_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell); count_launch(); }
+        { emit_pairs_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell, cap, st); count_launch(); }
     else
-        { emit_pairs_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell); count_launch(); }
+        { emit_pairs_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, boxes, offsets, pair_elem, pair_cell, cap, st); count_launch(); }
 }
 
 }  // namespace l2x

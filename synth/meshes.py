@@ -328,3 +328,30 @@ def body_motion(body: dict, step: int, n_steps: int) -> np.ndarray:
     Xw = X0 + np.stack([np.zeros_like(wave), np.zeros_like(wave), wave], axis=1)
     drift = 0.02 * np.array([np.sin(2 * np.pi * t), np.cos(2 * np.pi * t), 0.0])
     return place_body(Xw, body["R"] @ Rz, body["centre"] + drift)
+
+
+def combine_bodies(parts):
+    """One mesh made of several bodies: list of (X, E) -> (X, E, node_ranges, elem_ranges)."""
+    Xs, Es, nr, er = [], [], [], []
+    n0 = e0 = 0
+    for X, E in parts:
+        Xs.append(X)
+        Es.append(E + n0)
+        nr.append((n0, n0 + X.shape[0]))
+        er.append((e0, e0 + E.shape[0]))
+        n0 += X.shape[0]
+        e0 += E.shape[0]
+    return np.concatenate(Xs), np.concatenate(Es).astype(np.int32), nr, er
+
+
+def batch_workload(n_bodies=64, n_cells=256, min_tets=1000, max_tets=200000, seed=0):
+    """Moving bodies on a staggered n_cells^3 grid: (grid, bodies, E, node_ranges, elem_ranges);
+    positions at step t come from ``batch_coords(bodies, t, n_steps)``."""
+    bodies = batch_bodies(n_bodies, min_tets, max_tets, seed)
+    grid = Grid(3, (n_cells,) * 3, (1.0 / n_cells,) * 3, (0.0, 0.0, 0.0), True)
+    X, E, nr, er = combine_bodies([(b["X0"], b["E"]) for b in bodies])
+    return grid, bodies, E, nr, er
+
+
+def batch_coords(bodies, step, n_steps):
+    return np.concatenate([body_motion(b, step, n_steps) for b in bodies])
