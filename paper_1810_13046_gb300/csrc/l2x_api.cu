@@ -43,6 +43,11 @@ struct l2x_coupling {
     ElemBox* boxes = nullptr;
     int64_t* counts = nullptr;
     int64_t* offsets = nullptr;      // n_grids*m + 1
+    int64_t* nbox = nullptr;         // nodes of each element's candidate box, per grid (n_grids*m)
+    int64_t* loc_off = nullptr;      // offsets of the element-local matrices (n_grids*m + 1)
+    double* loc_val = nullptr;       // element-local matrices, (d+1) values per box node
+    uint8_t* loc_flag = nullptr;     // box node touched by a pair of positive volume
+    int64_t loc_cap = 0;
     int32_t* node_box = nullptr;     // n_grids * 6
     int64_t pair_begin[kMaxGrids + 1]{};
     // pairs
@@ -68,6 +73,8 @@ struct l2x_coupling {
     int64_t* row_count = nullptr;    // n_nodes + 1
     int32_t* tcursor = nullptr;      // fill cursors of the B^T rows
     int64_t tcursor_cap = 0;
+    int64_t* tflags = nullptr;       // non-empty-row flags of B^T (scan scratch)
+    int64_t tflags_cap = 0;
     void* pcg_ws = nullptr;
     void* vec_tmp = nullptr;         // n_grids * n_nodes doubles
     DevStatus* st = nullptr;
@@ -235,6 +242,26 @@ void make_subgrids(l2x_coupling* h) {
     }
 }
 
+// Row list of B_g^T (non-empty rows) and the flag scratch, for up to `rows` rows
+// and `entries` entries.
+l2x_status ensure_tlist(l2x_coupling* h, CsrT& T, int64_t rows, int64_t entries) {
+    const int64_t need = rows < entries ? rows : entries;
+    if (need > T.list_cap || !T.list) {
+        dfree(T.list);
+        T.list_cap = 0;
+        const int64_t c = need + need / 4 + 16;
+        L2X_TRY(dalloc(&T.list, c));
+        T.list_cap = c;
+    }
+    if (!T.n_list) L2X_TRY(dalloc(&T.n_list, 1));
+    if (rows + 1 > h->tflags_cap || !h->tflags) {
+        dfree(h->tflags);
+        L2X_TRY(dalloc(&h->tflags, rows + 1));
+        h->tflags_cap = rows + 1;
+    }
+    return L2X_OK;
+}
+
 // Topology-only structures: node adjacency and the sparsity of M_s.
 l2x_status build_topology(l2x_coupling* h, cudaStream_t s) {
     const int64_t n = h->n_nodes, m = h->n_elems;
@@ -279,9 +306,12 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
     L2X_CUDA(cudaStreamSynchronize(s));
     // (I) candidate boxes, counts, offsets
     auto ph_pairs = std::make_unique<PhaseScope>(h, L2X_PH_PAIRS, s);
-    launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->node_box, h->elem_vol, h->elem_grad,
-                      h->elem_flag, h->st, s);
+    launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->nbox, h->node_box, h->elem_vol,
+                      h->elem_grad, h->elem_flag, h->st, s);
     launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
+    launch_scan_i64(h->nbox, h->loc_off, (int64_t)G * m, h->scan_tmp, s);
+    int64_t loc_total = 0;
+    L2X_CUDA(cudaMemcpyAsync(&loc_total, h->loc_off + (int64_t)G * m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     std::vector<int64_t> gb(G + 1);
     for (int g = 0; g <= G; ++g)
         L2X_CUDA(cudaMemcpyAsync(&gb[g], h->offsets + (int64_t)g * m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -308,6 +338,15 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         L2X_TRY(dalloc(&h->pair_perm, cap));
         h->pair_cap = cap;
     }
+    if (loc_total > h->loc_cap || !h->loc_val) {
+        dfree(h->loc_val);
+        dfree(h->loc_flag);
+        h->loc_cap = 0;
+        const int64_t c = loc_total + loc_total / 4 + 64;
+        L2X_TRY(dalloc(&h->loc_val, (size_t)c * (d + 1)));
+        L2X_TRY(dalloc(&h->loc_flag, c));
+        h->loc_cap = c;
+    }
     launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, h->pair_cap, h->st, s);
     ph_pairs.reset();
     // (II)-(III) clip + quadrature
@@ -326,8 +365,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         }
         PhaseScope ph(h, L2X_PH_CLIP, s);
         launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, NP, h->pair_cap, h->X, h->E, h->elem_grad,
-                          h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->pair_cap, h->vols,
-                          h->st, s);
+                          h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st, s);
     }
     // (IV) B_g by rows
     for (int g = 0; g < G; ++g) {
@@ -335,7 +373,9 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         Csr& B = h->B[g];
         const ElemBox* bx = h->boxes + (int64_t)g * m;
         const int64_t* off = h->offsets + (int64_t)g * m;
-        launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, h->row_count,
+        const int64_t* lof = h->loc_off + (int64_t)g * m;
+        launch_elem_local(d, m, bx, off, lof, h->loc_cap, h->blocks, h->vols, h->loc_val, h->loc_flag, h->st, s);
+        launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, h->row_count,
                       nullptr, nullptr, nullptr, h->st, s);
         if (!B.ptr) L2X_TRY(dalloc(&B.ptr, n + 1));
         launch_scan_i64(h->row_count, B.ptr, n, h->scan_tmp, s);
@@ -357,14 +397,14 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         }
         if (plain) {
             PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
-            launch_b_rows(2, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, nullptr,
+            launch_b_rows(2, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, nullptr,
                           B.ptr, B.col, B.val, h->st, s);
             launch_scatter_plain(d, h->sg[g], h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks, h->vols,
                                  B, s);
         } else {
             {
                 PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
-                launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols,
+                launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag,
                               nullptr, B.ptr, B.col, B.val, h->st, s);
                 if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, nnz, s);
             }
@@ -404,7 +444,9 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
                 L2X_TRY(dalloc(&h->tcursor, rows + rows / 4 + 16));
                 h->tcursor_cap = rows + rows / 4 + 16;
             }
+            L2X_TRY(ensure_tlist(h, T, rows, nnz));
             launch_transpose_count(B, h->sg[g], T, T.ptr, h->st, s);
+            launch_transpose_list(T, T.ptr, h->tflags, h->scan_tmp, h->st, s);
             launch_scan_i64(T.ptr, T.ptr, rows, h->scan_tmp, s);
             launch_transpose_fill(B, h->sg[g], T, h->tcursor, h->st, s);
             launch_transpose_sort(T, h->st, s);
@@ -460,30 +502,34 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     const int G = h->n_grids, d = h->dim;
     L2X_CUDA(cudaMemcpyAsync(h->X, coords_src, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
     launch_reset_status(h->st, s);
-    launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->node_box, h->elem_vol, h->elem_grad,
-                      h->elem_flag, h->st, s);
+    launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->nbox, h->node_box, h->elem_vol,
+                      h->elem_grad, h->elem_flag, h->st, s);
     launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
+    launch_scan_i64(h->nbox, h->loc_off, (int64_t)G * m, h->scan_tmp, s);
     launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, h->pair_cap, h->st, s);
     launch_pair_classes(d, G, h->sg, m, h->offsets, h->pair_cap, h->pair_cap, h->X, h->E, h->pair_elem, h->pair_cell,
                         h->pair_key, h->pair_perm, h->buckets, s);
     launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, h->pair_cap, h->pair_cap, h->X, h->E,
-                      h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->pair_cap,
-                      h->vols, h->st, s);
+                      h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st,
+                      s);
     for (int g = 0; g < G; ++g) {
         Csr& B = h->B[g];
         const ElemBox* bx = h->boxes + (int64_t)g * m;
         const int64_t* off = h->offsets + (int64_t)g * m;
-        launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, h->row_count,
+        const int64_t* lof = h->loc_off + (int64_t)g * m;
+        launch_elem_local(d, m, bx, off, lof, h->loc_cap, h->blocks, h->vols, h->loc_val, h->loc_flag, h->st, s);
+        launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, h->row_count,
                       nullptr, nullptr, nullptr, h->st, s);
         launch_scan_i64(h->row_count, B.ptr, n, h->scan_tmp, s);
         launch_check_capacity(B.ptr + n, h->B_cap[g], h->st, s);
-        launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, off, h->blocks, h->pair_cap, h->vols, nullptr,
+        launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, nullptr,
                       B.ptr, B.col, B.val, h->st, s);
         B.n_rows = n;
         B.nnz = h->B_cap[g];  // an upper bound: the row pointers hold the actual count
         if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, h->B_cap[g], s);
         CsrT& T = h->T[g];
         launch_transpose_count(B, h->sg[g], T, T.ptr, h->st, s);
+        launch_transpose_list(T, T.ptr, h->tflags, h->scan_tmp, h->st, s);
         launch_scan_i64(T.ptr, T.ptr, T.n_rows, h->scan_tmp, s);
         launch_transpose_fill(B, h->sg[g], T, h->tcursor, h->st, s);
         launch_transpose_sort(T, h->st, s);
@@ -557,16 +603,19 @@ l2x_status l2x_destroy(l2x_handle h) {
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     dfree(h->X); dfree(h->E); dfree(h->adj_ptr); dfree(h->adj); dfree(h->cursor); dfree(h->elem_vol);
     dfree(h->elem_grad); dfree(h->elem_flag); dfree(h->buckets); dfree(h->pair_key); dfree(h->pair_perm);
+    dfree(h->nbox); dfree(h->loc_off); dfree(h->loc_val); dfree(h->loc_flag);
     dfree(h->boxes); dfree(h->counts); dfree(h->offsets); dfree(h->node_box); dfree(h->pair_elem);
     dfree(h->pair_cell); dfree(h->blocks); dfree(h->vols);
     for (int g = 0; g < kMaxGrids; ++g) {
         dfree(h->B[g].ptr); dfree(h->B[g].col); dfree(h->B[g].val); dfree(h->B[g].val32);
         dfree(h->T[g].ptr); dfree(h->T[g].col); dfree(h->T[g].val); dfree(h->T[g].val32);
+        dfree(h->T[g].list); dfree(h->T[g].n_list);
     }
     dfree(h->M.ptr); dfree(h->M.col); dfree(h->M.val); dfree(h->M.val32); dfree(h->M_dinv); dfree(h->M_dinv32);
     if (h->scan_tmp) cudaFree(h->scan_tmp);
     dfree(h->row_count);
     dfree(h->tcursor);
+    dfree(h->tflags);
     if (h->pcg_ws) cudaFree(h->pcg_ws);
     if (h->vec_tmp) cudaFree(h->vec_tmp);
     dfree(h->st);
@@ -610,6 +659,8 @@ l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const 
         L2X_TRY(dalloc(&h->boxes, (size_t)(G * m)));
         L2X_TRY(dalloc(&h->counts, (size_t)(G * m)));
         L2X_TRY(dalloc(&h->offsets, (size_t)(G * m + 1)));
+        L2X_TRY(dalloc(&h->nbox, (size_t)(G * m)));
+        L2X_TRY(dalloc(&h->loc_off, (size_t)(G * m + 1)));
         L2X_TRY(dalloc(&h->node_box, (size_t)(6 * G)));
         L2X_TRY(ensure_scan(h, (int64_t)G * m > n ? (int64_t)G * m : n));
         L2X_TRY(reset_status(h, s));
@@ -741,6 +792,21 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
         L2X_TRY(dalloc(&h->pair_perm, pcap));
         h->pair_cap = pcap;
     }
+    {
+        int64_t loc_total = 0;
+        L2X_CUDA(cudaMemcpyAsync(&loc_total, h->loc_off + (int64_t)G * h->n_elems, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+        L2X_CUDA(cudaStreamSynchronize(s));
+        const int64_t lcap = (int64_t)(capacity_margin * (double)loc_total) + 1024;
+        if (lcap > h->loc_cap) {
+            dfree(h->loc_val);
+            dfree(h->loc_flag);
+            h->loc_cap = 0;
+            L2X_TRY(dalloc(&h->loc_val, (size_t)lcap * (d + 1)));
+            L2X_TRY(dalloc(&h->loc_flag, lcap));
+            h->loc_cap = lcap;
+        }
+    }
     int64_t max_rows = 0;
     for (int g = 0; g < G; ++g) {
         Csr& B = h->B[g];
@@ -772,6 +838,7 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
             L2X_TRY(dalloc(&T.ptr, rows + 1));
             h->T_rows_cap[g] = rows + 1;
         }
+        L2X_TRY(ensure_tlist(h, T, rows, h->B_cap[g]));
         if (rows > max_rows) max_rows = rows;
     }
     if (max_rows > h->tcursor_cap) {
@@ -905,14 +972,7 @@ l2x_status l2x_export_pair_blocks(l2x_handle h, int32_t grid, double* blocks, do
     const int NS = (h->dim + 1) << h->dim;
     int64_t p0 = h->pair_begin[grid], np = h->pair_begin[grid + 1] - p0;
     L2X_CUDA(cudaMemcpyAsync(vols, h->vols + p0, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
-    if (h->opts.path == L2X_PATH_PLAIN) {
-        L2X_CUDA(cudaMemcpyAsync(blocks, h->blocks + p0 * NS, sizeof(double) * np * NS, cudaMemcpyDeviceToDevice, s));
-    } else {
-        // structure-of-arrays -> pair-major
-        for (int slot = 0; slot < NS; ++slot)
-            L2X_CUDA(cudaMemcpy2DAsync(blocks + slot, sizeof(double) * NS, h->blocks + slot * h->pair_cap + p0,
-                                       sizeof(double), sizeof(double), np, cudaMemcpyDeviceToDevice, s));
-    }
+    L2X_CUDA(cudaMemcpyAsync(blocks, h->blocks + p0 * NS, sizeof(double) * np * NS, cudaMemcpyDeviceToDevice, s));
     L2X_CUDA(cudaStreamSynchronize(s));
     return L2X_OK;
 }
@@ -936,15 +996,8 @@ l2x_status l2x_export_pair_range(l2x_handle h, int32_t grid, int64_t e_first, in
     if (elem) L2X_CUDA(cudaMemcpyAsync(elem, h->pair_elem + p0, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, s));
     if (cell) L2X_CUDA(cudaMemcpyAsync(cell, h->pair_cell + p0, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, s));
     if (vols) L2X_CUDA(cudaMemcpyAsync(vols, h->vols + p0, sizeof(double) * np, cudaMemcpyDeviceToDevice, s));
-    if (blocks) {
-        if (h->opts.path == L2X_PATH_PLAIN) {
-            L2X_CUDA(cudaMemcpyAsync(blocks, h->blocks + p0 * NS, sizeof(double) * np * NS, cudaMemcpyDeviceToDevice, s));
-        } else {
-            for (int slot = 0; slot < NS; ++slot)
-                L2X_CUDA(cudaMemcpy2DAsync(blocks + slot, sizeof(double) * NS, h->blocks + slot * h->pair_cap + p0,
-                                           sizeof(double), sizeof(double), np, cudaMemcpyDeviceToDevice, s));
-        }
-    }
+    if (blocks)
+        L2X_CUDA(cudaMemcpyAsync(blocks, h->blocks + p0 * NS, sizeof(double) * np * NS, cudaMemcpyDeviceToDevice, s));
     L2X_CUDA(cudaStreamSynchronize(s));
     return L2X_OK;
 }

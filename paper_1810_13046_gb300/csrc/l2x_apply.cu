@@ -30,7 +30,7 @@ struct SpmvPack {
 // 8 lanes per row; accumulation in the vector type.
 template <typename TV, typename TM>
 __global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM> P, const DevStatus* st) {
-    if (st->flags & FLAG_CAPACITY) return;
+    if (st->flags & kAbortFlags) return;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t grp = tid >> 3;
     const int l8 = threadIdx.x & 7;
@@ -61,40 +61,26 @@ __global__ void spmv_B_plain_kernel(int64_t n_rows, const int64_t* __restrict__ 
 }
 
 // ------------------------------------------------------------------ B^T z
+// One thread per non-empty row of B_g^T (a fluid node the mesh touches): gather,
+// no atomics.  The row list and its length are device values.
 template <typename TV, typename TM>
-struct SpmvTPack {
-    const int64_t* ptr[kMaxGrids];
-    const int32_t* col[kMaxGrids];
-    const TM* val[kMaxGrids];
-    int32_t lo[kMaxGrids][3];
-    int32_t n[kMaxGrids][3];
-    int32_t nnode[kMaxGrids][3];
-    int64_t n_rows[kMaxGrids];
-    int64_t row_base[kMaxGrids + 1];
-    const TV* z[kMaxGrids];
-    TV* f[kMaxGrids];
-};
-
-// One thread per row of B_g^T (fluid node of the touched box): gather, no atomics.
-template <typename TV, typename TM>
-__global__ void spmv_BT_fused_kernel(int n_grids, SpmvTPack<TV, TM> P, TV scale, const DevStatus* st) {
-    if (st->flags & FLAG_CAPACITY) return;
+__global__ void spmv_BT_fused_kernel(const int32_t* __restrict__ list, const int64_t* __restrict__ n_list,
+                                     const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                     const TM* __restrict__ val, CsrT T, int nn0, int nn1, const TV* __restrict__ z,
+                                     TV* __restrict__ f, TV scale, const DevStatus* st) {
+    if (st->flags & kAbortFlags) return;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= P.row_base[n_grids]) return;
-    int g = 0;
-    while (g + 1 < n_grids && t >= P.row_base[g + 1]) ++g;
-    const int64_t r = t - P.row_base[g];
-    const int64_t lo = P.ptr[g][r], hi = P.ptr[g][r + 1];
-    if (lo == hi) return;
+    if (t >= *n_list) return;
+    const int64_t r = list[t];
+    const int64_t lo = ptr[r], hi = ptr[r + 1];
     TV acc = TV(0);
-    const TV* __restrict__ z = P.z[g];
-    for (int64_t q = lo; q < hi; ++q) acc += (TV)__ldg(P.val[g] + q) * __ldg(z + __ldg(P.col[g] + q));
-    const int x = (int)(r % P.n[g][0]);
-    const int64_t rr = r / P.n[g][0];
-    const int y = (int)(rr % P.n[g][1]);
-    const int zz = (int)(rr / P.n[g][1]);
-    const int64_t node = (x + P.lo[g][0]) + (int64_t)P.nnode[g][0] * ((y + P.lo[g][1]) + (int64_t)P.nnode[g][1] * (zz + P.lo[g][2]));
-    P.f[g][node] += scale * acc;
+    for (int64_t q = lo; q < hi; ++q) acc += (TV)__ldg(val + q) * __ldg(z + __ldg(col + q));
+    const int x = (int)(r % T.n[0]);
+    const int64_t rr = r / T.n[0];
+    const int y = (int)(rr % T.n[1]);
+    const int zz = (int)(rr / T.n[1]);
+    const int64_t node = (x + T.lo[0]) + (int64_t)nn0 * ((y + T.lo[1]) + (int64_t)nn1 * (zz + T.lo[2]));
+    f[node] += scale * acc;
 }
 
 __global__ void spmv_BT_plain_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
@@ -719,7 +705,7 @@ void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const voi
     }
 }
 
-void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const CsrT* T, const SubGrid* sg,
+void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const CsrT* Tm, const SubGrid* sg,
                     const void* const* z, void* const* f, double scale, const DevStatus* st, cudaStream_t s) {
     if (path == L2X_PATH_PLAIN) {
         for (int g = 0; g < n_grids; ++g)
@@ -728,42 +714,15 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
                                                                             (const double*)z[g], (double*)f[g], scale); count_launch(); }
         return;
     }
-    auto fill = [&](auto& P, bool f32) {
-        int64_t base = 0;
-        for (int g = 0; g < n_grids; ++g) {
-            P.ptr[g] = T[g].ptr;
-            P.col[g] = T[g].col;
-            for (int k = 0; k < 3; ++k) {
-                P.lo[g][k] = T[g].lo[k];
-                P.n[g][k] = T[g].n[k];
-                P.nnode[g][k] = sg[g].nnode[k];
-            }
-            P.n_rows[g] = T[g].n_rows;
-            P.row_base[g] = base;
-            base += T[g].n_rows;
+    for (int g = 0; g < n_grids; ++g) {
+        const CsrT& T = Tm[g];
+        const int64_t nl = T.list_cap < T.n_rows ? T.list_cap : T.n_rows;
+        if (nl <= 0) continue;
+        if (precision == L2X_MIXED) {
+            { spmv_BT_fused_kernel<float, float><<<nblk(nl, 256), 256, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val32, T, sg[g].nnode[0], sg[g].nnode[1], (const float*)z[g], (float*)f[g], (float)scale, st); count_launch(); }
+        } else {
+            { spmv_BT_fused_kernel<double, double><<<nblk(nl, 256), 256, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val, T, sg[g].nnode[0], sg[g].nnode[1], (const double*)z[g], (double*)f[g], scale, st); count_launch(); }
         }
-        P.row_base[n_grids] = base;
-        (void)f32;
-        return base;
-    };
-    if (precision == L2X_MIXED) {
-        SpmvTPack<float, float> P{};
-        int64_t total = fill(P, true);
-        for (int g = 0; g < n_grids; ++g) {
-            P.val[g] = T[g].val32;
-            P.z[g] = (const float*)z[g];
-            P.f[g] = (float*)f[g];
-        }
-        if (total > 0) { spmv_BT_fused_kernel<float, float><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, (float)scale, st); count_launch(); }
-    } else {
-        SpmvTPack<double, double> P{};
-        int64_t total = fill(P, false);
-        for (int g = 0; g < n_grids; ++g) {
-            P.val[g] = T[g].val;
-            P.z[g] = (const double*)z[g];
-            P.f[g] = (double*)f[g];
-        }
-        if (total > 0) { spmv_BT_fused_kernel<double, double><<<nblk(total, 256), 256, 0, s>>>(n_grids, P, scale, st); count_launch(); }
     }
 }
 

@@ -50,29 +50,78 @@ __global__ void segment_sort_kernel(int64_t n, const int64_t* __restrict__ ptr, 
     }
 }
 
+// Warp per element: node-box matrix of the element on one grid.  Lane = node of
+// the box; it sums, over the (up to 2^d) candidate cells of the element around
+// that node in z, y, x order, block[a][corner] of the pairs whose intersection
+// volume is positive.  Fixed order, registers only: reproducible.
+template <int D>
+__global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, const int64_t* __restrict__ offsets,
+                                  const int64_t* __restrict__ loc_off, int64_t loc_cap,
+                                  const double* __restrict__ blocks, const double* __restrict__ vols,
+                                  double* __restrict__ loc_val, uint8_t* __restrict__ loc_flag, DevStatus* st) {
+    constexpr int NA = D + 1, NB = 1 << D;
+    const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= m || (st->flags & kAbortFlags)) return;
+    const ElemBox b = boxes[e];
+    const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = D == 3 ? box_ext(b, 2) : 1;
+    const int64_t L0 = loc_off[e], L1 = loc_off[e + 1];
+    if (L1 == L0) return;
+    if (L1 > loc_cap) {
+        if (lane == 0) atomicOr(&st->flags, FLAG_CAPACITY);
+        return;
+    }
+    const int nbx = ex + 1, nby = ey + 1;
+    const int64_t nbox = L1 - L0;
+    const int64_t q0 = offsets[e];
+    for (int64_t jj = lane; jj < nbox; jj += 32) {
+        const int jx = (int)(jj % nbx);
+        const int64_t r = jj / nbx;
+        const int jy = (int)(r % nby), jz = (int)(r / nby);
+        double acc[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[a] = 0.0;
+        bool touched = false;
+        const int cz0 = D == 3 ? max(jz - 1, 0) : 0, cz1 = D == 3 ? min(jz, ez - 1) : 0;
+        for (int cz = cz0; cz <= cz1; ++cz)
+            for (int cy = max(jy - 1, 0); cy <= min(jy, ey - 1); ++cy)
+                for (int cx = max(jx - 1, 0); cx <= min(jx, ex - 1); ++cx) {
+                    const int64_t q = q0 + cx + (int64_t)ex * (cy + (int64_t)ey * cz);
+                    if (__double_as_longlong(vols[q]) > 0) {  // volume > 0
+                        touched = true;
+                        const int cb = (jx - cx) | ((jy - cy) << 1) | (D == 3 ? (jz - cz) << 2 : 0);
+                        const double* blk = blocks + q * (NA * NB) + cb;
+#pragma unroll
+                        for (int a = 0; a < NA; ++a) acc[a] += blk[a * NB];
+                    }
+                }
+        loc_flag[L0 + jj] = touched ? 1 : 0;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) loc_val[(L0 + jj) * NA + a] = acc[a];
+    }
+}
+
 // One warp per solid node i (row of B_g).  The row's columns lie in the union of
-// the node boxes of the incident elements' candidate cells.  Every lane owns box
-// nodes j and gathers, in a fixed order (adjacency order, then the element's
-// cells around j in z, y, x order), the entries block[a][b] of the pairs
-// (element with local vertex a, cell with corner b at j) whose intersection
-// volume is positive; sums stay in registers, so the result is reproducible and
+// the node boxes of the incident elements; every lane owns columns j and sums,
+// in adjacency order, the entry (local vertex of i, node j) of each incident
+// element's node-box matrix; registers only, so the result is reproducible and
 // needs no atomics.  Touched columns are emitted in ascending order.
 // pass 0: row_count[i] = number of touched columns; pass 1: columns and values;
 // pass 2: columns only, values zeroed (the plain path adds them with atomics).
 template <int D>
 __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
     int pass, SubGrid sg, int64_t n_nodes, const int64_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
-    const ElemBox* __restrict__ boxes, const int64_t* __restrict__ offsets, const double* __restrict__ blocks,
-    int64_t slot_stride, const double* __restrict__ vols, int64_t* __restrict__ row_count,
-    const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cols, double* __restrict__ vals, DevStatus* st) {
-    constexpr int NB = 1 << D;
+    const ElemBox* __restrict__ boxes, const int64_t* __restrict__ loc_off, const double* __restrict__ loc_val,
+    const uint8_t* __restrict__ loc_flag, int64_t* __restrict__ row_count, const int64_t* __restrict__ row_ptr,
+    int32_t* __restrict__ cols, double* __restrict__ vals, DevStatus* st) {
+    constexpr int NA = D + 1;
     __shared__ ElemBox s_box[kRowWarps][kRowAdj];
     __shared__ int64_t s_off[kRowWarps][kRowAdj];
     __shared__ int32_t s_ea[kRowWarps][kRowAdj];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i = blockIdx.x * (int64_t)kRowWarps + w;
     if (i >= n_nodes) return;
-    if (st->flags & FLAG_CAPACITY) return;  // a captured step whose pairs or entries did not fit
+    if (st->flags & kAbortFlags) return;  // a captured step whose pairs or entries did not fit
     const int64_t a0 = adj_ptr[i], a1 = adj_ptr[i + 1];
     const bool staged = a1 - a0 <= kRowAdj;
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
@@ -82,7 +131,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
         const ElemBox b = boxes[e];
         if (staged) {
             s_box[w][t - a0] = b;
-            s_off[w][t - a0] = offsets[e];
+            s_off[w][t - a0] = loc_off[e];
             s_ea[w][t - a0] = ea;
         }
 #pragma unroll
@@ -121,26 +170,15 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
                 for (int64_t t = a0; t < a1; ++t) {
                     const int32_t ea = staged ? s_ea[w][t - a0] : adj[t];
                     const ElemBox b = staged ? s_box[w][t - a0] : boxes[ea >> 2];
+                    const int ux = jx - b.lo[0], uy = jy - b.lo[1], uz = D == 3 ? jz - b.lo[2] : 0;
                     const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = box_ext(b, 2);
-                    // cells c of the element's box with c_k in {j_k - 1, j_k}
-                    const int cx0 = max(jx - 1, b.lo[0]), cx1 = min(jx, b.lo[0] + ex - 1);
-                    const int cy0 = max(jy - 1, b.lo[1]), cy1 = min(jy, b.lo[1] + ey - 1);
-                    const int cz0 = D == 3 ? max(jz - 1, b.lo[2]) : 0, cz1 = D == 3 ? min(jz, b.lo[2] + ez - 1) : 0;
-                    if (cx0 > cx1 || cy0 > cy1 || cz0 > cz1) continue;
-                    const int64_t q0 = staged ? s_off[w][t - a0] : offsets[ea >> 2];
-                    const int a = ea & 3;
-                    for (int cz = cz0; cz <= cz1; ++cz)
-                        for (int cy = cy0; cy <= cy1; ++cy)
-                            for (int cx = cx0; cx <= cx1; ++cx) {
-                                const int64_t q = q0 + (cx - b.lo[0]) + (int64_t)ex * ((cy - b.lo[1]) + (int64_t)ey * (cz - b.lo[2]));
-                                if (__double_as_longlong(vols[q]) > 0) {  // volume > 0
-                                    touched = true;
-                                    if (pass == 1) {
-                                        const int cb = (jx - cx) | ((jy - cy) << 1) | (D == 3 ? (jz - cz) << 2 : 0);
-                                        acc += blocks[(int64_t)(a * NB + cb) * slot_stride + q];
-                                    }
-                                }
-                            }
+                    if (ux < 0 || ux > ex || uy < 0 || uy > ey || uz < 0 || (D == 3 && uz > ez)) continue;
+                    const int64_t L0 = staged ? s_off[w][t - a0] : loc_off[ea >> 2];
+                    const int64_t li = L0 + ux + (int64_t)(ex + 1) * (uy + (int64_t)(ey + 1) * uz);
+                    if (loc_flag[li]) {
+                        touched = true;
+                        if (pass == 1) acc += loc_val[li * NA + (ea & 3)];
+                    }
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, touched);
@@ -237,7 +275,7 @@ __global__ void transpose_count_kernel(int64_t n_rows, const int64_t* __restrict
                                        SubGrid sg, CsrT T, int64_t* cnt, const DevStatus* st) {
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= n_rows || (st->flags & FLAG_CAPACITY)) return;
+    if (i >= n_rows || (st->flags & kAbortFlags)) return;
     for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
         atomicAdd((unsigned long long*)(cnt + tbox_index(sg, T, col[q])), 1ull);
 }
@@ -248,7 +286,7 @@ __global__ void transpose_fill_kernel(int64_t n_rows, const int64_t* __restrict_
                                       const DevStatus* st) {
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (i >= n_rows || (st->flags & FLAG_CAPACITY)) return;
+    if (i >= n_rows || (st->flags & kAbortFlags)) return;
     for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32) {
         const int64_t r = tbox_index(sg, T, col[q]);
         const int64_t pos = T.ptr[r] + atomicAdd(cursor + r, 1);
@@ -263,13 +301,16 @@ __global__ void transpose_fill_kernel(int64_t n_rows, const int64_t* __restrict_
 constexpr int kSortWarps = 4;
 constexpr int kSortMax = 512;
 
-__global__ void __launch_bounds__(kSortWarps * 32) transpose_sort_kernel(int64_t n, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(kSortWarps * 32) transpose_sort_kernel(const int32_t* __restrict__ list,
+                                                                        const int64_t* __restrict__ n_list,
+                                                                        const int64_t* __restrict__ ptr,
                                                                         int32_t* key, double* val, const DevStatus* st) {
     __shared__ int32_t sk[kSortWarps][kSortMax];
     __shared__ double sv[kSortWarps][kSortMax];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = blockIdx.x * (int64_t)kSortWarps + w;
-    if (i >= n || (st->flags & FLAG_CAPACITY)) return;
+    const int64_t li = blockIdx.x * (int64_t)kSortWarps + w;
+    if (li >= *n_list || (st->flags & kAbortFlags)) return;
+    const int64_t i = list[li];
     const int64_t lo = ptr[i], hi = ptr[i + 1];
     const int len = (int)(hi - lo);
     if (len <= 1) return;
@@ -303,6 +344,21 @@ __global__ void __launch_bounds__(kSortWarps * 32) transpose_sort_kernel(int64_t
     }
 }
 
+__global__ void nonempty_flags_kernel(int64_t n, const int64_t* __restrict__ counts, int64_t* flags,
+                                      const DevStatus* st) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flags[i] = (st->flags & kAbortFlags) ? 0 : (counts[i] > 0 ? 1 : 0);
+}
+
+__global__ void nonempty_list_kernel(int64_t n, const int64_t* __restrict__ counts, const int64_t* __restrict__ pos,
+                                     int64_t list_cap, int32_t* list, int64_t* n_list, const DevStatus* st) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) *n_list = min(pos[n], list_cap);
+    if (i >= n || (st->flags & kAbortFlags)) return;
+    if (counts[i] > 0 && pos[i] < list_cap) list[pos[i]] = (int32_t)i;
+}
+
 __global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
@@ -324,18 +380,27 @@ void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E
     { segment_sort_kernel<double><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, adj_ptr, adj, nullptr); count_launch(); }
 }
 
+void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t* offsets_g,
+                       const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
+                       double* loc_val, uint8_t* loc_flag, DevStatus* st, cudaStream_t s) {
+    if (m <= 0) return;
+    const unsigned nb = nblk(m * 32, 256);
+    if (dim == 2) { elem_local_kernel<2><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, st); count_launch(); }
+    else { elem_local_kernel<3><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, st); count_launch(); }
+}
+
 void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const int64_t* adj_ptr,
-                   const int32_t* adj, const ElemBox* boxes_g, const int64_t* offsets_g,
-                   const double* blocks, int64_t slot_stride, const double* vols, int64_t* row_count,
+                   const int32_t* adj, const ElemBox* boxes_g, const int64_t* loc_off_g,
+                   const double* loc_val, const uint8_t* loc_flag, int64_t* row_count,
                    const int64_t* row_ptr, int32_t* cols, double* vals, DevStatus* st, cudaStream_t s) {
     if (n_nodes <= 0) return;
     unsigned nb = nblk(n_nodes, kRowWarps);
     if (dim == 2)
-        { b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, offsets_g, blocks,
-                                                      slot_stride, vols, row_count, row_ptr, cols, vals, st); count_launch(); }
+        { b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, loc_off_g, loc_val,
+                                                        loc_flag, row_count, row_ptr, cols, vals, st); count_launch(); }
     else
-        { b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, offsets_g, blocks,
-                                                      slot_stride, vols, row_count, row_ptr, cols, vals, st); count_launch(); }
+        { b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, loc_off_g, loc_val,
+                                                        loc_flag, row_count, row_ptr, cols, vals, st); count_launch(); }
 }
 
 void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
@@ -372,7 +437,16 @@ void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32
 }
 
 void launch_transpose_sort(const CsrT& T, const DevStatus* st, cudaStream_t s) {
-    if (T.n_rows > 0) { transpose_sort_kernel<<<nblk(T.n_rows, kSortWarps), kSortWarps * 32, 0, s>>>(T.n_rows, T.ptr, T.col, T.val, st); count_launch(); }
+    const int64_t n = T.list_cap < T.n_rows ? T.list_cap : T.n_rows;
+    if (n > 0) { transpose_sort_kernel<<<nblk(n, kSortWarps), kSortWarps * 32, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val, st); count_launch(); }
+}
+
+void launch_transpose_list(const CsrT& T, const int64_t* counts, int64_t* flags, void* scan_tmp,
+                           const DevStatus* st, cudaStream_t s) {
+    if (T.n_rows <= 0) return;
+    { nonempty_flags_kernel<<<nblk(T.n_rows, 256), 256, 0, s>>>(T.n_rows, counts, flags, st); count_launch(); }
+    launch_scan_i64(flags, flags, T.n_rows, scan_tmp, s);
+    { nonempty_list_kernel<<<nblk(T.n_rows, 256), 256, 0, s>>>(T.n_rows, counts, flags, T.list_cap, T.list, T.n_list, st); count_launch(); }
 }
 
 void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s) {

@@ -101,7 +101,8 @@ __global__ void pair_scatter_kernel(int G, int64_t m, const int64_t* __restrict_
 }
 
 // Fused, step 4: one thread per pair, in class order.  Gradients come from the
-// element pass; blocks are written structure-of-arrays at the pair's index.
+// element pass; every thread writes its pair's block as one contiguous run
+// (pair-major), i.e. whole cache lines.
 template <int D, typename R>
 __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(int G, SubGridSet sgs, int64_t m,
                                                                   const int64_t* __restrict__ offsets, int64_t n_cap,
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(int G, SubGrid
                                                                   const int32_t* __restrict__ perm,
                                                                   const int32_t* __restrict__ pair_elem,
                                                                   const int32_t* __restrict__ pair_cell,
-                                                                  double* __restrict__ blocks, int64_t slot_stride,
+                                                                  double* __restrict__ blocks,
                                                                   double* __restrict__ vols, DevStatus* st) {
     constexpr int NA = D + 1, NB = 1 << D;
     const int64_t n = min(offsets[(int64_t)G * m], n_cap);
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(int G, SubGrid
         pair_integrals<D, R>(T, gr, flag == 1, scale, blk, &vol);
     }
 #pragma unroll
-    for (int j = 0; j < NA * NB; ++j) blocks[j * slot_stride + p] = blk[j];
+    for (int j = 0; j < NA * NB; ++j) blocks[p * (NA * NB) + j] = blk[j];
     vols[p] = vol;
 }
 
@@ -235,13 +236,13 @@ void launch_pair_classes(int dim, int G, const SubGrid* sg, int64_t m, const int
 void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t m, const int64_t* offsets,
                        int64_t n_launch, int64_t n_cap, const double* X, const int32_t* E, const double* elem_grad,
                        const int8_t* elem_flag, const int32_t* pair_elem, const int32_t* pair_cell,
-                       const int32_t* perm, double* blocks, int64_t slot_stride, double* vols, DevStatus* st,
+                       const int32_t* perm, double* blocks, double* vols, DevStatus* st,
                        cudaStream_t s) {
     if (n_launch <= 0) return;
     SubGridSet sgs{};
     for (int g = 0; g < G; ++g) sgs.g[g] = sg[g];
     const unsigned nb = (unsigned)((n_launch + kClipThreads - 1) / kClipThreads);
-#define L2X_CLIP_ARGS G, sgs, m, offsets, n_cap, X, E, elem_grad, elem_flag, perm, pair_elem, pair_cell, blocks, slot_stride, vols, st
+#define L2X_CLIP_ARGS G, sgs, m, offsets, n_cap, X, E, elem_grad, elem_flag, perm, pair_elem, pair_cell, blocks, vols, st
     if (dim == 2) {
         if (precision == L2X_MIXED) { clip_fused_kernel<2, float><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
         else { clip_fused_kernel<2, double><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }

@@ -21,6 +21,10 @@ enum : int32_t {
     FLAG_TIMEOUT = 32,
 };
 
+// Flags after which the remaining kernels of a captured step skip their work
+// (the step's result is reported invalid by l2x_graph_sync_status).
+constexpr int32_t kAbortFlags = FLAG_OUTOFGRID | FLAG_DEGENERATE | FLAG_NONFINITE | FLAG_CAPACITY;
+
 struct DevStatus {
     int32_t flags;
     int32_t bad_elem;     // first element that raised OUTOFGRID / DEGENERATE (min)
@@ -57,6 +61,8 @@ struct Csr {
 };
 
 // Transposed coupling matrix restricted to the box of fluid nodes the mesh touches.
+// Rows are indexed by box position; `list` holds the non-empty rows (n_list[0]
+// of them, a device value) so that sorting and the force gather skip the rest.
 struct CsrT {
     int32_t lo[3] = {0, 0, 0};   // first node of the box per axis
     int32_t n[3] = {1, 1, 1};    // box nodes per axis
@@ -65,6 +71,9 @@ struct CsrT {
     int32_t* col = nullptr;      // solid node
     double* val = nullptr;
     float* val32 = nullptr;
+    int32_t* list = nullptr;     // non-empty rows (capacity list_cap)
+    int64_t* n_list = nullptr;   // device: number of non-empty rows
+    int64_t list_cap = 0;
 };
 
 // Counts kernel launches of the library (l2x_api.cu).
@@ -72,8 +81,10 @@ void count_launch();
 
 // ---------------------------------------------------------------- launchers
 // pairs (l2x_pairs.cu)
+// Per element and grid: candidate box, pair count (counts) and node count of the
+// box (nbox, for the element-local matrices); volume, gradients, orientation.
 void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const double* X,
-                       const int32_t* E, ElemBox* boxes, int64_t* counts, int32_t* node_box,
+                       const int32_t* E, ElemBox* boxes, int64_t* counts, int64_t* nbox, int32_t* node_box,
                        double* elem_vol, double* elem_grad, int8_t* elem_flag, DevStatus* st, cudaStream_t s);
 void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
 size_t scan_tmp_bytes(int64_t n);
@@ -84,8 +95,8 @@ void launch_reset_status(DevStatus* st, cudaStream_t s);
 // FLAG_CAPACITY if *total > cap (device value); kernels after it skip their work
 void launch_check_capacity(const int64_t* total, int64_t cap, DevStatus* st, cudaStream_t s);
 
-// clipping + quadrature (l2x_clip.cu).  Pair blocks are stored at
-// blocks[slot * slot_stride + p * pair_stride], slot = a * 2^d + b.
+// clipping + quadrature (l2x_clip.cu).  Pair blocks are stored pair-major:
+// blocks[p * (d+1) * 2^d + a * 2^d + b].
 // Fused: pairs of all grids are first bucketed by scheduling class (similar
 // control flow per warp, launch_pair_classes), then clipped in bucket order.
 // Sizes are read on the device from offsets[G * m] (bounded by n_cap); n_launch
@@ -99,8 +110,7 @@ void launch_pair_classes(int dim, int G, const SubGrid* sg, int64_t m, const int
 void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t m, const int64_t* offsets,
                        int64_t n_launch, int64_t n_cap, const double* X, const int32_t* E, const double* elem_grad,
                        const int8_t* elem_flag, const int32_t* pair_elem, const int32_t* pair_cell,
-                       const int32_t* perm, double* blocks, int64_t slot_stride, double* vols, DevStatus* st,
-                       cudaStream_t s);
+                       const int32_t* perm, double* blocks, double* vols, DevStatus* st, cudaStream_t s);
 void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
                        int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, double* blocks,
                        double* vols, DevStatus* st, cudaStream_t s);
@@ -114,11 +124,19 @@ void launch_scatter_plain(int dim, const SubGrid& sg, const int32_t* E, int64_t 
 // adj_ptr must hold n_nodes + 1 entries; cursor n_nodes int32 (scratch).
 void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E, int64_t* adj_ptr,
                            int32_t* adj, int32_t* cursor, void* scan_tmp, cudaStream_t s);
-// Row-wise assembly of B_g.  pass 0: row_count[i] = nonzeros of row i;
-// pass 1: cols + vals (fused, from SoA blocks); pass 2: cols only, vals zeroed (plain).
+// Element-local matrices of grid g: for every element and every node of its
+// candidate node box, the sums over the element's pairs of block[a][b] at that
+// node (loc_val, (d+1) per node) and whether a pair of positive volume touches
+// it (loc_flag).  loc_off_g: offsets of the elements' node boxes.
+void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t* offsets_g,
+                       const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
+                       double* loc_val, uint8_t* loc_flag, DevStatus* st, cudaStream_t s);
+// Row-wise assembly of B_g from the element-local matrices.  pass 0:
+// row_count[i] = nonzeros of row i; pass 1: cols + vals; pass 2: cols only,
+// vals zeroed (the plain path adds them with atomics).
 void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const int64_t* adj_ptr,
-                   const int32_t* adj, const ElemBox* boxes_g, const int64_t* offsets_g,
-                   const double* blocks, int64_t slot_stride, const double* vols, int64_t* row_count,
+                   const int32_t* adj, const ElemBox* boxes_g, const int64_t* loc_off_g,
+                   const double* loc_val, const uint8_t* loc_flag, int64_t* row_count,
                    const int64_t* row_ptr, int32_t* cols, double* vals, DevStatus* st, cudaStream_t s);
 // P1 mass matrix structure (pass 0 counts, pass 1 columns) and values.
 void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
@@ -133,6 +151,10 @@ void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int6
 void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32_t* cursor, const DevStatus* st,
                            cudaStream_t s);
 void launch_transpose_sort(const CsrT& T, const DevStatus* st, cudaStream_t s);
+// Non-empty rows of B_g^T from the row counts (before they are scanned):
+// flags (int64, n_rows + 1) is scratch; fills T.list and *T.n_list.
+void launch_transpose_list(const CsrT& T, const int64_t* counts, int64_t* flags, void* scan_tmp,
+                           const DevStatus* st, cudaStream_t s);
 void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 
 // apply (l2x_apply.cu)

@@ -23,7 +23,7 @@ __device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
 template <int D>
 __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const double* __restrict__ X,
                                   const int32_t* __restrict__ E, ElemBox* __restrict__ boxes,
-                                  int64_t* __restrict__ counts, int32_t* __restrict__ node_box,
+                                  int64_t* __restrict__ counts, int64_t* __restrict__ nbox, int32_t* __restrict__ node_box,
                                   double* __restrict__ elem_vol, double* __restrict__ elem_grad,
                                   int8_t* __restrict__ elem_flag, DevStatus* st) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -94,6 +94,7 @@ __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const 
         b.ext = ext[0] | (ext[1] << 10) | (ext[2] << 20);
         boxes[g * m + e] = b;
         counts[g * m + e] = count;
+        nbox[g * m + e] = count > 0 ? (int64_t)(ext[0] + 1) * (ext[1] + 1) * (D == 3 ? ext[2] + 1 : 1) : 0;
         if (count > 0) {
             for (int k = 0; k < D; ++k) {
                 atomicMin(node_box + g * 6 + k, b.lo[k]);
@@ -234,7 +235,7 @@ void launch_check_capacity(const int64_t* total, int64_t cap, DevStatus* st, cud
 }
 
 void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const double* X,
-                       const int32_t* E, ElemBox* boxes, int64_t* counts, int32_t* node_box,
+                       const int32_t* E, ElemBox* boxes, int64_t* counts, int64_t* nbox, int32_t* node_box,
                        double* elem_vol, double* elem_grad, int8_t* elem_flag, DevStatus* st, cudaStream_t s) {
     SubGridSet sgs{};
     for (int g = 0; g < n_grids; ++g) sgs.g[g] = sg_host[g];
@@ -242,9 +243,9 @@ void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
     int64_t blocks = (m + threads - 1) / threads;
     if (blocks == 0) return;
     if (dim == 2)
-        { elem_boxes_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, elem_grad, elem_flag, st); count_launch(); }
+        { elem_boxes_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, nbox, node_box, elem_vol, elem_grad, elem_flag, st); count_launch(); }
     else
-        { elem_boxes_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, node_box, elem_vol, elem_grad, elem_flag, st); count_launch(); }
+        { elem_boxes_kernel<3><<<(unsigned)blocks, threads, 0, s>>>(n_grids, sgs, m, X, E, boxes, counts, nbox, node_box, elem_vol, elem_grad, elem_flag, st); count_launch(); }
 }
 
 size_t scan_tmp_bytes(int64_t n) {
