@@ -245,9 +245,14 @@ class Arm:
         self.u32, self.f32, self.dev, self.world, self.flush = u32, f32, dev, world, flush
 
     def coupling(self, path, precision, X=None):
+        """A coupling on the first configuration; fused forms pick their work-chunk
+        sizes with the library's autotuner."""
         l2x = self.l2x
-        return l2x.Coupling(self.grid, self.positions[0] if X is None else X, self.E, path=path,
-                            precision=precision, cg_rtol=1e-9 if precision == l2x.MIXED else 1e-13)
+        c = l2x.Coupling(self.grid, self.positions[0] if X is None else X, self.E, path=path,
+                         precision=precision, cg_rtol=1e-9 if precision == l2x.MIXED else 1e-13)
+        if path == l2x.FUSED:
+            self.tuned = c.autotune()
+        return c
 
     def per_call(self, path, precision, steps, warmup, timing=False):
         """One library call per operation: update_geometry, transfer_velocity, transfer_force."""
@@ -486,6 +491,7 @@ def main():
                            "cg_iters": f64["info"]["cg_iters"]},
             "e2e": {"value": e_value, "unit": UNIT, "ms_per_step": e_step_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "autotuned": getattr(arm, "tuned", None),
             "gpu_launches": int(pc["launches"] / n_pc * args.steps),
             "gpu_launches_note": "per step as counted on the per-call form; the captured graph replays the same "
                                  "kernel nodes",

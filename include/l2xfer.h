@@ -120,6 +120,8 @@ typedef struct l2x_info {
     double cg_residual;        /* relative residual reached by the last solve (max over components) */
     double phase_ms[8];        /* device time per phase since l2x_set_timing(h, 1) (CUDA events) */
     int64_t phase_calls[8];    /* timed intervals per phase */
+    int32_t clip_block;        /* pairs per thread block of the clip kernel (l2x_autotune) */
+    int32_t pcg_rows_per_block;/* rows per thread block of the cooperative PCG (l2x_autotune) */
 } l2x_info;
 
 typedef struct l2x_coupling* l2x_handle;
@@ -205,6 +207,14 @@ l2x_status l2x_export_pair_range(l2x_handle h, int32_t grid, int64_t e_first, in
                                  double* blocks, double* vols, void* stream);
 l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t* cols,
                           double* vals, void* stream);
+
+/* Picks work-chunk sizes for this coupling by timing candidates on it (CUDA
+ * events, best of two after a warm-up run): pairs per block of the clip kernel
+ * (64, 128, 256) and rows per block of the cooperative PCG (32, 64, 128).  Call
+ * after a build; later builds, solves and captured steps use the choice
+ * (reported in l2x_info).  Runs the clip kernel and the solve a few times on the
+ * stream and synchronises it. */
+l2x_status l2x_autotune(l2x_handle h, void* stream);
 
 /* Enables (1, also clears the totals) or disables (0) CUDA-event timing of the
  * phases listed above, recorded on the stream of each call; l2x_query resolves

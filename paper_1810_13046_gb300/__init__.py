@@ -54,7 +54,8 @@ class _Info(ctypes.Structure):
                 ("n_pairs", ctypes.c_int64 * 3), ("n_pairs_total", ctypes.c_int64), ("nnz_B", ctypes.c_int64 * 3),
                 ("nnz_M", ctypes.c_int64), ("n_fluid", ctypes.c_int64 * 3), ("nnode", (ctypes.c_int32 * 3) * 3),
                 ("cg_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cg_residual", ctypes.c_double),
-                ("phase_ms", ctypes.c_double * 8), ("phase_calls", ctypes.c_int64 * 8)]
+                ("phase_ms", ctypes.c_double * 8), ("phase_calls", ctypes.c_int64 * 8),
+                ("clip_block", ctypes.c_int32), ("pcg_rows_per_block", ctypes.c_int32)]
 
 
 PHASES = ["pairs", "clip", "rows", "transpose", "mass", "spmv_B", "pcg", "spmv_BT"]
@@ -97,6 +98,7 @@ def load_library(build_if_missing: bool = True):
                                    ctypes.POINTER(ctypes.c_int64), P, P, P, P, P], ctypes.c_int),
         "l2x_destroy": ([P], ctypes.c_int),
         "l2x_set_timing": ([P, ctypes.c_int32], ctypes.c_int),
+        "l2x_autotune": ([P, P], ctypes.c_int),
         "l2x_graph_create": ([P, P, PP, PP, PP, PP, ctypes.c_double, ctypes.c_int32, P,
                               ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "l2x_graph_launch": ([P, P], ctypes.c_int),
@@ -224,7 +226,15 @@ class Coupling:
                     nnode=[tuple(inf.nnode[g][k] for k in range(3)) for g in range(G)],
                     cg_iters=inf.cg_iters, cg_residual=inf.cg_residual,
                     phase_ms={p: inf.phase_ms[i] for i, p in enumerate(PHASES)},
-                    phase_calls={p: inf.phase_calls[i] for i, p in enumerate(PHASES)})
+                    phase_calls={p: inf.phase_calls[i] for i, p in enumerate(PHASES)},
+                    clip_block=inf.clip_block, pcg_rows_per_block=inf.pcg_rows_per_block)
+
+    def autotune(self):
+        """Pick work-chunk sizes by timing candidates on this coupling."""
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_autotune(self._h, _stream_ptr(self.device)))
+        i = self.info()
+        return dict(clip_block=i["clip_block"], pcg_rows_per_block=i["pcg_rows_per_block"])
 
     def set_timing(self, enable: bool = True):
         """CUDA-event timing of the library's phases (totals in info()['phase_ms'])."""

@@ -79,6 +79,9 @@ struct l2x_coupling {
     void* vec_tmp = nullptr;         // n_grids * n_nodes doubles
     DevStatus* st = nullptr;
     DevStatus* st_host = nullptr;    // pinned
+    // work-chunk sizes (l2x_autotune)
+    int clip_block = 128;            // threads (= pairs) per block of the clip kernel
+    int pcg_rpb = 64;                // rows per block of the cooperative PCG
     // last solve
     int cg_iters = 0;
     double cg_residual = 0.0;
@@ -254,6 +257,15 @@ l2x_status ensure_tlist(l2x_coupling* h, CsrT& T, int64_t rows, int64_t entries)
         T.list_cap = c;
     }
     if (!T.n_list) L2X_TRY(dalloc(&T.n_list, 1));
+    if (!T.n_long) L2X_TRY(dalloc(&T.n_long, 1));
+    // rows longer than kSortMax (512) entries: at most entries / 513 of them
+    const int64_t lneed = entries / 513 + 1;
+    if (lneed > T.long_cap || !T.long_rows) {
+        dfree(T.long_rows);
+        T.long_cap = 0;
+        L2X_TRY(dalloc(&T.long_rows, lneed));
+        T.long_cap = lneed;
+    }
     if (rows + 1 > h->tflags_cap || !h->tflags) {
         dfree(h->tflags);
         L2X_TRY(dalloc(&h->tflags, rows + 1));
@@ -365,7 +377,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         }
         PhaseScope ph(h, L2X_PH_CLIP, s);
         launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, NP, h->pair_cap, h->X, h->E, h->elem_grad,
-                          h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st, s);
+                          h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st, s, h->clip_block);
     }
     // (IV) B_g by rows
     for (int g = 0; g < G; ++g) {
@@ -511,7 +523,7 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
                         h->pair_key, h->pair_perm, h->buckets, s);
     launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, h->pair_cap, h->pair_cap, h->X, h->E,
                       h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st,
-                      s);
+                      s, h->clip_block);
     for (int g = 0; g < G; ++g) {
         Csr& B = h->B[g];
         const ElemBox* bx = h->boxes + (int64_t)g * m;
@@ -544,12 +556,12 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     for (int g = 0; g < G; ++g) tmp[g] = (char*)h->vec_tmp + es * n * g;
     launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, tmp, h->st, s);
     solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)tmp, u_s,
-                         h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s);
+                         h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
     if (zero_force)
         for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
     if (h->opts.force_mode == L2X_FORCE_DUAL) {
         solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, f_s, tmp, h->opts.cg_rtol,
-                             h->opts.cg_max_iter, h->pcg_ws, h->st, s);
+                             h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
         launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)tmp, f_f,
                        h->opts.force_scale, h->st, s);
     } else {
@@ -609,7 +621,7 @@ l2x_status l2x_destroy(l2x_handle h) {
     for (int g = 0; g < kMaxGrids; ++g) {
         dfree(h->B[g].ptr); dfree(h->B[g].col); dfree(h->B[g].val); dfree(h->B[g].val32);
         dfree(h->T[g].ptr); dfree(h->T[g].col); dfree(h->T[g].val); dfree(h->T[g].val32);
-        dfree(h->T[g].list); dfree(h->T[g].n_list);
+        dfree(h->T[g].list); dfree(h->T[g].n_list); dfree(h->T[g].long_rows); dfree(h->T[g].n_long);
     }
     dfree(h->M.ptr); dfree(h->M.col); dfree(h->M.val); dfree(h->M.val32); dfree(h->M_dinv); dfree(h->M_dinv32);
     if (h->scan_tmp) cudaFree(h->scan_tmp);
@@ -729,7 +741,8 @@ l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s
     PcgResult r;
     auto ph = std::make_unique<PhaseScope>(h, L2X_PH_PCG, s);
     l2x_status st = solve_mass_pcg(h->opts.path, h->opts.precision, h->M, h->M_dinv, h->M_dinv32, h->n_grids, y_s,
-                                   w_s, h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, h->st_host, s, &r);
+                                   w_s, h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, h->st_host, s, &r,
+                                   h->pcg_rpb);
     ph.reset();
     h->cg_iters = r.iters;
     h->cg_residual = r.residual;
@@ -934,12 +947,98 @@ l2x_status l2x_query(l2x_handle h, l2x_info* info) {
     info->nnz_M = h->M.nnz;
     info->cg_iters = h->cg_iters;
     info->cg_residual = h->cg_residual;
+    info->clip_block = h->clip_block;
+    info->pcg_rows_per_block = h->pcg_rpb;
     resolve_timing(h);
     for (int p = 0; p < L2X_NPHASE; ++p) {
         info->phase_ms[p] = h->phase_ms[p];
         info->phase_calls[p] = h->phase_calls[p];
     }
     return L2X_OK;
+}
+
+l2x_status l2x_autotune(l2x_handle h, void* stream) {
+    g_last_error.clear();
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->stream = s;
+    const int64_t m = h->n_elems, n = h->n_nodes;
+    const int G = h->n_grids, d = h->dim;
+    cudaEvent_t a = nullptr, b = nullptr;
+    L2X_CUDA(cudaEventCreate(&a));
+    L2X_CUDA(cudaEventCreate(&b));
+    auto timed = [&](auto&& fn) -> float {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(a, s);
+            fn();
+            cudaEventRecord(b, s);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (rep > 0 && ms < best) best = ms;  // first run warms up
+        }
+        return best;
+    };
+    l2x_status status = L2X_OK;
+    if (h->opts.path == L2X_PATH_FUSED && h->n_pairs > 0) {
+        // clip kernel: pairs per block, on the current pairs (class order of the last build)
+        float best = 1e30f;
+        int best_blk = h->clip_block;
+        for (int blk : {64, 128, 256}) {
+            const float ms = timed([&] {
+                launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, h->n_pairs, h->pair_cap, h->X, h->E,
+                                  h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks,
+                                  h->vols, h->st, s, blk);
+            });
+            if (ms < best) {
+                best = ms;
+                best_blk = blk;
+            }
+        }
+        h->clip_block = best_blk;
+    }
+    {
+        // PCG: rows per block, on M applied to a vector of ones
+        const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+        void* y[kMaxGrids];
+        void* w[kMaxGrids];
+        char* tmp = nullptr;
+        if (cudaMalloc((void**)&tmp, es * n * G * 2) != cudaSuccess) status = fail(L2X_ENOMEM, "autotune scratch");
+        if (status == L2X_OK) {
+            for (int g = 0; g < G; ++g) {
+                y[g] = tmp + es * n * g;
+                w[g] = tmp + es * n * (G + g);
+            }
+            // y = row sums of M (the mass of every node), through the diagonal scaling kernel-free path:
+            // fill y with 1/dinv (the diagonal), any positive right-hand side serves
+            std::vector<double> ones(n, 1.0);
+            std::vector<float> onesf(n, 1.0f);
+            for (int g = 0; g < G; ++g)
+                cudaMemcpyAsync(y[g], es == 8 ? (const void*)ones.data() : (const void*)onesf.data(), es * n,
+                                cudaMemcpyHostToDevice, s);
+            float best = 1e30f;
+            int best_rpb = h->pcg_rpb;
+            for (int rpb : {32, 64, 128}) {
+                const float ms = timed([&] {
+                    solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)y,
+                                         w, h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, rpb);
+                });
+                if (ms < best) {
+                    best = ms;
+                    best_rpb = rpb;
+                }
+            }
+            h->pcg_rpb = best_rpb;
+            cudaStreamSynchronize(s);
+            cudaFree(tmp);
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (status != L2X_OK) return status;
+    L2X_CUDA(cudaGetLastError());
+    return read_status(h, s);
 }
 
 l2x_status l2x_set_timing(l2x_handle h, int32_t enable) {

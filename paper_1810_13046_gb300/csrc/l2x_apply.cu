@@ -603,7 +603,7 @@ __global__ void store_f32_kernel(int64_t n, int nr, const double* x64, float* w0
 }
 
 template <typename TV, int NR>
-int pcg_blocks_for(int64_t n) {
+int pcg_blocks_for(int64_t n, int rows_per_block_req) {
     static int sms = 0, per_sm = 0;
     if (sms == 0) {
         int dev = 0;
@@ -612,7 +612,7 @@ int pcg_blocks_for(int64_t n) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_fused_kernel<TV, NR>, kPcgBlock, 0);
         if (per_sm < 1) per_sm = 1;
     }
-    const int64_t rows_per_block = kPcgBlock / kRowLanes;  // one pass of the product per block
+    const int64_t rows_per_block = rows_per_block_req > 0 ? rows_per_block_req : kPcgBlock / kRowLanes;
     int64_t want = (n + rows_per_block - 1) / rows_per_block;
     int64_t cap = (int64_t)sms * per_sm;
     int64_t b = want < cap ? want : cap;
@@ -623,7 +623,7 @@ int pcg_blocks_for(int64_t n) {
 template <typename TV>
 cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val, const TV* dinv, int64_t n,
                           int nr, const TV* const* y, TV* const* x, TV* vecs, double* partial, double rtol,
-                          int max_iter, DevStatus* st, cudaStream_t s) {
+                          int max_iter, DevStatus* st, cudaStream_t s, int rpb = 64) {
     PcgArgs<TV> A{};
     A.n = n;
     A.nrhs = nr;
@@ -649,13 +649,13 @@ cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val,
     count_launch();
     switch (nr) {
         case 1:
-            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 1>, dim3(pcg_blocks_for<TV, 1>(n)),
+            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 1>, dim3(pcg_blocks_for<TV, 1>(n, rpb)),
                                                dim3(kPcgBlock), args, 0, s);
         case 2:
-            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 2>, dim3(pcg_blocks_for<TV, 2>(n)),
+            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 2>, dim3(pcg_blocks_for<TV, 2>(n, rpb)),
                                                dim3(kPcgBlock), args, 0, s);
         default:
-            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 3>, dim3(pcg_blocks_for<TV, 3>(n)),
+            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 3>, dim3(pcg_blocks_for<TV, 3>(n, rpb)),
                                                dim3(kPcgBlock), args, 0, s);
     }
 }
@@ -728,7 +728,7 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
 
 void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, const float* diag_inv32, int nr,
                           const void* const* y, void* const* w, double rtol, int max_iter, void* ws, DevStatus* st,
-                          cudaStream_t s) {
+                          cudaStream_t s, int rpb) {
     const int64_t n = M.n_rows;
     if (n <= 0 || nr <= 0) return;
     const int64_t v = n * nr;
@@ -742,7 +742,7 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
     if (precision == L2X_FP64) {
         double* vecs = (double*)take(5 * v * 8);
         run_pcg_fused<double>(M.ptr, M.col, M.val, diag_inv, n, nr, (const double* const*)y, (double* const*)w, vecs,
-                              partial, rtol, max_iter, st, s);
+                              partial, rtol, max_iter, st, s, rpb);
         return;
     }
     float* vecs = (float*)take(5 * v * 4);
@@ -764,7 +764,7 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
             rhs[k] = ref == 0 ? yf[k] : r32 + k * n;
             dst[k] = d32 + k * n;
         }
-        run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s);
+        run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s, rpb);
         { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr, nr > 2 ? dst[2] : nullptr, ref == 0); count_launch(); }
         if (ref == 0) {
             cudaMemsetAsync(norms, 0, 4 * 8, s);
@@ -776,7 +776,7 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
 
 l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv, const float* diag_inv32,
                           int nr, const void* const* y, void* const* w, double rtol, int max_iter, void* ws,
-                          DevStatus* st, DevStatus* st_host, cudaStream_t s, PcgResult* res) {
+                          DevStatus* st, DevStatus* st_host, cudaStream_t s, PcgResult* res, int rpb) {
     const int64_t n = M.n_rows;
     res->iters = 0;
     res->residual = 0.0;
@@ -844,7 +844,7 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
         double* vecs = (double*)take(5 * v * 8);
         cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s);
         ce = run_pcg_fused<double>(M.ptr, M.col, M.val, diag_inv, n, nr, (const double* const*)y, (double* const*)w,
-                                   vecs, partial, rtol, max_iter, st, s);
+                                   vecs, partial, rtol, max_iter, st, s, rpb);
         if (ce != cudaSuccess) return L2X_ECUDA;
         if (cudaMemcpyAsync(st_host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return L2X_ECUDA;
@@ -881,7 +881,7 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
         }
         cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s);
         ce = run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner,
-                                  max_iter, st, s);
+                                  max_iter, st, s, rpb);
         if (ce != cudaSuccess) return L2X_ECUDA;
         { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr,
                                                  nr > 2 ? dst[2] : nullptr, ref == 0); count_launch(); }

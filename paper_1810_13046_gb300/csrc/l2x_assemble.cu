@@ -299,12 +299,16 @@ __global__ void transpose_fill_kernel(int64_t n_rows, const int64_t* __restrict_
 // entry's final position is its rank, counted against the row staged in shared
 // memory.  Rows longer than the staging area are sorted in place by one lane.
 constexpr int kSortWarps = 4;
-constexpr int kSortMax = 512;
+constexpr int kSortMax = 512;      // rows up to this length: one warp, shared memory
+constexpr int kSortLong = 256;     // threads per block for longer rows
+constexpr int kSortLongMax = 8192; // rows up to this length: one block, dynamic shared memory
 
 __global__ void __launch_bounds__(kSortWarps * 32) transpose_sort_kernel(const int32_t* __restrict__ list,
                                                                         const int64_t* __restrict__ n_list,
                                                                         const int64_t* __restrict__ ptr,
-                                                                        int32_t* key, double* val, const DevStatus* st) {
+                                                                        int32_t* key, double* val, const DevStatus* st,
+                                                                        int32_t* long_rows, int32_t* n_long,
+                                                                        int64_t long_cap) {
     __shared__ int32_t sk[kSortWarps][kSortMax];
     __shared__ double sv[kSortWarps][kSortMax];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -329,18 +333,55 @@ __global__ void __launch_bounds__(kSortWarps * 32) transpose_sort_kernel(const i
         }
         return;
     }
-    if (lane != 0) return;
+    // longer rows: sorted by transpose_sort_long_kernel, one block each
+    if (lane == 0) {
+        const int32_t slot = atomicAdd(n_long, 1);
+        if (slot < long_cap) long_rows[slot] = (int32_t)i;
+    }
+}
+
+// Block per long row of B_g^T: rank sort of up to kSortLongMax entries staged in
+// dynamic shared memory; still longer rows are sorted in place by one thread.
+__global__ void __launch_bounds__(kSortLong) transpose_sort_long_kernel(const int32_t* __restrict__ long_rows,
+                                                                       const int32_t* __restrict__ n_long,
+                                                                       int64_t long_cap,
+                                                                       const int64_t* __restrict__ ptr, int32_t* key,
+                                                                       double* val, const DevStatus* st) {
+    extern __shared__ unsigned char smem[];
+    double* sv = reinterpret_cast<double*>(smem);
+    int32_t* sk = reinterpret_cast<int32_t*>(smem + sizeof(double) * kSortLongMax);
+    const int64_t b = blockIdx.x;
+    if (b >= min((int64_t)*n_long, long_cap) || (st->flags & kAbortFlags)) return;
+    const int64_t r = long_rows[b];
+    const int64_t lo = ptr[r], hi = ptr[r + 1];
+    const int len = (int)(hi - lo);
+    if (len <= kSortLongMax) {
+        for (int a = threadIdx.x; a < len; a += blockDim.x) {
+            sk[a] = key[lo + a];
+            sv[a] = val[lo + a];
+        }
+        __syncthreads();
+        for (int a = threadIdx.x; a < len; a += blockDim.x) {
+            const int32_t k = sk[a];
+            int rank = 0;
+            for (int c = 0; c < len; ++c) rank += sk[c] < k;
+            key[lo + rank] = k;
+            val[lo + rank] = sv[a];
+        }
+        return;
+    }
+    if (threadIdx.x != 0) return;
     for (int64_t a = lo + 1; a < hi; ++a) {
         const int32_t kk = key[a];
         const double vv = val[a];
-        int64_t b = a - 1;
-        while (b >= lo && key[b] > kk) {
-            key[b + 1] = key[b];
-            val[b + 1] = val[b];
-            --b;
+        int64_t c = a - 1;
+        while (c >= lo && key[c] > kk) {
+            key[c + 1] = key[c];
+            val[c + 1] = val[c];
+            --c;
         }
-        key[b + 1] = kk;
-        val[b + 1] = vv;
+        key[c + 1] = kk;
+        val[c + 1] = vv;
     }
 }
 
@@ -438,7 +479,16 @@ void launch_transpose_fill(const Csr& B, const SubGrid& sg, const CsrT& T, int32
 
 void launch_transpose_sort(const CsrT& T, const DevStatus* st, cudaStream_t s) {
     const int64_t n = T.list_cap < T.n_rows ? T.list_cap : T.n_rows;
-    if (n > 0) { transpose_sort_kernel<<<nblk(n, kSortWarps), kSortWarps * 32, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val, st); count_launch(); }
+    if (n <= 0) return;
+    cudaMemsetAsync(T.n_long, 0, sizeof(int32_t), s);
+    { transpose_sort_kernel<<<nblk(n, kSortWarps), kSortWarps * 32, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val, st, T.long_rows, T.n_long, T.long_cap); count_launch(); }
+    static bool attr_set = false;
+    const int smem = (int)((sizeof(double) + sizeof(int32_t)) * kSortLongMax);
+    if (!attr_set) {
+        cudaFuncSetAttribute(transpose_sort_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr_set = true;
+    }
+    if (T.long_cap > 0) { transpose_sort_long_kernel<<<(unsigned)T.long_cap, kSortLong, smem, s>>>(T.long_rows, T.n_long, T.long_cap, T.ptr, T.col, T.val, st); count_launch(); }
 }
 
 void launch_transpose_list(const CsrT& T, const int64_t* counts, int64_t* flags, void* scan_tmp,

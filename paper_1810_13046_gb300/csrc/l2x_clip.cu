@@ -104,7 +104,7 @@ __global__ void pair_scatter_kernel(int G, int64_t m, const int64_t* __restrict_
 // element pass; every thread writes its pair's block as one contiguous run
 // (pair-major), i.e. whole cache lines.
 template <int D, typename R>
-__global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(int G, SubGridSet sgs, int64_t m,
+__global__ void __launch_bounds__(256) clip_fused_kernel(int G, SubGridSet sgs, int64_t m,
                                                                   const int64_t* __restrict__ offsets, int64_t n_cap,
                                                                   const double* __restrict__ X,
                                                                   const int32_t* __restrict__ E,
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kClipThreads) clip_fused_kernel(int G, SubGrid
                                                                   double* __restrict__ vols, DevStatus* st) {
     constexpr int NA = D + 1, NB = 1 << D;
     const int64_t n = min(offsets[(int64_t)G * m], n_cap);
-    const int64_t i = blockIdx.x * (int64_t)kClipThreads + threadIdx.x;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t p = perm[i];
     const int g = grid_of_pair(p, G, m, offsets);
@@ -237,10 +237,12 @@ void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t
                        int64_t n_launch, int64_t n_cap, const double* X, const int32_t* E, const double* elem_grad,
                        const int8_t* elem_flag, const int32_t* pair_elem, const int32_t* pair_cell,
                        const int32_t* perm, double* blocks, double* vols, DevStatus* st,
-                       cudaStream_t s) {
+                       cudaStream_t s, int block) {
     if (n_launch <= 0) return;
     SubGridSet sgs{};
     for (int g = 0; g < G; ++g) sgs.g[g] = sg[g];
+    if (block != 64 && block != 128 && block != 256) block = kClipThreads;
+    const int kClipThreads = block;
     const unsigned nb = (unsigned)((n_launch + kClipThreads - 1) / kClipThreads);
 #define L2X_CLIP_ARGS G, sgs, m, offsets, n_cap, X, E, elem_grad, elem_flag, perm, pair_elem, pair_cell, blocks, vols, st
     if (dim == 2) {

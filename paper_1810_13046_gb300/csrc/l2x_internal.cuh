@@ -74,6 +74,9 @@ struct CsrT {
     int32_t* list = nullptr;     // non-empty rows (capacity list_cap)
     int64_t* n_list = nullptr;   // device: number of non-empty rows
     int64_t list_cap = 0;
+    int32_t* long_rows = nullptr;  // rows longer than a warp sorts (capacity long_cap)
+    int32_t* n_long = nullptr;     // device: their number
+    int64_t long_cap = 0;
 };
 
 // Counts kernel launches of the library (l2x_api.cu).
@@ -110,7 +113,8 @@ void launch_pair_classes(int dim, int G, const SubGrid* sg, int64_t m, const int
 void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t m, const int64_t* offsets,
                        int64_t n_launch, int64_t n_cap, const double* X, const int32_t* E, const double* elem_grad,
                        const int8_t* elem_flag, const int32_t* pair_elem, const int32_t* pair_cell,
-                       const int32_t* perm, double* blocks, double* vols, DevStatus* st, cudaStream_t s);
+                       const int32_t* perm, double* blocks, double* vols, DevStatus* st, cudaStream_t s,
+                       int block = 128);
 void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
                        int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, double* blocks,
                        double* vols, DevStatus* st, cudaStream_t s);
@@ -179,11 +183,11 @@ struct PcgResult {
 // refinement.  Convergence is reported through the device status word.
 void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, const float* diag_inv32, int n_rhs,
                           const void* const* y, void* const* w, double rtol, int max_iter, void* ws, DevStatus* st,
-                          cudaStream_t s);
+                          cudaStream_t s, int rows_per_block = 64);
 l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv,
                           const float* diag_inv32, int n_rhs, const void* const* y, void* const* w,
                           double rtol, int max_iter, void* ws, DevStatus* st, DevStatus* st_host,
-                          cudaStream_t s, PcgResult* res);
+                          cudaStream_t s, PcgResult* res, int rows_per_block = 64);
 size_t pcg_ws_bytes(int64_t n, int n_rhs, int max_blocks);
 int pcg_max_blocks();
 

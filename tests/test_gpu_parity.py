@@ -278,3 +278,20 @@ def test_autograd_velocity_and_force_transfer():
     for g in range(3):
         ref = oc.dense_T(g) @ gf[g].cpu().numpy()
         assert rel_l2(f[g].grad.cpu().numpy(), ref) <= 1e-11
+
+
+def test_autotune_keeps_results():
+    """The autotuner only changes work-chunk sizes: pair blocks are identical and
+    the transfers agree to solver tolerance after tuning."""
+    l2x = _l2x()
+    w = workload("beam32")
+    c = gpu_coupling(w, cg_rtol=1e-14)
+    u = [torch.from_numpy(f).cuda() for f in w.fields]
+    before = torch.stack(c.transfer_velocity(u)).cpu().numpy()
+    b0 = c.export_pair_blocks(0)[0].clone()
+    choice = c.autotune()
+    assert choice["clip_block"] in (64, 128, 256) and choice["pcg_rows_per_block"] in (32, 64, 128)
+    c.update_geometry(torch.from_numpy(w.coords).cuda())
+    assert torch.equal(c.export_pair_blocks(0)[0], b0)
+    after = torch.stack(c.transfer_velocity(u)).cpu().numpy()
+    assert rel_l2(after, before) <= 1e-13
