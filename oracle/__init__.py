@@ -10,6 +10,9 @@ CUDA path.
   P1 mass matrix (the "S = M_s" case of the mortar integrals, with the P1 mass
   matrix of Sec. 2.1 "Spatial Discretization"), the solve ``S w = B v`` of the
   algebraic transfer and the transpose force transfer ``f = s * T^T r``.
+* With ``multiplier="dual"`` the multiplier space is spanned by the dual basis
+  of Eq. (biorth) (the "pseudo" L2-projection of Sec. 2.3): B is assembled from
+  the dual weights and S is diagonal.
 
 Readings of the paper taken here (each is a stated choice, not paper text):
 * one Q1 space per staggered velocity grid; grid g has nodes at ``o_g + i*h``
@@ -17,7 +20,12 @@ Readings of the paper taken here (each is a stated choice, not paper text):
 * the force input of the DUAL mode is an integrated residual r, so
   ``T^T r = B^T M^{-1} r``; the NODAL mode takes nodal force coefficients and
   returns ``B^T f``;
-* a solid element must lie inside the cells covered by every Q1 grid.
+* a solid element must lie inside the cells covered by every Q1 grid;
+* the dual basis is built element by element: on element E the function dual
+  to the hat function of its vertex a is mu_a = (d+2) lambda_a - 1, and the
+  global dual function of node i is the sum of these over the elements around
+  i.  Then int_E mu_a lambda_b = delta_ab |E|/(d+1), which is Eq. (biorth) with
+  (mu_i, 1) = sum_{E ni i} |E|/(d+1), so S = diag(int phi_i).
 """
 from __future__ import annotations
 
@@ -187,18 +195,34 @@ def corner_nodes(sg: SubGrid, pc: np.ndarray) -> np.ndarray:
 
 # ----------------------------------------------------------------------------- (IV)
 
-def assemble_B(sg: SubGrid, X, E, nthreads: int = 1, return_pairs: bool = False):
+def dual_blocks(blocks: np.ndarray) -> np.ndarray:
+    """int_{E cap C} mu_a psi_b for the element dual basis mu_a = (d+2) lambda_a - 1.
+
+    The barycentrics sum to one, so int_{E cap C} psi_b = sum_a' int lambda_a' psi_b
+    and the dual integral is (d+2) * block[a][b] - sum_a' block[a'][b].
+    """
+    d = blocks.shape[1] - 1
+    return (d + 2) * blocks - blocks.sum(axis=1, keepdims=True)
+
+
+def assemble_B(sg: SubGrid, X, E, nthreads: int = 1, return_pairs: bool = False,
+               multiplier: str = "standard"):
     """Mixed coupling matrix B (n_solid x n_fluid) of one Q1 grid, Eq. of the mortar integrals.
 
-    Entries of pairs whose intersection volume is exactly zero are left out.
+    B_ij = int N_fsi,i psi_j with N_fsi,i = phi_i (``multiplier="standard"``) or
+    the dual function of node i (``"dual"``).  Entries of pairs whose
+    intersection volume is exactly zero are left out.
     """
+    if multiplier not in ("standard", "dual"):
+        raise ValueError(multiplier)
     pe, pc = candidate_pairs(sg, X, E)
     blocks, vols = pair_blocks(sg, X, E, pe, pc, nthreads)
     d = sg.dim
     keep = vols > 0.0
+    w = dual_blocks(blocks[keep]) if multiplier == "dual" else blocks[keep]
     rows = np.repeat(E[pe[keep]].astype(np.int64)[:, :, None], 1 << d, axis=2)
     cols = np.repeat(corner_nodes(sg, pc[keep])[:, None, :], d + 1, axis=1)
-    B = sp.coo_matrix((blocks[keep].ravel(), (rows.ravel(), cols.ravel())),
+    B = sp.coo_matrix((w.ravel(), (rows.ravel(), cols.ravel())),
                       shape=(X.shape[0], sg.n_nodes)).tocsr()
     B.sum_duplicates()
     B.sort_indices()
@@ -229,6 +253,18 @@ def mass_matrix(X, E):
     M.sum_duplicates()
     M.sort_indices()
     return M
+
+
+def lumped_mass(X, E):
+    """S of the dual multiplier space: diag(int phi_i) = diag(sum_{E ni i} |E|/(d+1))."""
+    d = X.shape[1]
+    vol = element_volumes(X, E)
+    if np.any(vol == 0.0):
+        raise OracleError("degenerate element")
+    diag = np.zeros(X.shape[0])
+    for a in range(d + 1):
+        np.add.at(diag, E[:, a], vol / (d + 1))
+    return sp.diags(diag, format="csr")
 
 
 def solve_mass(M, Y: np.ndarray, rtol: float = 1e-15, max_iter: int = 10000):
@@ -272,35 +308,48 @@ def solve_mass(M, Y: np.ndarray, rtol: float = 1e-15, max_iter: int = 10000):
 
 
 class Coupling:
-    """B_g for every velocity grid and M_s for one mesh in its current configuration."""
+    """B_g for every velocity grid and S for one mesh in its current configuration.
 
-    def __init__(self, grid, X, E, nthreads: int = 1):
+    ``multiplier="standard"``: S = M_s (multipliers in V_s); ``"dual"``: the dual
+    basis of Eq. (biorth), S = diag(int phi_i).  ``self.M`` holds S.
+    """
+
+    def __init__(self, grid, X, E, nthreads: int = 1, multiplier: str = "standard"):
         self.grid = grid
+        self.multiplier = multiplier
         self.X = np.ascontiguousarray(X, dtype=np.float64)
         self.E = np.ascontiguousarray(E, dtype=np.int32)
         self.sub = [subgrid(grid, g) for g in range(n_grids(grid))]
         self.B = []
         self.pairs = []
         for sg in self.sub:
-            B, pr = assemble_B(sg, self.X, self.E, nthreads, return_pairs=True)
+            B, pr = assemble_B(sg, self.X, self.E, nthreads, return_pairs=True, multiplier=multiplier)
             self.B.append(B)
             self.pairs.append(pr)
-        self.M = mass_matrix(self.X, self.E)
+        self.M = lumped_mass(self.X, self.E) if multiplier == "dual" else mass_matrix(self.X, self.E)
 
-    def transfer_velocity(self, fields):
-        """w_g = M^{-1} B_g v_g for every grid g  ->  (n_solid, n_grids)."""
-        Y = np.stack([self.B[g] @ np.asarray(fields[g], dtype=np.float64)
-                      for g in range(len(self.B))], axis=1)
+    def solve_S(self, Y):
+        """S^{-1} Y: a division by the diagonal for the dual basis, else :func:`solve_mass`."""
+        if self.multiplier == "dual":
+            Y = np.asarray(Y, dtype=np.float64)
+            dg = self.M.diagonal()
+            return Y / (dg if Y.ndim == 1 else dg[:, None])
         return solve_mass(self.M, Y)
 
+    def transfer_velocity(self, fields):
+        """w_g = S^{-1} B_g v_g for every grid g  ->  (n_solid, n_grids)."""
+        Y = np.stack([self.B[g] @ np.asarray(fields[g], dtype=np.float64)
+                      for g in range(len(self.B))], axis=1)
+        return self.solve_S(Y)
+
     def transfer_force(self, F, mode: str = "nodal", scale: float = 1.0):
-        """Fluid force per grid: s * B_g^T M^{-1} r_g (dual) or s * B_g^T f_g (nodal)."""
+        """Fluid force per grid: s * B_g^T S^{-1} r_g (dual) or s * B_g^T f_g (nodal)."""
         F = np.asarray(F, dtype=np.float64)
         if F.ndim == 1:
             F = F[:, None]
-        Z = solve_mass(self.M, F) if mode == "dual" else F
+        Z = self.solve_S(F) if mode == "dual" else F
         return [scale * (self.B[g].T @ Z[:, g]) for g in range(len(self.B))]
 
     def dense_T(self, g: int):
-        """Dense transfer operator T_g = M^{-1} B_g (small instances only)."""
-        return solve_mass(self.M, self.B[g].toarray())
+        """Dense transfer operator T_g = S^{-1} B_g (small instances only)."""
+        return self.solve_S(self.B[g].toarray())

@@ -133,12 +133,14 @@ def _order_ccw(points, centre, normal=None):
     return sorted(points, key=functools.cmp_to_key(cmp))
 
 
-def pair_block_exact(dim, verts, cell_lo, h):
+def pair_block_exact(dim, verts, cell_lo, h, dual=False):
     """Exact block int_{E cap C} lambda_a psi_b and vol(E cap C).
 
     ``verts``: element vertex coordinates (floats), ``cell_lo``: the cell's lower
     corner (floats), ``h``: cell widths (floats).  Returns (block, vol) with
-    block[a][b] Fractions, b = corner bits (x bit 0)."""
+    block[a][b] Fractions, b = corner bits (x bit 0).  With ``dual`` the weight
+    lambda_a is replaced by the element dual function (dim+2) lambda_a - 1
+    (Eq. (biorth)), integrated as it stands."""
     V = [[Fr(verts[i][k]) - Fr(cell_lo[k]) for k in range(dim)] for i in range(dim + 1)]
     H = [Fr(h[k]) for k in range(dim)]
     # barycentric coordinates: lambda(x) = L @ (x, 1)
@@ -176,6 +178,8 @@ def pair_block_exact(dim, verts, cell_lo, h):
 
     def integrand(x):
         lam = [sum(L[a][k] * x[k] for k in range(dim)) + L[a][dim] for a in range(dim + 1)]
+        if dual:
+            lam = [(dim + 2) * la - 1 for la in lam]
         t = [x[k] / H[k] for k in range(dim)]
         out = []
         for a in range(dim + 1):

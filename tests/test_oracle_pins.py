@@ -337,3 +337,117 @@ def test_subcell_sampling_converges():
             for a in range(3):
                 Bs[E[e, a]] += np.bincount(col, weights=lam[a] * psi * dx * dx, minlength=B.shape[1])
     assert np.abs(Bs - B).max() <= 2e-3 * np.abs(B).max()
+
+
+# --------------------------------------------------------------- dual multiplier basis ("pseudo" L2 projection)
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_dual_basis_is_biorthogonal(dim):
+    """Eq. (biorth) on one element: the element dual function (d+2) lambda_a - 1
+    satisfies int_E mu_a lambda_b = delta_ab int_E mu_a, and int_E mu_a = |E|/(d+1)
+    (exact rational integration of products of affine functions)."""
+    rng = np.random.default_rng(5)
+    V = [[Fr(float(x)) for x in row] for row in rng.random((dim + 1, dim))]
+    A = [[V[j][r] for j in range(dim + 1)] for r in range(dim)] + [[Fr(1)] * (dim + 1)]
+
+    def lam(x, a):
+        return exact._solve(A, list(x) + [Fr(1)])[a]
+
+    rows = [[V[i + 1][c] - V[0][c] for c in range(dim)] for i in range(dim)]
+    volE = abs(exact._det(rows)) / math.factorial(dim)
+    for a in range(dim + 1):
+        def mu(x, a=a):
+            return (dim + 2) * lam(x, a) - 1
+        mass = _dirichlet_product_integral(V, [mu])
+        assert mass == volE / (dim + 1)
+        for b in range(dim + 1):
+            got = _dirichlet_product_integral(V, [mu, lambda x, b=b: lam(x, b)])
+            assert got == (mass if a == b else 0)
+
+
+@pytest.mark.parametrize("name,stride", [("disk2d_small", 5), ("beam16", 23)])
+def test_dual_blocks_match_exact_rational(name, stride):
+    """The dual weights of the oracle (from the lambda blocks and the partition of
+    unity of the barycentrics) equal exact rational integration of
+    ((d+2) lambda_a - 1) psi_b over E cap C."""
+    w = synth.workload(name)
+    d = w.dim
+    vol_e = oracle.element_volumes(w.coords, w.elems)
+    for g in range(oracle.n_grids(w.grid)):
+        sg = oracle.subgrid(w.grid, g)
+        pe, pc = oracle.candidate_pairs(sg, w.coords, w.elems)
+        blocks, _ = oracle.pair_blocks(sg, w.coords, w.elems, pe, pc)
+        dual = oracle.dual_blocks(blocks)
+        for p in range(g, len(pe), stride):
+            e, c = int(pe[p]), int(pc[p])
+            blk, _ = exact.pair_block_exact(d, w.coords[w.elems[e]], _cell_lo(sg, c), sg.h[:d], dual=True)
+            ex = np.array([[float(x) for x in row] for row in blk])
+            assert np.abs(ex - dual[p]).max() <= 1e-14 * (d + 2) * vol_e[e], (p, ex, dual[p])
+
+
+@pytest.mark.parametrize("name", ["disk2d", "beam16"])
+def test_dual_rows_sum_to_the_lumped_mass(name):
+    """sum_j B_ij = int mu_i = int phi_i = S_ii for the dual basis (Q1 partition
+    of unity), so S^{-1} B maps constants to constants; S = diag(int phi_i)."""
+    w = synth.workload(name)
+    phi, vol = _phi_integrals(w.coords, w.elems)
+    C = oracle.Coupling(w.grid, w.coords, w.elems, multiplier="dual")
+    S = C.M.toarray()
+    assert np.abs(S - np.diag(phi)).max() <= 1e-15 * phi.max() * 4
+    for B in C.B:
+        rs = np.asarray(B.sum(axis=1)).ravel()
+        assert np.abs(rs - phi).max() <= 1e-13 * phi.max()
+        assert abs(B.sum() - vol.sum()) <= 1e-13 * vol.sum()
+
+
+@pytest.mark.parametrize("name", ["disk2d", "beam16", "leaflet32"])
+def test_dual_projection_reproduces_affine_fields(name):
+    """The pseudo L2 projection is exact on P1: an affine fluid field is returned
+    at the solid nodes, without any iterative solve."""
+    w = synth.workload(name)
+    d = w.dim
+    C = oracle.Coupling(w.grid, w.coords, w.elems, multiplier="dual")
+    coef = np.array([-0.4, 0.9, 1.7, -1.1])[: d + 1]
+    fields = [coef[0] + synth.grid_node_coords(w.grid, g) @ coef[1:] - g
+              for g in range(oracle.n_grids(w.grid))]
+    W = C.transfer_velocity(fields)
+    ex = np.stack([coef[0] + w.coords @ coef[1:] - g for g in range(len(fields))], axis=1)
+    assert np.abs(W - ex).max() <= 1e-13 * np.abs(ex).max()
+
+
+def test_dual_force_transfer_is_the_adjoint():
+    """f . (T u) = (T^T f) . u for T = S^{-1} B of the dual basis."""
+    w = synth.workload("beam16")
+    rng = np.random.default_rng(9)
+    C = oracle.Coupling(w.grid, w.coords, w.elems, multiplier="dual")
+    U = [rng.standard_normal(C.sub[g].n_nodes) for g in range(3)]
+    F = rng.standard_normal((w.coords.shape[0], 3))
+    TU = C.transfer_velocity(U)
+    TtF = C.transfer_force(F, mode="dual", scale=1.0)
+    for g in range(3):
+        lhs, rhs = F[:, g] @ TU[:, g], TtF[g] @ U[g]
+        assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.abs(F[:, g]).sum())
+
+
+def test_dual_and_standard_projections_differ_off_p1():
+    """On a field that is not P1 on the solid the two multiplier spaces give
+    different (both consistent) transfers: the dual one is a local
+    approximation, not the L2 projection; the L2 projection minimises the L2
+    error over V_s, so its error is not larger (checked through B of the
+    standard space: (M w - B v) = 0 only for the standard w)."""
+    w = synth.workload("disk2d")
+    Cs = oracle.Coupling(w.grid, w.coords, w.elems)
+    Cd = oracle.Coupling(w.grid, w.coords, w.elems, multiplier="dual")
+    v = [synth.sin_cos_2d(synth.grid_node_coords(w.grid, 0))]
+    ws = Cs.transfer_velocity(v)[:, 0]
+    wd = Cd.transfer_velocity(v)[:, 0]
+    assert np.abs(ws - wd).max() > 1e-6
+    r_std = Cs.M @ ws - Cs.B[0] @ v[0]
+    r_dual = Cs.M @ wd - Cs.B[0] @ v[0]
+    assert np.abs(r_std).max() <= 1e-13 * np.abs(Cs.B[0] @ v[0]).max()
+    assert np.abs(r_dual).max() > 1e-9
+    # L2 error against v restricted to the solid: (w - v)^T M (w - v) minimal for ws
+    # expressed with the Galerkin identity ||v - w||^2 = ||v||^2 - 2 w.Bv + w.Mw
+    def err(wv):
+        return -2 * wv @ (Cs.B[0] @ v[0]) + wv @ (Cs.M @ wv)
+    assert err(ws) <= err(wd)
