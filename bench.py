@@ -244,21 +244,22 @@ class Arm:
         self.torch, self.l2x, self.grid, self.positions, self.E = torch, l2x, grid, positions, E
         self.u32, self.f32, self.dev, self.world, self.flush = u32, f32, dev, world, flush
 
-    def coupling(self, path, precision, X=None):
+    def coupling(self, path, precision, X=None, multiplier=0):
         """A coupling on the first configuration; fused forms pick their work-chunk
         sizes with the library's autotuner."""
         l2x = self.l2x
         c = l2x.Coupling(self.grid, self.positions[0] if X is None else X, self.E, path=path,
-                         precision=precision, cg_rtol=1e-9 if precision == l2x.MIXED else 1e-13)
+                         precision=precision, cg_rtol=1e-9 if precision == l2x.MIXED else 1e-13,
+                         multiplier=multiplier)
         if path == l2x.FUSED:
             self.tuned = c.autotune()
         return c
 
-    def per_call(self, path, precision, steps, warmup, timing=False):
+    def per_call(self, path, precision, steps, warmup, timing=False, multiplier=0):
         """One library call per operation: update_geometry, transfer_velocity, transfer_force."""
         torch, l2x = self.torch, self.l2x
         dt = torch.float32 if precision == l2x.MIXED else torch.float64
-        c = self.coupling(path, precision)
+        c = self.coupling(path, precision, multiplier=multiplier)
         uf = [u.to(dt) for u in self.u32]
         fs = [f.to(dt) for f in self.f32]
         ff = [torch.zeros(n, dtype=dt, device=self.dev) for n in c.fluid_sizes()]
@@ -302,11 +303,11 @@ class Arm:
         return dict(c=c, info=info, build_ms=tb / steps, apply_ms=ta / steps, launches=launches,
                     pairs=pairs_per_step, uf=uf, fs=fs)
 
-    def graph(self, precision, steps, warmup):
+    def graph(self, precision, steps, warmup, multiplier=0):
         """The whole step captured as one CUDA graph and replayed."""
         torch, l2x = self.torch, self.l2x
         dt = torch.float32 if precision == l2x.MIXED else torch.float64
-        c = self.coupling(l2x.FUSED, precision)
+        c = self.coupling(l2x.FUSED, precision, multiplier=multiplier)
         uf = [u.to(dt) for u in self.u32]
         fs = [f.to(dt) for f in self.f32]
         us = [torch.zeros(c.n_nodes, dtype=dt, device=self.dev) for _ in range(3)]
@@ -397,6 +398,17 @@ def main():
     clip_pairs_per_launch = pc["pairs"] / max(1, calls["clip"] // n_pc)
     plain = arm.per_call(l2x.PLAIN, l2x.FP64, args.plain_steps, 2)
     f64 = arm.per_call(l2x.FUSED, l2x.FP64, args.plain_steps, 2)
+    tuned = getattr(arm, "tuned", None)
+
+    # the dual multiplier basis (pseudo L2 projection, S diagonal: no CG), same step
+    n_dual = max(3, args.steps // 4)
+    dgr = arm.graph(l2x.MIXED, n_dual, 3, multiplier=l2x.DUAL_BASIS)
+    dpc = arm.per_call(l2x.FUSED, l2x.MIXED, n_dual, 3, multiplier=l2x.DUAL_BASIS)
+    d_ms, d_pairs, d_value = aggregate(dgr["step_ms"], dgr["pairs"], world)
+    dual = {"form": "fused, captured step graph, mixed precision, dual multiplier basis",
+            "value": d_value, "unit": UNIT, "ms_per_step": d_ms, "steps": n_dual,
+            "per_call_build_ms": dpc["build_ms"], "per_call_apply_ms": dpc["apply_ms"]}
+    del dgr, dpc
 
     # end to end through the public API from pinned host buffers (the captured step):
     # positions, velocities and forces in; solid velocities and fluid forces out
@@ -491,7 +503,8 @@ def main():
                            "cg_iters": f64["info"]["cg_iters"]},
             "e2e": {"value": e_value, "unit": UNIT, "ms_per_step": e_step_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "autotuned": getattr(arm, "tuned", None),
+            "autotuned": tuned,
+            "pseudo_l2_dual": dual,
             "gpu_launches": int(pc["launches"] / n_pc * args.steps),
             "gpu_launches_note": "per step as counted on the per-call form; the captured graph replays the same "
                                  "kernel nodes",

@@ -5,10 +5,18 @@
  * The method is the variational transfer of Sec. 2.3 ("Variational Transfer:
  * the L2-Projection Approach"):
  *
- *   B_ij = ∫ psi_j phi_i         mixed coupling matrix (mortar integral),
- *   S_ij = ∫ phi_j phi_i = M_s   solid P1 mass matrix (multipliers = V_s),
+ *   B_ij = ∫ psi_j N_i           mixed coupling matrix (mortar integral),
+ *   S_ij = ∫ phi_j N_i           multiplier matrix,
  *   w_s  = S^{-1} B v_f = T v_f  velocity transfer, one scalar component at a time,
  *   f_f  = s T^T f               force transfer by the transpose, s = L_ref/(rho_f U_ref^2),
+ *
+ * where N_i spans the space of Lagrange multipliers: either the P1 hat
+ * functions themselves (N_i = phi_i, S = M_s, the solid mass matrix; the
+ * "standard" L2-projection), or the dual basis biorthogonal to them, Eq.
+ * (biorth) (the "pseudo" L2-projection; S is then diagonal).  The dual basis
+ * is built element by element: on a simplex E the function dual to the hat
+ * function of vertex a is (d+2) lambda_a - 1 (lambda_a the barycentric
+ * coordinate), so ∫_E N_a lambda_b = delta_ab |E|/(d+1) and S = diag(∫ phi_i).
  *
  * assembled in the current configuration of the solid mesh by the four steps
  * given after the transfer operator: (I) overlap detection, (II) quadrature
@@ -62,6 +70,7 @@ enum { L2X_PATH_PLAIN = 0, L2X_PATH_FUSED = 1 };
 enum { L2X_FP64 = 0, L2X_MIXED = 1 };
 enum { L2X_FORCE_NODAL = 0, L2X_FORCE_DUAL = 1 };
 enum { L2X_MAT_B0 = 0, L2X_MAT_B1 = 1, L2X_MAT_B2 = 2, L2X_MAT_M = 3 };
+enum { L2X_MULT_STANDARD = 0, L2X_MULT_DUAL = 1 };
 
 /* Phases timed by l2x_set_timing (indices of l2x_info.phase_ms). */
 enum {
@@ -102,8 +111,11 @@ typedef struct l2x_opts {
     int32_t precision;    /* L2X_FP64 or L2X_MIXED (fused path only) */
     double cg_rtol;       /* relative residual target of the mass-matrix solve */
     int32_t cg_max_iter;
-    int32_t force_mode;   /* L2X_FORCE_DUAL: f_f += s B^T M^-1 r; NODAL: f_f += s B^T f */
+    int32_t force_mode;   /* L2X_FORCE_DUAL: f_f += s B^T S^-1 r; NODAL: f_f += s B^T f */
     double force_scale;   /* s = L_ref / (rho_f U_ref^2); 1 by default */
+    int32_t multiplier;   /* L2X_MULT_STANDARD (S = M_s, solved by Jacobi-PCG) or
+                             L2X_MULT_DUAL (dual basis of Eq. (biorth), S diagonal: no solve) */
+    int32_t reserved;     /* 0 */
 } l2x_opts;
 
 typedef struct l2x_info {
@@ -122,20 +134,24 @@ typedef struct l2x_info {
     int64_t phase_calls[8];    /* timed intervals per phase */
     int32_t clip_block;        /* pairs per thread block of the clip kernel (l2x_autotune) */
     int32_t pcg_rows_per_block;/* rows per thread block of the cooperative PCG (l2x_autotune) */
+    int32_t multiplier;        /* L2X_MULT_STANDARD or L2X_MULT_DUAL */
+    int32_t reserved2;
 } l2x_info;
 
 typedef struct l2x_coupling* l2x_handle;
 typedef struct l2x_step_graph* l2x_graph;
 
 /* Fills *opts with the defaults: fused path, FP64, cg_rtol 1e-13, 200 iterations,
- * DUAL force mode, scale 1. */
+ * DUAL force mode, scale 1, standard multipliers (S = M_s). */
 void l2x_default_opts(l2x_opts* opts);
 
 /* Steps (I)-(IV) of Sec. 2.3 plus the mass matrix: candidate (element, cell)
  * pairs from bounding boxes, exact clipping of every simplex against its cells,
  * quadrature of lambda_a * psi_b on the clipped polytopes, CSR assembly of B_g
  * (rows: solid nodes, columns: nodes of grid g) for every velocity grid and of
- * M_s.  Synchronises `stream` (pair counts decide allocation sizes).
+ * S (M_s, or its diagonal form diag(∫ phi_i) for the dual basis; the dual rows
+ * of B are (d+2) times the lambda integrals minus their sum over the element's
+ * vertices).  Synchronises `stream` (pair counts decide allocation sizes).
  * Errors: EINVAL (arguments), EOUTOFGRID, EDEGENERATE, ENONFINITE, ENOMEM, ECUDA.
  * On success *out owns all device storage of the coupling. */
 l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const l2x_opts* opts,
@@ -146,21 +162,22 @@ l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const 
 l2x_status l2x_update_geometry(l2x_handle h, const double* coords, void* stream);
 
 /* Velocity transfer (Step 1 of the FSI algorithm, Sec. 3): for every velocity
- * grid g, u_s[g] = M_s^{-1} B_g u_f[g] by Jacobi-preconditioned CG.
+ * grid g, u_s[g] = S^{-1} B_g u_f[g], by Jacobi-preconditioned CG for S = M_s
+ * and by a division fused into the product with B_g for the dual basis.
  * u_f: n_grids device arrays of n_fluid[g] entries; u_s: n_grids arrays of
  * n_nodes entries (written).  Returns ENOTCONVERGED if cg_rtol was not met. */
 l2x_status l2x_transfer_velocity(l2x_handle h, const void* const* u_f, void* const* u_s,
                                  void* stream);
 
 /* Force transfer by the transpose (Step 4 of Sec. 3): for every grid g,
- *   DUAL : f_f[g] += s * B_g^T M_s^{-1} f_s[g]   (= s T_g^T f_s[g])
- *   NODAL: f_f[g] += s * B_g^T f_s[g]
+ *   DUAL : f_f[g] += s * B_g^T S^{-1} f_s[g]   (= s T_g^T f_s[g])
+ *   NODAL: f_f[g] += s * B_g^T f_s[g]          (f_s: multiplier coefficients)
  * f_s: n_grids arrays of n_nodes entries; f_f: n_grids fluid arrays, accumulated. */
 l2x_status l2x_transfer_force(l2x_handle h, const void* const* f_s, void* const* f_f,
                               void* stream);
 
 /* Building blocks of the two transfers (used by the autograd binding):
- * y_s[g] = B_g x_f[g];  f_f[g] += scale * B_g^T z_s[g];  w_s[g] = M_s^{-1} y_s[g]. */
+ * y_s[g] = B_g x_f[g];  f_f[g] += scale * B_g^T z_s[g];  w_s[g] = S^{-1} y_s[g]. */
 l2x_status l2x_apply_B(l2x_handle h, const void* const* x_f, void* const* y_s, void* stream);
 l2x_status l2x_apply_BT(l2x_handle h, const void* const* z_s, void* const* f_f, double scale,
                         void* stream);
@@ -171,7 +188,7 @@ l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s
  * current configuration and both transfers run, with no host synchronisation,
  * by one cudaGraphLaunch per step.  Each replay copies the node positions from
  * coords_src (device, n_nodes x dim, read at replay time), rebuilds B_g, B_g^T
- * and M_s, writes u_s = M_s^-1 B u_f and f_f (+)= s B^T (M_s^-1) f_s (zeroed first
+ * and S, writes u_s = S^-1 B u_f and f_f (+)= s B^T (S^-1) f_s (zeroed first
  * if zero_force != 0); all pointers are fixed at creation.  Pair and entry
  * capacities are the current sizes times capacity_margin (>= 1); a replay that
  * needs more sets a flag and skips its work, reported by l2x_graph_sync_status
@@ -194,7 +211,8 @@ l2x_status l2x_query(l2x_handle h, l2x_info* info);
  * (i0,i1,i2) of grid g at i0 + ncell0*(i1 + ncell1*i2)), element-major with
  * cells in z, y, x order.  Pair blocks (fused path only): blocks[p*(d+1)*2^d +
  * a*2^d + b] = ∫_{E∩C} lambda_a psi_b, corner b = bits (x, y, z); vols[p] =
- * |E∩C|.  CSR (which = L2X_MAT_B0..B2 or L2X_MAT_M): row_ptr (n_rows+1, int64),
+ * |E∩C| (the lambda integrals, for either multiplier space).  CSR (which =
+ * L2X_MAT_B0..B2 or L2X_MAT_M for S): row_ptr (n_rows+1, int64),
  * cols (int32, ascending within a row), vals (double). */
 l2x_status l2x_export_pairs(l2x_handle h, int32_t grid, int32_t* elem, int32_t* cell, void* stream);
 l2x_status l2x_export_pair_blocks(l2x_handle h, int32_t grid, double* blocks, double* vols,

@@ -24,6 +24,7 @@ __all__ = ["kernel_launch_count", "PHASES", "StepGraph", "Coupling", "Grid", "Ve
 PLAIN, FUSED = 0, 1
 FP64, MIXED = 0, 1
 NODAL, DUAL = 0, 1
+STANDARD_BASIS, DUAL_BASIS = 0, 1   # multiplier space: S = M_s, or the dual basis of Eq. (biorth)
 MAT_M = 3
 
 
@@ -45,7 +46,8 @@ class _Mesh(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("precision", ctypes.c_int32), ("cg_rtol", ctypes.c_double),
-                ("cg_max_iter", ctypes.c_int32), ("force_mode", ctypes.c_int32), ("force_scale", ctypes.c_double)]
+                ("cg_max_iter", ctypes.c_int32), ("force_mode", ctypes.c_int32), ("force_scale", ctypes.c_double),
+                ("multiplier", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -55,7 +57,8 @@ class _Info(ctypes.Structure):
                 ("nnz_M", ctypes.c_int64), ("n_fluid", ctypes.c_int64 * 3), ("nnode", (ctypes.c_int32 * 3) * 3),
                 ("cg_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cg_residual", ctypes.c_double),
                 ("phase_ms", ctypes.c_double * 8), ("phase_calls", ctypes.c_int64 * 8),
-                ("clip_block", ctypes.c_int32), ("pcg_rows_per_block", ctypes.c_int32)]
+                ("clip_block", ctypes.c_int32), ("pcg_rows_per_block", ctypes.c_int32),
+                ("multiplier", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 PHASES = ["pairs", "clip", "rows", "transpose", "mass", "spmv_B", "pcg", "spmv_BT"]
@@ -172,7 +175,7 @@ class Coupling:
 
     def __init__(self, grid, coords: torch.Tensor, elems: torch.Tensor, path: int = FUSED,
                  precision: int = FP64, cg_rtol: float | None = None, cg_max_iter: int = 200,
-                 force_mode: int = DUAL, force_scale: float = 1.0):
+                 force_mode: int = DUAL, force_scale: float = 1.0, multiplier: int = STANDARD_BASIS):
         lib = load_library()
         if not coords.is_cuda or not elems.is_cuda:
             raise ValueError("coords and elems must be CUDA tensors")
@@ -192,6 +195,8 @@ class Coupling:
         opts.cg_max_iter = cg_max_iter
         opts.force_mode = force_mode
         opts.force_scale = force_scale
+        opts.multiplier = multiplier
+        self.multiplier = multiplier
         self.force_mode = force_mode
         self.force_scale = force_scale
         mesh = _Mesh()
@@ -227,7 +232,8 @@ class Coupling:
                     cg_iters=inf.cg_iters, cg_residual=inf.cg_residual,
                     phase_ms={p: inf.phase_ms[i] for i, p in enumerate(PHASES)},
                     phase_calls={p: inf.phase_calls[i] for i, p in enumerate(PHASES)},
-                    clip_block=inf.clip_block, pcg_rows_per_block=inf.pcg_rows_per_block)
+                    clip_block=inf.clip_block, pcg_rows_per_block=inf.pcg_rows_per_block,
+                    multiplier=inf.multiplier)
 
     def autotune(self):
         """Pick work-chunk sizes by timing candidates on this coupling."""

@@ -284,12 +284,14 @@ l2x_status build_topology(l2x_coupling* h, cudaStream_t s) {
     L2X_TRY(dalloc(&h->row_count, n + 1));
     L2X_TRY(ensure_scan(h, n));
     launch_node_adjacency(h->dim, n, m, h->E, h->adj_ptr, h->adj, h->cursor, h->scan_tmp, s);
-    // mass structure
-    launch_mass_structure(0, h->dim, n, h->E, h->adj_ptr, h->adj, h->row_count, nullptr, nullptr, h->st, s);
     L2X_TRY(dalloc(&h->M.ptr, n + 1));
-    launch_scan_i64(h->row_count, h->M.ptr, n, h->scan_tmp, s);
-    int64_t nnz = 0;
-    L2X_CUDA(cudaMemcpyAsync(&nnz, h->M.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int64_t nnz = n;  // dual basis: S is diagonal (structure written with its values)
+    if (h->opts.multiplier == L2X_MULT_STANDARD) {
+        // sparsity of M_s
+        launch_mass_structure(0, h->dim, n, h->E, h->adj_ptr, h->adj, h->row_count, nullptr, nullptr, h->st, s);
+        launch_scan_i64(h->row_count, h->M.ptr, n, h->scan_tmp, s);
+        L2X_CUDA(cudaMemcpyAsync(&nnz, h->M.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    }
     L2X_TRY(read_status(h, s));
     h->M.n_rows = n;
     h->M.nnz = nnz;
@@ -298,8 +300,21 @@ l2x_status build_topology(l2x_coupling* h, cudaStream_t s) {
     L2X_TRY(dalloc(&h->M.val32, nnz));
     L2X_TRY(dalloc(&h->M_dinv, n));
     L2X_TRY(dalloc(&h->M_dinv32, n));
-    launch_mass_structure(1, h->dim, n, h->E, h->adj_ptr, h->adj, nullptr, h->M.ptr, h->M.col, h->st, s);
+    if (h->opts.multiplier == L2X_MULT_STANDARD)
+        launch_mass_structure(1, h->dim, n, h->E, h->adj_ptr, h->adj, nullptr, h->M.ptr, h->M.col, h->st, s);
     return L2X_OK;
+}
+
+// Values of S (M_s, or diag(int phi_i) for the dual basis) and their FP32 copies.
+void launch_S_values(l2x_coupling* h, cudaStream_t s) {
+    const int64_t n = h->n_nodes;
+    if (h->opts.multiplier == L2X_MULT_DUAL)
+        launch_lumped_mass(h->dim, n, h->adj_ptr, h->adj, h->elem_vol, h->M.ptr, h->M.col, h->M.val, h->M_dinv, s);
+    else
+        launch_mass_values(h->dim, n, h->E, h->adj_ptr, h->adj, h->elem_vol, h->M.ptr, h->M.col, h->M.val,
+                           h->M_dinv, s);
+    launch_to_f32(h->M.val, h->M.val32, h->M.nnz, s);
+    launch_to_f32(h->M_dinv, h->M_dinv32, n, s);
 }
 
 // Everything that depends on the node positions.
@@ -386,7 +401,8 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         const ElemBox* bx = h->boxes + (int64_t)g * m;
         const int64_t* off = h->offsets + (int64_t)g * m;
         const int64_t* lof = h->loc_off + (int64_t)g * m;
-        launch_elem_local(d, m, bx, off, lof, h->loc_cap, h->blocks, h->vols, h->loc_val, h->loc_flag, h->st, s);
+        launch_elem_local(d, m, bx, off, lof, h->loc_cap, h->blocks, h->vols, h->loc_val, h->loc_flag,
+                          h->opts.multiplier == L2X_MULT_DUAL, h->st, s);
         launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, h->row_count,
                       nullptr, nullptr, nullptr, h->st, s);
         if (!B.ptr) L2X_TRY(dalloc(&B.ptr, n + 1));
@@ -412,7 +428,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
             launch_b_rows(2, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, nullptr,
                           B.ptr, B.col, B.val, h->st, s);
             launch_scatter_plain(d, h->sg[g], h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks, h->vols,
-                                 B, s);
+                                 B, h->opts.multiplier == L2X_MULT_DUAL, s);
         } else {
             {
                 PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
@@ -465,11 +481,9 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
             if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, nnz, s);
         }
     }
-    // mass matrix values
+    // values of S
     PhaseScope ph_mass(h, L2X_PH_MASS, s);
-    launch_mass_values(d, n, h->E, h->adj_ptr, h->adj, h->elem_vol, h->M.ptr, h->M.col, h->M.val, h->M_dinv, s);
-    launch_to_f32(h->M.val, h->M.val32, h->M.nnz, s);
-    launch_to_f32(h->M_dinv, h->M_dinv32, n, s);
+    launch_S_values(h, s);
     return read_status(h, s);
 }
 
@@ -493,6 +507,7 @@ l2x_status validate(const l2x_grid* grid, const l2x_mesh* mesh, const l2x_opts* 
         if (o->path == L2X_PATH_PLAIN && o->precision != L2X_FP64) return fail(L2X_EINVAL, "the plain path is FP64 only");
         if (!(o->cg_rtol > 0.0) || o->cg_max_iter <= 0) return fail(L2X_EINVAL, "bad CG settings");
         if (o->force_mode != L2X_FORCE_NODAL && o->force_mode != L2X_FORCE_DUAL) return fail(L2X_EINVAL, "bad force mode");
+        if (o->multiplier != L2X_MULT_STANDARD && o->multiplier != L2X_MULT_DUAL) return fail(L2X_EINVAL, "bad multiplier space");
     }
     return L2X_OK;
 }
@@ -529,7 +544,8 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         const ElemBox* bx = h->boxes + (int64_t)g * m;
         const int64_t* off = h->offsets + (int64_t)g * m;
         const int64_t* lof = h->loc_off + (int64_t)g * m;
-        launch_elem_local(d, m, bx, off, lof, h->loc_cap, h->blocks, h->vols, h->loc_val, h->loc_flag, h->st, s);
+        launch_elem_local(d, m, bx, off, lof, h->loc_cap, h->blocks, h->vols, h->loc_val, h->loc_flag,
+                          h->opts.multiplier == L2X_MULT_DUAL, h->st, s);
         launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, h->row_count,
                       nullptr, nullptr, nullptr, h->st, s);
         launch_scan_i64(h->row_count, B.ptr, n, h->scan_tmp, s);
@@ -547,21 +563,27 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         launch_transpose_sort(T, h->st, s);
         if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, h->T_cap[g], s);
     }
-    launch_mass_values(d, n, h->E, h->adj_ptr, h->adj, h->elem_vol, h->M.ptr, h->M.col, h->M.val, h->M_dinv, s);
-    launch_to_f32(h->M.val, h->M.val32, h->M.nnz, s);
-    launch_to_f32(h->M_dinv, h->M_dinv32, n, s);
+    launch_S_values(h, s);
     // transfers
     const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
     void* tmp[kMaxGrids];
     for (int g = 0; g < G; ++g) tmp[g] = (char*)h->vec_tmp + es * n * g;
-    launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, tmp, h->st, s);
-    solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)tmp, u_s,
-                         h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
+    const bool diag = h->opts.multiplier == L2X_MULT_DUAL;
+    if (diag) {
+        launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, u_s, h->st, s, h->M_dinv);
+    } else {
+        launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, tmp, h->st, s);
+        solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)tmp, u_s,
+                             h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
+    }
     if (zero_force)
         for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
     if (h->opts.force_mode == L2X_FORCE_DUAL) {
-        solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, f_s, tmp, h->opts.cg_rtol,
-                             h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
+        if (diag)
+            launch_diag_solve(h->opts.precision, n, G, h->M_dinv, f_s, tmp, h->st, s);
+        else
+            solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, f_s, tmp, h->opts.cg_rtol,
+                                 h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
         launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)tmp, f_f,
                        h->opts.force_scale, h->st, s);
     } else {
@@ -588,6 +610,8 @@ void l2x_default_opts(l2x_opts* o) {
     o->cg_max_iter = 200;
     o->force_mode = L2X_FORCE_DUAL;
     o->force_scale = 1.0;
+    o->multiplier = L2X_MULT_STANDARD;
+    o->reserved = 0;
 }
 
 const char* l2x_status_string(l2x_status s) {
@@ -738,6 +762,14 @@ l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s
     L2X_TRY(check_ptrs(y_s, h->n_grids, "y_s"));
     L2X_TRY(check_ptrs((const void* const*)w_s, h->n_grids, "w_s"));
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->opts.multiplier == L2X_MULT_DUAL) {  // diagonal S: one division per entry
+        PhaseScope ph(h, L2X_PH_PCG, s);
+        launch_diag_solve(h->opts.precision, h->n_nodes, h->n_grids, h->M_dinv, y_s, w_s, h->st, s);
+        h->cg_iters = 0;
+        h->cg_residual = 0.0;
+        L2X_CUDA(cudaGetLastError());
+        return L2X_OK;
+    }
     PcgResult r;
     auto ph = std::make_unique<PhaseScope>(h, L2X_PH_PCG, s);
     l2x_status st = solve_mass_pcg(h->opts.path, h->opts.precision, h->M, h->M_dinv, h->M_dinv32, h->n_grids, y_s,
@@ -756,6 +788,15 @@ l2x_status l2x_transfer_velocity(l2x_handle h, const void* const* u_f, void* con
     if (!h) return fail(L2X_EINVAL, "NULL handle");
     L2X_TRY(check_ptrs(u_f, h->n_grids, "u_f"));
     L2X_TRY(check_ptrs((const void* const*)u_s, h->n_grids, "u_s"));
+    if (h->opts.multiplier == L2X_MULT_DUAL) {  // S diagonal: the division is fused into B u_f
+        cudaStream_t s = (cudaStream_t)stream;
+        PhaseScope ph(h, L2X_PH_SPMV_B, s);
+        launch_spmv_B(h->opts.path, h->opts.precision, h->n_grids, h->B, u_f, u_s, h->st, s, h->M_dinv);
+        h->cg_iters = 0;
+        h->cg_residual = 0.0;
+        L2X_CUDA(cudaGetLastError());
+        return L2X_OK;
+    }
     const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
     void* y[kMaxGrids];
     for (int g = 0; g < h->n_grids; ++g) y[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
@@ -949,6 +990,7 @@ l2x_status l2x_query(l2x_handle h, l2x_info* info) {
     info->cg_residual = h->cg_residual;
     info->clip_block = h->clip_block;
     info->pcg_rows_per_block = h->pcg_rpb;
+    info->multiplier = h->opts.multiplier;
     resolve_timing(h);
     for (int p = 0; p < L2X_NPHASE; ++p) {
         info->phase_ms[p] = h->phase_ms[p];
@@ -998,7 +1040,7 @@ l2x_status l2x_autotune(l2x_handle h, void* stream) {
         }
         h->clip_block = best_blk;
     }
-    {
+    if (h->opts.multiplier == L2X_MULT_STANDARD) {
         // PCG: rows per block, on M applied to a vector of ones
         const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
         void* y[kMaxGrids];

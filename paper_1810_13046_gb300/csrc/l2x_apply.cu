@@ -25,6 +25,7 @@ struct SpmvPack {
     const TM* val[kMaxGrids];
     const TV* x[kMaxGrids];
     TV* y[kMaxGrids];
+    const double* scale;  // optional row scaling (1/S_ii of a diagonal S), shared by the grids
 };
 
 // 8 lanes per row; accumulation in the vector type.
@@ -48,16 +49,30 @@ __global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM
     acc += __shfl_xor_sync(0xffffffffu, acc, 4);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    if (active && l8 == 0) P.y[g][row] = acc;
+    if (active && l8 == 0) P.y[g][row] = P.scale ? (TV)((double)acc * __ldg(P.scale + row)) : acc;
 }
 
 __global__ void spmv_B_plain_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                    const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+                                    const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
+                                    const double* __restrict__ scale) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_rows) return;
     double s = 0.0;
     for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) s += val[q] * x[col[q]];
-    y[i] = s;
+    y[i] = scale ? s * scale[i] : s;
+}
+
+// w_k = y_k / S_ii for a diagonal S; the product in FP64, one rounding to TV.
+template <typename TV>
+__global__ void diag_solve_kernel(int64_t n, int nr, const double* __restrict__ dinv, const TV* y0, const TV* y1,
+                                  const TV* y2, TV* w0, TV* w1, TV* w2, const DevStatus* st) {
+    if (st->flags & kAbortFlags) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double di = dinv[i];
+    w0[i] = (TV)((double)y0[i] * di);
+    if (nr > 1) w1[i] = (TV)((double)y1[i] * di);
+    if (nr > 2) w2[i] = (TV)((double)y2[i] * di);
 }
 
 // ------------------------------------------------------------------ B^T z
@@ -677,14 +692,28 @@ size_t pcg_ws_bytes(int64_t n, int n_rhs, int max_blocks) {
            (size_t)max_blocks * 3 * kMaxRhs * sizeof(double) + 64 * sizeof(double) + 16384;
 }
 
+void launch_diag_solve(int precision, int64_t n, int nr, const double* dinv, const void* const* y,
+                       void* const* w, const DevStatus* st, cudaStream_t s) {
+    if (n <= 0 || nr <= 0) return;
+    if (precision == L2X_MIXED) {
+        const float* yy[3] = {(const float*)y[0], nr > 1 ? (const float*)y[1] : nullptr, nr > 2 ? (const float*)y[2] : nullptr};
+        float* ww[3] = {(float*)w[0], nr > 1 ? (float*)w[1] : nullptr, nr > 2 ? (float*)w[2] : nullptr};
+        { diag_solve_kernel<float><<<nblk(n, 256), 256, 0, s>>>(n, nr, dinv, yy[0], yy[1], yy[2], ww[0], ww[1], ww[2], st); count_launch(); }
+    } else {
+        const double* yy[3] = {(const double*)y[0], nr > 1 ? (const double*)y[1] : nullptr, nr > 2 ? (const double*)y[2] : nullptr};
+        double* ww[3] = {(double*)w[0], nr > 1 ? (double*)w[1] : nullptr, nr > 2 ? (double*)w[2] : nullptr};
+        { diag_solve_kernel<double><<<nblk(n, 256), 256, 0, s>>>(n, nr, dinv, yy[0], yy[1], yy[2], ww[0], ww[1], ww[2], st); count_launch(); }
+    }
+}
+
 void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const void* const* x, void* const* y,
-                   const DevStatus* st, cudaStream_t s) {
+                   const DevStatus* st, cudaStream_t s, const double* row_scale) {
     const int64_t n = B[0].n_rows;
     if (n <= 0) return;
     if (path == L2X_PATH_PLAIN) {
         for (int g = 0; g < n_grids; ++g)
             { spmv_B_plain_kernel<<<nblk(n, 256), 256, 0, s>>>(n, B[g].ptr, B[g].col, B[g].val, (const double*)x[g],
-                                                             (double*)y[g]); count_launch(); }
+                                                             (double*)y[g], row_scale); count_launch(); }
         return;
     }
     const int64_t threads = n * n_grids * 8;
@@ -694,6 +723,7 @@ void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const voi
             P.ptr[g] = B[g].ptr; P.col[g] = B[g].col; P.val[g] = B[g].val32;
             P.x[g] = (const float*)x[g]; P.y[g] = (float*)y[g];
         }
+        P.scale = row_scale;
         { spmv_B_fused_kernel<float, float><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P, st); count_launch(); }
     } else {
         SpmvPack<double, double> P{};
@@ -701,6 +731,7 @@ void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const voi
             P.ptr[g] = B[g].ptr; P.col[g] = B[g].col; P.val[g] = B[g].val;
             P.x[g] = (const double*)x[g]; P.y[g] = (double*)y[g];
         }
+        P.scale = row_scale;
         { spmv_B_fused_kernel<double, double><<<nblk(threads, 256), 256, 0, s>>>(n_grids, n, P, st); count_launch(); }
     }
 }

@@ -58,7 +58,8 @@ template <int D>
 __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, const int64_t* __restrict__ offsets,
                                   const int64_t* __restrict__ loc_off, int64_t loc_cap,
                                   const double* __restrict__ blocks, const double* __restrict__ vols,
-                                  double* __restrict__ loc_val, uint8_t* __restrict__ loc_flag, DevStatus* st) {
+                                  double* __restrict__ loc_val, uint8_t* __restrict__ loc_flag, int dual,
+                                  DevStatus* st) {
     constexpr int NA = D + 1, NB = 1 << D;
     const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -95,6 +96,15 @@ __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, 
                         for (int a = 0; a < NA; ++a) acc[a] += blk[a * NB];
                     }
                 }
+        if (dual) {
+            // dual multiplier basis (d+2) lambda_a - 1: the lambda integrals sum
+            // to the integral of psi (partition of unity of the barycentrics)
+            double sum = 0.0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) sum += acc[a];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) acc[a] = (double)(D + 2) * acc[a] - sum;
+        }
         loc_flag[L0 + jj] = touched ? 1 : 0;
 #pragma unroll
         for (int a = 0; a < NA; ++a) loc_val[(L0 + jj) * NA + a] = acc[a];
@@ -262,6 +272,24 @@ __global__ void mass_values_kernel(int64_t n_nodes, const int32_t* __restrict__ 
     diag_inv[i] = dgl > 0.0 ? 1.0 / dgl : 0.0;
 }
 
+// Thread per solid node: S_ii = sum of |E|/(d+1) over the elements around i, in
+// adjacency order (reproducible); the diagonal CSR structure is rewritten too.
+template <int D>
+__global__ void lumped_mass_kernel(int64_t n_nodes, const int64_t* __restrict__ adj_ptr,
+                                   const int32_t* __restrict__ adj, const double* __restrict__ elem_vol,
+                                   int64_t* row_ptr, int32_t* cols, double* vals, double* diag_inv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_nodes) return;
+    double s = 0.0;
+    for (int64_t t = adj_ptr[i]; t < adj_ptr[i + 1]; ++t) s += elem_vol[adj[t] >> 2];
+    s = s / (double)(D + 1);
+    row_ptr[i] = i;
+    if (i == n_nodes - 1) row_ptr[n_nodes] = n_nodes;
+    cols[i] = (int32_t)i;
+    vals[i] = s;
+    diag_inv[i] = s > 0.0 ? 1.0 / s : 0.0;
+}
+
 __device__ __forceinline__ int64_t tbox_index(const SubGrid& sg, const CsrT& T, int32_t j) {
     int x = j % sg.nnode[0];
     int r = j / sg.nnode[0];
@@ -423,11 +451,11 @@ void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E
 
 void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t* offsets_g,
                        const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
-                       double* loc_val, uint8_t* loc_flag, DevStatus* st, cudaStream_t s) {
+                       double* loc_val, uint8_t* loc_flag, int dual, DevStatus* st, cudaStream_t s) {
     if (m <= 0) return;
     const unsigned nb = nblk(m * 32, 256);
-    if (dim == 2) { elem_local_kernel<2><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, st); count_launch(); }
-    else { elem_local_kernel<3><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, st); count_launch(); }
+    if (dim == 2) { elem_local_kernel<2><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
+    else { elem_local_kernel<3><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
 }
 
 void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const int64_t* adj_ptr,
@@ -462,6 +490,16 @@ void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_
         { mass_values_kernel<2><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv); count_launch(); }
     else
         { mass_values_kernel<3><<<nblk(n_nodes, 128), 128, 0, s>>>(n_nodes, E, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv); count_launch(); }
+}
+
+void launch_lumped_mass(int dim, int64_t n_nodes, const int64_t* adj_ptr, const int32_t* adj,
+                        const double* elem_vol, int64_t* row_ptr, int32_t* cols, double* vals, double* diag_inv,
+                        cudaStream_t s) {
+    if (n_nodes <= 0) return;
+    if (dim == 2)
+        { lumped_mass_kernel<2><<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv); count_launch(); }
+    else
+        { lumped_mass_kernel<3><<<nblk(n_nodes, 256), 256, 0, s>>>(n_nodes, adj_ptr, adj, elem_vol, row_ptr, cols, vals, diag_inv); count_launch(); }
 }
 
 void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, const DevStatus* st,

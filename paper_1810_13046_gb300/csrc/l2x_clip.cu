@@ -188,7 +188,7 @@ __global__ void scatter_plain_kernel(SubGrid sg, const int32_t* __restrict__ E, 
                                      const int32_t* __restrict__ pair_elem, const int32_t* __restrict__ pair_cell,
                                      const double* __restrict__ blocks, const double* __restrict__ vols,
                                      const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                     double* __restrict__ val) {
+                                     double* __restrict__ val, int dual) {
     constexpr int NA = D + 1, NB = 1 << D;
     const int64_t p = p_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= p_end) return;
@@ -211,8 +211,16 @@ __global__ void scatter_plain_kernel(SubGrid sg, const int32_t* __restrict__ E, 
                 int64_t mid = (l + r) >> 1;
                 if (col[mid] < node) l = mid + 1; else r = mid;
             }
-            if (l < hi && col[l] == node)
-                atomicAdd(val + l, blocks[p * (NA * NB) + a * NB + b]);
+            if (l < hi && col[l] == node) {
+                const double* blk = blocks + p * (NA * NB);
+                double v = blk[a * NB + b];
+                if (dual) {  // (d+2) lambda_a - 1: the lambda integrals sum to the integral of psi_b
+                    double sum = 0.0;
+                    for (int a2 = 0; a2 < NA; ++a2) sum += blk[a2 * NB + b];
+                    v = (double)(D + 2) * v - sum;
+                }
+                atomicAdd(val + l, v);
+            }
         }
     }
 }
@@ -269,14 +277,14 @@ void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_
 
 void launch_scatter_plain(int dim, const SubGrid& sg, const int32_t* E, int64_t p_begin, int64_t p_end,
                           const int32_t* pair_elem, const int32_t* pair_cell, const double* blocks,
-                          const double* vols, const Csr& B, cudaStream_t s) {
+                          const double* vols, const Csr& B, int dual, cudaStream_t s) {
     int64_t n = p_end - p_begin;
     if (n <= 0) return;
     unsigned nb = (unsigned)((n + 255) / 256);
     if (dim == 2)
-        { scatter_plain_kernel<2><<<nb, 256, 0, s>>>(sg, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, B.ptr, B.col, B.val); count_launch(); }
+        { scatter_plain_kernel<2><<<nb, 256, 0, s>>>(sg, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, B.ptr, B.col, B.val, dual); count_launch(); }
     else
-        { scatter_plain_kernel<3><<<nb, 256, 0, s>>>(sg, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, B.ptr, B.col, B.val); count_launch(); }
+        { scatter_plain_kernel<3><<<nb, 256, 0, s>>>(sg, E, p_begin, p_end, pair_elem, pair_cell, blocks, vols, B.ptr, B.col, B.val, dual); count_launch(); }
 }
 
 }  // namespace l2x

@@ -121,7 +121,7 @@ void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_
 // plain assembly: atomicAdd of every pair block into the pre-built CSR of B_g
 void launch_scatter_plain(int dim, const SubGrid& sg, const int32_t* E, int64_t p_begin, int64_t p_end,
                           const int32_t* pair_elem, const int32_t* pair_cell, const double* blocks,
-                          const double* vols, const Csr& B, cudaStream_t s);
+                          const double* vols, const Csr& B, int dual, cudaStream_t s);
 
 // assembly (l2x_assemble.cu)
 // node -> (element, local vertex) adjacency, entries e*4 + a sorted per node.
@@ -134,7 +134,7 @@ void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E
 // it (loc_flag).  loc_off_g: offsets of the elements' node boxes.
 void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t* offsets_g,
                        const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
-                       double* loc_val, uint8_t* loc_flag, DevStatus* st, cudaStream_t s);
+                       double* loc_val, uint8_t* loc_flag, int dual, DevStatus* st, cudaStream_t s);
 // Row-wise assembly of B_g from the element-local matrices.  pass 0:
 // row_count[i] = nonzeros of row i; pass 1: cols + vals; pass 2: cols only,
 // vals zeroed (the plain path adds them with atomics).
@@ -149,6 +149,11 @@ void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E,
 void launch_mass_values(int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
                         const int32_t* adj, const double* elem_vol, const int64_t* row_ptr,
                         const int32_t* cols, double* vals, double* diag_inv, cudaStream_t s);
+// S of the dual multiplier basis: diagonal CSR (row i holds column i) with
+// S_ii = sum over the elements around i of |E|/(d+1), and its inverse.
+void launch_lumped_mass(int dim, int64_t n_nodes, const int64_t* adj_ptr, const int32_t* adj,
+                        const double* elem_vol, int64_t* row_ptr, int32_t* cols, double* vals, double* diag_inv,
+                        cudaStream_t s);
 // B_g^T over the box of touched fluid nodes.
 void launch_transpose_count(const Csr& B, const SubGrid& sg, const CsrT& T, int64_t* cnt, const DevStatus* st,
                             cudaStream_t s);
@@ -165,7 +170,11 @@ void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 // y[g] = B_g x[g] (n_rows = solid nodes).  Fused: 8 lanes per row, all grids in
 // one launch; plain: one thread per row, FP64 only.
 void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const void* const* x,
-                   void* const* y, const DevStatus* st, cudaStream_t s);
+                   void* const* y, const DevStatus* st, cudaStream_t s, const double* row_scale = nullptr);
+// w_k = y_k / S_ii for a diagonal S (dinv = 1/S_ii), k < nr; vectors in the
+// precision's type, the product taken in FP64.
+void launch_diag_solve(int precision, int64_t n, int nr, const double* dinv, const void* const* y,
+                       void* const* w, const DevStatus* st, cudaStream_t s);
 // f[g] += scale * B_g^T z[g].  Fused: gather over the rows of B_g^T (no atomics);
 // plain: scatter with atomics from the rows of B_g.
 void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const CsrT* T,

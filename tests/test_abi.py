@@ -67,3 +67,22 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert st == 1 and not h.value
     assert b"dim" in lib.l2x_last_error()
     assert lib.l2x_destroy(None) == 0
+
+
+def test_bad_multiplier_space_is_rejected_without_a_gpu():
+    lib = l2x.load_library()
+    g = l2x._Grid()
+    g.dim, g.staggered = 2, 0
+    for k in range(2):
+        g.ncell[k] = 4
+        g.h[k] = 0.25
+    m = l2x._Mesh()
+    m.dim, m.n_nodes, m.n_elems = 2, 3, 1
+    m.coords = m.elems = 16  # never dereferenced: validation fails first
+    o = l2x._Opts()
+    lib.l2x_default_opts(ctypes.byref(o))
+    assert o.multiplier == l2x.STANDARD_BASIS
+    o.multiplier = 7
+    h = ctypes.c_void_p()
+    assert lib.l2x_build_coupling(ctypes.byref(g), ctypes.byref(m), ctypes.byref(o), None, ctypes.byref(h)) == 1
+    assert b"multiplier" in lib.l2x_last_error()
