@@ -353,3 +353,49 @@ class Coupling:
     def dense_T(self, g: int):
         """Dense transfer operator T_g = S^{-1} B_g (small instances only)."""
         return self.solve_S(self.B[g].toarray())
+
+
+# ----------------------------------------------------------------------------- Picard iteration (Sec. 3)
+
+def picard_norms(f_new, f_prev):
+    """Step 6: (max |f_new - f_prev|, max |f_new|) over all components and nodes."""
+    a = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in f_new])
+    b = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in f_prev])
+    return float(np.max(np.abs(a - b))), float(np.max(np.abs(a)))
+
+
+def picard_converged(d_norm: float, eps_abs: float, eps_rel: float, f0_norm: float) -> bool:
+    """Eq. (AC) or Eq. (RC); the norm of the first iteration's force is f0_norm
+    (infinity norm, a reading: the paper leaves that norm unnamed)."""
+    return d_norm < eps_abs or (f0_norm > 0.0 and d_norm / f0_norm < eps_rel)
+
+
+def picard_time_step(C: "Coupling", v_f0, solid, fluid, eps_abs: float, eps_rel: float, max_iter: int = 50,
+                     scale: float = 1.0):
+    """One time step of the segregated FSI algorithm of Sec. 3 on a fixed T.
+
+    Step 1 w = T v (velocity transfer); Steps 2-3 ``f = solid(w)`` (the caller's
+    solid solve, returning the reaction force); Step 4 f~ = s T^T f; Step 5
+    ``v = fluid(f~)`` (the caller's fluid solve); Step 6 the infinity-norm tests.
+    Returns (v, w, f, iterations, history of (||f_l - f_{l-1}||, ||f_l||)).
+    The force before the first iteration is taken as zero (a reading).
+    """
+    v = [np.asarray(x, dtype=np.float64) for x in v_f0]
+    f_prev = None
+    f0 = None
+    hist = []
+    for it in range(1, max_iter + 1):
+        w = C.transfer_velocity(v)
+        f = np.asarray(solid(w), dtype=np.float64)
+        ft = C.transfer_force(f, mode="dual", scale=scale)
+        v = [np.asarray(x, dtype=np.float64) for x in fluid(ft)]
+        cur = [f[:, g] for g in range(f.shape[1])]
+        prev = f_prev if f_prev is not None else [np.zeros_like(c) for c in cur]
+        dn, fn = picard_norms(cur, prev)
+        hist.append((dn, fn))
+        if f0 is None:
+            f0 = fn
+        f_prev = cur
+        if it > 1 and picard_converged(dn, eps_abs, eps_rel, f0):
+            return v, w, f, it, hist
+    return v, w, f, max_iter, hist

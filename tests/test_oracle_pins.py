@@ -451,3 +451,41 @@ def test_dual_and_standard_projections_differ_off_p1():
     def err(wv):
         return -2 * wv @ (Cs.B[0] @ v[0]) + wv @ (Cs.M @ wv)
     assert err(ws) <= err(wd)
+
+
+# --------------------------------------------------------------- Picard iteration (Sec. 3, Steps 1-6)
+
+def test_picard_norms_and_criteria_closed_form():
+    """Infinity norms of a hand-made example and the two criteria (AC), (RC)."""
+    fn = [np.array([1.0, -4.0, 2.0]), np.array([0.5, 0.0, -3.5])]
+    fp = [np.array([1.5, -4.0, 2.0]), np.array([0.5, 1.25, -3.5])]
+    assert oracle.picard_norms(fn, fp) == (1.25, 4.0)
+    assert oracle.picard_converged(1.25, 2.0, 0.0, 4.0)          # (AC)
+    assert oracle.picard_converged(1.25, 1.0, 0.5, 4.0)          # (RC): 1.25/4 < 0.5
+    assert not oracle.picard_converged(1.25, 1.0, 0.3, 4.0)
+    assert not oracle.picard_converged(1.25, 1.0, 0.5, 0.0)      # no reference norm: (AC) only
+    assert not oracle.picard_converged(float("nan"), 1.0, 0.5, 4.0)
+
+
+def test_picard_loop_reaches_the_fixed_point_of_a_linear_model():
+    """With a linear solid (f = -k (w - w_target)) and fluid (v = v0 + beta f~)
+    the Picard map is an affine contraction; its limit solves
+    (I + beta k T^T T) v = v0 + beta k T^T w_target, computed directly."""
+    w_ = synth.workload("disk2d_small")
+    C = oracle.Coupling(w_.grid, w_.coords, w_.elems)
+    T = C.dense_T(0)
+    rng = np.random.default_rng(3)
+    v0 = rng.standard_normal(T.shape[1])
+    wt = rng.standard_normal(T.shape[0])
+    lam = np.linalg.norm(T, 2) ** 2
+    k, beta = 1.0, 0.8 / lam
+    solid = lambda w: (-k * (w[:, 0] - wt))[:, None]
+    fluid = lambda ft: [v0 + beta * ft[0]]
+    v, w, f, it, hist = oracle.picard_time_step(C, [v0], solid, fluid, eps_abs=1e-13, eps_rel=1e-14, max_iter=400)
+    assert it < 400
+    A = np.eye(T.shape[1]) + beta * k * T.T @ T
+    v_star = np.linalg.solve(A, v0 + beta * k * T.T @ wt)
+    assert np.abs(v[0] - v_star).max() <= 1e-10 * np.abs(v_star).max()
+    # the force differences die out (a contraction in this model)
+    d = [h[0] for h in hist[1:]]
+    assert d[-1] <= 1e-9 * d[0]
