@@ -342,11 +342,17 @@ class Coupling:
                       for g in range(len(self.B))], axis=1)
         return self.solve_S(Y)
 
-    def transfer_force(self, F, mode: str = "nodal", scale: float = 1.0):
-        """Fluid force per grid: s * B_g^T S^{-1} r_g (dual) or s * B_g^T f_g (nodal)."""
+    def transfer_force(self, F, mode: str = "nodal", scale: float = 1.0, mask=None):
+        """Fluid force per grid: s * B_g^T S^{-1} r_g (dual) or s * B_g^T f_g (nodal).
+
+        ``mask`` (one flag per solid node) restricts the input to the interface:
+        entries of nodes outside it count as zero (Sec. 4's plate passes only the
+        forces of its top and bottom edges)."""
         F = np.asarray(F, dtype=np.float64)
         if F.ndim == 1:
             F = F[:, None]
+        if mask is not None:
+            F = np.where(np.asarray(mask, dtype=bool)[:, None], F, 0.0)
         Z = self.solve_S(F) if mode == "dual" else F
         return [scale * (self.B[g].T @ Z[:, g]) for g in range(len(self.B))]
 

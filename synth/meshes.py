@@ -133,6 +133,18 @@ def _block_nodes(nx, ny, nz, size):
     return np.stack([gx.ravel(order="F"), gy.ravel(order="F"), gz.ravel(order="F")], axis=1)
 
 
+def block_face_mask(nx: int, ny: int, nz: int, axis: int = 2) -> np.ndarray:
+    """Nodes of a block mesh (``beam_mesh`` numbering) on its two faces normal to
+    ``axis``: the top and bottom faces of a beam or plate for axis 2."""
+    i = np.arange((nx + 1) * (ny + 1) * (nz + 1))
+    idx = [i % (nx + 1), (i // (nx + 1)) % (ny + 1), i // ((nx + 1) * (ny + 1))]
+    n = (nx, ny, nz)[axis]
+    return (idx[axis] == 0) | (idx[axis] == n)
+
+
+BEAM_HEXES = {"beam128": (80, 20, 5), "beam64": (40, 10, 3), "beam32": (20, 5, 2), "beam16": (8, 2, 1)}
+
+
 def beam_mesh(nx: int = 80, ny: int = 20, nz: int = 5, size=(0.4, 0.1, 0.02)):
     """Box beam centred at the origin, nx*ny*nz hexahedra x 6 Kuhn tetrahedra."""
     X = _block_nodes(nx, ny, nz, size)
@@ -270,8 +282,8 @@ def workload(name: str, seed: int = 0, field_dtype=np.float64) -> Workload:
         wl.force = rng.standard_normal((X.shape[0], 1))
         return wl
     if name in ("beam128", "beam16", "beam32", "beam64"):
-        n, hexes = {"beam128": (128, (80, 20, 5)), "beam64": (64, (40, 10, 3)),
-                    "beam32": (32, (20, 5, 2)), "beam16": (16, (8, 2, 1))}[name]
+        n = {"beam128": 128, "beam64": 64, "beam32": 32, "beam16": 16}[name]
+        hexes = BEAM_HEXES[name]
         grid = Grid(3, (n, n, n), (1.0 / n,) * 3, (0.0, 0.0, 0.0), True)
         X, E = beam_mesh(*hexes)
         X = place_body(X, random_rotation(rng), (0.5, 0.5, 0.5))

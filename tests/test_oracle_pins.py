@@ -489,3 +489,39 @@ def test_picard_loop_reaches_the_fixed_point_of_a_linear_model():
     # the force differences die out (a contraction in this model)
     d = [h[0] for h in hist[1:]]
     assert d[-1] <= 1e-9 * d[0]
+
+
+# --------------------------------------------------------------- interface-restricted force transfer
+
+@pytest.mark.parametrize("multiplier", ["standard", "dual"])
+def test_masked_force_transfer_conserves_force_and_moment(multiplier):
+    """With the input restricted to the top and bottom faces Gamma of the beam,
+    the fluid force keeps the total force and the first moment of the solid
+    force on Gamma: sum_j f~_j = s sum_{i in Gamma} r_i and sum_j x_j f~_j =
+    s sum_{i in Gamma} X_i r_i (DUAL mode: Q1 and P1 reproduce 1 and x, and
+    B 1 = S 1 for either basis); NODAL mode: sum_j f~_j = s sum_{i in Gamma}
+    f_i int phi_i."""
+    w = synth.workload("beam32")
+    mask = synth.block_face_mask(*synth.BEAM_HEXES["beam32"], axis=2)
+    assert 0 < mask.sum() < mask.size
+    C = oracle.Coupling(w.grid, w.coords, w.elems, multiplier=multiplier)
+    rng = np.random.default_rng(13)
+    R = rng.standard_normal((w.coords.shape[0], 3))
+    s = 0.7
+    ft = C.transfer_force(R, mode="dual", scale=s, mask=mask)
+    fn = C.transfer_force(R, mode="nodal", scale=s, mask=mask)
+    phi, _ = _phi_integrals(w.coords, w.elems)
+    for g in range(3):
+        P = synth.grid_node_coords(w.grid, g)
+        r = np.where(mask, R[:, g], 0.0)
+        assert abs(ft[g].sum() - s * r.sum()) <= 1e-12 * np.abs(r).sum()
+        mom = P.T @ ft[g]
+        ref = s * (w.coords.T @ r)
+        assert np.abs(mom - ref).max() <= 1e-12 * np.abs(r).sum()
+        assert abs(fn[g].sum() - s * (phi * r).sum()) <= 1e-12 * (phi * np.abs(r)).sum()
+    # nodes outside Gamma do not contribute
+    R2 = R.copy()
+    R2[~mask] = 1e3 * rng.standard_normal((int((~mask).sum()), 3))
+    ft2 = C.transfer_force(R2, mode="dual", scale=s, mask=mask)
+    for g in range(3):
+        assert np.array_equal(ft2[g], ft[g])
