@@ -303,6 +303,38 @@ class Arm:
         return dict(c=c, info=info, build_ms=tb / steps, apply_ms=ta / steps, launches=launches,
                     pairs=pairs_per_step, uf=uf, fs=fs)
 
+    def picard(self, c, uf, fs, iters):
+        """Picard iterations on one assembled coupling (Sec. 3): per iteration the
+        enqueue-only velocity and force transfers and the Step-6 infinity norms
+        (the caller's solid and fluid solves are not part of the library)."""
+        torch = self.torch
+        dt = uf[0].dtype
+        us = [torch.zeros(c.n_nodes, dtype=dt, device=self.dev) for _ in range(3)]
+        ff = [torch.zeros(n, dtype=dt, device=self.dev) for n in c.fluid_sizes()]
+        fprev = [torch.zeros(c.n_nodes, dtype=dt, device=self.dev) for _ in range(3)]
+        norms = torch.zeros(2, dtype=torch.float64, device=self.dev)
+        stream = torch.cuda.current_stream(self.dev)
+
+        def it():
+            c.transfer_velocity_async(uf, us)
+            for z in ff:
+                z.zero_()
+            c.transfer_force_async(fs, ff)
+            c.picard_norms(fs, fprev, copy=True, out=norms)
+
+        for _ in range(3):
+            it()
+        c.sync_status()
+        self.flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(iters):
+            it()
+        e1.record(stream)
+        e1.synchronize()
+        c.sync_status()
+        return e0.elapsed_time(e1) / iters
+
     def graph(self, precision, steps, warmup, multiplier=0):
         """The whole step captured as one CUDA graph and replayed."""
         torch, l2x = self.torch, self.l2x
@@ -396,6 +428,12 @@ def main():
     n_pc = max(3, args.steps // 4)
     clip_launch_ms = ph["clip"] / max(1, calls["clip"])
     clip_pairs_per_launch = pc["pairs"] / max(1, calls["clip"] // n_pc)
+    picard_ms = arm.picard(pc["c"], pc["uf"], pc["fs"], 20)
+    picard = {"iteration_ms": picard_ms, "iterations_per_time_step": 3,
+              "time_step_ms": pc["build_ms"] + 3 * picard_ms,
+              "pairs_per_s": pc["pairs"] / ((pc["build_ms"] + 3 * picard_ms) * 1e-3),
+              "form": "per-call assembly, then 3 x (enqueue-only velocity + force transfer + Step-6 norms), "
+                      "mixed precision, standard multipliers"}
     plain = arm.per_call(l2x.PLAIN, l2x.FP64, args.plain_steps, 2)
     f64 = arm.per_call(l2x.FUSED, l2x.FP64, args.plain_steps, 2)
     tuned = getattr(arm, "tuned", None)
@@ -505,6 +543,7 @@ def main():
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "autotuned": tuned,
             "pseudo_l2_dual": dual,
+            "picard": picard,
             "gpu_launches": int(pc["launches"] / n_pc * args.steps),
             "gpu_launches_note": "per step as counted on the per-call form; the captured graph replays the same "
                                  "kernel nodes",

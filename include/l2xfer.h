@@ -183,6 +183,50 @@ l2x_status l2x_apply_BT(l2x_handle h, const void* const* z_s, void* const* f_f, 
                         void* stream);
 l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s, void* stream);
 
+/* Interface restriction of the force input (Sec. 2's interface Gamma_fsi; in
+ * the plate benchmark of Sec. 4 only the reaction forces of the top and bottom
+ * edges are communicated).  mask: device array of n_nodes bytes, nonzero =
+ * node on the interface; the library copies it (stream-ordered).  Afterwards
+ * every force transfer (per call, enqueue-only, captured steps created later)
+ * uses mask_i * f_s[g][i] in place of f_s[g][i], i.e. f_f += s T^T (mask ⊙ f_s)
+ * (DUAL) or s B^T (mask ⊙ f_s) (NODAL).  NULL removes the restriction. */
+l2x_status l2x_set_force_mask(l2x_handle h, const uint8_t* mask, void* stream);
+
+/* Picard iterations on one assembled T (Sec. 3, "Fluid-Structure Interaction
+ * algorithm": Steps 1 and 4 are repeated within a time step while Steps 2, 3
+ * and 5, the caller's solid and fluid solvers, run in between).  The
+ * enqueue-only forms below do not synchronise the host, so a whole Picard
+ * iteration can be captured into the caller's own CUDA graph:
+ *
+ * l2x_transfer_velocity_async / l2x_transfer_force_async: the same results as
+ * l2x_transfer_velocity / l2x_transfer_force (fused path only).  The mass-matrix
+ * solve runs a fixed schedule: the FP64 PCG stops on cg_rtol inside the kernel;
+ * the mixed form runs one FP32 solve and one FP64 residual correction.  A solve
+ * that misses cg_rtol is recorded in the handle's device status.
+ * l2x_sync_status: waits for `stream`, returns the recorded status of the
+ * enqueued calls since the last check (ENOTCONVERGED, or an assembly error) and
+ * clears it; l2x_query then reports the last solve's iterations and residual. */
+l2x_status l2x_transfer_velocity_async(l2x_handle h, const void* const* u_f, void* const* u_s, void* stream);
+l2x_status l2x_transfer_force_async(l2x_handle h, const void* const* f_s, void* const* f_f, void* stream);
+l2x_status l2x_sync_status(l2x_handle h, void* stream);
+
+/* Step 6 of Sec. 3, the convergence test of the Picard iteration, Eqs. (AC) and
+ * (RC).  l2x_picard_norms reduces over the n_grids solid arrays f_new and f_prev
+ * (n_nodes entries each, the precision's type) on the device:
+ *   norms[0] = max_{g,i} |f_new[g][i] - f_prev[g][i]|,  norms[1] = max_{g,i} |f_new[g][i]|
+ * into `norms` (2 device doubles, 8-byte aligned, written; NaN in an input
+ * makes the norm NaN).  With copy != 0 it also sets f_prev = f_new in the same
+ * pass (the arrays must not overlap).  Enqueue-only.
+ * l2x_picard_converged reads norms (synchronising `stream`; host_norms, 2
+ * doubles, may be NULL) and sets *converged = 1 when
+ *   norms[0] < eps_abs  (AC)   or   norms[0] / f0_norm < eps_rel  (RC),
+ * where f0_norm is the caller's norm of the force of the first Picard
+ * iteration (for example its norms[1]); f0_norm <= 0 disables (RC). */
+l2x_status l2x_picard_norms(l2x_handle h, const void* const* f_new, void* const* f_prev, int32_t copy,
+                            double* norms, void* stream);
+l2x_status l2x_picard_converged(const double* norms, double eps_abs, double eps_rel, double f0_norm,
+                                int32_t* converged, double* host_norms, void* stream);
+
 /* One time step as a CUDA graph (the batched moving-bodies pattern): a mesh made
  * of many bodies (disjoint node sets in one l2x_mesh) is re-assembled in its
  * current configuration and both transfers run, with no host synchronisation,

@@ -5,8 +5,11 @@ argument marshalling only, every step of the transfer runs in the library's CUDA
 kernels.  PyTorch supplies device memory and the current CUDA stream.
 
 The method is the variational transfer of Sec. 2.3 of the paper (mortar
-integrals ``B_ij = ∫ psi_j phi_i``, ``S = M_s``, ``w_s = S^-1 B v_f``, forces by
-``T^T``), assembled by the four steps given there.
+integrals ``B_ij = ∫ psi_j N_i``, ``S_ij = ∫ phi_j N_i`` with N_i = phi_i
+(``S = M_s``) or the dual basis of Eq. (biorth) (S diagonal),
+``w_s = S^-1 B v_f``, forces by ``T^T``), assembled by the four steps given
+there, plus the Picard-iteration helpers of Sec. 3 (enqueue-only transfers and
+the infinity norms of Step 6) and an interface mask on the force input.
 """
 from __future__ import annotations
 
@@ -19,7 +22,7 @@ import torch
 from . import build as _build
 
 __all__ = ["kernel_launch_count", "PHASES", "StepGraph", "Coupling", "Grid", "VelocityTransfer", "ForceTransfer", "L2XError", "library_path", "load_library",
-           "PLAIN", "FUSED", "FP64", "MIXED", "NODAL", "DUAL"]
+           "PLAIN", "FUSED", "FP64", "MIXED", "NODAL", "DUAL", "STANDARD_BASIS", "DUAL_BASIS"]
 
 PLAIN, FUSED = 0, 1
 FP64, MIXED = 0, 1
@@ -91,6 +94,13 @@ def load_library(build_if_missing: bool = True):
         "l2x_transfer_velocity": ([P, PP, PP, P], ctypes.c_int),
         "l2x_transfer_force": ([P, PP, PP, P], ctypes.c_int),
         "l2x_apply_B": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_transfer_velocity_async": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_set_force_mask": ([P, P, P], ctypes.c_int),
+        "l2x_transfer_force_async": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_sync_status": ([P, P], ctypes.c_int),
+        "l2x_picard_norms": ([P, PP, PP, ctypes.c_int32, P, P], ctypes.c_int),
+        "l2x_picard_converged": ([P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "l2x_apply_BT": ([P, PP, PP, ctypes.c_double, P], ctypes.c_int),
         "l2x_solve_mass": ([P, PP, PP, P], ctypes.c_int),
         "l2x_query": ([P, ctypes.POINTER(_Info)], ctypes.c_int),
@@ -197,6 +207,7 @@ class Coupling:
         opts.force_scale = force_scale
         opts.multiplier = multiplier
         self.multiplier = multiplier
+        self.force_mask = None
         self.force_mode = force_mode
         self.force_scale = force_scale
         mesh = _Mesh()
@@ -275,7 +286,8 @@ class Coupling:
         return out
 
     def transfer_velocity(self, u_f, out=None):
-        """u_s[g] = M_s^-1 B_g u_f[g] for every velocity grid g."""
+        """u_s[g] = S^-1 B_g u_f[g] for every velocity grid g (S = M_s, or diagonal
+        for the dual multiplier basis)."""
         u_f = self._fields(u_f, self.fluid_sizes())
         u_s = out if out is not None else self._solid()
         with torch.cuda.device(self.device):
@@ -283,7 +295,7 @@ class Coupling:
         return u_s
 
     def transfer_force(self, f_s, f_f=None):
-        """f_f[g] += s B_g^T M_s^-1 f_s[g] (DUAL) or s B_g^T f_s[g] (NODAL); returns f_f."""
+        """f_f[g] += s B_g^T S^-1 f_s[g] (DUAL) or s B_g^T f_s[g] (NODAL); returns f_f."""
         f_s = self._fields(f_s, [self.n_nodes] * self.n_grids)
         if f_f is None:
             f_f = [torch.zeros(n, dtype=self.dtype, device=self.device) for n in self.fluid_sizes()]
@@ -312,6 +324,63 @@ class Coupling:
         with torch.cuda.device(self.device):
             _check(load_library().l2x_solve_mass(self._h, _ptrs(y_s), _ptrs(w), _stream_ptr(self.device)))
         return w
+
+    # ------------------------------------------------------------------ interface restriction
+    def set_force_mask(self, mask):
+        """Restrict the force input to the nodes where ``mask`` (bool/uint8 tensor of
+        n_nodes) is set; ``None`` removes the restriction."""
+        if mask is None:
+            self.force_mask = None
+            ptr = None
+        else:
+            m = mask.to(device=self.device, dtype=torch.uint8).contiguous()
+            if m.numel() != self.n_nodes:
+                raise ValueError("mask needs one entry per solid node")
+            self.force_mask = m
+            ptr = ctypes.c_void_p(m.data_ptr())
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_set_force_mask(self._h, ptr, _stream_ptr(self.device)))
+
+    # ------------------------------------------------------------------ Picard iterations
+    def transfer_velocity_async(self, u_f, u_s):
+        """Enqueue-only velocity transfer (no host synchronisation; capturable).
+        Solver status is read by :meth:`sync_status`."""
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_transfer_velocity_async(self._h, _ptrs(u_f), _ptrs(u_s),
+                                                              _stream_ptr(self.device)))
+        return u_s
+
+    def transfer_force_async(self, f_s, f_f):
+        """Enqueue-only force transfer (accumulates into f_f)."""
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_transfer_force_async(self._h, _ptrs(f_s), _ptrs(f_f),
+                                                           _stream_ptr(self.device)))
+        return f_f
+
+    def sync_status(self):
+        """Wait for the stream and raise on a recorded error of enqueued calls."""
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_sync_status(self._h, _stream_ptr(self.device)))
+
+    def picard_norms(self, f_new, f_prev, copy: bool = True, out=None):
+        """Device tensor [max|f_new - f_prev|, max|f_new|] over all components
+        (Step 6's infinity norms); f_prev <- f_new when ``copy``."""
+        norms = out if out is not None else torch.empty(2, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_picard_norms(self._h, _ptrs(f_new), _ptrs(f_prev), int(bool(copy)),
+                                                   ctypes.c_void_p(norms.data_ptr()), _stream_ptr(self.device)))
+        return norms
+
+    @staticmethod
+    def picard_converged(norms, eps_abs: float, eps_rel: float, f0_norm: float):
+        """Eqs. (AC)/(RC) on device norms: returns (converged, (norm_diff, norm_new))."""
+        conv = ctypes.c_int32()
+        hn = (ctypes.c_double * 2)()
+        with torch.cuda.device(norms.device):
+            _check(load_library().l2x_picard_converged(ctypes.c_void_p(norms.data_ptr()), float(eps_abs),
+                                                       float(eps_rel), float(f0_norm), ctypes.byref(conv), hn,
+                                                       _stream_ptr(norms.device)))
+        return bool(conv.value), (hn[0], hn[1])
 
     # ------------------------------------------------------------------ captured steps
     def capture_step(self, coords_src, u_f, u_s, f_s, f_f, margin: float = 1.5, zero_force: bool = True,
@@ -414,7 +483,7 @@ class StepGraph:
 # ---------------------------------------------------------------------- autograd
 
 class VelocityTransfer(torch.autograd.Function):
-    """u_s = M_s^-1 B u_f per grid; backward: grad_u_f = B^T M_s^-1 grad_u_s (the exact adjoint)."""
+    """u_s = S^-1 B u_f per grid; backward: grad_u_f = B^T S^-1 grad_u_s (the exact adjoint)."""
 
     @staticmethod
     def forward(ctx, coupling: Coupling, *u_f):
@@ -432,8 +501,9 @@ class VelocityTransfer(torch.autograd.Function):
 
 
 class ForceTransfer(torch.autograd.Function):
-    """f_f = s B^T M_s^-1 f_s (DUAL) or s B^T f_s (NODAL) per grid; backward applies
-    the adjoint s M_s^-1 B (DUAL) or s B (NODAL) to grad_f_f."""
+    """f_f = s B^T S^-1 (m ⊙ f_s) (DUAL) or s B^T (m ⊙ f_s) (NODAL) per grid, m the
+    interface mask (all ones unless set); backward applies the adjoint
+    s m ⊙ S^-1 B (DUAL) or s m ⊙ B (NODAL) to grad_f_f."""
 
     @staticmethod
     def forward(ctx, coupling: Coupling, *f_s):
@@ -448,4 +518,7 @@ class ForceTransfer(torch.autograd.Function):
         y = c.apply_B(gf)
         if c.force_mode == DUAL:
             y = c.solve_mass(y)
+        m = getattr(c, "force_mask", None)
+        if m is not None:  # adjoint of the restriction f -> mask * f
+            y = [v * m.to(v.dtype) for v in y]
         return (None, *[c.force_scale * v for v in y])

@@ -77,6 +77,9 @@ struct l2x_coupling {
     int64_t tflags_cap = 0;
     void* pcg_ws = nullptr;
     void* vec_tmp = nullptr;         // n_grids * n_nodes doubles
+    void* vec_mask = nullptr;        // n_grids * n_nodes doubles: the masked force input
+    uint8_t* fmask = nullptr;        // interface mask of the force input (n_nodes), when has_fmask
+    bool has_fmask = false;
     DevStatus* st = nullptr;
     DevStatus* st_host = nullptr;    // pinned
     // work-chunk sizes (l2x_autotune)
@@ -519,6 +522,55 @@ l2x_status check_ptrs(const void* const* a, int n, const char* what) {
     return L2X_OK;
 }
 
+// Velocity transfer without host synchronisation (fused path): B u_f with the
+// division by a diagonal S fused in, or B u_f followed by the cooperative PCG
+// (fixed schedule in the mixed form; non-convergence recorded in the status).
+void enqueue_velocity(l2x_coupling* h, const void* const* u_f, void* const* u_s, cudaStream_t s) {
+    const int G = h->n_grids;
+    if (h->opts.multiplier == L2X_MULT_DUAL) {
+        launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, u_s, h->st, s, h->M_dinv);
+        return;
+    }
+    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+    void* tmp[kMaxGrids];
+    for (int g = 0; g < G; ++g) tmp[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
+    launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, tmp, h->st, s);
+    solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)tmp, u_s,
+                         h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
+}
+
+// Force transfer without host synchronisation (fused path): f_f += s B^T S^-1 f_s
+// (dual force mode) or s B^T f_s (nodal).
+// The force input restricted to the interface mask (a copy in vec_mask), or f_s itself.
+const void* const* masked_force(l2x_coupling* h, const void* const* f_s, const void** buf, cudaStream_t s) {
+    if (!h->has_fmask) return f_s;
+    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+    for (int g = 0; g < h->n_grids; ++g) buf[g] = (char*)h->vec_mask + es * h->n_nodes * g;
+    launch_mask_copy(h->opts.precision, h->n_nodes, h->n_grids, h->fmask, f_s, (void* const*)buf, h->st, s);
+    return buf;
+}
+
+void enqueue_force(l2x_coupling* h, const void* const* f_s_in, void* const* f_f, cudaStream_t s) {
+    const int G = h->n_grids;
+    const void* mbuf[kMaxGrids];
+    const void* const* f_s = masked_force(h, f_s_in, mbuf, s);
+    if (h->opts.force_mode == L2X_FORCE_DUAL) {
+        const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+        void* tmp[kMaxGrids];
+        for (int g = 0; g < G; ++g) tmp[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
+        if (h->opts.multiplier == L2X_MULT_DUAL)
+            launch_diag_solve(h->opts.precision, h->n_nodes, G, h->M_dinv, f_s, tmp, h->st, s);
+        else
+            solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, f_s, tmp, h->opts.cg_rtol,
+                                 h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
+        launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)tmp, f_f,
+                       h->opts.force_scale, h->st, s);
+    } else {
+        launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, f_s, f_f, h->opts.force_scale,
+                       h->st, s);
+    }
+}
+
 // Enqueues one whole time step without host synchronisation: copy of the new
 // node positions, re-assembly with the capacities of the handle (overflow sets
 // FLAG_CAPACITY and later kernels skip their work), velocity transfer and dual
@@ -565,30 +617,12 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     }
     launch_S_values(h, s);
     // transfers
-    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
-    void* tmp[kMaxGrids];
-    for (int g = 0; g < G; ++g) tmp[g] = (char*)h->vec_tmp + es * n * g;
-    const bool diag = h->opts.multiplier == L2X_MULT_DUAL;
-    if (diag) {
-        launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, u_s, h->st, s, h->M_dinv);
-    } else {
-        launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, tmp, h->st, s);
-        solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)tmp, u_s,
-                             h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
-    }
-    if (zero_force)
+    enqueue_velocity(h, u_f, u_s, s);
+    if (zero_force) {
+        const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
         for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
-    if (h->opts.force_mode == L2X_FORCE_DUAL) {
-        if (diag)
-            launch_diag_solve(h->opts.precision, n, G, h->M_dinv, f_s, tmp, h->st, s);
-        else
-            solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, f_s, tmp, h->opts.cg_rtol,
-                                 h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
-        launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)tmp, f_f,
-                       h->opts.force_scale, h->st, s);
-    } else {
-        launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, f_s, f_f, h->opts.force_scale, h->st, s);
     }
+    enqueue_force(h, f_s, f_f, s);
     return L2X_OK;
 }
 
@@ -654,6 +688,8 @@ l2x_status l2x_destroy(l2x_handle h) {
     dfree(h->tflags);
     if (h->pcg_ws) cudaFree(h->pcg_ws);
     if (h->vec_tmp) cudaFree(h->vec_tmp);
+    if (h->vec_mask) cudaFree(h->vec_mask);
+    dfree(h->fmask);
     dfree(h->st);
     if (h->st_host) cudaFreeHost(h->st_host);
     delete h;
@@ -804,16 +840,97 @@ l2x_status l2x_transfer_velocity(l2x_handle h, const void* const* u_f, void* con
     return l2x_solve_mass(h, (const void* const*)y, u_s, stream);
 }
 
-l2x_status l2x_transfer_force(l2x_handle h, const void* const* f_s, void* const* f_f, void* stream) {
+l2x_status l2x_transfer_force(l2x_handle h, const void* const* f_s_in, void* const* f_f, void* stream) {
     if (!h) return fail(L2X_EINVAL, "NULL handle");
-    L2X_TRY(check_ptrs(f_s, h->n_grids, "f_s"));
+    L2X_TRY(check_ptrs(f_s_in, h->n_grids, "f_s"));
     L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
+    const void* mbuf[kMaxGrids];
+    const void* const* f_s = masked_force(h, f_s_in, mbuf, (cudaStream_t)stream);
     if (h->opts.force_mode == L2X_FORCE_NODAL) return l2x_apply_BT(h, f_s, f_f, h->opts.force_scale, stream);
     const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
     void* z[kMaxGrids];
     for (int g = 0; g < h->n_grids; ++g) z[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
     L2X_TRY(l2x_solve_mass(h, f_s, z, stream));
     return l2x_apply_BT(h, (const void* const*)z, f_f, h->opts.force_scale, stream);
+}
+
+l2x_status l2x_set_force_mask(l2x_handle h, const uint8_t* mask, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!mask) {
+        h->has_fmask = false;
+        return L2X_OK;
+    }
+    if (!h->fmask) L2X_TRY(dalloc(&h->fmask, h->n_nodes));
+    if (!h->vec_mask && cudaMalloc(&h->vec_mask, sizeof(double) * h->n_nodes * h->n_grids) != cudaSuccess)
+        return fail(L2X_ENOMEM, "masked force scratch");
+    L2X_CUDA(cudaMemcpyAsync(h->fmask, mask, h->n_nodes, cudaMemcpyDeviceToDevice, s));
+    h->has_fmask = true;
+    return L2X_OK;
+}
+
+l2x_status l2x_transfer_velocity_async(l2x_handle h, const void* const* u_f, void* const* u_s, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    if (h->opts.path != L2X_PATH_FUSED) return fail(L2X_EINVAL, "enqueue-only transfers need the fused path");
+    L2X_TRY(check_ptrs(u_f, h->n_grids, "u_f"));
+    L2X_TRY(check_ptrs((const void* const*)u_s, h->n_grids, "u_s"));
+    enqueue_velocity(h, u_f, u_s, (cudaStream_t)stream);
+    L2X_CUDA(cudaGetLastError());
+    return L2X_OK;
+}
+
+l2x_status l2x_transfer_force_async(l2x_handle h, const void* const* f_s, void* const* f_f, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    if (h->opts.path != L2X_PATH_FUSED) return fail(L2X_EINVAL, "enqueue-only transfers need the fused path");
+    L2X_TRY(check_ptrs(f_s, h->n_grids, "f_s"));
+    L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
+    enqueue_force(h, f_s, f_f, (cudaStream_t)stream);
+    L2X_CUDA(cudaGetLastError());
+    return L2X_OK;
+}
+
+l2x_status l2x_sync_status(l2x_handle h, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    L2X_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    L2X_CUDA(cudaGetLastError());
+    const DevStatus ds = *h->st_host;
+    h->cg_iters = ds.cg_iters;
+    h->cg_residual = ds.cg_residual;
+    L2X_TRY(reset_status(h, s));
+    L2X_TRY(flags_to_status(ds));
+    if (ds.flags & FLAG_NOTCONVERGED) return fail(L2X_ENOTCONVERGED, "CG did not reach cg_rtol in an enqueued solve");
+    return L2X_OK;
+}
+
+l2x_status l2x_picard_norms(l2x_handle h, const void* const* f_new, void* const* f_prev, int32_t copy,
+                            double* norms, void* stream) {
+    if (!h || !norms) return fail(L2X_EINVAL, "NULL handle or norms");
+    L2X_TRY(check_ptrs(f_new, h->n_grids, "f_new"));
+    L2X_TRY(check_ptrs((const void* const*)f_prev, h->n_grids, "f_prev"));
+    if (((uintptr_t)norms & 7) != 0) return fail(L2X_EINVAL, "norms must be 8-byte aligned");
+    launch_picard_norms(h->opts.precision, h->n_nodes, h->n_grids, f_new, f_prev, copy != 0, norms,
+                        (cudaStream_t)stream);
+    L2X_CUDA(cudaGetLastError());
+    return L2X_OK;
+}
+
+l2x_status l2x_picard_converged(const double* norms, double eps_abs, double eps_rel, double f0_norm,
+                                int32_t* converged, double* host_norms, void* stream) {
+    if (!norms || !converged) return fail(L2X_EINVAL, "NULL norms or converged");
+    cudaStream_t s = (cudaStream_t)stream;
+    double hn[2] = {0.0, 0.0};
+    L2X_CUDA(cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s));
+    L2X_CUDA(cudaStreamSynchronize(s));
+    if (host_norms) {
+        host_norms[0] = hn[0];
+        host_norms[1] = hn[1];
+    }
+    const bool abs_ok = hn[0] < eps_abs;
+    const bool rel_ok = f0_norm > 0.0 && hn[0] / f0_norm < eps_rel;
+    *converged = (abs_ok || rel_ok) ? 1 : 0;
+    return L2X_OK;
 }
 
 l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* const* u_f, void* const* u_s,

@@ -62,6 +62,19 @@ __global__ void spmv_B_plain_kernel(int64_t n_rows, const int64_t* __restrict__ 
     y[i] = scale ? s * scale[i] : s;
 }
 
+// out_k = mask ⊙ f_k (interface restriction of the force input).
+template <typename TV>
+__global__ void mask_copy_kernel(int64_t n, int nr, const uint8_t* __restrict__ mask, const TV* f0, const TV* f1,
+                                 const TV* f2, TV* o0, TV* o1, TV* o2, const DevStatus* st) {
+    if (st->flags & kAbortFlags) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool on = mask[i] != 0;
+    o0[i] = on ? f0[i] : TV(0);
+    if (nr > 1) o1[i] = on ? f1[i] : TV(0);
+    if (nr > 2) o2[i] = on ? f2[i] : TV(0);
+}
+
 // w_k = y_k / S_ii for a diagonal S; the product in FP64, one rounding to TV.
 template <typename TV>
 __global__ void diag_solve_kernel(int64_t n, int nr, const double* __restrict__ dinv, const TV* y0, const TV* y1,
@@ -73,6 +86,59 @@ __global__ void diag_solve_kernel(int64_t n, int nr, const double* __restrict__ 
     w0[i] = (TV)((double)y0[i] * di);
     if (nr > 1) w1[i] = (TV)((double)y1[i] * di);
     if (nr > 2) w2[i] = (TV)((double)y2[i] * di);
+}
+
+// ------------------------------------------------------------------ Picard norms
+template <typename TV>
+struct PicardPack {
+    const TV* fn[kMaxGrids];
+    TV* fp[kMaxGrids];
+};
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    // |x| as its bit pattern: for non-negative doubles the unsigned order is the
+    // numeric order, and NaN (any payload) sorts above +inf
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// out[0] = max |f_new - f_prev|, out[1] = max |f_new| over all grids and nodes
+// (as bit patterns, combined by atomicMax); f_prev = f_new when copy != 0.
+template <typename TV>
+__global__ void picard_norms_kernel(int64_t n, int G, PicardPack<TV> P, int copy, unsigned long long* out) {
+    __shared__ unsigned long long s_d[32], s_f[32];
+    unsigned long long dmax = 0, fmax = 0;
+    const int64_t total = n * G;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int g = (int)(t / n);
+        const int64_t i = t - (int64_t)g * n;
+        const TV a = P.fn[g][i];
+        const TV b = P.fp[g][i];
+        const unsigned long long d = abs_bits((double)a - (double)b), f = abs_bits((double)a);
+        dmax = d > dmax ? d : dmax;
+        fmax = f > fmax ? f : fmax;
+        if (copy) P.fp[g][i] = a;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long d = __shfl_xor_sync(0xffffffffu, dmax, o);
+        const unsigned long long f = __shfl_xor_sync(0xffffffffu, fmax, o);
+        dmax = d > dmax ? d : dmax;
+        fmax = f > fmax ? f : fmax;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_d[w] = dmax;
+        s_f[w] = fmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            dmax = s_d[k] > dmax ? s_d[k] : dmax;
+            fmax = s_f[k] > fmax ? s_f[k] : fmax;
+        }
+        atomicMax(out, dmax);
+        atomicMax(out + 1, fmax);
+    }
 }
 
 // ------------------------------------------------------------------ B^T z
@@ -690,6 +756,39 @@ size_t pcg_ws_bytes(int64_t n, int n_rhs, int max_blocks) {
     size_t v = (size_t)n * n_rhs;
     return 5 * v * sizeof(double) + 2 * v * sizeof(double) + 2 * v * sizeof(float) +
            (size_t)max_blocks * 3 * kMaxRhs * sizeof(double) + 64 * sizeof(double) + 16384;
+}
+
+void launch_picard_norms(int precision, int64_t n, int G, const void* const* f_new, void* const* f_prev, int copy,
+                         double* norms, cudaStream_t s) {
+    cudaMemsetAsync(norms, 0, 2 * sizeof(double), s);
+    if (n <= 0 || G <= 0) return;
+    const int64_t total = n * G;
+    int64_t nb = (total + 255) / 256;
+    if (nb > 152 * 8) nb = 152 * 8;
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(norms);
+    if (precision == L2X_MIXED) {
+        PicardPack<float> P{};
+        for (int g = 0; g < G; ++g) { P.fn[g] = (const float*)f_new[g]; P.fp[g] = (float*)f_prev[g]; }
+        { picard_norms_kernel<float><<<(unsigned)nb, 256, 0, s>>>(n, G, P, copy, out); count_launch(); }
+    } else {
+        PicardPack<double> P{};
+        for (int g = 0; g < G; ++g) { P.fn[g] = (const double*)f_new[g]; P.fp[g] = (double*)f_prev[g]; }
+        { picard_norms_kernel<double><<<(unsigned)nb, 256, 0, s>>>(n, G, P, copy, out); count_launch(); }
+    }
+}
+
+void launch_mask_copy(int precision, int64_t n, int nr, const uint8_t* mask, const void* const* f, void* const* out,
+                      const DevStatus* st, cudaStream_t s) {
+    if (n <= 0 || nr <= 0) return;
+    if (precision == L2X_MIXED) {
+        const float* ff[3] = {(const float*)f[0], nr > 1 ? (const float*)f[1] : nullptr, nr > 2 ? (const float*)f[2] : nullptr};
+        float* oo[3] = {(float*)out[0], nr > 1 ? (float*)out[1] : nullptr, nr > 2 ? (float*)out[2] : nullptr};
+        { mask_copy_kernel<float><<<nblk(n, 256), 256, 0, s>>>(n, nr, mask, ff[0], ff[1], ff[2], oo[0], oo[1], oo[2], st); count_launch(); }
+    } else {
+        const double* ff[3] = {(const double*)f[0], nr > 1 ? (const double*)f[1] : nullptr, nr > 2 ? (const double*)f[2] : nullptr};
+        double* oo[3] = {(double*)out[0], nr > 1 ? (double*)out[1] : nullptr, nr > 2 ? (double*)out[2] : nullptr};
+        { mask_copy_kernel<double><<<nblk(n, 256), 256, 0, s>>>(n, nr, mask, ff[0], ff[1], ff[2], oo[0], oo[1], oo[2], st); count_launch(); }
+    }
 }
 
 void launch_diag_solve(int precision, int64_t n, int nr, const double* dinv, const void* const* y,

@@ -171,6 +171,14 @@ void launch_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
 // one launch; plain: one thread per row, FP64 only.
 void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const void* const* x,
                    void* const* y, const DevStatus* st, cudaStream_t s, const double* row_scale = nullptr);
+// Step 6 of the FSI algorithm: norms[0] = max |f_new - f_prev|, norms[1] =
+// max |f_new| over the G components of n entries (device doubles); f_prev =
+// f_new in the same pass when copy != 0.
+void launch_picard_norms(int precision, int64_t n, int G, const void* const* f_new, void* const* f_prev, int copy,
+                         double* norms, cudaStream_t s);
+// out_k = f_k where mask != 0, else 0 (k < nr).
+void launch_mask_copy(int precision, int64_t n, int nr, const uint8_t* mask, const void* const* f, void* const* out,
+                      const DevStatus* st, cudaStream_t s);
 // w_k = y_k / S_ii for a diagonal S (dinv = 1/S_ii), k < nr; vectors in the
 // precision's type, the product taken in FP64.
 void launch_diag_solve(int precision, int64_t n, int nr, const double* dinv, const void* const* y,
