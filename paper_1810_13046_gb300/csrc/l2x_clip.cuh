@@ -38,22 +38,84 @@ struct ElemT {
     double T[D + 1][D];   // vertices in cell-local coordinates
 };
 
-// Sutherland-Hodgman step against an axis plane at coordinate c: keep v[k] >= c
-// (upper = false) or v[k] <= c (upper = true).  Crossing points lie on the plane
-// exactly.  Inside tests are integer comparisons; FP64 arithmetic only at crossings.
+// Sutherland-Hodgman clipping of a convex polygon against one half-space, in
+// three phases so that a warp runs the FP64 crossing arithmetic together:
+// (1) the inside flags of all vertices as a bit mask, (2) the two crossings (a
+// convex polygon cut by a plane has exactly one exit edge, inside -> outside,
+// and one entry edge), (3) the output in traversal order: every inside vertex,
+// each crossing point after the first vertex of its edge.  The crossing on
+// edge (p, q) is p + t (q - p), t = s_p / (s_p - s_q), s the signed plane
+// values.  When rounding leaves the inside vertices in more than one run the
+// edges are handled one by one (same formula, same order).
+
+// Emits the clipped polygon: inside vertices of `in`, crossing points X0 (after
+// vertex e0) and X1 (after vertex e1).
+template <int D>
+__device__ __forceinline__ int clip_emit(const double (*in)[D], int n, unsigned inside, int e0, const double* X0,
+                                         int e1, const double* X1, double (*out)[D]) {
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        if ((inside >> i) & 1u) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) out[m][j] = in[i][j];
+            ++m;
+        }
+        if (i == e0 || i == e1) {
+            const double* X = i == e0 ? X0 : X1;
+#pragma unroll
+            for (int j = 0; j < D; ++j) out[m][j] = X[j];
+            ++m;
+        }
+    }
+    return m;
+}
+
+// Exit and entry edges of a single run of inside vertices (bit i = vertex i);
+// false if the inside vertices do not form exactly one cyclic run.
+__device__ __forceinline__ bool one_run(unsigned inside, int n, int& e_exit, int& e_entry) {
+    const unsigned all = (1u << n) - 1u;
+    const unsigned next = ((inside >> 1) | (inside << (n - 1))) & all;  // bit i = inside[i+1]
+    const unsigned ex = inside & ~next, en = ~inside & next & all;
+    if (__popc(ex) != 1 || __popc(en) != 1) return false;
+    e_exit = __ffs(ex) - 1;
+    e_entry = __ffs(en) - 1;
+    return true;
+}
+
+// Against an axis plane at coordinate c: keep v[k] >= c (upper = false) or
+// v[k] <= c (upper = true).  Inside tests are integer comparisons of order keys;
+// crossing points are snapped onto the plane.
 template <int D>
 __device__ __forceinline__ int clip_axis(const double (*in)[D], int n, double (*out)[D], int k, double c,
                                          bool upper) {
-    int m = 0;
     const long long kc = order_key(c);
-    long long kp = order_key(in[0][k]);
-    const long long k0 = kp;
+    unsigned inside = 0;
+    for (int i = 0; i < n; ++i) {
+        const long long kk = order_key(in[i][k]);
+        inside |= (unsigned)(upper ? kk <= kc : kk >= kc) << i;
+    }
+    int e0, e1;
+    if (inside != 0 && inside != (1u << n) - 1u && one_run(inside, n, e0, e1)) {
+        double X[2][D];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int i = r == 0 ? e0 : e1;
+            const double* p = in[i];
+            const double* q = in[i + 1 == n ? 0 : i + 1];
+            const double sp = p[k] - c, sq = q[k] - c;
+            const double t = div_nr(sp, sp - sq);
+#pragma unroll
+            for (int j = 0; j < D; ++j) X[r][j] = fma(t, q[j] - p[j], p[j]);
+            X[r][k] = c;
+        }
+        return clip_emit<D>(in, n, inside, e0, X[0], e1, X[1], out);
+    }
+    int m = 0;
     for (int i = 0; i < n; ++i) {
         const double* p = in[i];
         const double* q = in[i + 1 == n ? 0 : i + 1];
-        const long long kq = i + 1 == n ? k0 : order_key(q[k]);
-        const bool ip = upper ? kp <= kc : kp >= kc;
-        const bool iq = upper ? kq <= kc : kq >= kc;
+        const bool ip = (inside >> i) & 1u;
+        const bool iq = (inside >> (i + 1 == n ? 0 : i + 1)) & 1u;
         if (ip) {
 #pragma unroll
             for (int j = 0; j < D; ++j) out[m][j] = p[j];
@@ -67,44 +129,56 @@ __device__ __forceinline__ int clip_axis(const double (*in)[D], int n, double (*
             out[m][k] = c;
             ++m;
         }
-        kp = kq;
     }
     return m;
 }
 
-// Sutherland-Hodgman step against the half-space g.v + c0 >= 0.
+// Against the half-space g.v + c0 >= 0.
 template <int D>
 __device__ __forceinline__ int clip_plane(const double (*in)[D], int n, double (*out)[D], const double* g,
                                           double c0) {
-    int m = 0;
-    double sp = c0, s0;
-#pragma unroll
-    for (int j = 0; j < D; ++j) sp = fma(g[j], in[0][j], sp);
-    s0 = sp;
+    double sv[kMaxPoly];
+    unsigned inside = 0;
     for (int i = 0; i < n; ++i) {
-        const double* p = in[i];
-        const double* q = in[i + 1 == n ? 0 : i + 1];
-        double sq;
-        if (i + 1 == n) {
-            sq = s0;
-        } else {
-            sq = c0;
+        double s = c0;
 #pragma unroll
-            for (int j = 0; j < D; ++j) sq = fma(g[j], q[j], sq);
+        for (int j = 0; j < D; ++j) s = fma(g[j], in[i][j], s);
+        sv[i] = s;
+        inside |= (unsigned)nonneg_d(s) << i;
+    }
+    int e0, e1;
+    if (inside != 0 && inside != (1u << n) - 1u && one_run(inside, n, e0, e1)) {
+        double X[2][D];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int i = r == 0 ? e0 : e1;
+            const int i1 = i + 1 == n ? 0 : i + 1;
+            const double* p = in[i];
+            const double* q = in[i1];
+            const double sp = sv[i], sq = sv[i1];
+            const double t = div_nr(sp, sp - sq);
+#pragma unroll
+            for (int j = 0; j < D; ++j) X[r][j] = fma(t, q[j] - p[j], p[j]);
         }
-        const bool ip = nonneg_d(sp), iq = nonneg_d(sq);
+        return clip_emit<D>(in, n, inside, e0, X[0], e1, X[1], out);
+    }
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const int i1 = i + 1 == n ? 0 : i + 1;
+        const double* p = in[i];
+        const double* q = in[i1];
+        const bool ip = (inside >> i) & 1u, iq = (inside >> i1) & 1u;
         if (ip) {
 #pragma unroll
             for (int j = 0; j < D; ++j) out[m][j] = p[j];
             ++m;
         }
         if (ip != iq) {
-            const double t = div_nr(sp, sp - sq);
+            const double t = div_nr(sv[i], sv[i] - sv[i1]);
 #pragma unroll
             for (int j = 0; j < D; ++j) out[m][j] = fma(t, q[j] - p[j], p[j]);
             ++m;
         }
-        sp = sq;
     }
     return m;
 }
