@@ -135,7 +135,9 @@ typedef struct l2x_info {
     int32_t clip_block;        /* pairs per thread block of the clip kernel (l2x_autotune) */
     int32_t pcg_rows_per_block;/* rows per thread block of the cooperative PCG (l2x_autotune) */
     int32_t multiplier;        /* L2X_MULT_STANDARD or L2X_MULT_DUAL */
-    int32_t reserved2;
+    int32_t pcg_cluster;       /* > 0: the solve runs in one thread-block cluster of this many CTAs */
+    double tuned_clip_ms;      /* l2x_autotune: time of the chosen clip launch (0 before tuning) */
+    double tuned_solve_ms;     /* l2x_autotune: time of the chosen mass-matrix solve of all components */
 } l2x_info;
 
 typedef struct l2x_coupling* l2x_handle;
@@ -272,11 +274,18 @@ l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t
 
 /* Picks work-chunk sizes for this coupling by timing candidates on it (CUDA
  * events, best of two after a warm-up run): pairs per block of the clip kernel
- * (64, 128, 256) and rows per block of the cooperative PCG (32, 64, 128).  Call
- * after a build; later builds, solves and captured steps use the choice
- * (reported in l2x_info).  Runs the clip kernel and the solve a few times on the
- * stream and synchronises it. */
+ * (64, 128, 256) and the form of the Jacobi-PCG: the grid-wide cooperative
+ * kernel with 32 to 1024 rows per block, or, when the search direction fits,
+ * one thread-block cluster of 8 or 16 CTAs holding it in distributed shared
+ * memory.  Call after a build; later builds, solves and captured steps use the
+ * choice (reported in l2x_info).  Runs the clip kernel and the solve a few times
+ * on the stream and synchronises it. */
 l2x_status l2x_autotune(l2x_handle h, void* stream);
+
+/* Sets the work shape l2x_autotune would pick: clip_block in {64, 128, 256},
+ * pcg_rows_per_block in [1, 4096] (grid-wide PCG), pcg_cluster 0 (grid-wide)
+ * or the CTAs of the single-cluster PCG (EINVAL if the system does not fit). */
+l2x_status l2x_set_work_shape(l2x_handle h, int32_t clip_block, int32_t pcg_rows_per_block, int32_t pcg_cluster);
 
 /* Enables (1, also clears the totals) or disables (0) CUDA-event timing of the
  * phases listed above, recorded on the stream of each call; l2x_query resolves

@@ -1,6 +1,7 @@
 // C-ABI entry points of l2xfer: handle management and the orchestration of the
 // assembly (steps I-IV of Sec. 2.3) and of the two transfers.
 #include <atomic>
+#include <cmath>
 #include <memory>
 #include <climits>
 #include <cstdio>
@@ -85,6 +86,8 @@ struct l2x_coupling {
     // work-chunk sizes (l2x_autotune)
     int clip_block = 128;            // threads (= pairs) per block of the clip kernel
     int pcg_rpb = 64;                // rows per block of the cooperative PCG
+    int pcg_clu = 0;                 // > 0: single-cluster PCG with this many CTAs
+    double tuned_clip_ms = 0.0, tuned_solve_ms = 0.0;
     // last solve
     int cg_iters = 0;
     double cg_residual = 0.0;
@@ -536,7 +539,7 @@ void enqueue_velocity(l2x_coupling* h, const void* const* u_f, void* const* u_s,
     for (int g = 0; g < G; ++g) tmp[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
     launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, tmp, h->st, s);
     solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)tmp, u_s,
-                         h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
+                         h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb, h->pcg_clu);
 }
 
 // Force transfer without host synchronisation (fused path): f_f += s B^T S^-1 f_s
@@ -562,7 +565,7 @@ void enqueue_force(l2x_coupling* h, const void* const* f_s_in, void* const* f_f,
             launch_diag_solve(h->opts.precision, h->n_nodes, G, h->M_dinv, f_s, tmp, h->st, s);
         else
             solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, f_s, tmp, h->opts.cg_rtol,
-                                 h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb);
+                                 h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb, h->pcg_clu);
         launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)tmp, f_f,
                        h->opts.force_scale, h->st, s);
     } else {
@@ -745,6 +748,7 @@ l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const 
             for (int32_t v : eh)
                 if (v < 0 || v >= n) return fail(L2X_EINVAL, "element references a node outside [0, n_nodes)");
         }
+        pcg_cluster_prepare();
         L2X_TRY(build_topology(h, s));
         size_t ws = pcg_ws_bytes(n, G, pcg_max_blocks());
         if (cudaMalloc(&h->pcg_ws, ws) != cudaSuccess) return fail(L2X_ENOMEM, "CG workspace");
@@ -810,7 +814,7 @@ l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s
     auto ph = std::make_unique<PhaseScope>(h, L2X_PH_PCG, s);
     l2x_status st = solve_mass_pcg(h->opts.path, h->opts.precision, h->M, h->M_dinv, h->M_dinv32, h->n_grids, y_s,
                                    w_s, h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, h->st_host, s, &r,
-                                   h->pcg_rpb);
+                                   h->pcg_rpb, h->pcg_clu);
     ph.reset();
     h->cg_iters = r.iters;
     h->cg_residual = r.residual;
@@ -1107,7 +1111,10 @@ l2x_status l2x_query(l2x_handle h, l2x_info* info) {
     info->cg_residual = h->cg_residual;
     info->clip_block = h->clip_block;
     info->pcg_rows_per_block = h->pcg_rpb;
+    info->pcg_cluster = h->pcg_clu;
     info->multiplier = h->opts.multiplier;
+    info->tuned_clip_ms = h->tuned_clip_ms;
+    info->tuned_solve_ms = h->tuned_solve_ms;
     resolve_timing(h);
     for (int p = 0; p < L2X_NPHASE; ++p) {
         info->phase_ms[p] = h->phase_ms[p];
@@ -1156,6 +1163,7 @@ l2x_status l2x_autotune(l2x_handle h, void* stream) {
             }
         }
         h->clip_block = best_blk;
+        h->tuned_clip_ms = best;
     }
     if (h->opts.multiplier == L2X_MULT_STANDARD) {
         // PCG: rows per block, on M applied to a vector of ones
@@ -1169,26 +1177,37 @@ l2x_status l2x_autotune(l2x_handle h, void* stream) {
                 y[g] = tmp + es * n * g;
                 w[g] = tmp + es * n * (G + g);
             }
-            // y = row sums of M (the mass of every node), through the diagonal scaling kernel-free path:
-            // fill y with 1/dinv (the diagonal), any positive right-hand side serves
-            std::vector<double> ones(n, 1.0);
-            std::vector<float> onesf(n, 1.0f);
+            // a fixed, non-smooth right-hand side (the iteration count then resembles a transfer's)
+            std::vector<double> rhs(n);
+            std::vector<float> rhsf(n);
+            for (int64_t i = 0; i < n; ++i) {
+                rhs[i] = 1.0 + 0.5 * std::sin(0.37 * (double)i);
+                rhsf[i] = (float)rhs[i];
+            }
             for (int g = 0; g < G; ++g)
-                cudaMemcpyAsync(y[g], es == 8 ? (const void*)ones.data() : (const void*)onesf.data(), es * n,
+                cudaMemcpyAsync(y[g], es == 8 ? (const void*)rhs.data() : (const void*)rhsf.data(), es * n,
                                 cudaMemcpyHostToDevice, s);
             float best = 1e30f;
-            int best_rpb = h->pcg_rpb;
-            for (int rpb : {32, 64, 128}) {
+            int best_rpb = h->pcg_rpb, best_clu = 0;
+            struct Shape { int rpb, clu; };
+            std::vector<Shape> shapes;
+            for (int rpb : {32, 64, 128, 256, 512, 1024}) shapes.push_back({rpb, 0});
+            for (int clu : {8, 16})
+                if (pcg_cluster_usable(h->opts.precision, n, G, clu)) shapes.push_back({h->pcg_rpb, clu});
+            for (const Shape& sh : shapes) {
                 const float ms = timed([&] {
                     solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, G, (const void* const*)y,
-                                         w, h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, rpb);
+                                         w, h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, sh.rpb, sh.clu);
                 });
                 if (ms < best) {
                     best = ms;
-                    best_rpb = rpb;
+                    best_rpb = sh.rpb;
+                    best_clu = sh.clu;
                 }
             }
             h->pcg_rpb = best_rpb;
+            h->pcg_clu = best_clu;
+            h->tuned_solve_ms = best;
             cudaStreamSynchronize(s);
             cudaFree(tmp);
         }
@@ -1198,6 +1217,18 @@ l2x_status l2x_autotune(l2x_handle h, void* stream) {
     if (status != L2X_OK) return status;
     L2X_CUDA(cudaGetLastError());
     return read_status(h, s);
+}
+
+l2x_status l2x_set_work_shape(l2x_handle h, int32_t clip_block, int32_t pcg_rows_per_block, int32_t pcg_cluster) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    if (clip_block != 64 && clip_block != 128 && clip_block != 256) return fail(L2X_EINVAL, "clip_block must be 64, 128 or 256");
+    if (pcg_rows_per_block < 1 || pcg_rows_per_block > 4096) return fail(L2X_EINVAL, "pcg_rows_per_block must be in [1, 4096]");
+    if (pcg_cluster != 0 && !pcg_cluster_usable(h->opts.precision, h->n_nodes, h->n_grids, pcg_cluster))
+        return fail(L2X_EINVAL, "the system does not fit one cluster of that size");
+    h->clip_block = clip_block;
+    h->pcg_rpb = pcg_rows_per_block;
+    h->pcg_clu = pcg_cluster;
+    return L2X_OK;
 }
 
 l2x_status l2x_set_timing(l2x_handle h, int32_t enable) {

@@ -550,6 +550,240 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
     }
 }
 
+// ------------------------------------------------------------------ PCG (one thread-block cluster)
+// The same Chronopoulos-Gear Jacobi-PCG for systems whose search direction u
+// fits in the distributed shared memory of one cluster of C CTAs (C <= 16).
+// CTA c owns rows [c*S, min(n, (c+1)*S)); its slice of u lives in its own
+// shared memory as [row][rhs], and the product w = M u reads the other slices
+// through DSMEM.  The per-iteration sums are gathered through DSMEM in a fixed
+// order (every CTA forms identical scalars) and the two barriers per iteration
+// are hardware cluster barriers, which is what makes small systems fast: the
+// grid-wide form pays two device-wide barriers and an L2 round trip for the
+// partial sums in every iteration.
+constexpr int kCluThreads = 512;
+constexpr int kCluMax = 16;
+
+template <typename TV, int NR>
+__global__ void __launch_bounds__(kCluThreads, 1) pcg_cluster_kernel(PcgArgs<TV> A, int S) {
+    cg::cluster_group cluster = cg::this_cluster();
+    constexpr int NV = 3 * NR;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    TV* su = reinterpret_cast<TV*>(dyn_smem);  // S x NR: this CTA's rows of u
+    __shared__ const TV* s_base[kCluMax];       // every CTA's slice (DSMEM addresses)
+    __shared__ double s_part[NV];               // this CTA's partial sums, read by all CTAs
+    __shared__ double s_gather[kCluMax * NV];
+    __shared__ double s_red[NV * 32];
+    __shared__ double s_tot[NV];
+    __shared__ double s_alpha[NR], s_beta[NR];
+    __shared__ int s_conv[NR], s_all;
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int64_t n = A.n;
+    const int64_t r0 = min(n, (int64_t)rank * S), r1 = min(n, r0 + S);
+    const int glane = threadIdx.x % kRowLanes;
+    const int grow = threadIdx.x / kRowLanes;
+    constexpr int kRowsPerPass = kCluThreads / kRowLanes;
+    if (threadIdx.x < C) s_base[threadIdx.x] = cluster.map_shared_rank(su, (unsigned)threadIdx.x);
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += kCluThreads) {
+        const TV di = A.dinv[i];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const TV yi = A.y[k][i];
+            A.x[k][i] = TV(0);
+            A.r[k * n + i] = yi;
+            su[(i - r0) * NR + k] = di * yi;
+        }
+    }
+    if (threadIdx.x < NR) s_conv[threadIdx.x] = 0;
+    cluster.sync();
+    // value of column j of the distributed vector held in the slices
+    auto fetch = [&](int32_t j, int k) -> TV {
+        if (j >= r0 && j < r1) return su[(j - r0) * NR + k];
+        const unsigned owner = (unsigned)j / (unsigned)S;
+        return s_base[owner][(j - (int64_t)owner * S) * NR + k];
+    };
+    double alpha = 0.0, gamma_old = 0.0, rho0 = 0.0, rho = 0.0;
+    int it = 0, it_local = 0, restarts = 0;
+    for (;;) {
+        DotAcc<TV> dg[NR], dd[NR], dr[NR];
+        for (int64_t base = r0; base < r1; base += kRowsPerPass) {
+            const int64_t i = base + grow;
+            const bool live = i < r1;
+            TV acc[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) acc[k] = TV(0);
+            if (live) {
+                const int64_t hi = A.ptr[i + 1];
+                for (int64_t q = A.ptr[i] + glane; q < hi; q += kRowLanes) {
+                    const TV v = A.val[q];
+                    const int32_t j = A.col[q];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc[k] += v * fetch(j, k);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+#pragma unroll
+                for (int o = kRowLanes / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            }
+            if (live && glane == 0) {
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const TV ri = A.r[k * n + i], ui = su[(i - r0) * NR + k];
+                    A.w[k * n + i] = acc[k];
+                    dg[k].add(ri, ui);
+                    dd[k].add(acc[k], ui);
+                    dr[k].add(ri, ri);
+                }
+            }
+        }
+        {
+            double v[NV];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                v[3 * k + 0] = dg[k].value();
+                v[3 * k + 1] = dd[k].value();
+                v[3 * k + 2] = dr[k].value();
+            }
+            block_sum_n<NV>(v, s_red, s_part);
+        }
+        cluster.sync();  // partial sums published; every read of u for this product is done
+        if (threadIdx.x < C * NV)
+            s_gather[threadIdx.x] = *cluster.map_shared_rank(&s_part[threadIdx.x % NV], (unsigned)(threadIdx.x / NV));
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double t = 0.0;
+            for (int c = 0; c < C; ++c) t += s_gather[c * NV + threadIdx.x];
+            s_tot[threadIdx.x] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < NR) {
+            const int k = threadIdx.x;
+            const double gam = s_tot[3 * k], del = s_tot[3 * k + 1];
+            rho = s_tot[3 * k + 2];
+            if (it == 0 && it_local == 0 && restarts == 0) rho0 = rho;
+            const bool conv = rho <= A.rtol * A.rtol * rho0;
+            double beta = 0.0;
+            if (!conv) {
+                if (it_local == 0) {
+                    alpha = div_nr(gam, del);
+                } else {
+                    beta = div_nr(gam, gamma_old);
+                    alpha = div_nr(gam, del - beta * div_nr(gam, alpha));
+                }
+                gamma_old = gam;
+            }
+            s_alpha[k] = alpha;
+            s_beta[k] = beta;
+            s_conv[k] = conv ? 1 : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int all = 1;
+#pragma unroll
+            for (int k = 0; k < NR; ++k) all &= s_conv[k];
+            s_all = all;
+        }
+        __syncthreads();
+        if (s_all && sizeof(TV) == 8 && restarts < 2) {
+            // FP64: true residual y - M x; the slices of x go through the u buffers
+            // (every CTA has finished its product and its gather of the sums)
+            for (int64_t i = r0 + threadIdx.x; i < r1; i += kCluThreads)
+#pragma unroll
+                for (int k = 0; k < NR; ++k) su[(i - r0) * NR + k] = A.x[k][i];
+            cluster.sync();
+            DotAcc<TV> dt[NR];
+            for (int64_t i = r0 + threadIdx.x; i < r1; i += kCluThreads) {
+                const int64_t hi = A.ptr[i + 1];
+                TV acc[NR];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) acc[k] = TV(0);
+                for (int64_t q = A.ptr[i]; q < hi; ++q) {
+                    const TV v = A.val[q];
+                    const int32_t j = A.col[q];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) acc[k] += v * fetch(j, k);
+                }
+                const TV di = A.dinv[i];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    const TV rt = A.y[k][i] - acc[k];
+                    A.r[k * n + i] = rt;
+                    A.u[k * n + i] = di * rt;  // staged: the slices still hold x
+                    dt[k].add(rt, rt);
+                }
+            }
+            {
+                double v[NV];
+#pragma unroll
+                for (int j = 0; j < NV; ++j) v[j] = 0.0;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) v[k] = dt[k].value();
+                block_sum_n<NV>(v, s_red, s_part);
+            }
+            cluster.sync();  // sums published; every read of the x slices is done
+            if (threadIdx.x < C * NR)
+                s_gather[threadIdx.x] = *cluster.map_shared_rank(&s_part[threadIdx.x % NR], (unsigned)(threadIdx.x / NR));
+            __syncthreads();
+            if (threadIdx.x < NR) {
+                double t = 0.0;
+                for (int c = 0; c < C; ++c) t += s_gather[c * NR + threadIdx.x];
+                const bool ok = t <= A.rtol * A.rtol * rho0;
+                s_conv[threadIdx.x] = ok ? 1 : 0;
+                if (!ok) rho = t;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int all = 1;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) all &= s_conv[k];
+                s_all = all;
+            }
+            for (int64_t i = r0 + threadIdx.x; i < r1; i += kCluThreads)
+#pragma unroll
+                for (int k = 0; k < NR; ++k) su[(i - r0) * NR + k] = A.u[k * n + i];
+            __syncthreads();
+            if (s_all) break;
+            ++restarts;
+            it_local = 0;
+            cluster.sync();  // new u slices visible before the next product
+            continue;
+        }
+        if (s_all || it >= A.max_iter) break;
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += kCluThreads) {
+            const TV di = A.dinv[i];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                if (s_conv[k]) continue;
+                const int64_t o = k * n + i;
+                const TV b = (TV)s_beta[k], a = (TV)s_alpha[k];
+                const TV ui = su[(i - r0) * NR + k];
+                const TV pn = it_local == 0 ? ui : ui + b * A.p[o];
+                const TV sn = it_local == 0 ? A.w[o] : A.w[o] + b * A.s[o];
+                A.p[o] = pn;
+                A.s[o] = sn;
+                A.x[k][i] += a * pn;
+                const TV rn = A.r[o] - a * sn;
+                A.r[o] = rn;
+                su[(i - r0) * NR + k] = di * rn;
+            }
+        }
+        cluster.sync();  // new u slices visible before the next product
+        ++it;
+        ++it_local;
+    }
+    if (rank == 0) {
+        double rel = threadIdx.x < NR && rho0 > 0.0 ? sqrt(rho / rho0) : 0.0;
+        for (int o = 16; o > 0; o >>= 1) rel = fmax(rel, __shfl_xor_sync(0xffffffffu, rel, o));
+        if (threadIdx.x == 0) {
+            A.st->cg_iters = it;
+            A.st->cg_residual = rel;
+            if (!s_all) atomicOr(&A.st->flags, FLAG_NOTCONVERGED);
+        }
+    }
+    cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 // ------------------------------------------------------------------ PCG (plain, unfused, FP64)
 __global__ void plain_init_kernel(int64_t n, int nr, const double* y0, const double* y1, const double* y2,
                                   double* x0, double* x1, double* x2, const double* dinv, double* r, double* z,
@@ -701,10 +935,48 @@ int pcg_blocks_for(int64_t n, int rows_per_block_req) {
     return b < 1 ? 1 : (int)b;
 }
 
+// Dynamic shared memory of the cluster PCG: one CTA's rows of u (S x NR values).
+constexpr size_t kCluSmemMax = 220 * 1024;
+
+template <typename TV, int NR>
+bool cluster_fits(int64_t n, int C, int& S, size_t& smem) {
+    if (C < 2 || C > kCluMax || n <= 0) return false;
+    const int64_t s_rows = (n + C - 1) / C;
+    smem = (size_t)s_rows * NR * sizeof(TV);
+    S = (int)s_rows;
+    return smem <= kCluSmemMax;
+}
+
+template <typename TV, int NR>
+cudaError_t launch_pcg_cluster(const PcgArgs<TV>& A, int C, cudaStream_t s) {
+    int S = 0;
+    size_t smem = 0;
+    if (!cluster_fits<TV, NR>(A.n, C, S, smem)) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kCluThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pcg_cluster_kernel<TV, NR>, A, S);
+}
+
+template <typename TV, int NR>
+void prepare_cluster_kernel() {
+    cudaFuncSetAttribute(pcg_cluster_kernel<TV, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCluSmemMax);
+    cudaFuncSetAttribute(pcg_cluster_kernel<TV, NR>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
 template <typename TV>
 cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val, const TV* dinv, int64_t n,
                           int nr, const TV* const* y, TV* const* x, TV* vecs, double* partial, double rtol,
-                          int max_iter, DevStatus* st, cudaStream_t s, int rpb = 64) {
+                          int max_iter, DevStatus* st, cudaStream_t s, int rpb = 64, int clu = 0) {
     PcgArgs<TV> A{};
     A.n = n;
     A.nrhs = nr;
@@ -728,6 +1000,19 @@ cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val,
     A.st = st;
     void* args[] = {&A};
     count_launch();
+    if (clu > 0) {
+        int S = 0;
+        size_t smem = 0;
+        const bool fits = nr == 1 ? cluster_fits<TV, 1>(n, clu, S, smem)
+                                  : nr == 2 ? cluster_fits<TV, 2>(n, clu, S, smem) : cluster_fits<TV, 3>(n, clu, S, smem);
+        if (fits) {
+            switch (nr) {
+                case 1: return launch_pcg_cluster<TV, 1>(A, clu, s);
+                case 2: return launch_pcg_cluster<TV, 2>(A, clu, s);
+                default: return launch_pcg_cluster<TV, 3>(A, clu, s);
+            }
+        }
+    }
     switch (nr) {
         case 1:
             return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 1>, dim3(pcg_blocks_for<TV, 1>(n, rpb)),
@@ -742,6 +1027,46 @@ cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val,
 }
 
 }  // namespace
+
+void pcg_cluster_prepare() {
+    static bool done = false;
+    if (done) return;
+    prepare_cluster_kernel<double, 1>(); prepare_cluster_kernel<double, 2>(); prepare_cluster_kernel<double, 3>();
+    prepare_cluster_kernel<float, 1>(); prepare_cluster_kernel<float, 2>(); prepare_cluster_kernel<float, 3>();
+    done = true;
+}
+
+bool pcg_cluster_usable(int precision, int64_t n, int nr, int C) {
+    int S = 0;
+    size_t smem = 0;
+    bool fits;
+    if (precision == L2X_MIXED)
+        fits = nr == 1 ? cluster_fits<float, 1>(n, C, S, smem) : nr == 2 ? cluster_fits<float, 2>(n, C, S, smem) : cluster_fits<float, 3>(n, C, S, smem);
+    else
+        fits = nr == 1 ? cluster_fits<double, 1>(n, C, S, smem) : nr == 2 ? cluster_fits<double, 2>(n, C, S, smem) : cluster_fits<double, 3>(n, C, S, smem);
+    if (!fits) return false;
+    // the FP64 form of the solve needs both instantiations (the mixed form runs FP32 solves only)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kCluThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cudaError_t e = precision == L2X_MIXED
+                        ? cudaOccupancyMaxActiveClusters(&clusters, pcg_cluster_kernel<float, 3>, &cfg)
+                        : cudaOccupancyMaxActiveClusters(&clusters, pcg_cluster_kernel<double, 3>, &cfg);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters > 0;
+}
 
 int pcg_max_blocks() {
     int dev = 0;
@@ -858,7 +1183,7 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
 
 void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, const float* diag_inv32, int nr,
                           const void* const* y, void* const* w, double rtol, int max_iter, void* ws, DevStatus* st,
-                          cudaStream_t s, int rpb) {
+                          cudaStream_t s, int rpb, int clu) {
     const int64_t n = M.n_rows;
     if (n <= 0 || nr <= 0) return;
     const int64_t v = n * nr;
@@ -872,7 +1197,7 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
     if (precision == L2X_FP64) {
         double* vecs = (double*)take(5 * v * 8);
         run_pcg_fused<double>(M.ptr, M.col, M.val, diag_inv, n, nr, (const double* const*)y, (double* const*)w, vecs,
-                              partial, rtol, max_iter, st, s, rpb);
+                              partial, rtol, max_iter, st, s, rpb, clu);
         return;
     }
     float* vecs = (float*)take(5 * v * 4);
@@ -894,7 +1219,7 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
             rhs[k] = ref == 0 ? yf[k] : r32 + k * n;
             dst[k] = d32 + k * n;
         }
-        run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s, rpb);
+        run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s, rpb, clu);
         { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr, nr > 2 ? dst[2] : nullptr, ref == 0); count_launch(); }
         if (ref == 0) {
             cudaMemsetAsync(norms, 0, 4 * 8, s);
@@ -906,7 +1231,7 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
 
 l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv, const float* diag_inv32,
                           int nr, const void* const* y, void* const* w, double rtol, int max_iter, void* ws,
-                          DevStatus* st, DevStatus* st_host, cudaStream_t s, PcgResult* res, int rpb) {
+                          DevStatus* st, DevStatus* st_host, cudaStream_t s, PcgResult* res, int rpb, int clu) {
     const int64_t n = M.n_rows;
     res->iters = 0;
     res->residual = 0.0;
@@ -974,7 +1299,7 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
         double* vecs = (double*)take(5 * v * 8);
         cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s);
         ce = run_pcg_fused<double>(M.ptr, M.col, M.val, diag_inv, n, nr, (const double* const*)y, (double* const*)w,
-                                   vecs, partial, rtol, max_iter, st, s, rpb);
+                                   vecs, partial, rtol, max_iter, st, s, rpb, clu);
         if (ce != cudaSuccess) return L2X_ECUDA;
         if (cudaMemcpyAsync(st_host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return L2X_ECUDA;
@@ -1011,7 +1336,7 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
         }
         cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s);
         ce = run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner,
-                                  max_iter, st, s, rpb);
+                                  max_iter, st, s, rpb, clu);
         if (ce != cudaSuccess) return L2X_ECUDA;
         { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr,
                                                  nr > 2 ? dst[2] : nullptr, ref == 0); count_launch(); }

@@ -200,12 +200,18 @@ struct PcgResult {
 // refinement.  Convergence is reported through the device status word.
 void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, const float* diag_inv32, int n_rhs,
                           const void* const* y, void* const* w, double rtol, int max_iter, void* ws, DevStatus* st,
-                          cudaStream_t s, int rows_per_block = 64);
+                          cudaStream_t s, int rows_per_block = 64, int cluster = 0);
 l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv,
                           const float* diag_inv32, int n_rhs, const void* const* y, void* const* w,
                           double rtol, int max_iter, void* ws, DevStatus* st, DevStatus* st_host,
-                          cudaStream_t s, PcgResult* res, int rows_per_block = 64);
+                          cudaStream_t s, PcgResult* res, int rows_per_block = 64, int cluster = 0);
 size_t pcg_ws_bytes(int64_t n, int n_rhs, int max_blocks);
 int pcg_max_blocks();
+// Single-cluster PCG (cluster > 0 in the solves above: one cluster of that many
+// CTAs holds the search direction in distributed shared memory).  prepare sets
+// the kernel attributes once (call outside stream capture); usable tells
+// whether a system of n rows and nr right-hand sides fits and can launch.
+void pcg_cluster_prepare();
+bool pcg_cluster_usable(int precision, int64_t n, int nr, int cluster);
 
 }  // namespace l2x

@@ -290,7 +290,8 @@ def test_autotune_keeps_results():
     before = torch.stack(c.transfer_velocity(u)).cpu().numpy()
     b0 = c.export_pair_blocks(0)[0].clone()
     choice = c.autotune()
-    assert choice["clip_block"] in (64, 128, 256) and choice["pcg_rows_per_block"] in (32, 64, 128)
+    assert choice["clip_block"] in (64, 128, 256) and choice["pcg_rows_per_block"] in (32, 64, 128, 256, 512, 1024)
+    assert choice["pcg_cluster"] in (0, 8, 16)
     c.update_geometry(torch.from_numpy(w.coords).cuda())
     assert torch.equal(c.export_pair_blocks(0)[0], b0)
     after = torch.stack(c.transfer_velocity(u)).cpu().numpy()
