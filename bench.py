@@ -421,6 +421,7 @@ def main():
     # with compensated dots and FP64 refinement
     with ClockSampler(local) as clocks:
         gr = arm.graph(l2x.MIXED, args.steps, args.warmup)
+    tuned = dict(arm.tuned)  # the chosen form's work shape
     step_ms, total_pairs, value = aggregate(gr["step_ms"], gr["pairs"], world)
 
     # per-call form of the same precision, with per-phase timing (roofline of the clip kernel)
@@ -437,7 +438,6 @@ def main():
                       "mixed precision, standard multipliers"}
     plain = arm.per_call(l2x.PLAIN, l2x.FP64, args.plain_steps, 2)
     f64 = arm.per_call(l2x.FUSED, l2x.FP64, args.plain_steps, 2)
-    tuned = getattr(arm, "tuned", None)
 
     # the dual multiplier basis (pseudo L2 projection, S diagonal: no CG), same step
     n_dual = max(3, args.steps // 4)
