@@ -70,11 +70,11 @@ def _load():
         build()
         lib = ctypes.CDLL(_LIB_PATH)
         P = ctypes.c_void_p
-        lib.orc_count_pairs.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int64, P, P, P, P]
+        lib.orc_count_pairs.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int64, P, P, P, P]
         lib.orc_count_pairs.restype = ctypes.c_int
-        lib.orc_emit_pairs.argtypes = [ctypes.c_int, P, P, P, ctypes.c_int64, P, P, P, P, P]
+        lib.orc_emit_pairs.argtypes = [ctypes.c_int, P, P, P, P, ctypes.c_int64, P, P, P, P, P]
         lib.orc_emit_pairs.restype = None
-        lib.orc_pair_blocks.argtypes = [ctypes.c_int, P, P, P, P, P, ctypes.c_int64, P, P, P, P,
+        lib.orc_pair_blocks.argtypes = [ctypes.c_int, P, P, P, P, P, P, ctypes.c_int64, P, P, P, P,
                                         ctypes.c_int]
         lib.orc_pair_blocks.restype = ctypes.c_int
         _lib = lib
@@ -89,11 +89,13 @@ def _ptr(a: np.ndarray):
 
 @dataclass
 class SubGrid:
-    """One Q1 grid: ``ncell`` cells of width ``h`` from ``origin``."""
+    """One Q1 grid: ``ncell`` cells of width ``h`` from ``origin`` or, on a
+    stretched grid, cells between the node coordinates ``axis[k]``."""
     dim: int
     ncell: np.ndarray   # int64[3]
     origin: np.ndarray  # float64[3]
     h: np.ndarray       # float64[3]
+    axis: list | None = None  # stretched: per axis the ncell[k] + 1 node coordinates
 
     @property
     def nnode(self):
@@ -103,26 +105,53 @@ class SubGrid:
     def n_nodes(self) -> int:
         return int(np.prod(self.nnode))
 
+    def cell_frame(self, k: int, i: int):
+        """(lower corner, width) of cell i along axis k."""
+        if self.axis is not None:
+            return float(self.axis[k][i]), float(self.axis[k][i + 1] - self.axis[k][i])
+        return float(self.origin[k] + i * self.h[k]), float(self.h[k])
+
+    def _axis_ptrs(self):
+        if self.axis is None:
+            return None, None
+        keep = [np.ascontiguousarray(a, dtype=np.float64) for a in self.axis]
+        arr = (ctypes.c_void_p * 3)()
+        for k, a in enumerate(keep):
+            arr[k] = a.ctypes.data
+        keep.append(arr)
+        return ctypes.cast(arr, ctypes.c_void_p), keep
+
 
 def subgrid(grid, g: int) -> SubGrid:
-    """Velocity grid g of a base grid (attributes dim, ncell, h, origin, staggered).
+    """Velocity grid g of a base grid (attributes dim, ncell, h, origin, staggered,
+    and ``axis`` for a stretched grid).
 
     Staggered: along axis g the nodes are the base grid nodes, along the other
-    axes they are the base cell centres, so those axes have one cell fewer.
+    axes they are the base cell centres (midpoints of consecutive base nodes on a
+    stretched grid), so those axes have one cell fewer.
     """
     d = grid.dim
     nc = np.ones(3, dtype=np.int64)
     o = np.zeros(3)
     h = np.ones(3)
+    base_axis = getattr(grid, "axis", None)
+    axis = [] if base_axis is not None else None
     for k in range(d):
         h[k] = grid.h[k]
-        if grid.staggered and k != g:
+        shifted = grid.staggered and k != g
+        if shifted:
             nc[k] = grid.ncell[k] - 1
             o[k] = grid.origin[k] + 0.5 * grid.h[k]
         else:
             nc[k] = grid.ncell[k]
             o[k] = grid.origin[k]
-    return SubGrid(d, nc, o, h)
+        if axis is not None:
+            x = np.asarray(base_axis[k], dtype=np.float64)
+            if x.shape != (grid.ncell[k] + 1,) or not np.all(np.diff(x) > 0):
+                raise OracleError("a stretched axis needs ncell+1 strictly increasing node coordinates")
+            axis.append(0.5 * (x[:-1] + x[1:]) if shifted else x.copy())
+            o[k] = axis[k][0]
+    return SubGrid(d, nc, o, h, axis)
 
 
 def n_grids(grid) -> int:
@@ -140,7 +169,8 @@ def candidate_pairs(sg: SubGrid, X: np.ndarray, E: np.ndarray):
     m = E.shape[0]
     counts = np.zeros(m, dtype=np.int64)
     bad = np.zeros(1, dtype=np.int64)
-    st = lib.orc_count_pairs(d, _ptr(sg.ncell), _ptr(sg.origin), _ptr(sg.h), m, _ptr(X), _ptr(E),
+    ax, keep = sg._axis_ptrs()
+    st = lib.orc_count_pairs(d, _ptr(sg.ncell), _ptr(sg.origin), _ptr(sg.h), ax, m, _ptr(X), _ptr(E),
                              _ptr(counts), _ptr(bad))
     if st == EOUTOFGRID:
         raise OracleError(f"element {int(bad[0])} leaves the grid")
@@ -149,7 +179,7 @@ def candidate_pairs(sg: SubGrid, X: np.ndarray, E: np.ndarray):
     n = int(offsets[-1])
     pe = np.zeros(n, dtype=np.int32)
     pc = np.zeros(n, dtype=np.int64)
-    lib.orc_emit_pairs(d, _ptr(sg.ncell), _ptr(sg.origin), _ptr(sg.h), m, _ptr(X), _ptr(E),
+    lib.orc_emit_pairs(d, _ptr(sg.ncell), _ptr(sg.origin), _ptr(sg.h), ax, m, _ptr(X), _ptr(E),
                        _ptr(offsets), _ptr(pe), _ptr(pc))
     return pe, pc
 
@@ -167,7 +197,8 @@ def pair_blocks(sg: SubGrid, X, E, pe, pc, nthreads: int = 1):
     n = pe.shape[0]
     blocks = np.zeros((n, d + 1, 1 << d))
     vols = np.zeros(n)
-    st = lib.orc_pair_blocks(d, _ptr(sg.ncell), _ptr(sg.origin), _ptr(sg.h), _ptr(X), _ptr(E), n,
+    ax, keep = sg._axis_ptrs()
+    st = lib.orc_pair_blocks(d, _ptr(sg.ncell), _ptr(sg.origin), _ptr(sg.h), ax, _ptr(X), _ptr(E), n,
                              _ptr(pe), _ptr(pc), _ptr(blocks), _ptr(vols), int(nthreads))
     if st == EDEGENERATE:
         raise OracleError("degenerate element")

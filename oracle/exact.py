@@ -133,16 +133,19 @@ def _order_ccw(points, centre, normal=None):
     return sorted(points, key=functools.cmp_to_key(cmp))
 
 
-def pair_block_exact(dim, verts, cell_lo, h, dual=False):
+def pair_block_exact(dim, verts, cell_lo, h, dual=False, cell_hi=None):
     """Exact block int_{E cap C} lambda_a psi_b and vol(E cap C).
 
     ``verts``: element vertex coordinates (floats), ``cell_lo``: the cell's lower
     corner (floats), ``h``: cell widths (floats).  Returns (block, vol) with
     block[a][b] Fractions, b = corner bits (x bit 0).  With ``dual`` the weight
     lambda_a is replaced by the element dual function (dim+2) lambda_a - 1
-    (Eq. (biorth)), integrated as it stands."""
+    (Eq. (biorth)), integrated as it stands.  ``cell_hi`` (floats) gives the
+    upper corner instead of ``h``: the widths are then the exact differences
+    (a cell of a stretched grid)."""
     V = [[Fr(verts[i][k]) - Fr(cell_lo[k]) for k in range(dim)] for i in range(dim + 1)]
-    H = [Fr(h[k]) for k in range(dim)]
+    H = ([Fr(h[k]) for k in range(dim)] if cell_hi is None
+         else [Fr(cell_hi[k]) - Fr(cell_lo[k]) for k in range(dim)])
     # barycentric coordinates: lambda(x) = L @ (x, 1)
     A = [[V[j][r] for j in range(dim + 1)] for r in range(dim)] + [[Fr(1)] * (dim + 1)]
     L = []

@@ -54,19 +54,49 @@ static void elem_bbox(int dim, const double* X, const int32_t* E, int64_t e, dou
     }
 }
 
+/* Number of entries of the increasing array x[0..n) that are <= v (upper) or
+ * < v (lower): plain binary search, comparisons only. */
+static int64_t count_le(const double* x, int64_t n, double v) {
+    int64_t l = 0, r = n;
+    while (l < r) {
+        int64_t m = (l + r) / 2;
+        if (x[m] <= v) l = m + 1; else r = m;
+    }
+    return l;
+}
+static int64_t count_lt(const double* x, int64_t n, double v) {
+    int64_t l = 0, r = n;
+    while (l < r) {
+        int64_t m = (l + r) / 2;
+        if (x[m] < v) l = m + 1; else r = m;
+    }
+    return l;
+}
+
 /* Cell index range of element e along every axis; returns ORC_EOUTOFGRID if
- * the range leaves the grid. */
+ * the range leaves the grid.  Cells are half-open [x_i, x_{i+1}): the lowest
+ * cell holds the lowest bbox coordinate, the highest cell is the last one that
+ * starts below the highest coordinate.  Uniform axes (axis == NULL or
+ * axis[k] == NULL): x_i = origin + i h, evaluated as one rounded subtraction and
+ * one correctly rounded division; stretched axes: the ncell+1 node coordinates
+ * axis[k], searched by comparisons. */
 int orc_cell_range(int dim, const int64_t* ncell, const double* origin, const double* h,
-                   const double* X, const int32_t* E, int64_t e, int64_t* ilo, int64_t* ihi) {
+                   const double* const* axis, const double* X, const int32_t* E, int64_t e,
+                   int64_t* ilo, int64_t* ihi) {
     double lo[3], hi[3];
     elem_bbox(dim, X, E, e, lo, hi);
     for (int k = 0; k < dim; ++k) {
-        volatile double dlo = lo[k] - origin[k];
-        volatile double dhi = hi[k] - origin[k];
-        volatile double qlo = dlo / h[k];
-        volatile double qhi = dhi / h[k];
-        ilo[k] = (int64_t)floor(qlo);
-        ihi[k] = (int64_t)ceil(qhi) - 1;
+        if (axis && axis[k]) {
+            ilo[k] = count_le(axis[k], ncell[k] + 1, lo[k]) - 1;
+            ihi[k] = count_lt(axis[k], ncell[k] + 1, hi[k]) - 1;
+        } else {
+            volatile double dlo = lo[k] - origin[k];
+            volatile double dhi = hi[k] - origin[k];
+            volatile double qlo = dlo / h[k];
+            volatile double qhi = dhi / h[k];
+            ilo[k] = (int64_t)floor(qlo);
+            ihi[k] = (int64_t)ceil(qhi) - 1;
+        }
         if (ihi[k] < ilo[k]) ihi[k] = ilo[k];  /* zero extent along k */
         if (ilo[k] < 0 || ihi[k] >= ncell[k]) return ORC_EOUTOFGRID;
     }
@@ -76,11 +106,11 @@ int orc_cell_range(int dim, const int64_t* ncell, const double* origin, const do
 /* counts[e] = number of candidate cells of element e.  Returns 0 or a status;
  * *bad_elem receives the first element that left the grid. */
 int orc_count_pairs(int dim, const int64_t* ncell, const double* origin, const double* h,
-                    int64_t n_elems, const double* X, const int32_t* E, int64_t* counts,
-                    int64_t* bad_elem) {
+                    const double* const* axis, int64_t n_elems, const double* X, const int32_t* E,
+                    int64_t* counts, int64_t* bad_elem) {
     for (int64_t e = 0; e < n_elems; ++e) {
         int64_t ilo[3], ihi[3];
-        if (orc_cell_range(dim, ncell, origin, h, X, E, e, ilo, ihi) != ORC_OK) {
+        if (orc_cell_range(dim, ncell, origin, h, axis, X, E, e, ilo, ihi) != ORC_OK) {
             *bad_elem = e;
             return ORC_EOUTOFGRID;
         }
@@ -93,11 +123,11 @@ int orc_count_pairs(int dim, const int64_t* ncell, const double* origin, const d
 
 /* Writes the pair list; offsets[e] = first pair of element e. */
 void orc_emit_pairs(int dim, const int64_t* ncell, const double* origin, const double* h,
-                    int64_t n_elems, const double* X, const int32_t* E, const int64_t* offsets,
-                    int32_t* pair_elem, int64_t* pair_cell) {
+                    const double* const* axis, int64_t n_elems, const double* X, const int32_t* E,
+                    const int64_t* offsets, int32_t* pair_elem, int64_t* pair_cell) {
     for (int64_t e = 0; e < n_elems; ++e) {
         int64_t ilo[3] = {0, 0, 0}, ihi[3] = {0, 0, 0};
-        orc_cell_range(dim, ncell, origin, h, X, E, e, ilo, ihi);
+        orc_cell_range(dim, ncell, origin, h, axis, X, E, e, ilo, ihi);
         int64_t p = offsets[e];
         int64_t z0 = dim == 3 ? ilo[2] : 0, z1 = dim == 3 ? ihi[2] : 0;
         for (int64_t iz = z0; iz <= z1; ++iz)
@@ -319,9 +349,9 @@ static void integrate_simplex(int dim, const simplex* S, double Minv[4][4], cons
  * Everything is done in coordinates relative to the cell's lower corner, so that
  * the cell is [0, h_0] x [0, h_1] (x [0, h_2]) and no digits are lost to the
  * absolute position of the pair. */
-static int pair_block(int dim, const int64_t* ncell, const double* origin, const double* h,
-                      const double* X, const int32_t* E, int64_t e, int64_t cell, double* block,
-                      double* vol, slist* L0, slist* L1) {
+static int pair_block(int dim, const int64_t* ncell, const double* origin, const double* h_uniform,
+                      const double* const* axis, const double* X, const int32_t* E, int64_t e,
+                      int64_t cell, double* block, double* vol, slist* L0, slist* L1) {
     int na = dim + 1, nb = 1 << dim;
     for (int i = 0; i < na * nb; ++i) block[i] = 0.0;
     *vol = 0.0;
@@ -329,8 +359,17 @@ static int pair_block(int dim, const int64_t* ncell, const double* origin, const
     ci[0] = cell % ncell[0];
     ci[1] = (cell / ncell[0]) % ncell[1];
     if (dim == 3) ci[2] = cell / (ncell[0] * ncell[1]);
-    double clo[3], zero[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < dim; ++k) clo[k] = origin[k] + (double)ci[k] * h[k];
+    /* the cell is [clo, clo + h] per axis: uniform, or between two stretched nodes */
+    double clo[3], h[3], zero[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < dim; ++k) {
+        if (axis && axis[k]) {
+            clo[k] = axis[k][ci[k]];
+            h[k] = axis[k][ci[k] + 1] - axis[k][ci[k]];
+        } else {
+            clo[k] = origin[k] + (double)ci[k] * h_uniform[k];
+            h[k] = h_uniform[k];
+        }
+    }
     simplex S;
     memset(&S, 0, sizeof(S));
     for (int v = 0; v < na; ++v) {
@@ -358,8 +397,9 @@ static int pair_block(int dim, const int64_t* ncell, const double* origin, const
 
 /* Blocks of all pairs: blocks[p * (d+1) * 2^d + a * 2^d + b], vols[p]. */
 int orc_pair_blocks(int dim, const int64_t* ncell, const double* origin, const double* h,
-                    const double* X, const int32_t* E, int64_t n_pairs, const int32_t* pair_elem,
-                    const int64_t* pair_cell, double* blocks, double* vols, int nthreads) {
+                    const double* const* axis, const double* X, const int32_t* E, int64_t n_pairs,
+                    const int32_t* pair_elem, const int64_t* pair_cell, double* blocks, double* vols,
+                    int nthreads) {
     int nbl = (dim + 1) << dim;
     int status = ORC_OK;
 #ifdef _OPENMP
@@ -371,7 +411,7 @@ int orc_pair_blocks(int dim, const int64_t* ncell, const double* origin, const d
 #pragma omp for schedule(dynamic, 256)
 #endif
         for (int64_t p = 0; p < n_pairs; ++p) {
-            int st = pair_block(dim, ncell, origin, h, X, E, pair_elem[p], pair_cell[p],
+            int st = pair_block(dim, ncell, origin, h, axis, X, E, pair_elem[p], pair_cell[p],
                                 blocks + p * nbl, vols + p, &L0, &L1);
             if (st) {
 #ifdef _OPENMP

@@ -10,4 +10,5 @@ from .meshes import (  # noqa: F401
     Grid, disk_mesh, beam_mesh, leaflet_mesh, deformed_beam_mesh, random_rotation,
     place_body, grid_node_coords, taylor_green, sin_cos_2d, workload, batch_bodies,
     body_motion, combine_bodies, batch_workload, batch_coords, block_face_mask, BEAM_HEXES,
+    stretched_axis, stretched_grid,
 )

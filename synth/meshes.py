@@ -28,6 +28,9 @@ class Grid:
     h: tuple
     origin: tuple
     staggered: bool
+    # stretched (rectilinear) grids: per axis the ncell[k] + 1 base-node
+    # coordinates, strictly increasing; None = uniform (origin + i * h)
+    axis: tuple | None = None
 
     @property
     def n_grids(self) -> int:
@@ -51,12 +54,43 @@ class Grid:
     def n_fluid_nodes(self, g: int) -> int:
         return int(np.prod(self.sub_nnode(g)))
 
+    def base_axis(self, k: int) -> np.ndarray:
+        """Base-grid node coordinates along axis k."""
+        if self.axis is not None:
+            return np.asarray(self.axis[k], dtype=np.float64)
+        return self.origin[k] + np.arange(self.ncell[k] + 1, dtype=np.float64) * self.h[k]
+
+    def sub_axis(self, g: int, k: int) -> np.ndarray:
+        """Node coordinates of velocity grid g along axis k: the base nodes along
+        axis g (and on a non-staggered grid), the base cell centres otherwise."""
+        if self.axis is None:
+            return self.sub_origin(g)[k] + np.arange(self.sub_nnode(g)[k], dtype=np.float64) * self.h[k]
+        x = self.base_axis(k)
+        if not self.staggered or k == g:
+            return x
+        return 0.5 * (x[:-1] + x[1:])
+
+
+def stretched_axis(n: int, lo: float = 0.0, hi: float = 1.0, amp: float = 0.5) -> np.ndarray:
+    """n + 1 nodes on [lo, hi] from x = xi + amp sin(2 pi xi) / (2 pi), xi uniform:
+    strictly increasing for amp < 1, spacing (1 - amp)/n at the centre and
+    (1 + amp)/n at the ends (points concentrated around the middle, where the
+    bodies sit)."""
+    xi = np.arange(n + 1, dtype=np.float64) / n
+    x = xi + amp * np.sin(2.0 * np.pi * xi) / (2.0 * np.pi)
+    x[0], x[-1] = 0.0, 1.0
+    return lo + (hi - lo) * x
+
+
+def stretched_grid(dim: int, n: int, amp: float = 0.5, staggered: bool = True) -> "Grid":
+    """Stretched grid on [0,1]^dim with n cells per axis (same stretching on every axis)."""
+    ax = tuple(stretched_axis(n, 0.0, 1.0, amp) for _ in range(dim))
+    return Grid(dim, (n,) * dim, (1.0 / n,) * dim, (0.0,) * dim, staggered, ax)
+
 
 def grid_node_coords(grid: Grid, g: int) -> np.ndarray:
     """Coordinates (n_nodes, dim) of the nodes of velocity grid ``g``, x fastest."""
-    nn = grid.sub_nnode(g)
-    o = grid.sub_origin(g)
-    axes = [o[k] + np.arange(nn[k], dtype=np.float64) * grid.h[k] for k in range(grid.dim)]
+    axes = [grid.sub_axis(g, k) for k in range(grid.dim)]
     mesh = np.meshgrid(*axes, indexing="ij")
     # ravel in Fortran order so that axis 0 runs fastest
     return np.stack([m.ravel(order="F") for m in mesh], axis=1)
@@ -272,19 +306,25 @@ def workload(name: str, seed: int = 0, field_dtype=np.float64) -> Workload:
     * ``beam512``      : 512x512x256 staggered grids on [0,1]^2x[0,0.5], 4.0M-tet deformed beam.
     * ``beam16`` / ``beam32``: small rotated beams for tests (16^3 / 32^3 grids).
     * ``disk2d_small`` : 16x16 grid, 2-ring disk.
+    * ``disk2d_s``, ``beam16s``, ``beam32s``, ``beam64s``: the same bodies on stretched
+      grids (``stretched_axis`` with amp 0.5: cells at the centre half as wide as a
+      uniform grid's of the same count; beam64s has beam128's resolution at the body).
     """
     rng = np.random.default_rng(seed)
-    if name in ("disk2d", "disk2d_small"):
-        n, K = (64, 9) if name == "disk2d" else (16, 3)
-        grid = Grid(2, (n, n), (1.0 / n, 1.0 / n), (0.0, 0.0), False)
+    if name in ("disk2d", "disk2d_small", "disk2d_s"):
+        n, K = (16, 3) if name == "disk2d_small" else (64, 9)
+        grid = (stretched_grid(2, n, 0.5, staggered=False) if name == "disk2d_s"
+                else Grid(2, (n, n), (1.0 / n, 1.0 / n), (0.0, 0.0), False))
         X, E = disk_mesh(K, 0.2, (0.5, 0.5), 0.1, seed)
         wl = Workload(name, grid, X, E, _fields_for(grid, "sincos", field_dtype))
         wl.force = rng.standard_normal((X.shape[0], 1))
         return wl
-    if name in ("beam128", "beam16", "beam32", "beam64"):
-        n = {"beam128": 128, "beam64": 64, "beam32": 32, "beam16": 16}[name]
-        hexes = BEAM_HEXES[name]
-        grid = Grid(3, (n, n, n), (1.0 / n,) * 3, (0.0, 0.0, 0.0), True)
+    if name in ("beam128", "beam16", "beam32", "beam64", "beam16s", "beam32s", "beam64s"):
+        base = name.rstrip("s")
+        n = {"beam128": 128, "beam64": 64, "beam32": 32, "beam16": 16}[base]
+        hexes = BEAM_HEXES[base] if name != "beam64s" else BEAM_HEXES["beam128"]
+        grid = (stretched_grid(3, n, 0.5) if name.endswith("s")
+                else Grid(3, (n, n, n), (1.0 / n,) * 3, (0.0, 0.0, 0.0), True))
         X, E = beam_mesh(*hexes)
         X = place_body(X, random_rotation(rng), (0.5, 0.5, 0.5))
         wl = Workload(name, grid, X, E, _fields_for(grid, "tg", field_dtype))

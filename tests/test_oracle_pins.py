@@ -525,3 +525,119 @@ def test_masked_force_transfer_conserves_force_and_moment(multiplier):
     ft2 = C.transfer_force(R2, mode="dual", scale=s, mask=mask)
     for g in range(3):
         assert np.array_equal(ft2[g], ft[g])
+
+
+# --------------------------------------------------------------- stretched (rectilinear) grids
+
+def _cell_box(sg, c):
+    d = sg.dim
+    ci = [c % sg.ncell[0], (c // sg.ncell[0]) % sg.ncell[1]]
+    if d == 3:
+        ci.append(c // (sg.ncell[0] * sg.ncell[1]))
+    lo = [float(sg.axis[k][ci[k]]) for k in range(d)]
+    hi = [float(sg.axis[k][ci[k] + 1]) for k in range(d)]
+    return lo, hi
+
+
+@pytest.mark.parametrize("name,stride", [("disk2d_s", 7), ("beam16s", 17)])
+def test_stretched_pair_blocks_match_exact_rational(name, stride):
+    """On a stretched grid every cell has its own widths; the blocks agree with
+    exact rational integration over the exact cell [x_i, x_{i+1}] to 1e-14 |E|."""
+    w = synth.workload(name)
+    d = w.dim
+    vol_e = oracle.element_volumes(w.coords, w.elems)
+    for g in range(oracle.n_grids(w.grid)):
+        sg = oracle.subgrid(w.grid, g)
+        assert sg.axis is not None
+        pe, pc = oracle.candidate_pairs(sg, w.coords, w.elems)
+        blocks, vols = oracle.pair_blocks(sg, w.coords, w.elems, pe, pc)
+        for p in range(g, len(pe), stride):
+            e, c = int(pe[p]), int(pc[p])
+            lo, hi = _cell_box(sg, c)
+            blk, vol = exact.pair_block_exact(d, w.coords[w.elems[e]], lo, None, cell_hi=hi)
+            ex = np.array([[float(x) for x in row] for row in blk])
+            assert abs(float(vol) - vols[p]) <= 1e-14 * vol_e[e]
+            assert np.abs(ex - blocks[p]).max() <= 1e-14 * vol_e[e], (p, ex, blocks[p])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_stretched_candidate_pairs_match_bruteforce(dim):
+    """Candidate cells on stretched axes are exactly the half-open cells
+    [x_i, x_{i+1}) with x_{i+1} > lo and x_i < hi, including vertices placed
+    exactly on nodes; elements leaving the grid are reported."""
+    rng = np.random.default_rng(17 + dim)
+    n = 12
+    grid = synth.stretched_grid(dim, n, 0.6, staggered=(dim == 3))
+    for g in range(oracle.n_grids(grid)):
+        sg = oracle.subgrid(grid, g)
+        ax = sg.axis
+        m = 60
+        lo_b = np.array([ax[k][1] for k in range(dim)])
+        hi_b = np.array([ax[k][-2] for k in range(dim)])
+        X = lo_b + (hi_b - lo_b) * rng.random((m * (dim + 1), dim))
+        # a third of the coordinates exactly on a node
+        on = rng.random(X.shape) < 0.33
+        for k in range(dim):
+            idx = rng.integers(1, len(ax[k]) - 1, size=X.shape[0])
+            X[on[:, k], k] = ax[k][idx[on[:, k]]]
+        E = np.arange(m * (dim + 1), dtype=np.int32).reshape(m, dim + 1)
+        pe, pc = oracle.candidate_pairs(sg, X, E)
+        got = set(zip(pe.tolist(), pc.tolist()))
+        ref = set()
+        nc = sg.ncell
+        for e in range(m):
+            V = X[E[e]]
+            lo, hi = V.min(axis=0), V.max(axis=0)
+            ranges = []
+            for k in range(dim):
+                cells = [i for i in range(nc[k]) if ax[k][i + 1] > lo[k] and ax[k][i] < hi[k]]
+                if not cells:  # zero extent exactly on a node: the cell that starts there
+                    cells = [int(np.searchsorted(ax[k], lo[k], side="right")) - 1]
+                ranges.append(cells)
+            for cz in (ranges[2] if dim == 3 else [0]):
+                for cy in ranges[1]:
+                    for cx in ranges[0]:
+                        ref.add((e, cx + nc[0] * (cy + nc[1] * cz)))
+        assert got == ref
+    # leaving the grid is reported
+    sg = oracle.subgrid(grid, 0)
+    Xb = np.zeros((dim + 1, dim)) + 0.5
+    Xb[0, 0] = -1e-3
+    with pytest.raises(oracle.OracleError):
+        oracle.candidate_pairs(sg, Xb, np.arange(dim + 1, dtype=np.int32)[None])
+
+
+@pytest.mark.parametrize("name", ["disk2d_s", "beam16s", "beam32s"])
+def test_stretched_row_sums_and_affine_reproduction(name):
+    """P1 row sums, the total volume and affine reproduction hold on stretched
+    grids (Q1 on a rectilinear cell contains the affine functions)."""
+    w = synth.workload(name)
+    d = w.dim
+    phi, vol = _phi_integrals(w.coords, w.elems)
+    C = oracle.Coupling(w.grid, w.coords, w.elems, nthreads=4)
+    for g, B in enumerate(C.B):
+        rs = np.asarray(B.sum(axis=1)).ravel()
+        assert np.abs(rs - phi).max() <= 1e-14 * phi.max()
+        assert abs(C.pairs[g][3].sum() - vol.sum()) <= 1e-14 * vol.sum()
+    coef = np.array([0.3, 1.5, -0.7, 2.0])[: d + 1]
+    fields = [coef[0] + synth.grid_node_coords(w.grid, g) @ coef[1:] + g for g in range(oracle.n_grids(w.grid))]
+    W = C.transfer_velocity(fields)
+    ex = np.stack([coef[0] + w.coords @ coef[1:] + g for g in range(len(fields))], axis=1)
+    assert np.abs(W - ex).max() <= 1e-13 * np.abs(ex).max()
+
+
+def test_uniform_grid_given_as_node_arrays_matches_the_uniform_path():
+    """A uniform grid passed as explicit node arrays (dyadic spacing: the nodes
+    are exact) gives the same pairs and the same blocks as the uniform path."""
+    w = synth.workload("beam16")
+    n = w.grid.ncell[0]
+    ax = tuple(np.arange(n + 1, dtype=np.float64) / n for _ in range(3))
+    grid_s = synth.Grid(3, w.grid.ncell, w.grid.h, w.grid.origin, True, ax)
+    for g in range(3):
+        su, ss = oracle.subgrid(w.grid, g), oracle.subgrid(grid_s, g)
+        pu = oracle.candidate_pairs(su, w.coords, w.elems)
+        ps = oracle.candidate_pairs(ss, w.coords, w.elems)
+        assert np.array_equal(pu[0], ps[0]) and np.array_equal(pu[1], ps[1])
+        bu, vu = oracle.pair_blocks(su, w.coords, w.elems, *pu)
+        bs, vs = oracle.pair_blocks(ss, w.coords, w.elems, *ps)
+        assert np.abs(bu - bs).max() <= 1e-16 and np.abs(vu - vs).max() <= 1e-16
