@@ -47,6 +47,9 @@ WORKLOAD_DESCS = {
                    "0.3x0.3x0.01, 952,200 P1 tets / 213,444 nodes; Taylor-Green u_f (f32); N(0,1) nodal forces"),
     "beam512": ("3-D staggered Q1 grids 512x512x256 cells (h=1/512) on [0,1]^2x[0,0.5]; deformed beam "
                 "0.4x0.1x0.02, 3,993,600 P1 tets / 702,027 nodes; Taylor-Green u_f (f32); N(0,1) nodal forces"),
+    "beam64s": ("3-D staggered Q1 grids 64^3 cells on [0,1]^3, stretched x = xi + 0.5 sin(2 pi xi)/(2 pi) per axis "
+                "(cells 1/128 wide at the body, 3/128 at the walls); the rotated 48,000-tet beam of beam128; "
+                "Taylor-Green u_f (f32); N(0,1) nodal forces"),
     "batch64": ("3-D staggered Q1 grids 256^3 cells (h=1/256); 64 moving bodies (beams and plates, seeded poses, "
                 "log-uniform 1k-200k tets; 2,234,256 tets / 535,718 nodes in all), rigid motion plus a travelling "
                 "wave, 8 configurations of a 200-step motion replayed in turn; B_g, M_s rebuilt every step"),

@@ -85,13 +85,23 @@ enum {
     L2X_NPHASE = 8
 };
 
-/* Base (pressure) grid: ncell[k] cells of width h[k] from origin[k], k < dim. */
+/* Base (pressure) grid: ncell[k] cells of width h[k] from origin[k], k < dim,
+ * or a stretched (rectilinear) grid as the fluid solvers of Sec. 4 use: when
+ * axis[0] is not NULL, axis[k] (k < dim) are HOST arrays of ncell[k] + 1 finite,
+ * strictly increasing base-node coordinates, read during l2x_build_coupling
+ * only (origin and h are then ignored).  The velocity grids of a staggered
+ * stretched grid have the base nodes along their own axis and the midpoints
+ * 0.5 * (x_i + x_{i+1}) of consecutive base nodes along the others.  Cells are
+ * half-open [x_i, x_{i+1}); the candidate cells of an element along axis k are
+ * those with x_{i+1} > lo and x_i < hi, found by comparisons only.  Set axis to
+ * NULL for a uniform grid. */
 typedef struct l2x_grid {
     int32_t dim;        /* 2 or 3 */
     int32_t staggered;  /* 0: one nodal Q1 grid; 1: dim staggered velocity grids */
     int32_t ncell[3];
     double origin[3];
     double h[3];
+    const double* axis[3];
 } l2x_grid;
 
 /* P1 simplex mesh in its current configuration.  coords: n_nodes x dim,

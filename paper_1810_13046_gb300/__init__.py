@@ -39,7 +39,7 @@ class L2XError(RuntimeError):
 
 class _Grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("staggered", ctypes.c_int32), ("ncell", ctypes.c_int32 * 3),
-                ("origin", ctypes.c_double * 3), ("h", ctypes.c_double * 3)]
+                ("origin", ctypes.c_double * 3), ("h", ctypes.c_double * 3), ("axis", ctypes.c_void_p * 3)]
 
 
 class _Mesh(ctypes.Structure):
@@ -159,23 +159,37 @@ class Grid:
     """Base (pressure) grid: ``ncell`` cells of width ``h`` from ``origin``.
 
     ``staggered=True`` gives one Q1 velocity grid per axis (Sec. 2.2's staggered
-    arrangement); ``False`` gives one nodal Q1 grid."""
+    arrangement); ``False`` gives one nodal Q1 grid.  ``axis``: a stretched grid's
+    base-node coordinates per axis (ncell[k] + 1 increasing values), or None."""
     dim: int
     ncell: tuple
     h: tuple
     origin: tuple
     staggered: bool
+    axis: tuple | None = None
 
 
-def _as_cgrid(grid) -> _Grid:
+def _as_cgrid(grid):
+    """The C struct, and the host arrays its axis pointers refer to (keep both
+    alive for the duration of the call)."""
+    import numpy as np
     g = _Grid()
     g.dim = int(grid.dim)
     g.staggered = int(bool(grid.staggered))
+    keep = []
+    axis = getattr(grid, "axis", None)
     for k in range(3):
         g.ncell[k] = int(grid.ncell[k]) if k < grid.dim else 1
         g.origin[k] = float(grid.origin[k]) if k < grid.dim else 0.0
         g.h[k] = float(grid.h[k]) if k < grid.dim else 1.0
-    return g
+        g.axis[k] = None
+        if axis is not None and k < grid.dim:
+            a = np.ascontiguousarray(axis[k], dtype=np.float64)
+            if a.shape != (int(grid.ncell[k]) + 1,):
+                raise ValueError("a stretched axis needs ncell[k] + 1 node coordinates")
+            keep.append(a)
+            g.axis[k] = a.ctypes.data
+    return g, keep
 
 
 class Coupling:
@@ -218,7 +232,7 @@ class Coupling:
         mesh.n_elems = self.elems.shape[0]
         mesh.coords = self.coords.data_ptr()
         mesh.elems = self.elems.data_ptr()
-        self._grid_c = _as_cgrid(grid)
+        self._grid_c, axis_arrays = _as_cgrid(grid)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib.l2x_build_coupling(ctypes.byref(self._grid_c), ctypes.byref(mesh), ctypes.byref(opts),

@@ -29,6 +29,8 @@ struct l2x_coupling {
     l2x_grid grid{};
     l2x_opts opts{};
     SubGrid sg[kMaxGrids]{};
+    double* grid_ax[kMaxGrids][3]{};   // stretched grids: node coordinates per velocity grid and axis
+    double* grid_iw[kMaxGrids][3]{};   // and inverse cell widths
     cudaStream_t stream = nullptr;
     // own copies of the mesh
     double* X = nullptr;
@@ -231,15 +233,22 @@ l2x_status reset_status(l2x_coupling* h, cudaStream_t s) {
 
 void make_subgrids(l2x_coupling* h) {
     const l2x_grid& G = h->grid;
+    const bool stretched = G.axis[0] != nullptr;
     for (int g = 0; g < h->n_grids; ++g) {
         SubGrid& s = h->sg[g];
         for (int k = 0; k < 3; ++k) {
             if (k < G.dim) {
                 bool shifted = G.staggered && k != g;
                 s.ncell[k] = shifted ? G.ncell[k] - 1 : G.ncell[k];
-                s.origin[k] = shifted ? G.origin[k] + 0.5 * G.h[k] : G.origin[k];
-                s.h[k] = G.h[k];
-                s.inv_h[k] = 1.0 / G.h[k];
+                if (stretched) {
+                    s.origin[k] = 0.0;
+                    s.h[k] = 1.0;  // element gradients per unit length, scaled per cell
+                    s.inv_h[k] = 1.0;
+                } else {
+                    s.origin[k] = shifted ? G.origin[k] + 0.5 * G.h[k] : G.origin[k];
+                    s.h[k] = G.h[k];
+                    s.inv_h[k] = 1.0 / G.h[k];
+                }
             } else {
                 s.ncell[k] = 1;
                 s.origin[k] = 0.0;
@@ -247,8 +256,35 @@ void make_subgrids(l2x_coupling* h) {
                 s.inv_h[k] = 1.0;
             }
             s.nnode[k] = k < G.dim ? s.ncell[k] + 1 : 1;
+            s.ax[k] = nullptr;
+            s.inv_w[k] = nullptr;
         }
     }
+}
+
+// Device copies of the node coordinates and inverse cell widths of every
+// velocity grid of a stretched grid (host arrays of the caller's l2x_grid).
+l2x_status upload_axes(l2x_coupling* h, const l2x_grid* grid, cudaStream_t s) {
+    if (!grid->axis[0]) return L2X_OK;
+    for (int g = 0; g < h->n_grids; ++g) {
+        SubGrid& sg = h->sg[g];
+        for (int k = 0; k < grid->dim; ++k) {
+            const double* x = grid->axis[k];
+            const bool shifted = grid->staggered && k != g;
+            const int nn = sg.nnode[k];
+            std::vector<double> node(nn), iw(nn - 1);
+            for (int i = 0; i < nn; ++i) node[i] = shifted ? 0.5 * (x[i] + x[i + 1]) : x[i];
+            for (int i = 0; i + 1 < nn; ++i) iw[i] = 1.0 / (node[i + 1] - node[i]);
+            L2X_TRY(dalloc(&h->grid_ax[g][k], nn));
+            L2X_TRY(dalloc(&h->grid_iw[g][k], nn - 1));
+            L2X_CUDA(cudaMemcpyAsync(h->grid_ax[g][k], node.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+            L2X_CUDA(cudaMemcpyAsync(h->grid_iw[g][k], iw.data(), sizeof(double) * (nn - 1), cudaMemcpyHostToDevice, s));
+            L2X_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+            sg.ax[k] = h->grid_ax[g][k];
+            sg.inv_w[k] = h->grid_iw[g][k];
+        }
+    }
+    return L2X_OK;
 }
 
 // Row list of B_g^T (non-empty rows) and the flag scratch, for up to `rows` rows
@@ -500,9 +536,19 @@ l2x_status validate(const l2x_grid* grid, const l2x_mesh* mesh, const l2x_opts* 
     if (mesh->n_nodes <= 0 || mesh->n_elems <= 0) return fail(L2X_EINVAL, "empty mesh");
     if (mesh->n_nodes >= INT_MAX || mesh->n_elems >= (INT_MAX >> 2)) return fail(L2X_EINVAL, "mesh too large for int32 indices");
     if (!mesh->coords || !mesh->elems) return fail(L2X_EINVAL, "mesh arrays must not be NULL");
+    const bool stretched = grid->axis[0] != nullptr;
     for (int k = 0; k < grid->dim; ++k) {
         if (grid->ncell[k] < (grid->staggered ? 2 : 1)) return fail(L2X_EINVAL, "ncell too small");
-        if (!(grid->h[k] > 0.0)) return fail(L2X_EINVAL, "h must be positive");
+        if (stretched) {
+            const double* x = grid->axis[k];
+            if (!x) return fail(L2X_EINVAL, "a stretched grid needs a node array on every axis");
+            for (int i = 0; i <= grid->ncell[k]; ++i) {
+                if (!std::isfinite(x[i])) return fail(L2X_EINVAL, "non-finite stretched node coordinate");
+                if (i > 0 && !(x[i] > x[i - 1])) return fail(L2X_EINVAL, "stretched node coordinates must increase strictly");
+            }
+        } else if (!(grid->h[k] > 0.0)) {
+            return fail(L2X_EINVAL, "h must be positive");
+        }
     }
     int64_t nodes = 1;
     for (int k = 0; k < grid->dim; ++k) nodes *= (int64_t)grid->ncell[k] + 1;
@@ -685,6 +731,11 @@ l2x_status l2x_destroy(l2x_handle h) {
         dfree(h->T[g].list); dfree(h->T[g].n_list); dfree(h->T[g].long_rows); dfree(h->T[g].n_long);
     }
     dfree(h->M.ptr); dfree(h->M.col); dfree(h->M.val); dfree(h->M.val32); dfree(h->M_dinv); dfree(h->M_dinv32);
+    for (int g = 0; g < kMaxGrids; ++g)
+        for (int k = 0; k < 3; ++k) {
+            dfree(h->grid_ax[g][k]);
+            dfree(h->grid_iw[g][k]);
+        }
     if (h->scan_tmp) cudaFree(h->scan_tmp);
     dfree(h->row_count);
     dfree(h->tcursor);
@@ -718,6 +769,7 @@ l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const 
     h->opts = o;
     h->stream = s;
     make_subgrids(h);
+    for (int k = 0; k < 3; ++k) h->grid.axis[k] = nullptr;  // the caller's arrays are read during the build only
     auto body = [&]() -> l2x_status {
         const int64_t n = h->n_nodes, m = h->n_elems;
         const int d = h->dim, G = h->n_grids;
@@ -749,6 +801,7 @@ l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const 
                 if (v < 0 || v >= n) return fail(L2X_EINVAL, "element references a node outside [0, n_nodes)");
         }
         pcg_cluster_prepare();
+        L2X_TRY(upload_axes(h, grid, s));
         L2X_TRY(build_topology(h, s));
         size_t ws = pcg_ws_bytes(n, G, pcg_max_blocks());
         if (cudaMalloc(&h->pcg_ws, ws) != cudaSuccess) return fail(L2X_ENOMEM, "CG workspace");

@@ -9,28 +9,55 @@ namespace {
 
 constexpr int kClipThreads = 128;
 
-__device__ __forceinline__ void cell_lower(const SubGrid& sg, int dim, int32_t cell, double* clo, int* ci) {
+// Lower corner, width and inverse width of a cell per axis: uniform grids
+// origin + i h; stretched grids the cell between nodes x_i and x_{i+1}.
+__device__ __forceinline__ void cell_frame(const SubGrid& sg, int dim, int32_t cell, double* clo, double* w,
+                                           double* iw) {
+    int ci[3];
     int c = cell;
     ci[0] = c % sg.ncell[0];
     c /= sg.ncell[0];
     ci[1] = c % sg.ncell[1];
     ci[2] = dim == 3 ? c / sg.ncell[1] : 0;
-    for (int k = 0; k < dim; ++k) clo[k] = __dadd_rn(sg.origin[k], __dmul_rn((double)ci[k], sg.h[k]));
+    for (int k = 0; k < dim; ++k) {
+        if (sg.ax[0]) {
+            clo[k] = __ldg(sg.ax[k] + ci[k]);
+            w[k] = __ldg(sg.ax[k] + ci[k] + 1) - clo[k];
+            iw[k] = __ldg(sg.inv_w[k] + ci[k]);
+        } else {
+            clo[k] = __dadd_rn(sg.origin[k], __dmul_rn((double)ci[k], sg.h[k]));
+            w[k] = sg.h[k];
+            iw[k] = sg.inv_h[k];
+        }
+    }
 }
 
-// Element vertices of pair p in cell-local coordinates.
+// Element vertices of pair p in cell-local coordinates; w receives the cell widths.
 template <int D>
 __device__ __forceinline__ void pair_vertices(const SubGrid& sg, const double* __restrict__ X, const int32_t* __restrict__ E,
-                                              int32_t e, int32_t cell, double (&T)[D + 1][D]) {
-    double clo[3];
-    int ci[3];
-    cell_lower(sg, D, cell, clo, ci);
+                                              int32_t e, int32_t cell, double (&T)[D + 1][D], double* w) {
+    double clo[3], iw[3];
+    cell_frame(sg, D, cell, clo, w, iw);
 #pragma unroll
     for (int a = 0; a <= D; ++a) {
         const int32_t v = __ldg(E + (int64_t)e * (D + 1) + a);
 #pragma unroll
-        for (int k = 0; k < D; ++k) T[a][k] = (__ldg(X + (int64_t)v * D + k) - clo[k]) * sg.inv_h[k];
+        for (int k = 0; k < D; ++k) T[a][k] = (__ldg(X + (int64_t)v * D + k) - clo[k]) * iw[k];
     }
+}
+
+// Cell volume of the local frame, and gradients brought into it: on a
+// stretched grid the element gradients are stored per unit length and scaled by
+// the widths of the pair's cell; on a uniform grid they are stored in cell units.
+template <int D>
+__device__ __forceinline__ double frame_scale(const SubGrid& sg, const double* w, double (&gr)[D + 1][D]) {
+    if (sg.ax[0]) {
+#pragma unroll
+        for (int a = 0; a <= D; ++a)
+#pragma unroll
+            for (int k = 0; k < D; ++k) gr[a][k] *= w[k];
+    }
+    return w[0] * w[1] * (D == 3 ? w[2] : 1.0);
 }
 
 struct SubGridSet {
@@ -59,8 +86,8 @@ __global__ void pair_class_kernel(int G, SubGridSet sgs, int64_t m, const int64_
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p < n) {
         const int g = grid_of_pair(p, G, m, offsets);
-        double T[D + 1][D];
-        pair_vertices<D>(sgs.g[g], X, E, pair_elem[p], pair_cell[p], T);
+        double T[D + 1][D], w[3];
+        pair_vertices<D>(sgs.g[g], X, E, pair_elem[p], pair_cell[p], T, w);
         const int key = min(pair_class<D>(T), kClasses - 1);
         keys[p] = (uint8_t)key;
         atomicAdd(&hist[key], 1);
@@ -132,13 +159,13 @@ __global__ void __launch_bounds__(256) clip_fused_kernel(int G, SubGridSet sgs, 
 #pragma unroll
         for (int j = 0; j < NA * NB; ++j) blk[j] = 0.0;
     } else {
-        double T[NA][D], gr[NA][D];
-        pair_vertices<D>(sg, X, E, e, pair_cell[p], T);
+        double T[NA][D], gr[NA][D], w[3];
+        pair_vertices<D>(sg, X, E, e, pair_cell[p], T, w);
 #pragma unroll
         for (int a = 0; a < NA; ++a)
 #pragma unroll
             for (int k = 0; k < D; ++k) gr[a][k] = __ldg(elem_grad + ((int64_t)e * NA + a) * D + k);
-        const double scale = sg.h[0] * sg.h[1] * (D == 3 ? sg.h[2] : 1.0);
+        const double scale = frame_scale<D>(sg, w, gr);
         pair_integrals<D, R>(T, gr, flag == 1, scale, blk, &vol);
     }
 #pragma unroll
@@ -157,15 +184,14 @@ __global__ void clip_plain_kernel(SubGrid sg, const double* __restrict__ X, cons
     const int64_t p = p_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= p_end) return;
     const int32_t e = pair_elem[p];
-    double clo[3];
-    int ci[3];
-    cell_lower(sg, D, pair_cell[p], clo, ci);
+    double clo[3], w[3], iw[3];
+    cell_frame(sg, D, pair_cell[p], clo, w, iw);
     double Xe[NA][D], T[NA][D], ge[NA][D];
     for (int a = 0; a < NA; ++a) {
         const int32_t v = E[(int64_t)e * NA + a];
         for (int k = 0; k < D; ++k) {
             Xe[a][k] = X[(int64_t)v * D + k];
-            T[a][k] = (Xe[a][k] - clo[k]) * sg.inv_h[k];
+            T[a][k] = (Xe[a][k] - clo[k]) * iw[k];
         }
     }
     double blk[NA * NB];
@@ -176,7 +202,7 @@ __global__ void clip_plain_kernel(SubGrid sg, const double* __restrict__ X, cons
         atomicMin(&st->bad_elem, e);
         for (int i = 0; i < NA * NB; ++i) blk[i] = 0.0;
     } else {
-        const double scale = sg.h[0] * sg.h[1] * (D == 3 ? sg.h[2] : 1.0);
+        const double scale = frame_scale<D>(sg, w, ge);
         pair_integrals<D, double>(T, ge, pos, scale, blk, &vol);
     }
     for (int i = 0; i < NA * NB; ++i) blocks[p * (NA * NB) + i] = blk[i];

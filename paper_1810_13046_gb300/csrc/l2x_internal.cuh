@@ -38,8 +38,12 @@ struct SubGrid {
     int32_t ncell[3];   // Q1 cells per axis (1 on unused axes)
     int32_t nnode[3];   // ncell + 1 (1 on unused axes)
     double origin[3];
-    double h[3];
+    double h[3];        // uniform grids; 1 on a stretched grid (gradients in physical units)
     double inv_h[3];
+    // stretched (rectilinear) grid: per used axis the nnode node coordinates and
+    // the ncell inverse cell widths (device arrays); null on a uniform grid
+    const double* ax[3];
+    const double* inv_w[3];
 };
 
 // Per-element candidate box on one grid: lowest cell index and extent per axis.

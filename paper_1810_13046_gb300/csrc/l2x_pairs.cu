@@ -20,6 +20,24 @@ struct SubGridSet {
 
 __device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
 
+// Entries of the increasing array x[0..n) that are <= v, resp. < v.
+__device__ __forceinline__ int count_le(const double* __restrict__ x, int n, double v) {
+    int l = 0, r = n;
+    while (l < r) {
+        const int m = (l + r) >> 1;
+        if (__ldg(x + m) <= v) l = m + 1; else r = m;
+    }
+    return l;
+}
+__device__ __forceinline__ int count_lt(const double* __restrict__ x, int n, double v) {
+    int l = 0, r = n;
+    while (l < r) {
+        const int m = (l + r) >> 1;
+        if (__ldg(x + m) < v) l = m + 1; else r = m;
+    }
+    return l;
+}
+
 template <int D>
 __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const double* __restrict__ X,
                                   const int32_t* __restrict__ E, ElemBox* __restrict__ boxes,
@@ -78,11 +96,20 @@ __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const 
         int64_t count = 1;
         bool ok = finite;
         for (int k = 0; k < D; ++k) {
-            double qlo = __ddiv_rn(__dsub_rn(lo[k], sg.origin[k]), sg.h[k]);
-            double qhi = __ddiv_rn(__dsub_rn(hi[k], sg.origin[k]), sg.h[k]);
-            double flo = floor(qlo), chi = ceil(qhi) - 1.0;
-            if (!(flo >= 0.0) || !(chi < (double)sg.ncell[k])) { ok = false; break; }
-            int il = (int)flo, ih = (int)chi;
+            int il, ih;
+            if (sg.ax[0]) {
+                // stretched axis: half-open cells [x_i, x_{i+1}); comparisons only
+                il = count_le(sg.ax[k], sg.nnode[k], lo[k]) - 1;
+                ih = count_lt(sg.ax[k], sg.nnode[k], hi[k]) - 1;
+                if (il < 0 || ih >= sg.ncell[k]) { ok = false; break; }
+            } else {
+                double qlo = __ddiv_rn(__dsub_rn(lo[k], sg.origin[k]), sg.h[k]);
+                double qhi = __ddiv_rn(__dsub_rn(hi[k], sg.origin[k]), sg.h[k]);
+                double flo = floor(qlo), chi = ceil(qhi) - 1.0;
+                if (!(flo >= 0.0) || !(chi < (double)sg.ncell[k])) { ok = false; break; }
+                il = (int)flo;
+                ih = (int)chi;
+            }
             if (ih < il) ih = il;
             ext[k] = ih - il + 1;
             b.lo[k] = il;

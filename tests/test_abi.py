@@ -86,3 +86,18 @@ def test_bad_multiplier_space_is_rejected_without_a_gpu():
     h = ctypes.c_void_p()
     assert lib.l2x_build_coupling(ctypes.byref(g), ctypes.byref(m), ctypes.byref(o), None, ctypes.byref(h)) == 1
     assert b"multiplier" in lib.l2x_last_error()
+
+
+def test_stretched_axis_is_validated_without_a_gpu():
+    """A stretched node array that does not increase strictly is rejected before any CUDA call."""
+    import numpy as np
+    lib = l2x.load_library()
+    grid = l2x.Grid(2, (4, 4), (0.25, 0.25), (0.0, 0.0), False,
+                    (np.array([0.0, 0.2, 0.5, 0.5, 1.0]), np.linspace(0.0, 1.0, 5)))
+    g, keep = l2x._as_cgrid(grid)
+    m = l2x._Mesh()
+    m.dim, m.n_nodes, m.n_elems = 2, 3, 1
+    m.coords = m.elems = 16  # never dereferenced: validation fails first
+    h = ctypes.c_void_p()
+    assert lib.l2x_build_coupling(ctypes.byref(g), ctypes.byref(m), None, None, ctypes.byref(h)) == 1
+    assert b"increase" in lib.l2x_last_error()
