@@ -194,6 +194,29 @@ def barrier(world):
 
 # ----------------------------------------------------------------------------- oracle legs
 
+def spmv_bytes(c, torch):
+    """Algorithmic bytes of one y = B u_f and one f_f += s B^T z over all grids in
+    the mixed form (FP32 values, int32 columns, int64 row pointers): every
+    matrix entry once, every touched vector entry once, results written once."""
+    bB = bT = 0
+    n = c.n_nodes
+    for g in range(c.n_grids):
+        rp, cols, _ = c.export_csr(g)
+        nnz = int(cols.numel())
+        touched = int(torch.unique(cols).numel())
+        bB += (n + 1) * 8 + nnz * 8 + touched * 4 + n * 4
+        bT += (touched + 1) * 8 + nnz * 8 + n * 4 + touched * 8
+    return bB, bT
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json copy bandwidth)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
 def oracle_step(w, elems, nthreads):
     """One step of the plain FP64 CPU oracle (assembly + both transfers)."""
     import oracle
@@ -442,6 +465,55 @@ def main():
     plain = arm.per_call(l2x.PLAIN, l2x.FP64, args.plain_steps, 2)
     f64 = arm.per_call(l2x.FUSED, l2x.FP64, args.plain_steps, 2)
 
+    # HBM rooflines of the two sparse products of the apply (per-call phase times)
+    peak_hbm, peak_src = hbm_peak()
+    bB, bT = spmv_bytes(pc["c"], torch)
+    tB = ph["spmv_B"] / max(1, calls["spmv_B"])
+    tT = ph["spmv_BT"] / max(1, calls["spmv_BT"])
+    apply_roof = {"bound": "hbm", "unit": "GB/s", "peak": peak_hbm, "peak_source": peak_src,
+                  "spmv_B": {"bytes": bB, "ms": tB, "achieved": bB / (tB * 1e-3) / 1e9,
+                             "frac": bB / (tB * 1e-3) / 1e9 / peak_hbm},
+                  "spmv_BT": {"bytes": bT, "ms": tT, "achieved": bT / (tT * 1e-3) / 1e9,
+                              "frac": bT / (tT * 1e-3) / 1e9 / peak_hbm},
+                  "pcg_ms_per_solve": ph["pcg"] / max(1, calls["pcg"]),
+                  "note": "the mass-matrix solve is latency-bound at these sizes (grid barriers per iteration)"}
+
+    # per-result error of the chosen (mixed) form against the FP64 GPU path, same configuration
+    def results(r):
+        c = r["c"]
+        c.update_geometry(positions[0])
+        u = c.transfer_velocity(r["uf"])
+        f = c.transfer_force(r["fs"])
+        return [x.double() for x in u], [x.double() for x in f]
+    um, fm = results(pc)
+    u64, f64r = results(f64)
+    def rel(a, b):
+        nb = float(torch.linalg.norm(b))
+        return float(torch.linalg.norm(a - b)) / nb if nb > 0 else None  # None: a zero reference component
+
+    mixed_err = {"u_s": [rel(a, b) for a, b in zip(um, u64)], "f_f": [rel(a, b) for a, b in zip(fm, f64r)],
+                 "u_s_all": rel(torch.cat(um), torch.cat(u64)), "f_f_all": rel(torch.cat(fm), torch.cat(f64r)),
+                 "against": "fused FP64 GPU path on the same configuration (which matches the FP64 oracle to 1e-12)"}
+
+    # differentiable transfer: forward u_s = S^-1 B u_f and the hand-written backward
+    cg = pc["c"]
+    ua = [u.clone().requires_grad_(True) for u in pc["uf"]]
+    gw = [torch.ones(cg.n_nodes, dtype=ua[0].dtype, device=dev) for _ in ua]
+    for _ in range(3):
+        out = l2x.VelocityTransfer.apply(cg, *ua)
+        torch.autograd.backward(out, gw)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_ag = 10
+    a0.record(torch.cuda.current_stream(dev))
+    for _ in range(n_ag):
+        out = l2x.VelocityTransfer.apply(cg, *ua)
+        torch.autograd.backward(out, gw)
+    a1.record(torch.cuda.current_stream(dev))
+    a1.synchronize()
+    autograd = {"forward_backward_ms": a0.elapsed_time(a1) / n_ag,
+                "form": "VelocityTransfer forward (B, S^-1) + backward (S^-1, B^T), mixed precision"}
+
     # the dual multiplier basis (pseudo L2 projection, S diagonal: no CG), same step
     n_dual = max(3, args.steps // 4)
     dgr = arm.graph(l2x.MIXED, n_dual, 3, multiplier=l2x.DUAL_BASIS)
@@ -552,6 +624,9 @@ def main():
             "gpu_launches_note": "per step as counted on the per-call form; the captured graph replays the same "
                                  "kernel nodes",
             "roofline": roof,
+            "apply_roofline": apply_roof,
+            "mixed_vs_fp64": mixed_err,
+            "autograd": autograd,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(),
         }

@@ -80,6 +80,7 @@ struct l2x_coupling {
     int64_t tflags_cap = 0;
     void* pcg_ws = nullptr;
     void* vec_tmp = nullptr;         // n_grids * n_nodes doubles
+    void* vec_tmp2 = nullptr;        // n_grids * n_nodes doubles (force side of a captured step)
     void* vec_mask = nullptr;        // n_grids * n_nodes doubles: the masked force input
     uint8_t* fmask = nullptr;        // interface mask of the force input (n_nodes), when has_fmask
     bool has_fmask = false;
@@ -666,11 +667,39 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     }
     launch_S_values(h, s);
     // transfers
-    enqueue_velocity(h, u_f, u_s, s);
-    if (zero_force) {
-        const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
-        for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
+    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+    if (h->opts.multiplier == L2X_MULT_STANDARD && h->opts.force_mode == L2X_FORCE_DUAL) {
+        // the two solves with M_s are independent: one PCG on the 2G right-hand
+        // sides [B u_f ; f_s] (its iterations are latency-bound, so this costs
+        // about one solve)
+        void* yv[kMaxGrids];
+        void* zf[kMaxGrids];
+        for (int g = 0; g < G; ++g) {
+            yv[g] = (char*)h->vec_tmp + es * n * g;
+            zf[g] = (char*)h->vec_tmp2 + es * n * g;
+        }
+        launch_spmv_B(L2X_PATH_FUSED, h->opts.precision, G, h->B, u_f, yv, h->st, s);
+        const void* mbuf[kMaxGrids];
+        const void* const* fs = masked_force(h, f_s, mbuf, s);
+        const void* ys[2 * kMaxGrids];
+        void* ws[2 * kMaxGrids];
+        for (int g = 0; g < G; ++g) {
+            ys[g] = yv[g];
+            ws[g] = u_s[g];
+            ys[G + g] = fs[g];
+            ws[G + g] = zf[g];
+        }
+        solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, 2 * G, ys, ws, h->opts.cg_rtol,
+                             h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb, h->pcg_clu);
+        if (zero_force)
+            for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
+        launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)zf, f_f,
+                       h->opts.force_scale, h->st, s);
+        return L2X_OK;
     }
+    enqueue_velocity(h, u_f, u_s, s);
+    if (zero_force)
+        for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
     enqueue_force(h, f_s, f_f, s);
     return L2X_OK;
 }
@@ -742,6 +771,7 @@ l2x_status l2x_destroy(l2x_handle h) {
     dfree(h->tflags);
     if (h->pcg_ws) cudaFree(h->pcg_ws);
     if (h->vec_tmp) cudaFree(h->vec_tmp);
+    if (h->vec_tmp2) cudaFree(h->vec_tmp2);
     if (h->vec_mask) cudaFree(h->vec_mask);
     dfree(h->fmask);
     dfree(h->st);
@@ -803,9 +833,10 @@ l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const 
         pcg_cluster_prepare();
         L2X_TRY(upload_axes(h, grid, s));
         L2X_TRY(build_topology(h, s));
-        size_t ws = pcg_ws_bytes(n, G, pcg_max_blocks());
+        size_t ws = pcg_ws_bytes(n, 2 * G, pcg_max_blocks());  // a captured step solves both transfers at once
         if (cudaMalloc(&h->pcg_ws, ws) != cudaSuccess) return fail(L2X_ENOMEM, "CG workspace");
         if (cudaMalloc(&h->vec_tmp, sizeof(double) * n * G) != cudaSuccess) return fail(L2X_ENOMEM, "vector scratch");
+        if (cudaMalloc(&h->vec_tmp2, sizeof(double) * n * G) != cudaSuccess) return fail(L2X_ENOMEM, "vector scratch");
         return build_geometry(h, s);
     };
     l2x_status st = body();

@@ -5,6 +5,7 @@
 #include <cooperative_groups.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "l2x_fp.cuh"
 #include "l2x_internal.cuh"
@@ -144,24 +145,71 @@ __global__ void picard_norms_kernel(int64_t n, int G, PicardPack<TV> P, int copy
 // ------------------------------------------------------------------ B^T z
 // One thread per non-empty row of B_g^T (a fluid node the mesh touches): gather,
 // no atomics.  The row list and its length are device values.
+// kBTLanes lanes per non-empty row of B_g^T (a fluid node the mesh touches),
+// all grids in one launch: gather, no atomics.  The row lists and their lengths
+// are device values; the launch covers their capacities.
+constexpr int kBTLanes = 4;
+
 template <typename TV, typename TM>
-__global__ void spmv_BT_fused_kernel(const int32_t* __restrict__ list, const int64_t* __restrict__ n_list,
-                                     const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                     const TM* __restrict__ val, CsrT T, int nn0, int nn1, const TV* __restrict__ z,
-                                     TV* __restrict__ f, TV scale, const DevStatus* st) {
+struct SpmvTPack {
+    const int32_t* list[kMaxGrids];
+    const int64_t* n_list[kMaxGrids];
+    const int64_t* ptr[kMaxGrids];
+    const int32_t* col[kMaxGrids];
+    const TM* val[kMaxGrids];
+    const TV* z[kMaxGrids];
+    TV* f[kMaxGrids];
+    int lo[kMaxGrids][3];
+    int nb[kMaxGrids][2];       // rows of the B^T box along x, y
+    int nn[kMaxGrids][2];       // fluid nodes of grid g along x, y
+    int64_t start[kMaxGrids + 1];  // first row slot of every grid (capacities)
+    int G;
+};
+
+template <typename TV, typename TM>
+__global__ void spmv_BT_fused_kernel(SpmvTPack<TV, TM> P, TV scale, const DevStatus* st) {
     if (st->flags & kAbortFlags) return;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= *n_list) return;
-    const int64_t r = list[t];
-    const int64_t lo = ptr[r], hi = ptr[r + 1];
-    TV acc = TV(0);
-    for (int64_t q = lo; q < hi; ++q) acc += (TV)__ldg(val + q) * __ldg(z + __ldg(col + q));
-    const int x = (int)(r % T.n[0]);
-    const int64_t rr = r / T.n[0];
-    const int y = (int)(rr % T.n[1]);
-    const int zz = (int)(rr / T.n[1]);
-    const int64_t node = (x + T.lo[0]) + (int64_t)nn0 * ((y + T.lo[1]) + (int64_t)nn1 * (zz + T.lo[2]));
-    f[node] += scale * acc;
+    // slots of the listed rows of all grids, grid after grid (device counts)
+    int64_t first[kMaxGrids + 1];
+    first[0] = 0;
+    for (int g = 0; g < P.G; ++g) {
+        const int64_t cap = P.start[g + 1] - P.start[g];
+        const int64_t nl = *P.n_list[g];
+        first[g + 1] = first[g] + (nl < cap ? nl : cap);
+    }
+    const int64_t total = first[P.G];
+    const int lane = threadIdx.x % kBTLanes;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x / kBTLanes;
+    // every lane group runs the same number of passes (warp-uniform shuffles)
+    const int64_t slot0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kBTLanes;
+    const int64_t warp_slot0 = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) / kBTLanes;
+    for (int64_t base = warp_slot0; base < total; base += stride) {
+        const int64_t slot = slot0 + (base - warp_slot0);
+        const bool active = slot < total;
+        int g = 0;
+        while (g + 1 < P.G && slot >= first[g + 1]) ++g;
+        TV acc = TV(0);
+        int64_t r = 0;
+        if (active) {
+            r = P.list[g][slot - first[g]];
+            const int64_t hi = P.ptr[g][r + 1];
+            const int32_t* __restrict__ col = P.col[g];
+            const TM* __restrict__ val = P.val[g];
+            const TV* __restrict__ z = P.z[g];
+            for (int64_t q = P.ptr[g][r] + lane; q < hi; q += kBTLanes) acc += (TV)__ldg(val + q) * __ldg(z + __ldg(col + q));
+        }
+#pragma unroll
+        for (int o = kBTLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (active && lane == 0) {
+            const int x = (int)(r % P.nb[g][0]);
+            const int64_t rr = r / P.nb[g][0];
+            const int y = (int)(rr % P.nb[g][1]);
+            const int zz = (int)(rr / P.nb[g][1]);
+            const int64_t node =
+                (x + P.lo[g][0]) + (int64_t)P.nn[g][0] * ((y + P.lo[g][1]) + (int64_t)P.nn[g][1] * (zz + P.lo[g][2]));
+            P.f[g][node] += scale * acc;
+        }
+    }
 }
 
 __global__ void spmv_BT_plain_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
@@ -175,7 +223,14 @@ __global__ void spmv_BT_plain_kernel(int64_t n_rows, const int64_t* __restrict__
 
 // ------------------------------------------------------------------ PCG (fused, cooperative)
 constexpr int kPcgThreads = 256;
-constexpr int kMaxRhs = 3;
+// right-hand sides of one solve: the components of one transfer (<= 3), or of
+// both transfers of a captured step solved together (<= 6)
+constexpr int kMaxRhs = 6;
+
+template <typename T>
+struct VecPack {
+    T* p[kMaxRhs];
+};
 
 // Dot-product accumulator: exact double for FP64 vectors; for FP32 vectors the
 // product is split exactly (fma) and summed with an error-compensated pair of
@@ -870,16 +925,15 @@ __global__ void plain_scalars_kernel(int nr, double* scal, const double* rr0, do
 // ------------------------------------------------------------------ mixed-precision refinement
 // r64 = y - M x64 (FP64), norms[k] += |r64|^2
 __global__ void residual_f64_kernel(int64_t n, int nr, const int64_t* ptr, const int32_t* col, const double* val,
-                                    const float* y0, const float* y1, const float* y2, const double* x64,
-                                    double* r64, float* r32, double* norms) {
+                                    VecPack<const float> y, const double* x64, double* r64, float* r32,
+                                    double* norms) {
     __shared__ double sh[32];
-    const float* y[3] = {y0, y1, y2};
     for (int k = 0; k < nr; ++k) {
         double acc = 0.0;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
             double s = 0.0;
             for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], x64[k * n + col[e]], s);
-            double ri = (double)y[k][i] - s;
+            double ri = (double)y.p[k][i] - s;
             r64[k * n + i] = ri;
             r32[k * n + i] = (float)ri;
             acc = fma(ri, ri, acc);
@@ -889,32 +943,27 @@ __global__ void residual_f64_kernel(int64_t n, int nr, const int64_t* ptr, const
     }
 }
 
-__global__ void add_correction_kernel(int64_t n, int nr, double* x64, const float* d0, const float* d1,
-                                      const float* d2, int first) {
+__global__ void add_correction_kernel(int64_t n, int nr, double* x64, VecPack<const float> d, int first) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float* d[3] = {d0, d1, d2};
-    for (int k = 0; k < nr; ++k) x64[k * n + i] = (first ? 0.0 : x64[k * n + i]) + (double)d[k][i];
+    for (int k = 0; k < nr; ++k) x64[k * n + i] = (first ? 0.0 : x64[k * n + i]) + (double)d.p[k][i];
 }
 
-__global__ void norm2_f32_kernel(int64_t n, int nr, const float* y0, const float* y1, const float* y2,
-                                 double* out) {
+__global__ void norm2_f32_kernel(int64_t n, int nr, VecPack<const float> y, double* out) {
     __shared__ double sh[32];
-    const float* y[3] = {y0, y1, y2};
     for (int k = 0; k < nr; ++k) {
         double acc = 0.0;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-            acc = fma((double)y[k][i], (double)y[k][i], acc);
+            acc = fma((double)y.p[k][i], (double)y.p[k][i], acc);
         acc = block_sum(acc, sh);
         if (threadIdx.x == 0) atomicAdd(out + k, acc);
     }
 }
 
-__global__ void store_f32_kernel(int64_t n, int nr, const double* x64, float* w0, float* w1, float* w2) {
+__global__ void store_f32_kernel(int64_t n, int nr, const double* x64, VecPack<float> w) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float* w[3] = {w0, w1, w2};
-    for (int k = 0; k < nr; ++k) w[k][i] = (float)x64[k * n + i];
+    for (int k = 0; k < nr; ++k) w.p[k][i] = (float)x64[k * n + i];
 }
 
 template <typename TV, int NR>
@@ -1000,7 +1049,7 @@ cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val,
     A.st = st;
     void* args[] = {&A};
     count_launch();
-    if (clu > 0) {
+    if (clu > 0 && nr <= 3) {
         int S = 0;
         size_t smem = 0;
         const bool fits = nr == 1 ? cluster_fits<TV, 1>(n, clu, S, smem)
@@ -1020,9 +1069,17 @@ cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val,
         case 2:
             return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 2>, dim3(pcg_blocks_for<TV, 2>(n, rpb)),
                                                dim3(kPcgBlock), args, 0, s);
-        default:
+        case 4:
+            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 4>, dim3(pcg_blocks_for<TV, 4>(n, rpb)),
+                                               dim3(kPcgBlock), args, 0, s);
+        case 6:
+            return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 6>, dim3(pcg_blocks_for<TV, 6>(n, rpb)),
+                                               dim3(kPcgBlock), args, 0, s);
+        case 3:
             return cudaLaunchCooperativeKernel((const void*)pcg_fused_kernel<TV, 3>, dim3(pcg_blocks_for<TV, 3>(n, rpb)),
                                                dim3(kPcgBlock), args, 0, s);
+        default:
+            return cudaErrorInvalidValue;
     }
 }
 
@@ -1169,15 +1226,43 @@ void launch_spmv_BT(int path, int precision, int n_grids, const Csr* B, const Cs
                                                                             (const double*)z[g], (double*)f[g], scale); count_launch(); }
         return;
     }
-    for (int g = 0; g < n_grids; ++g) {
-        const CsrT& T = Tm[g];
-        const int64_t nl = T.list_cap < T.n_rows ? T.list_cap : T.n_rows;
-        if (nl <= 0) continue;
-        if (precision == L2X_MIXED) {
-            { spmv_BT_fused_kernel<float, float><<<nblk(nl, 256), 256, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val32, T, sg[g].nnode[0], sg[g].nnode[1], (const float*)z[g], (float*)f[g], (float)scale, st); count_launch(); }
-        } else {
-            { spmv_BT_fused_kernel<double, double><<<nblk(nl, 256), 256, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val, T, sg[g].nnode[0], sg[g].nnode[1], (const double*)z[g], (double*)f[g], scale, st); count_launch(); }
+    auto launch = [&](auto* tag_v, auto* tag_m, const auto* const* vals) {
+        using TV = std::remove_pointer_t<decltype(tag_v)>;
+        using TM = std::remove_pointer_t<decltype(tag_m)>;
+        SpmvTPack<TV, TM> P{};
+        P.G = n_grids;
+        int64_t acc = 0;
+        for (int g = 0; g < n_grids; ++g) {
+            const CsrT& T = Tm[g];
+            const int64_t nl = T.list_cap < T.n_rows ? T.list_cap : T.n_rows;
+            P.start[g] = acc;
+            acc += nl > 0 ? nl : 0;
+            P.list[g] = T.list;
+            P.n_list[g] = T.n_list;
+            P.ptr[g] = T.ptr;
+            P.col[g] = T.col;
+            P.val[g] = (const TM*)vals[g];
+            P.z[g] = (const TV*)z[g];
+            P.f[g] = (TV*)f[g];
+            for (int k = 0; k < 3; ++k) P.lo[g][k] = T.lo[k];
+            P.nb[g][0] = T.n[0];
+            P.nb[g][1] = T.n[1];
+            P.nn[g][0] = sg[g].nnode[0];
+            P.nn[g][1] = sg[g].nnode[1];
         }
+        P.start[n_grids] = acc;
+        if (acc <= 0) return;
+        unsigned nb = nblk(acc * kBTLanes, 256);
+        if (nb > 152 * 8) nb = 152 * 8;  // grid-stride over the rows actually listed
+        { spmv_BT_fused_kernel<TV, TM><<<nb, 256, 0, s>>>(P, (TV)scale, st); count_launch(); }
+    };
+    const void* vals[kMaxGrids];
+    if (precision == L2X_MIXED) {
+        for (int g = 0; g < n_grids; ++g) vals[g] = Tm[g].val32;
+        launch((float*)nullptr, (float*)nullptr, vals);
+    } else {
+        for (int g = 0; g < n_grids; ++g) vals[g] = Tm[g].val;
+        launch((double*)nullptr, (double*)nullptr, vals);
     }
 }
 
@@ -1205,28 +1290,34 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
     double* r64 = (double*)take(v * 8);
     float* r32 = (float*)take(v * 4);
     float* d32 = (float*)take(v * 4);
-    double* norms = (double*)take(8 * 8);
-    const float* yf[3] = {(const float*)y[0], nr > 1 ? (const float*)y[1] : nullptr, nr > 2 ? (const float*)y[2] : nullptr};
-    float* wf[3] = {(float*)w[0], nr > 1 ? (float*)w[1] : nullptr, nr > 2 ? (float*)w[2] : nullptr};
+    double* norms = (double*)take(2 * kMaxRhs * 8);
+    VecPack<const float> yf{};
+    VecPack<float> wf{};
+    for (int k = 0; k < nr; ++k) {
+        yf.p[k] = (const float*)y[k];
+        wf.p[k] = (float*)w[k];
+    }
     const unsigned nb = nblk(n, 256);
     const unsigned nbd = nb < 1024 ? nb : 1024;
     const double inner = rtol > 1e-7 ? rtol : 1e-7;
     // one FP32 solve and one FP64 residual correction, fixed (no host decisions)
     for (int ref = 0; ref < 2; ++ref) {
-        const float* rhs[3];
-        float* dst[3];
+        const float* rhs[kMaxRhs];
+        float* dst[kMaxRhs];
+        VecPack<const float> dp{};
         for (int k = 0; k < nr; ++k) {
-            rhs[k] = ref == 0 ? yf[k] : r32 + k * n;
+            rhs[k] = ref == 0 ? yf.p[k] : r32 + k * n;
             dst[k] = d32 + k * n;
+            dp.p[k] = dst[k];
         }
         run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s, rpb, clu);
-        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr, nr > 2 ? dst[2] : nullptr, ref == 0); count_launch(); }
+        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dp, ref == 0); count_launch(); }
         if (ref == 0) {
-            cudaMemsetAsync(norms, 0, 4 * 8, s);
-            { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf[0], yf[1], yf[2], x64, r64, r32, norms); count_launch(); }
+            cudaMemsetAsync(norms, 0, kMaxRhs * 8, s);
+            { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf, x64, r64, r32, norms); count_launch(); }
         }
     }
-    { store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf[0], wf[1], wf[2]); count_launch(); }
+    { store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf); count_launch(); }
 }
 
 l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* diag_inv, const float* diag_inv32,
@@ -1315,42 +1406,48 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
     double* r64 = (double*)take(v * 8);
     float* r32 = (float*)take(v * 4);
     float* d32 = (float*)take(v * 4);
-    double* norms = (double*)take(8 * 8);
-    const float* yf[3] = {(const float*)y[0], nr > 1 ? (const float*)y[1] : nullptr, nr > 2 ? (const float*)y[2] : nullptr};
-    float* wf[3] = {(float*)w[0], nr > 1 ? (float*)w[1] : nullptr, nr > 2 ? (float*)w[2] : nullptr};
+    double* norms = (double*)take(2 * kMaxRhs * 8);
+    VecPack<const float> yf{};
+    VecPack<float> wf{};
+    for (int k = 0; k < nr; ++k) {
+        yf.p[k] = (const float*)y[k];
+        wf.p[k] = (float*)w[k];
+    }
     unsigned nb = nblk(n, 256);
     unsigned nbd = nb < 1024 ? nb : 1024;
     const double inner = rtol > 1e-7 ? rtol : 1e-7;
-    cudaMemsetAsync(norms, 0, 8 * 8, s);
-    { norm2_f32_kernel<<<nbd, 256, 0, s>>>(n, nr, yf[0], yf[1], yf[2], norms + 4); count_launch(); }
+    cudaMemsetAsync(norms, 0, 2 * kMaxRhs * 8, s);
+    { norm2_f32_kernel<<<nbd, 256, 0, s>>>(n, nr, yf, norms + kMaxRhs); count_launch(); }
     int total_it = 0;
     double worst = 0.0;
     bool ok = false;
-    double hn[8];
+    double hn[2 * kMaxRhs];
     for (int ref = 0; ref < 4 && !ok; ++ref) {
-        const float* rhs[3];
-        float* dst[3];
+        const float* rhs[kMaxRhs];
+        float* dst[kMaxRhs];
+        VecPack<const float> dp{};
         for (int k = 0; k < nr; ++k) {
-            rhs[k] = ref == 0 ? yf[k] : r32 + k * n;
+            rhs[k] = ref == 0 ? yf.p[k] : r32 + k * n;
             dst[k] = d32 + k * n;
+            dp.p[k] = dst[k];
         }
         cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s);
         ce = run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner,
                                   max_iter, st, s, rpb, clu);
         if (ce != cudaSuccess) return L2X_ECUDA;
-        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dst[0], nr > 1 ? dst[1] : nullptr,
-                                                 nr > 2 ? dst[2] : nullptr, ref == 0); count_launch(); }
-        cudaMemsetAsync(norms, 0, 4 * 8, s);
-        { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf[0], yf[1], yf[2], x64, r64, r32, norms); count_launch(); }
+        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dp, ref == 0); count_launch(); }
+        cudaMemsetAsync(norms, 0, kMaxRhs * 8, s);
+        { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf, x64, r64, r32, norms); count_launch(); }
         if (cudaMemcpyAsync(st_host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
-        if (cudaMemcpyAsync(hn, norms, 8 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
+        if (cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return L2X_ECUDA;
         total_it += st_host->cg_iters;
         worst = 0.0;
-        for (int k = 0; k < nr; ++k) worst = fmax(worst, hn[4 + k] > 0.0 ? sqrt(hn[k] / hn[4 + k]) : 0.0);
+        for (int k = 0; k < nr; ++k)
+            worst = fmax(worst, hn[kMaxRhs + k] > 0.0 ? sqrt(hn[k] / hn[kMaxRhs + k]) : 0.0);
         ok = worst <= rtol;
     }
-    { store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf[0], wf[1], wf[2]); count_launch(); }
+    { store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf); count_launch(); }
     if (cudaGetLastError() != cudaSuccess) return L2X_ECUDA;
     res->iters = total_it;
     res->residual = worst;
