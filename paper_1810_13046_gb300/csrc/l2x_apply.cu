@@ -376,8 +376,8 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
         for (int k = 0; k < NR; ++k) {
             const TV yi = A.y[k][i];
             A.x[k][i] = TV(0);
-            A.r[k * n + i] = yi;
-            A.u[k * n + i] = di * yi;
+            A.r[i * NR + k] = yi;
+            A.u[i * NR + k] = di * yi;
         }
     }
     // per-rhs state kept by thread k of every block (identical in all blocks)
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
                     const TV v = A.val[q];
                     const int32_t j = A.col[q];
 #pragma unroll
-                    for (int k = 0; k < NR; ++k) acc[k] += v * A.u[k * n + j];
+                    for (int k = 0; k < NR; ++k) acc[k] += v * A.u[(int64_t)j * NR + k];
                 }
             }
 #pragma unroll
@@ -407,11 +407,14 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
 #pragma unroll
                 for (int o = kRowLanes / 2; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
             }
-            if (live && glane == 0) {
+            if (live) {
+                // the xor reduction left every lane of the row with the sums: lane
+                // glane takes components glane, glane + kRowLanes, ...
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
-                    const TV ri = A.r[k * n + i], ui = A.u[k * n + i];
-                    A.w[k * n + i] = acc[k];
+                    if (k % kRowLanes != glane) continue;
+                    const TV ri = A.r[i * NR + k], ui = A.u[i * NR + k];
+                    A.w[i * NR + k] = acc[k];
                     dg[k].add(ri, ui);
                     dd[k].add(acc[k], ui);
                     dr[k].add(ri, ri);
@@ -525,8 +528,8 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
 #pragma unroll
                 for (int k = 0; k < NR; ++k) {
                     const TV rt = A.y[k][i] - acc[k];
-                    A.r[k * n + i] = rt;
-                    A.u[k * n + i] = di * rt;
+                    A.r[i * NR + k] = rt;
+                    A.u[i * NR + k] = di * rt;
                     dt[k].add(rt, rt);
                 }
             }
@@ -572,22 +575,21 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
             continue;
         }
         if (s_all || it >= A.max_iter) break;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += kPcgBlock) {
-            const TV di = A.dinv[i];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                if (s_conv[k]) continue;
-                const int64_t o = k * n + i;
-                const TV b = (TV)s_beta[k], a = (TV)s_alpha[k];
-                const TV pn = it_local == 0 ? A.u[o] : A.u[o] + b * A.p[o];
-                const TV sn = it_local == 0 ? A.w[o] : A.w[o] + b * A.s[o];
-                A.p[o] = pn;
-                A.s[o] = sn;
-                A.x[k][i] += a * pn;
-                const TV rn = A.r[o] - a * sn;
-                A.r[o] = rn;
-                A.u[o] = di * rn;
-            }
+        // one thread per (row, component): the interleaved vectors are read and
+        // written contiguously
+        for (int64_t o = r0 * NR + threadIdx.x; o < r1 * NR; o += kPcgBlock) {
+            const int64_t i = o / NR;
+            const int k = (int)(o - i * NR);
+            if (s_conv[k]) continue;
+            const TV b = (TV)s_beta[k], a = (TV)s_alpha[k];
+            const TV pn = it_local == 0 ? A.u[o] : A.u[o] + b * A.p[o];
+            const TV sn = it_local == 0 ? A.w[o] : A.w[o] + b * A.s[o];
+            A.p[o] = pn;
+            A.s[o] = sn;
+            A.x[k][i] += a * pn;
+            const TV rn = A.r[o] - a * sn;
+            A.r[o] = rn;
+            A.u[o] = A.dinv[i] * rn;
         }
         grid.sync();
         ++it;

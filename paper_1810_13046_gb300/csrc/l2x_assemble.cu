@@ -340,31 +340,36 @@ __global__ void __launch_bounds__(kSortWarps * 32) transpose_sort_kernel(const i
     __shared__ int32_t sk[kSortWarps][kSortMax];
     __shared__ double sv[kSortWarps][kSortMax];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t li = blockIdx.x * (int64_t)kSortWarps + w;
-    if (li >= *n_list || (st->flags & kAbortFlags)) return;
-    const int64_t i = list[li];
-    const int64_t lo = ptr[i], hi = ptr[i + 1];
-    const int len = (int)(hi - lo);
-    if (len <= 1) return;
-    if (len <= kSortMax) {
-        for (int a = lane; a < len; a += 32) {
-            sk[w][a] = key[lo + a];
-            sv[w][a] = val[lo + a];
+    if (st->flags & kAbortFlags) return;
+    const int64_t nl = *n_list;
+    // grid-stride over the listed rows (the launch is sized for the SMs, not for
+    // the row capacity, which inside a captured step covers the whole grid)
+    for (int64_t li = blockIdx.x * (int64_t)kSortWarps + w; li < nl; li += (int64_t)gridDim.x * kSortWarps) {
+        const int64_t i = list[li];
+        const int64_t lo = ptr[i], hi = ptr[i + 1];
+        const int len = (int)(hi - lo);
+        if (len <= 1) continue;
+        if (len <= kSortMax) {
+            __syncwarp();
+            for (int a = lane; a < len; a += 32) {
+                sk[w][a] = key[lo + a];
+                sv[w][a] = val[lo + a];
+            }
+            __syncwarp();
+            for (int a = lane; a < len; a += 32) {
+                const int32_t k = sk[w][a];
+                int rank = 0;
+                for (int b = 0; b < len; ++b) rank += sk[w][b] < k;
+                key[lo + rank] = k;
+                val[lo + rank] = sv[w][a];
+            }
+            continue;
         }
-        __syncwarp();
-        for (int a = lane; a < len; a += 32) {
-            const int32_t k = sk[w][a];
-            int rank = 0;
-            for (int b = 0; b < len; ++b) rank += sk[w][b] < k;
-            key[lo + rank] = k;
-            val[lo + rank] = sv[w][a];
+        // longer rows: sorted by transpose_sort_long_kernel, one block each
+        if (lane == 0) {
+            const int32_t slot = atomicAdd(n_long, 1);
+            if (slot < long_cap) long_rows[slot] = (int32_t)i;
         }
-        return;
-    }
-    // longer rows: sorted by transpose_sort_long_kernel, one block each
-    if (lane == 0) {
-        const int32_t slot = atomicAdd(n_long, 1);
-        if (slot < long_cap) long_rows[slot] = (int32_t)i;
     }
 }
 
@@ -519,7 +524,9 @@ void launch_transpose_sort(const CsrT& T, const DevStatus* st, cudaStream_t s) {
     const int64_t n = T.list_cap < T.n_rows ? T.list_cap : T.n_rows;
     if (n <= 0) return;
     cudaMemsetAsync(T.n_long, 0, sizeof(int32_t), s);
-    { transpose_sort_kernel<<<nblk(n, kSortWarps), kSortWarps * 32, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val, st, T.long_rows, T.n_long, T.long_cap); count_launch(); }
+    unsigned nb = nblk(n, kSortWarps);
+    if (nb > 152 * 16) nb = 152 * 16;
+    { transpose_sort_kernel<<<nb, kSortWarps * 32, 0, s>>>(T.list, T.n_list, T.ptr, T.col, T.val, st, T.long_rows, T.n_long, T.long_cap); count_launch(); }
     static bool attr_set = false;
     const int smem = (int)((sizeof(double) + sizeof(int32_t)) * kSortLongMax);
     if (!attr_set) {
