@@ -143,6 +143,10 @@ __global__ void __launch_bounds__(256) clip_fused_kernel(int G, SubGridSet sgs, 
                                                                   double* __restrict__ blocks,
                                                                   double* __restrict__ vols, DevStatus* st) {
     constexpr int NA = D + 1, NB = 1 << D;
+    // this thread's polygon buffers: on-chip shared memory instead of local
+    // memory (whose lines the resident threads would evict from L1)
+    extern __shared__ double s_poly[];
+    double (*poly)[D] = reinterpret_cast<double (*)[D]>(s_poly + threadIdx.x * PolySlot<D>::kDoubles);
     const int64_t n = min(offsets[(int64_t)G * m], n_cap);
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(256) clip_fused_kernel(int G, SubGridSet sgs, 
 #pragma unroll
             for (int k = 0; k < D; ++k) gr[a][k] = __ldg(elem_grad + ((int64_t)e * NA + a) * D + k);
         const double scale = frame_scale<D>(sg, w, gr);
-        pair_integrals<D, R>(T, gr, flag == 1, scale, blk, &vol);
+        pair_integrals<D, R>(T, gr, flag == 1, scale, blk, &vol, poly);
     }
 #pragma unroll
     for (int j = 0; j < NA * NB; ++j) blocks[p * (NA * NB) + j] = blk[j];
@@ -203,7 +207,8 @@ __global__ void clip_plain_kernel(SubGrid sg, const double* __restrict__ X, cons
         for (int i = 0; i < NA * NB; ++i) blk[i] = 0.0;
     } else {
         const double scale = frame_scale<D>(sg, w, ge);
-        pair_integrals<D, double>(T, ge, pos, scale, blk, &vol);
+        double poly[2 * kMaxPoly][D];
+        pair_integrals<D, double>(T, ge, pos, scale, blk, &vol, poly);
     }
     for (int i = 0; i < NA * NB; ++i) blocks[p * (NA * NB) + i] = blk[i];
     vols[p] = vol;
@@ -278,13 +283,27 @@ void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t
     if (block != 64 && block != 128 && block != 256) block = kClipThreads;
     const int kClipThreads = block;
     const unsigned nb = (unsigned)((n_launch + kClipThreads - 1) / kClipThreads);
+    // dynamic shared memory of the polygon buffers (opt-in above 48 KB, set once,
+    // outside stream capture: the first launch comes from a build)
+    static bool smem_set = false;
+    if (!smem_set) {
+        const int mx2 = 256 * PolySlot<2>::kDoubles * (int)sizeof(double);
+        const int mx3 = 256 * PolySlot<3>::kDoubles * (int)sizeof(double);
+        cudaFuncSetAttribute(clip_fused_kernel<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx2);
+        cudaFuncSetAttribute(clip_fused_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx2);
+        cudaFuncSetAttribute(clip_fused_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx3);
+        cudaFuncSetAttribute(clip_fused_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx3);
+        smem_set = true;
+    }
+    const size_t sm2 = (size_t)kClipThreads * PolySlot<2>::kDoubles * sizeof(double);
+    const size_t sm3 = (size_t)kClipThreads * PolySlot<3>::kDoubles * sizeof(double);
 #define L2X_CLIP_ARGS G, sgs, m, offsets, n_cap, X, E, elem_grad, elem_flag, perm, pair_elem, pair_cell, blocks, vols, st
     if (dim == 2) {
-        if (precision == L2X_MIXED) { clip_fused_kernel<2, float><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
-        else { clip_fused_kernel<2, double><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        if (precision == L2X_MIXED) { clip_fused_kernel<2, float><<<nb, kClipThreads, sm2, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        else { clip_fused_kernel<2, double><<<nb, kClipThreads, sm2, s>>>(L2X_CLIP_ARGS); count_launch(); }
     } else {
-        if (precision == L2X_MIXED) { clip_fused_kernel<3, float><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
-        else { clip_fused_kernel<3, double><<<nb, kClipThreads, 0, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        if (precision == L2X_MIXED) { clip_fused_kernel<3, float><<<nb, kClipThreads, sm3, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        else { clip_fused_kernel<3, double><<<nb, kClipThreads, sm3, s>>>(L2X_CLIP_ARGS); count_launch(); }
     }
 #undef L2X_CLIP_ARGS
 }

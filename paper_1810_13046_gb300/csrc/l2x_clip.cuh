@@ -13,8 +13,11 @@
 //    (segments in 2-D) and coned to an apex A, which turns the polytope into
 //    signed simplices (divergence theorem).  A is an element vertex lying in
 //    the cell when there is one (then the element faces through it drop out
-//    and every cone is non-negative), else the centre of the overlap of the
-//    element's bounding box with the cell.
+//    and every cone is non-negative).  Otherwise, in 3-D, A lies on one crossed
+//    cell plane of every axis the element crosses (so the cones over those
+//    cell faces have zero volume and the faces drop out) and at the centre of
+//    the overlap of the element's bounding box with the cell along the other
+//    axes.
 //  * On each cone simplex (0, p, q[, r]) in u = t - A the monomial moments
 //    needed for lambda_a psi_b (u^S and u_j u^S, S a subset of the axes) are
 //    exact closed forms: for a simplex T and monomial prod_j u_{k_j} of degree
@@ -32,6 +35,12 @@
 namespace l2x {
 
 constexpr int kMaxPoly = 10;  // triangle + 6 planes -> 9; square + 4 planes -> 8
+// doubles of one thread's polygon buffers in shared memory: 2 * kMaxPoly
+// vertices plus one pad (an odd stride keeps a warp's accesses conflict-free)
+template <int D>
+struct PolySlot {
+    static constexpr int kDoubles = 2 * kMaxPoly * D + 1;
+};
 
 template <int D>
 struct ElemT {
@@ -426,7 +435,7 @@ __device__ __forceinline__ int pair_class(const double (&T)[D + 1][D]) {
 // (d+1)*2^d block and the intersection volume.
 template <int D, typename R>
 __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D + 1][D], bool positive,
-                               double scale, double* block, double* vol) {
+                               double scale, double* block, double* vol, double (*poly)[D]) {
     constexpr int NB = 1 << D;
     constexpr int NA = D + 1;
     using L = MomentLayout<D>;
@@ -443,6 +452,10 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     for (int k = 0; k < D; ++k) {
         if (apex_v >= 0) {
             A[k] = T[apex_v][k];
+        } else if (D == 3 && ((lower_mask >> k) & 1)) {
+            A[k] = 0.0;  // on the crossed plane: its cell face has a zero-volume cone
+        } else if (D == 3 && ((upper_mask >> k) & 1)) {
+            A[k] = 1.0;
         } else {
             const double lo = from_order_key(max(kmin[k], 0LL));
             const double hi = from_order_key(min(kmax[k], K1));
@@ -469,7 +482,9 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     R acc[L::kN];
 #pragma unroll
     for (int i = 0; i < L::kN; ++i) acc[i] = R(0);
-    double bufA[kMaxPoly][D], bufB[kMaxPoly][D];
+    // the two polygon buffers (2 * kMaxPoly vertices), owned by the caller
+    double (*bufA)[D] = poly;
+    double (*bufB)[D] = poly + kMaxPoly;
     if constexpr (D == 2) {
         // P = triangle clipped by the crossed cell lines (counter-clockwise), then
         // re-centred on its first vertex, which becomes the apex.
@@ -553,9 +568,11 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
             }
             accum_polygon<D, R>(cur, n, acc);
         }
-        // cell faces the element crosses, clipped to the element
+        // cell faces the element crosses, clipped to the element (a face whose
+        // plane holds the apex spans a cone of zero volume and is skipped)
 #pragma unroll 1
         for (int jp = 0; jp < n_planes; ++jp) {
+            if (plane_c[jp] == 0.0) continue;
             const int k = plane_k[jp];
             const int side = plane_up[jp];
             const int j1 = (k + 1) % 3, j2 = (k + 2) % 3;
