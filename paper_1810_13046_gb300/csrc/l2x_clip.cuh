@@ -11,13 +11,13 @@
 //    the cell faces clipped to the element (against the d+1 planes
 //    lambda_a = 0).  Every boundary polygon is fanned into triangles
 //    (segments in 2-D) and coned to an apex A, which turns the polytope into
-//    signed simplices (divergence theorem).  A is an element vertex lying in
-//    the cell when there is one (then the element faces through it drop out
-//    and every cone is non-negative).  Otherwise, in 3-D, A lies on one crossed
+//    signed simplices (divergence theorem).  In 3-D, A lies on one crossed
 //    cell plane of every axis the element crosses (so the cones over those
 //    cell faces have zero volume and the faces drop out) and at the centre of
 //    the overlap of the element's bounding box with the cell along the other
-//    axes.
+//    axes; an element inside the cell takes one of its vertices (the element
+//    faces through it drop out).  In 2-D the clipped polygon is fanned from
+//    its first vertex.
 //  * On each cone simplex (0, p, q[, r]) in u = t - A the monomial moments
 //    needed for lambda_a psi_b (u^S and u_j u^S, S a subset of the axes) are
 //    exact closed forms: for a simplex T and monomial prod_j u_{k_j} of degree
@@ -446,7 +446,9 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     long long kmin[D], kmax[D];
     int lower_mask, upper_mask, inside_mask;
     if (!classify_pair<D>(T, kmin, kmax, lower_mask, upper_mask, inside_mask)) return;  // no overlap of positive measure
-    const int apex_v = inside_mask ? __ffs(inside_mask) - 1 : -1;
+    // 3-D: an element vertex is the apex only when the element crosses no cell
+    // plane; otherwise the apex sits on the crossed planes (fewer faces to clip)
+    const int apex_v = (inside_mask && (D == 2 || (lower_mask | upper_mask) == 0)) ? __ffs(inside_mask) - 1 : -1;
     double A[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
