@@ -59,10 +59,10 @@ WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 flops per candidate pair executed by the fused clip kernel (mixed form) on this workload:
 # ncu SASS instruction counters of one launch over the three grids,
-# (2*DFMA + DADD + DMUL) / pairs = 497.3e6 / 716130; DRAM bytes per pair from the same capture
-# (read + write, 383.5e6 / 716130).  profiles/clip_fused_beam128.md.
-FP64_FLOPS_PER_PAIR = 694.4
-CLIP_DRAM_BYTES_PER_PAIR = 535.5
+# (2*DFMA + DADD + DMUL) / pairs = 266.4e6 / 716130; DRAM bytes per pair from the same capture
+# (read + write, 186.7e6 / 716130).  profiles/clip_fused_beam128.md.
+FP64_FLOPS_PER_PAIR = 372.0
+CLIP_DRAM_BYTES_PER_PAIR = 260.7
 
 
 def parse():
