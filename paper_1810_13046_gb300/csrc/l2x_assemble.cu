@@ -50,10 +50,15 @@ __global__ void segment_sort_kernel(int64_t n, const int64_t* __restrict__ ptr, 
     }
 }
 
-// Warp per element: node-box matrix of the element on one grid.  Lane = node of
-// the box; it sums, over the (up to 2^d) candidate cells of the element around
-// that node in z, y, x order, block[a][corner] of the pairs whose intersection
-// volume is positive.  Fixed order, registers only: reproducible.
+// kLocLanes lanes per element: node-box matrix of the element on one grid.  A
+// lane takes nodes of the box; for each it sums, over the (up to 2^d) candidate
+// cells of the element around that node in z, y, x order, block[a][corner] of
+// the pairs whose intersection volume is positive.  Fixed order, registers
+// only: reproducible.  Boxes hold 8 to 27 nodes for elements about a cell in
+// size, so several elements share a warp (more elements in flight hide the
+// latency of their dependent loads).
+constexpr int kLocLanes = 4;
+
 template <int D>
 __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, const int64_t* __restrict__ offsets,
                                   const int64_t* __restrict__ loc_off, int64_t loc_cap,
@@ -61,8 +66,8 @@ __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, 
                                   double* __restrict__ loc_val, uint8_t* __restrict__ loc_flag, int dual,
                                   DevStatus* st) {
     constexpr int NA = D + 1, NB = 1 << D;
-    const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kLocLanes;
+    const int lane = threadIdx.x % kLocLanes;
     if (e >= m || (st->flags & kAbortFlags)) return;
     const ElemBox b = boxes[e];
     const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = D == 3 ? box_ext(b, 2) : 1;
@@ -75,7 +80,7 @@ __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, 
     const int nbx = ex + 1, nby = ey + 1;
     const int64_t nbox = L1 - L0;
     const int64_t q0 = offsets[e];
-    for (int64_t jj = lane; jj < nbox; jj += 32) {
+    for (int64_t jj = lane; jj < nbox; jj += kLocLanes) {
         const int jx = (int)(jj % nbx);
         const int64_t r = jj / nbx;
         const int jy = (int)(r % nby), jz = (int)(r / nby);
@@ -458,7 +463,7 @@ void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t
                        const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
                        double* loc_val, uint8_t* loc_flag, int dual, DevStatus* st, cudaStream_t s) {
     if (m <= 0) return;
-    const unsigned nb = nblk(m * 32, 256);
+    const unsigned nb = nblk(m * kLocLanes, 256);
     if (dim == 2) { elem_local_kernel<2><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
     else { elem_local_kernel<3><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
 }
