@@ -182,6 +182,9 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
                 const int64_t r = idx / nx;
                 jy = lo[1] + (int)(r % ny);
                 jz = lo[2] + (int)(r / ny);
+                // the element-local matrices hold exact zeros at untouched nodes, so
+                // the value is read without waiting for the flag (same sums)
+#pragma unroll 4
                 for (int64_t t = a0; t < a1; ++t) {
                     const int32_t ea = staged ? s_ea[w][t - a0] : adj[t];
                     const ElemBox b = staged ? s_box[w][t - a0] : boxes[ea >> 2];
@@ -190,10 +193,8 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
                     if (ux < 0 || ux > ex || uy < 0 || uy > ey || uz < 0 || (D == 3 && uz > ez)) continue;
                     const int64_t L0 = staged ? s_off[w][t - a0] : loc_off[ea >> 2];
                     const int64_t li = L0 + ux + (int64_t)(ex + 1) * (uy + (int64_t)(ey + 1) * uz);
-                    if (loc_flag[li]) {
-                        touched = true;
-                        if (pass == 1) acc += loc_val[li * NA + (ea & 3)];
-                    }
+                    touched |= loc_flag[li] != 0;
+                    if (pass == 1) acc += loc_val[li * NA + (ea & 3)];
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, touched);
