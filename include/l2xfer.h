@@ -287,9 +287,10 @@ l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t
  * (64, 128, 256) and the form of the Jacobi-PCG: the grid-wide cooperative
  * kernel with 32 to 1024 rows per block, or, when the search direction fits,
  * one thread-block cluster of 8 or 16 CTAs holding it in distributed shared
- * memory.  Call after a build; later builds, solves and captured steps use the
- * choice (reported in l2x_info).  Runs the clip kernel and the solve a few times
- * on the stream and synchronises it. */
+ * memory.  The combined solve of a captured step (both transfers at once) gets
+ * its own rows per block.  Call after a build; later builds, solves and
+ * captured steps use the choice (reported in l2x_info).  Runs the clip kernel
+ * and the solves a few times on the stream and synchronises it. */
 l2x_status l2x_autotune(l2x_handle h, void* stream);
 
 /* Sets the work shape l2x_autotune would pick: clip_block in {64, 128, 256},

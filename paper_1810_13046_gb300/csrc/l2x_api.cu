@@ -90,6 +90,7 @@ struct l2x_coupling {
     int clip_block = 128;            // threads (= pairs) per block of the clip kernel
     int pcg_rpb = 64;                // rows per block of the cooperative PCG
     int pcg_clu = 0;                 // > 0: single-cluster PCG with this many CTAs
+    int pcg_rpb_step = 64;           // rows per block of a captured step's combined (2G right-hand sides) solve
     double tuned_clip_ms = 0.0, tuned_solve_ms = 0.0;
     // last solve
     int cg_iters = 0;
@@ -690,7 +691,7 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
             ws[G + g] = zf[g];
         }
         solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, 2 * G, ys, ws, h->opts.cg_rtol,
-                             h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb, h->pcg_clu);
+                             h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb_step, 0);
         if (zero_force)
             for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
         launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)zf, f_f,
@@ -1255,7 +1256,7 @@ l2x_status l2x_autotune(l2x_handle h, void* stream) {
         void* y[kMaxGrids];
         void* w[kMaxGrids];
         char* tmp = nullptr;
-        if (cudaMalloc((void**)&tmp, es * n * G * 2) != cudaSuccess) status = fail(L2X_ENOMEM, "autotune scratch");
+        if (cudaMalloc((void**)&tmp, es * n * G * 4) != cudaSuccess) status = fail(L2X_ENOMEM, "autotune scratch");
         if (status == L2X_OK) {
             for (int g = 0; g < G; ++g) {
                 y[g] = tmp + es * n * g;
@@ -1292,6 +1293,28 @@ l2x_status l2x_autotune(l2x_handle h, void* stream) {
             h->pcg_rpb = best_rpb;
             h->pcg_clu = best_clu;
             h->tuned_solve_ms = best;
+            if (h->opts.multiplier == L2X_MULT_STANDARD && 2 * G <= 6) {
+                // the combined solve of a captured step (both transfers, 2G right-hand sides)
+                const void* y2[2 * kMaxGrids];
+                void* w2[2 * kMaxGrids];
+                for (int g = 0; g < 2 * G; ++g) {
+                    y2[g] = y[g % G];
+                    w2[g] = tmp + es * n * (2 * G + g);
+                }
+                float best2 = 1e30f;
+                int best2_rpb = h->pcg_rpb_step;
+                for (int rpb : {32, 64, 128, 256, 512, 1024}) {
+                    const float ms = timed([&] {
+                        solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, 2 * G, y2, w2,
+                                             h->opts.cg_rtol, h->opts.cg_max_iter, h->pcg_ws, h->st, s, rpb, 0);
+                    });
+                    if (ms < best2) {
+                        best2 = ms;
+                        best2_rpb = rpb;
+                    }
+                }
+                h->pcg_rpb_step = best2_rpb;
+            }
             cudaStreamSynchronize(s);
             cudaFree(tmp);
         }
@@ -1311,6 +1334,7 @@ l2x_status l2x_set_work_shape(l2x_handle h, int32_t clip_block, int32_t pcg_rows
         return fail(L2X_EINVAL, "the system does not fit one cluster of that size");
     h->clip_block = clip_block;
     h->pcg_rpb = pcg_rows_per_block;
+    h->pcg_rpb_step = pcg_rows_per_block;
     h->pcg_clu = pcg_cluster;
     return L2X_OK;
 }
