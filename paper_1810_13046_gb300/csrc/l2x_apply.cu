@@ -275,6 +275,7 @@ struct PcgArgs {
     TV* w;
     double* partial;  // gridDim.x * 3 * kMaxRhs
     double rtol;
+    const double* rtol_k;  // optional per right-hand-side tolerances (device), in place of rtol
     int max_iter;
     DevStatus* st;
 };
@@ -484,7 +485,8 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
                 const double gam = s_tot[3 * k], del = s_tot[3 * k + 1];
                 rho = s_tot[3 * k + 2];
                 if (it == 0) rho0 = rho;
-                const bool conv = rho <= A.rtol * A.rtol * rho0;
+                const double tol = A.rtol_k ? A.rtol_k[k] : A.rtol;
+                const bool conv = rho <= tol * tol * rho0;
                 double beta = 0.0;
                 if (!conv) {
                     if (it_local == 0) {
@@ -719,7 +721,8 @@ __global__ void __launch_bounds__(kCluThreads, 1) pcg_cluster_kernel(PcgArgs<TV>
             const double gam = s_tot[3 * k], del = s_tot[3 * k + 1];
             rho = s_tot[3 * k + 2];
             if (it == 0 && it_local == 0 && restarts == 0) rho0 = rho;
-            const bool conv = rho <= A.rtol * A.rtol * rho0;
+            const double tol = A.rtol_k ? A.rtol_k[k] : A.rtol;
+            const bool conv = rho <= tol * tol * rho0;
             double beta = 0.0;
             if (!conv) {
                 if (it_local == 0) {
@@ -962,6 +965,17 @@ __global__ void norm2_f32_kernel(int64_t n, int nr, VecPack<const float> y, doub
     }
 }
 
+// Tolerance of the FP32 correction solve of right-hand side k: the residual
+// ||y - M x|| must end at rtol ||y||, and the correction solve M d = r reduces
+// ||r|| by its relative tolerance, so tau_k = rtol ||y_k|| / ||r_k||, kept in
+// [1e-7, 1] (FP32 cannot do better than about 1e-7).
+__global__ void inner_tol_kernel(int nr, double rtol, const double* rr, const double* yy, double* tau) {
+    const int k = threadIdx.x;
+    if (k >= nr) return;
+    double t = rr[k] > 0.0 ? rtol * sqrt(yy[k] / rr[k]) : 1.0;
+    tau[k] = fmin(1.0, fmax(1e-7, t));
+}
+
 __global__ void store_f32_kernel(int64_t n, int nr, const double* x64, VecPack<float> w) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1027,7 +1041,8 @@ void prepare_cluster_kernel() {
 template <typename TV>
 cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val, const TV* dinv, int64_t n,
                           int nr, const TV* const* y, TV* const* x, TV* vecs, double* partial, double rtol,
-                          int max_iter, DevStatus* st, cudaStream_t s, int rpb = 64, int clu = 0) {
+                          int max_iter, DevStatus* st, cudaStream_t s, int rpb = 64, int clu = 0,
+                          const double* rtol_k = nullptr) {
     PcgArgs<TV> A{};
     A.n = n;
     A.nrhs = nr;
@@ -1047,6 +1062,7 @@ cudaError_t run_pcg_fused(const int64_t* ptr, const int32_t* col, const TV* val,
     A.w = vecs + 4 * stride;
     A.partial = partial;
     A.rtol = rtol;
+    A.rtol_k = rtol_k;
     A.max_iter = max_iter;
     A.st = st;
     void* args[] = {&A};
@@ -1299,10 +1315,14 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
         yf.p[k] = (const float*)y[k];
         wf.p[k] = (float*)w[k];
     }
+    double* tau = (double*)take(kMaxRhs * 8);
     const unsigned nb = nblk(n, 256);
     const unsigned nbd = nb < 1024 ? nb : 1024;
     const double inner = rtol > 1e-7 ? rtol : 1e-7;
-    // one FP32 solve and one FP64 residual correction, fixed (no host decisions)
+    cudaMemsetAsync(norms + kMaxRhs, 0, kMaxRhs * 8, s);
+    { norm2_f32_kernel<<<nbd, 256, 0, s>>>(n, nr, yf, norms + kMaxRhs); count_launch(); }
+    // one FP32 solve and one FP64 residual correction, fixed (no host decisions);
+    // the correction solve stops at the tolerance that brings the residual to rtol
     for (int ref = 0; ref < 2; ++ref) {
         const float* rhs[kMaxRhs];
         float* dst[kMaxRhs];
@@ -1312,11 +1332,13 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
             dst[k] = d32 + k * n;
             dp.p[k] = dst[k];
         }
-        run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s, rpb, clu);
+        run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s,
+                             rpb, clu, ref == 0 ? nullptr : tau);
         { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dp, ref == 0); count_launch(); }
         if (ref == 0) {
             cudaMemsetAsync(norms, 0, kMaxRhs * 8, s);
             { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf, x64, r64, r32, norms); count_launch(); }
+            { inner_tol_kernel<<<1, 32, 0, s>>>(nr, rtol, norms, norms + kMaxRhs, tau); count_launch(); }
         }
     }
     { store_f32_kernel<<<nb, 256, 0, s>>>(n, nr, x64, wf); count_launch(); }
@@ -1424,6 +1446,7 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
     double worst = 0.0;
     bool ok = false;
     double hn[2 * kMaxRhs];
+    double* tau = (double*)take(kMaxRhs * 8);
     for (int ref = 0; ref < 4 && !ok; ++ref) {
         const float* rhs[kMaxRhs];
         float* dst[kMaxRhs];
@@ -1434,8 +1457,9 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
             dp.p[k] = dst[k];
         }
         cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s);
+        if (ref > 0) { inner_tol_kernel<<<1, 32, 0, s>>>(nr, rtol, norms, norms + kMaxRhs, tau); count_launch(); }
         ce = run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner,
-                                  max_iter, st, s, rpb, clu);
+                                  max_iter, st, s, rpb, clu, ref == 0 ? nullptr : tau);
         if (ce != cudaSuccess) return L2X_ECUDA;
         { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dp, ref == 0); count_launch(); }
         cudaMemsetAsync(norms, 0, kMaxRhs * 8, s);
