@@ -246,9 +246,12 @@ l2x_status l2x_picard_converged(const double* norms, double eps_abs, double eps_
  * coords_src (device, n_nodes x dim, read at replay time), rebuilds B_g, B_g^T
  * and S, writes u_s = S^-1 B u_f and f_f (+)= s B^T (S^-1) f_s (zeroed first
  * if zero_force != 0); all pointers are fixed at creation.  Pair and entry
- * capacities are the current sizes times capacity_margin (>= 1); a replay that
- * needs more sets a flag and skips its work, reported by l2x_graph_sync_status
- * as L2X_ECAPACITY (create the graph again).  Fused path only; `stream` must
+ * capacities are the current sizes times capacity_margin (>= 1), and the rows of
+ * B^T cover the fluid nodes the mesh touches at creation, padded on every side
+ * by capacity_margin - 1 times the touched extent (at least 2 nodes); a replay
+ * that needs more, or whose mesh leaves that box, sets a flag and skips its
+ * work, reported by l2x_graph_sync_status as L2X_ECAPACITY (create the graph
+ * again).  Fused path only; `stream` must
  * not be the legacy default stream.  While a graph exists, use the handle only
  * through it.  l2x_graph_sync_status waits for the stream and returns the
  * status of the last replay (capacity, degenerate or out-of-grid elements, CG). */

@@ -1,5 +1,6 @@
 // C-ABI entry points of l2xfer: handle management and the orchestration of the
 // assembly (steps I-IV of Sec. 2.3) and of the two transfers.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <memory>
@@ -573,6 +574,8 @@ l2x_status check_ptrs(const void* const* a, int n, const char* what) {
     return L2X_OK;
 }
 
+int64_t fluid_nodes(const SubGrid& sg) { return (int64_t)sg.nnode[0] * sg.nnode[1] * sg.nnode[2]; }
+
 // Velocity transfer without host synchronisation (fused path): B u_f with the
 // division by a diagonal S fused in, or B u_f followed by the cooperative PCG
 // (fixed schedule in the mixed form; non-convergence recorded in the status).
@@ -632,8 +635,20 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     const int G = h->n_grids, d = h->dim;
     L2X_CUDA(cudaMemcpyAsync(h->X, coords_src, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
     launch_reset_status(h->st, s);
+    launch_node_box_reset(h->node_box, G, s);
     launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->nbox, h->node_box, h->elem_vol,
                       h->elem_grad, h->elem_flag, h->st, s);
+    {
+        // the B^T rows of the captured step cover a fixed box: a step that leaves it
+        // is flagged here, before any kernel indexes rows by the box
+        NodeBoxSet lim{};
+        for (int g = 0; g < G; ++g)
+            for (int k = 0; k < 3; ++k) {
+                lim.lo[g][k] = h->T[g].lo[k];
+                lim.hi[g][k] = h->T[g].lo[k] + h->T[g].n[k] - 1;
+            }
+        launch_check_node_box(h->node_box, lim, G, h->st, s);
+    }
     launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
     launch_scan_i64(h->nbox, h->loc_off, (int64_t)G * m, h->scan_tmp, s);
     launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, h->pair_cap, h->st, s);
@@ -693,14 +708,14 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, 2 * G, ys, ws, h->opts.cg_rtol,
                              h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb_step, 0);
         if (zero_force)
-            for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
+            for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * fluid_nodes(h->sg[g]), s));
         launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)zf, f_f,
                        h->opts.force_scale, h->st, s);
         return L2X_OK;
     }
     enqueue_velocity(h, u_f, u_s, s);
     if (zero_force)
-        for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * h->T[g].n_rows, s));
+        for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * fluid_nodes(h->sg[g]), s));
     enqueue_force(h, f_s, f_f, s);
     return L2X_OK;
 }
@@ -1052,6 +1067,8 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
         L2X_TRY(dalloc(&h->pair_perm, pcap));
         h->pair_cap = pcap;
     }
+    int32_t nbh[kMaxGrids * 6];  // touched-node boxes of the last assembly
+    L2X_CUDA(cudaMemcpyAsync(nbh, h->node_box, sizeof(int32_t) * 6 * G, cudaMemcpyDeviceToHost, s));
     {
         int64_t loc_total = 0;
         L2X_CUDA(cudaMemcpyAsync(&loc_total, h->loc_off + (int64_t)G * h->n_elems, sizeof(int64_t),
@@ -1086,10 +1103,21 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
             L2X_TRY(dalloc(&T.val32, h->B_cap[g]));
             h->T_cap[g] = h->B_cap[g];
         }
+        // B^T rows over the nodes the mesh touches now, padded on every side by the
+        // capacity margin (at least 2 nodes); replays that leave the box report
+        // L2X_ECAPACITY
         int64_t rows = 1;
         for (int k = 0; k < 3; ++k) {
-            T.lo[k] = 0;
-            T.n[k] = h->sg[g].nnode[k];
+            const int nn = h->sg[g].nnode[k];
+            int lo = 0, hi = nn - 1;
+            if (k < d && nbh[g * 6 + k] <= nbh[g * 6 + 3 + k]) {
+                const int ext = nbh[g * 6 + 3 + k] - nbh[g * 6 + k] + 1;
+                const int pad = 2 + (int)std::ceil((capacity_margin - 1.0) * ext);
+                lo = std::max(0, nbh[g * 6 + k] - pad);
+                hi = std::min(nn - 1, nbh[g * 6 + 3 + k] + pad);
+            }
+            T.lo[k] = lo;
+            T.n[k] = hi - lo + 1;
             rows *= T.n[k];
         }
         T.n_rows = rows;

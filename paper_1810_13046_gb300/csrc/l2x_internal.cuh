@@ -100,6 +100,16 @@ void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
                        cudaStream_t s);
 void launch_reset_status(DevStatus* st, cudaStream_t s);
 // FLAG_CAPACITY if *total > cap (device value); kernels after it skip their work
+// Box of fluid nodes (inclusive bounds per axis) that a captured step's B^T rows cover, per grid.
+struct NodeBoxSet {
+    int32_t lo[kMaxGrids][3];
+    int32_t hi[kMaxGrids][3];
+};
+// node_box (6 per grid: min x,y,z then max x,y,z) set to empty.
+void launch_node_box_reset(int32_t* node_box, int n_grids, cudaStream_t s);
+// FLAG_CAPACITY if a grid's touched nodes leave lim.
+void launch_check_node_box(const int32_t* node_box, const NodeBoxSet& lim, int n_grids, DevStatus* st,
+                           cudaStream_t s);
 void launch_check_capacity(const int64_t* total, int64_t cap, DevStatus* st, cudaStream_t s);
 
 // clipping + quadrature (l2x_clip.cu).  Pair blocks are stored pair-major:

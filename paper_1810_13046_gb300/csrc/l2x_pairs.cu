@@ -247,6 +247,24 @@ __global__ void reset_status_kernel(DevStatus* st) {
     }
 }
 
+// Empty touched-node boxes (min = INT_MAX, max = INT_MIN) before the element pass.
+__global__ void node_box_reset_kernel(int32_t* node_box, int n_grids) {
+    const int t = threadIdx.x;
+    if (t < 6 * n_grids) node_box[t] = (t % 6) < 3 ? INT_MAX : INT_MIN;
+}
+
+// A captured step's B^T rows cover a fixed box per grid: flag a step whose
+// touched nodes leave it (its later kernels then skip their work).
+__global__ void check_node_box_kernel(const int32_t* node_box, NodeBoxSet lim, int n_grids, DevStatus* st) {
+    const int g = threadIdx.x;
+    if (g >= n_grids) return;
+    for (int k = 0; k < 3; ++k) {
+        const int lo = node_box[g * 6 + k], hi = node_box[g * 6 + 3 + k];
+        if (lo > hi) continue;  // no element on this grid
+        if (lo < lim.lo[g][k] || hi > lim.hi[g][k]) atomicOr(&st->flags, FLAG_CAPACITY);
+    }
+}
+
 __global__ void check_capacity_kernel(const int64_t* total, int64_t cap, DevStatus* st) {
     if (threadIdx.x == 0 && *total > cap) atomicOr(&st->flags, FLAG_CAPACITY);
 }
@@ -255,6 +273,15 @@ __global__ void check_capacity_kernel(const int64_t* total, int64_t cap, DevStat
 
 void launch_reset_status(DevStatus* st, cudaStream_t s) {
     { reset_status_kernel<<<1, 32, 0, s>>>(st); count_launch(); }
+}
+
+void launch_node_box_reset(int32_t* node_box, int n_grids, cudaStream_t s) {
+    { node_box_reset_kernel<<<1, 32, 0, s>>>(node_box, n_grids); count_launch(); }
+}
+
+void launch_check_node_box(const int32_t* node_box, const NodeBoxSet& lim, int n_grids, DevStatus* st,
+                           cudaStream_t s) {
+    { check_node_box_kernel<<<1, 32, 0, s>>>(node_box, lim, n_grids, st); count_launch(); }
 }
 
 void launch_check_capacity(const int64_t* total, int64_t cap, DevStatus* st, cudaStream_t s) {
