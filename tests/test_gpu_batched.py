@@ -94,3 +94,35 @@ def test_step_graph_reports_capacity_overflow():
     src.copy_(torch.from_numpy(X0).cuda())
     graph.launch()
     graph.status()
+
+
+def test_step_graph_reports_a_mesh_leaving_its_node_box():
+    """The B^T rows of a captured step cover the touched fluid nodes at capture,
+    padded by the capacity margin: a translated mesh that leaves that box is
+    reported as L2X_ECAPACITY, and the captured positions replay fine again."""
+    import paper_1810_13046_gb300 as l2x
+    import synth as sy
+    w = sy.workload("beam32")
+    c = l2x.Coupling(w.grid, torch.from_numpy(w.coords).cuda(), torch.from_numpy(w.elems).cuda())
+    n = w.coords.shape[0]
+    u_f = [torch.from_numpy(f).cuda() for f in w.fields]
+    f_s = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    u_s = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    f_f = [torch.zeros(m, dtype=torch.float64, device="cuda") for m in c.fluid_sizes()]
+    src = torch.from_numpy(w.coords).cuda()
+    n_pairs0 = c.info()["n_pairs_total"]
+    graph = c.capture_step(src, u_f, u_s, f_s, f_f, margin=1.3)
+    # a shift of 0.25 (8 cells on the 32^3 grid; the box is padded by about 6
+    # nodes) keeps the beam inside the grid and within the pair capacity, but
+    # moves it out of the padded box
+    src.copy_(torch.from_numpy(w.coords + np.array([0.25, 0.0, 0.0])).cuda())
+    graph.launch()
+    with pytest.raises(l2x.L2XError) as ei:
+        graph.status()
+    assert ei.value.status == 3
+    assert c.info()["n_pairs_total"] <= 1.3 * n_pairs0   # the pairs fitted: the box was the limit
+    src.copy_(torch.from_numpy(w.coords).cuda())
+    graph.launch()
+    graph.status()
+    ref = c.transfer_velocity(u_f)
+    assert rel_l2(torch.stack(u_s).cpu().numpy(), torch.stack(ref).cpu().numpy()) <= 1e-12
