@@ -82,6 +82,8 @@ struct l2x_coupling {
     void* pcg_ws = nullptr;
     void* vec_tmp = nullptr;         // n_grids * n_nodes doubles
     void* vec_tmp2 = nullptr;        // n_grids * n_nodes doubles (force side of a captured step)
+    cudaStream_t aux_stream = nullptr;  // second branch of captured steps (values of S)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void* vec_mask = nullptr;        // n_grids * n_nodes doubles: the masked force input
     uint8_t* fmask = nullptr;        // interface mask of the force input (n_nodes), when has_fmask
     bool has_fmask = false;
@@ -649,6 +651,12 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
             }
         launch_check_node_box(h->node_box, lim, G, h->st, s);
     }
+    // the values of S depend only on the element volumes: a second branch of the
+    // graph forms them while the main branch lists, clips and assembles
+    L2X_CUDA(cudaEventRecord(h->ev_fork, s));
+    L2X_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+    launch_S_values(h, h->aux_stream);
+    L2X_CUDA(cudaEventRecord(h->ev_join, h->aux_stream));
     launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
     launch_scan_i64(h->nbox, h->loc_off, (int64_t)G * m, h->scan_tmp, s);
     launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, h->pair_cap, h->st, s);
@@ -681,7 +689,7 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         launch_transpose_sort(T, h->st, s);
         if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, h->T_cap[g], s);
     }
-    launch_S_values(h, s);
+    L2X_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));  // S is formed
     // transfers
     const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
     if (h->opts.multiplier == L2X_MULT_STANDARD && h->opts.force_mode == L2X_FORCE_DUAL) {
@@ -788,6 +796,9 @@ l2x_status l2x_destroy(l2x_handle h) {
     if (h->pcg_ws) cudaFree(h->pcg_ws);
     if (h->vec_tmp) cudaFree(h->vec_tmp);
     if (h->vec_tmp2) cudaFree(h->vec_tmp2);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
     if (h->vec_mask) cudaFree(h->vec_mask);
     dfree(h->fmask);
     dfree(h->st);
@@ -1136,6 +1147,11 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
     }
     L2X_TRY(ensure_scan(h, max_rows));
     L2X_CUDA(cudaStreamSynchronize(s));
+    if (!h->aux_stream) {
+        L2X_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+        L2X_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        L2X_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
     // capture one step
     l2x_step_graph* gr = new l2x_step_graph();
     gr->h = h;
