@@ -218,14 +218,23 @@ def hbm_peak():
 
 
 def oracle_step(w, elems, nthreads):
-    """One step of the plain FP64 CPU oracle (assembly + both transfers)."""
+    """One step of the plain FP64 CPU oracle (assembly + both transfers).  A
+    subset of the elements is taken as a mesh of its own: the nodes it uses,
+    renumbered (nodes outside it would give empty rows of M_s)."""
     import oracle
+    used = np.unique(elems)
+    if used.size == w.coords.shape[0]:
+        X, E, force = w.coords, elems, w.force
+    else:
+        remap = np.full(w.coords.shape[0], -1, dtype=np.int64)
+        remap[used] = np.arange(used.size)
+        X, E, force = w.coords[used], remap[elems].astype(np.int32), w.force[used]
     t0 = time.perf_counter()
-    oc = oracle.Coupling(w.grid, w.coords, elems, nthreads=nthreads)
+    oc = oracle.Coupling(w.grid, X, E, nthreads=nthreads)
     t1 = time.perf_counter()
     fields = [f.astype(np.float32).astype(np.float64) for f in w.fields]
     us = oc.transfer_velocity(fields)
-    ff = oc.transfer_force(w.force.astype(np.float32).astype(np.float64), mode="dual")
+    ff = oc.transfer_force(force.astype(np.float32).astype(np.float64), mode="dual")
     t2 = time.perf_counter()
     npairs = sum(len(p[0]) for p in oc.pairs)
     return oc, us, ff, npairs, t1 - t0, t2 - t1
