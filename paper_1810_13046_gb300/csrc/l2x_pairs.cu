@@ -122,10 +122,16 @@ __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const 
         boxes[g * m + e] = b;
         counts[g * m + e] = count;
         nbox[g * m + e] = count > 0 ? (int64_t)(ext[0] + 1) * (ext[1] + 1) * (D == 3 ? ext[2] + 1 : 1) : 0;
-        if (count > 0) {
-            for (int k = 0; k < D; ++k) {
-                atomicMin(node_box + g * 6 + k, b.lo[k]);
-                atomicMax(node_box + g * 6 + 3 + k, b.lo[k] + ext[k]);
+        // touched-node box of the grid: reduced over the warp first (every element
+        // updates the same six words), then one atomic per warp
+        const unsigned act = __activemask();
+        const int leader = __ffs(act) - 1;
+        for (int k = 0; k < D; ++k) {
+            const int lo_k = __reduce_min_sync(act, count > 0 ? b.lo[k] : INT_MAX);
+            const int hi_k = __reduce_max_sync(act, count > 0 ? b.lo[k] + ext[k] : INT_MIN);
+            if ((int)(threadIdx.x & 31) == leader && lo_k <= hi_k) {
+                atomicMin(node_box + g * 6 + k, lo_k);
+                atomicMax(node_box + g * 6 + 3 + k, hi_k);
             }
         }
     }
