@@ -222,7 +222,6 @@ __global__ void spmv_BT_plain_kernel(int64_t n_rows, const int64_t* __restrict__
 }
 
 // ------------------------------------------------------------------ PCG (fused, cooperative)
-constexpr int kPcgThreads = 256;
 // right-hand sides of one solve: the components of one transfer (<= 3), or of
 // both transfers of a captured step solved together (<= 6)
 constexpr int kMaxRhs = 6;
@@ -355,7 +354,6 @@ template <typename TV, int NR>
 __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
     cg::grid_group grid = cg::this_grid();
     constexpr int NV = 3 * NR;                  // gamma, delta, rho per right-hand side
-    constexpr int NW = kPcgBlock / 32;
     __shared__ DF s_stage[NV][kPcgBlock];
     __shared__ DF s_dfo[NV];
     __shared__ double s_red[NV * 32];
@@ -369,7 +367,6 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_fused_kernel(PcgArgs<TV> A) {
     const int glane = threadIdx.x % kRowLanes;
     const int grow = threadIdx.x / kRowLanes;
     constexpr int kRowsPerPass = kPcgBlock / kRowLanes;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     DF* partial = reinterpret_cast<DF*>(A.partial);
     for (int64_t i = r0 + threadIdx.x; i < r1; i += kPcgBlock) {
         const TV di = A.dinv[i];
