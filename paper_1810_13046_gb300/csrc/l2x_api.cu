@@ -74,7 +74,7 @@ struct l2x_coupling {
     // scratch
     void* scan_tmp = nullptr;
     size_t scan_tmp_cap = 0;
-    int64_t* row_count = nullptr;    // n_nodes + 1
+    int64_t* row_count = nullptr;    // kMaxGrids * (n_nodes + 1): row counts per grid
     int32_t* tcursor = nullptr;      // fill cursors of the B^T rows
     int64_t tcursor_cap = 0;
     int64_t* tflags = nullptr;       // non-empty-row flags of B^T (scan scratch)
@@ -84,6 +84,14 @@ struct l2x_coupling {
     void* vec_tmp2 = nullptr;        // n_grids * n_nodes doubles (force side of a captured step)
     cudaStream_t aux_stream = nullptr;  // second branch of captured steps (values of S)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // captured steps: B_g^T of grid g >= 1 is formed on a branch of its own, with
+    // its own scratch (grid 0 uses the main stream and tcursor / tflags / scan_tmp)
+    cudaStream_t t_stream[kMaxGrids]{};
+    cudaEvent_t ev_tfork = nullptr, ev_tjoin[kMaxGrids]{};
+    int32_t* t_cursor[kMaxGrids]{};
+    int64_t* t_flags[kMaxGrids]{};
+    void* t_scan[kMaxGrids]{};
+    int64_t t_rows_cap[kMaxGrids]{};
     void* vec_mask = nullptr;        // n_grids * n_nodes doubles: the masked force input
     uint8_t* fmask = nullptr;        // interface mask of the force input (n_nodes), when has_fmask
     bool has_fmask = false;
@@ -328,7 +336,7 @@ l2x_status build_topology(l2x_coupling* h, cudaStream_t s) {
     L2X_TRY(dalloc(&h->adj_ptr, n + 1));
     L2X_TRY(dalloc(&h->adj, (size_t)(m * NA)));
     L2X_TRY(dalloc(&h->cursor, n));
-    L2X_TRY(dalloc(&h->row_count, n + 1));
+    L2X_TRY(dalloc(&h->row_count, (int64_t)kMaxGrids * (n + 1)));  // row counts of B_g, or of M_s
     L2X_TRY(ensure_scan(h, n));
     launch_node_adjacency(h->dim, n, m, h->E, h->adj_ptr, h->adj, h->cursor, h->scan_tmp, s);
     L2X_TRY(dalloc(&h->M.ptr, n + 1));
@@ -441,23 +449,38 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, NP, h->pair_cap, h->X, h->E, h->elem_grad,
                           h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st, s, h->clip_block);
     }
-    // (IV) B_g by rows
-    for (int g = 0; g < G; ++g) {
+    // (IV) B_g by rows.  The element-local matrices of all grids in one launch:
+    // boxes, pair offsets and local offsets run over the G*m (grid, element) slots
+    {
+        PhaseScope ph_loc(h, L2X_PH_ROWS, s);
+        launch_elem_local(d, (int64_t)G * m, h->boxes, h->offsets, h->loc_off, h->loc_cap, h->blocks, h->vols,
+                          h->loc_val, h->loc_flag, h->opts.multiplier == L2X_MULT_DUAL, h->st, s);
+    }
+    // rows of all grids per launch: pass 0 counts, one status read for the G
+    // nonzero totals, then pass 1 (values) or 2 (structure of the plain path)
+    RowsGrid rg[kMaxGrids];
+    int64_t nnz_g[kMaxGrids] = {};
+    {
         auto ph_rows = std::make_unique<PhaseScope>(h, L2X_PH_ROWS, s);
-        Csr& B = h->B[g];
-        const ElemBox* bx = h->boxes + (int64_t)g * m;
-        const int64_t* off = h->offsets + (int64_t)g * m;
-        const int64_t* lof = h->loc_off + (int64_t)g * m;
-        launch_elem_local(d, m, bx, off, lof, h->loc_cap, h->blocks, h->vols, h->loc_val, h->loc_flag,
-                          h->opts.multiplier == L2X_MULT_DUAL, h->st, s);
-        launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, h->row_count,
-                      nullptr, nullptr, nullptr, h->st, s);
-        if (!B.ptr) L2X_TRY(dalloc(&B.ptr, n + 1));
-        launch_scan_i64(h->row_count, B.ptr, n, h->scan_tmp, s);
-        int64_t nnz = 0;
-        L2X_CUDA(cudaMemcpyAsync(&nnz, B.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        for (int g = 0; g < G; ++g) {
+            if (!h->B[g].ptr) L2X_TRY(dalloc(&h->B[g].ptr, n + 1));
+            rg[g].boxes = h->boxes + (int64_t)g * m;
+            rg[g].loc_off = h->loc_off + (int64_t)g * m;
+            rg[g].row_count = h->row_count + (int64_t)g * (n + 1);
+            rg[g].nnode0 = h->sg[g].nnode[0];
+            rg[g].nnode1 = h->sg[g].nnode[1];
+        }
+        launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
+        for (int g = 0; g < G; ++g) {
+            launch_scan_i64(rg[g].row_count, h->B[g].ptr, n, h->scan_tmp, s);
+            L2X_CUDA(cudaMemcpyAsync(&nnz_g[g], h->B[g].ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        }
         ph_rows.reset();
         L2X_TRY(read_status(h, s));
+    }
+    for (int g = 0; g < G; ++g) {
+        Csr& B = h->B[g];
+        const int64_t nnz = nnz_g[g];
         B.n_rows = n;
         B.nnz = nnz;
         if (nnz > h->B_cap[g] || !B.col) {
@@ -470,19 +493,25 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
             L2X_TRY(dalloc(&B.val32, c));
             h->B_cap[g] = c;
         }
-        if (plain) {
-            PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
-            launch_b_rows(2, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, nullptr,
-                          B.ptr, B.col, B.val, h->st, s);
-            launch_scatter_plain(d, h->sg[g], h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks, h->vols,
-                                 B, h->opts.multiplier == L2X_MULT_DUAL, s);
-        } else {
-            {
-                PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
-                launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag,
-                              nullptr, B.ptr, B.col, B.val, h->st, s);
-                if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, nnz, s);
-            }
+        rg[g].row_ptr = B.ptr;
+        rg[g].cols = B.col;
+        rg[g].vals = B.val;
+    }
+    {
+        PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
+        launch_b_rows(plain ? 2 : 1, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
+        for (int g = 0; g < G; ++g) {
+            if (plain)
+                launch_scatter_plain(d, h->sg[g], h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks,
+                                     h->vols, h->B[g], h->opts.multiplier == L2X_MULT_DUAL, s);
+            else if (h->opts.precision == L2X_MIXED)
+                launch_to_f32(h->B[g].val, h->B[g].val32, nnz_g[g], s);
+        }
+    }
+    if (!plain) {
+        for (int g = 0; g < G; ++g) {
+            const Csr& B = h->B[g];
+            const int64_t nnz = nnz_g[g];
             PhaseScope ph_t(h, L2X_PH_TRANSPOSE, s);
             // B_g^T over the box of touched fluid nodes
             CsrT& T = h->T[g];
@@ -665,30 +694,49 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, h->pair_cap, h->pair_cap, h->X, h->E,
                       h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st,
                       s, h->clip_block);
+    launch_elem_local(d, (int64_t)G * m, h->boxes, h->offsets, h->loc_off, h->loc_cap, h->blocks, h->vols,
+                      h->loc_val, h->loc_flag, h->opts.multiplier == L2X_MULT_DUAL, h->st, s);
+    // rows of all grids per launch (the B_g arrays are fixed by the capture)
+    RowsGrid rg[kMaxGrids];
     for (int g = 0; g < G; ++g) {
+        rg[g].boxes = h->boxes + (int64_t)g * m;
+        rg[g].loc_off = h->loc_off + (int64_t)g * m;
+        rg[g].row_count = h->row_count + (int64_t)g * (n + 1);
+        rg[g].row_ptr = h->B[g].ptr;
+        rg[g].cols = h->B[g].col;
+        rg[g].vals = h->B[g].val;
+        rg[g].nnode0 = h->sg[g].nnode[0];
+        rg[g].nnode1 = h->sg[g].nnode[1];
+    }
+    launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
+    for (int g = 0; g < G; ++g) {
+        launch_scan_i64(rg[g].row_count, h->B[g].ptr, n, h->scan_tmp, s);
+        launch_check_capacity(h->B[g].ptr + n, h->B_cap[g], h->st, s);
+    }
+    launch_b_rows(1, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
+    // the G grids' FP32 copies and transposes are independent: one graph branch
+    // per grid
+    L2X_CUDA(cudaEventRecord(h->ev_tfork, s));
+    for (int g = 0; g < G; ++g) {
+        cudaStream_t ts = g == 0 ? s : h->t_stream[g];
+        if (g > 0) L2X_CUDA(cudaStreamWaitEvent(ts, h->ev_tfork, 0));
+        int32_t* cursor = g == 0 ? h->tcursor : h->t_cursor[g];
+        int64_t* flags = g == 0 ? h->tflags : h->t_flags[g];
+        void* scan = g == 0 ? h->scan_tmp : h->t_scan[g];
         Csr& B = h->B[g];
-        const ElemBox* bx = h->boxes + (int64_t)g * m;
-        const int64_t* off = h->offsets + (int64_t)g * m;
-        const int64_t* lof = h->loc_off + (int64_t)g * m;
-        launch_elem_local(d, m, bx, off, lof, h->loc_cap, h->blocks, h->vols, h->loc_val, h->loc_flag,
-                          h->opts.multiplier == L2X_MULT_DUAL, h->st, s);
-        launch_b_rows(0, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, h->row_count,
-                      nullptr, nullptr, nullptr, h->st, s);
-        launch_scan_i64(h->row_count, B.ptr, n, h->scan_tmp, s);
-        launch_check_capacity(B.ptr + n, h->B_cap[g], h->st, s);
-        launch_b_rows(1, d, h->sg[g], n, h->adj_ptr, h->adj, bx, lof, h->loc_val, h->loc_flag, nullptr,
-                      B.ptr, B.col, B.val, h->st, s);
         B.n_rows = n;
         B.nnz = h->B_cap[g];  // an upper bound: the row pointers hold the actual count
-        if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, h->B_cap[g], s);
+        if (h->opts.precision == L2X_MIXED) launch_to_f32(B.val, B.val32, h->B_cap[g], ts);
         CsrT& T = h->T[g];
-        launch_transpose_count(B, h->sg[g], T, T.ptr, h->st, s);
-        launch_transpose_list(T, T.ptr, h->tflags, h->scan_tmp, h->st, s);
-        launch_scan_i64(T.ptr, T.ptr, T.n_rows, h->scan_tmp, s);
-        launch_transpose_fill(B, h->sg[g], T, h->tcursor, h->st, s);
-        launch_transpose_sort(T, h->st, s);
-        if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, h->T_cap[g], s);
+        launch_transpose_count(B, h->sg[g], T, T.ptr, h->st, ts);
+        launch_transpose_list(T, T.ptr, flags, scan, h->st, ts);
+        launch_scan_i64(T.ptr, T.ptr, T.n_rows, scan, ts);
+        launch_transpose_fill(B, h->sg[g], T, cursor, h->st, ts);
+        launch_transpose_sort(T, h->st, ts);
+        if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, h->T_cap[g], ts);
+        if (g > 0) L2X_CUDA(cudaEventRecord(h->ev_tjoin[g], ts));
     }
+    for (int g = 1; g < G; ++g) L2X_CUDA(cudaStreamWaitEvent(s, h->ev_tjoin[g], 0));
     L2X_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));  // S is formed
     // transfers
     const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
@@ -799,6 +847,14 @@ l2x_status l2x_destroy(l2x_handle h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
+    if (h->ev_tfork) cudaEventDestroy(h->ev_tfork);
+    for (int g = 0; g < kMaxGrids; ++g) {
+        if (h->ev_tjoin[g]) cudaEventDestroy(h->ev_tjoin[g]);
+        if (h->t_stream[g]) cudaStreamDestroy(h->t_stream[g]);
+        dfree(h->t_cursor[g]);
+        dfree(h->t_flags[g]);
+        if (h->t_scan[g]) cudaFree(h->t_scan[g]);
+    }
     if (h->vec_mask) cudaFree(h->vec_mask);
     dfree(h->fmask);
     dfree(h->st);
@@ -1146,11 +1202,30 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
         h->tcursor_cap = max_rows;
     }
     L2X_TRY(ensure_scan(h, max_rows));
+    // scratch of the transposes on the branches of grids 1 .. G-1
+    for (int g = 1; g < G; ++g) {
+        const int64_t rows = h->T[g].n_rows;
+        if (rows <= h->t_rows_cap[g] && h->t_cursor[g]) continue;
+        dfree(h->t_cursor[g]);
+        dfree(h->t_flags[g]);
+        if (h->t_scan[g]) cudaFree(h->t_scan[g]);
+        h->t_scan[g] = nullptr;
+        h->t_rows_cap[g] = 0;
+        L2X_TRY(dalloc(&h->t_cursor[g], rows));
+        L2X_TRY(dalloc(&h->t_flags[g], rows + 1));
+        if (cudaMalloc(&h->t_scan[g], scan_tmp_bytes(rows)) != cudaSuccess) return fail(L2X_ENOMEM, "scan scratch");
+        h->t_rows_cap[g] = rows;
+    }
     L2X_CUDA(cudaStreamSynchronize(s));
     if (!h->aux_stream) {
         L2X_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
         L2X_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         L2X_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        L2X_CUDA(cudaEventCreateWithFlags(&h->ev_tfork, cudaEventDisableTiming));
+        for (int g = 1; g < kMaxGrids; ++g) {
+            L2X_CUDA(cudaStreamCreateWithFlags(&h->t_stream[g], cudaStreamNonBlocking));
+            L2X_CUDA(cudaEventCreateWithFlags(&h->ev_tjoin[g], cudaEventDisableTiming));
+        }
     }
     // capture one step
     l2x_step_graph* gr = new l2x_step_graph();

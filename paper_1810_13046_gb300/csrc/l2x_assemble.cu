@@ -123,20 +123,30 @@ __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, 
 // needs no atomics.  Touched columns are emitted in ascending order.
 // pass 0: row_count[i] = number of touched columns; pass 1: columns and values;
 // pass 2: columns only, values zeroed (the plain path adds them with atomics).
+// Rows of the n_grids matrices B_g in one launch: warp r takes row r % n_nodes
+// of grid r / n_nodes.
+struct RowsSet {
+    RowsGrid g[kMaxGrids];
+};
+
 template <int D>
 __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
-    int pass, SubGrid sg, int64_t n_nodes, const int64_t* __restrict__ adj_ptr, const int32_t* __restrict__ adj,
-    const ElemBox* __restrict__ boxes, const int64_t* __restrict__ loc_off, const double* __restrict__ loc_val,
-    const uint8_t* __restrict__ loc_flag, int64_t* __restrict__ row_count, const int64_t* __restrict__ row_ptr,
-    int32_t* __restrict__ cols, double* __restrict__ vals, DevStatus* st) {
+    int pass, int n_grids, RowsSet rs, int64_t n_nodes, const int64_t* __restrict__ adj_ptr,
+    const int32_t* __restrict__ adj, const double* __restrict__ loc_val, const uint8_t* __restrict__ loc_flag,
+    DevStatus* st) {
     constexpr int NA = D + 1;
     __shared__ ElemBox s_box[kRowWarps][kRowAdj];
     __shared__ int64_t s_off[kRowWarps][kRowAdj];
     __shared__ int32_t s_ea[kRowWarps][kRowAdj];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t i = blockIdx.x * (int64_t)kRowWarps + w;
-    if (i >= n_nodes) return;
+    const int64_t r_all = blockIdx.x * (int64_t)kRowWarps + w;
+    if (r_all >= n_grids * n_nodes) return;
     if (st->flags & kAbortFlags) return;  // a captured step whose pairs or entries did not fit
+    const int g = (int)(r_all / n_nodes);
+    const int64_t i = r_all - g * n_nodes;
+    const RowsGrid& rg = rs.g[g];
+    const ElemBox* __restrict__ boxes = rg.boxes;
+    const int64_t* __restrict__ loc_off = rg.loc_off;
     const int64_t a0 = adj_ptr[i], a1 = adj_ptr[i + 1];
     const bool staged = a1 - a0 <= kRowAdj;
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
         hi[2] = 0;
     }
     int64_t cnt = 0;
-    const int64_t out0 = pass >= 1 ? row_ptr[i] : 0;
+    const int64_t out0 = pass >= 1 ? rg.row_ptr[i] : 0;
     if (a0 < a1) {
         const int nx = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1, nz = hi[2] - lo[2] + 1;
         const int64_t total = (int64_t)nx * ny * nz;
@@ -200,13 +210,13 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
             const unsigned bal = __ballot_sync(0xffffffffu, touched);
             if (pass >= 1 && touched) {
                 const int pos = __popc(bal & ((1u << lane) - 1u));
-                cols[out0 + cnt + pos] = jx + sg.nnode[0] * (jy + sg.nnode[1] * jz);
-                vals[out0 + cnt + pos] = pass == 1 ? acc : 0.0;
+                rg.cols[out0 + cnt + pos] = jx + rg.nnode0 * (jy + rg.nnode1 * jz);
+                rg.vals[out0 + cnt + pos] = pass == 1 ? acc : 0.0;
             }
             cnt += __popc(bal);
         }
     }
-    if (pass == 0 && lane == 0) row_count[i] = cnt;
+    if (pass == 0 && lane == 0) rg.row_count[i] = cnt;
 }
 
 template <int D>
@@ -469,18 +479,17 @@ void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t
     else { elem_local_kernel<3><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
 }
 
-void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const int64_t* adj_ptr,
-                   const int32_t* adj, const ElemBox* boxes_g, const int64_t* loc_off_g,
-                   const double* loc_val, const uint8_t* loc_flag, int64_t* row_count,
-                   const int64_t* row_ptr, int32_t* cols, double* vals, DevStatus* st, cudaStream_t s) {
-    if (n_nodes <= 0) return;
-    unsigned nb = nblk(n_nodes, kRowWarps);
+void launch_b_rows(int pass, int dim, int n_grids, const RowsGrid* grids, int64_t n_nodes, const int64_t* adj_ptr,
+                   const int32_t* adj, const double* loc_val, const uint8_t* loc_flag, DevStatus* st,
+                   cudaStream_t s) {
+    if (n_nodes <= 0 || n_grids <= 0) return;
+    RowsSet rs{};
+    for (int g = 0; g < n_grids; ++g) rs.g[g] = grids[g];
+    const unsigned nb = nblk(n_grids * n_nodes, kRowWarps);
     if (dim == 2)
-        { b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, loc_off_g, loc_val,
-                                                        loc_flag, row_count, row_ptr, cols, vals, st); count_launch(); }
+        { b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, n_grids, rs, n_nodes, adj_ptr, adj, loc_val, loc_flag, st); count_launch(); }
     else
-        { b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, sg, n_nodes, adj_ptr, adj, boxes_g, loc_off_g, loc_val,
-                                                        loc_flag, row_count, row_ptr, cols, vals, st); count_launch(); }
+        { b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, n_grids, rs, n_nodes, adj_ptr, adj, loc_val, loc_flag, st); count_launch(); }
 }
 
 void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,

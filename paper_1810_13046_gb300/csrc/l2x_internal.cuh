@@ -149,13 +149,24 @@ void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E
 void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t* offsets_g,
                        const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
                        double* loc_val, uint8_t* loc_flag, int dual, DevStatus* st, cudaStream_t s);
-// Row-wise assembly of B_g from the element-local matrices.  pass 0:
-// row_count[i] = nonzeros of row i; pass 1: cols + vals; pass 2: cols only,
-// vals zeroed (the plain path adds them with atomics).
-void launch_b_rows(int pass, int dim, const SubGrid& sg, int64_t n_nodes, const int64_t* adj_ptr,
-                   const int32_t* adj, const ElemBox* boxes_g, const int64_t* loc_off_g,
-                   const double* loc_val, const uint8_t* loc_flag, int64_t* row_count,
-                   const int64_t* row_ptr, int32_t* cols, double* vals, DevStatus* st, cudaStream_t s);
+// One grid's matrix for launch_b_rows: its element boxes and local offsets (the
+// slots of grid g), its row counts (pass 0) or row pointers, columns and values
+// (passes 1, 2), and the node counts of its first two axes.
+struct RowsGrid {
+    const ElemBox* boxes = nullptr;
+    const int64_t* loc_off = nullptr;
+    int64_t* row_count = nullptr;
+    const int64_t* row_ptr = nullptr;
+    int32_t* cols = nullptr;
+    double* vals = nullptr;
+    int32_t nnode0 = 1, nnode1 = 1;
+};
+// Row-wise assembly of the n_grids matrices B_g from the element-local matrices,
+// in one launch.  pass 0: row_count[i] = nonzeros of row i; pass 1: cols + vals;
+// pass 2: cols only, vals zeroed (the plain path adds them with atomics).
+void launch_b_rows(int pass, int dim, int n_grids, const RowsGrid* grids, int64_t n_nodes, const int64_t* adj_ptr,
+                   const int32_t* adj, const double* loc_val, const uint8_t* loc_flag, DevStatus* st,
+                   cudaStream_t s);
 // P1 mass matrix structure (pass 0 counts, pass 1 columns) and values.
 void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
                            const int32_t* adj, int64_t* row_count, const int64_t* row_ptr, int32_t* cols,
