@@ -74,7 +74,16 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--plain-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--work-shape", default=None, metavar="CB,RPB,CL,RPBS",
+                    help="fix the fused forms' work shape (clip block, PCG rows per block, PCG cluster, rows "
+                         "per block of the captured step's combined solve) instead of autotuning it; for "
+                         "profiler runs, where the autotuner's timings are distorted")
+    args = ap.parse_args()
+    if args.work_shape is not None:
+        args.work_shape = tuple(int(x) for x in args.work_shape.split(","))
+        if len(args.work_shape) != 4:
+            ap.error("--work-shape takes four integers")
+    return args
 
 
 class ClockSampler:
@@ -276,9 +285,10 @@ def reference_arm(args, rank, world):
 class Arm:
     """Timing of one coupling form on one rank's inputs (positions resident in HBM)."""
 
-    def __init__(self, torch, l2x, grid, positions, E, u32, f32, dev, world, flush):
+    def __init__(self, torch, l2x, grid, positions, E, u32, f32, dev, world, flush, work_shape=None):
         self.torch, self.l2x, self.grid, self.positions, self.E = torch, l2x, grid, positions, E
         self.u32, self.f32, self.dev, self.world, self.flush = u32, f32, dev, world, flush
+        self.work_shape = work_shape
 
     def coupling(self, path, precision, X=None, multiplier=0):
         """A coupling on the first configuration; fused forms pick their work-chunk
@@ -287,7 +297,12 @@ class Arm:
         c = l2x.Coupling(self.grid, self.positions[0] if X is None else X, self.E, path=path,
                          precision=precision, cg_rtol=1e-9 if precision == l2x.MIXED else 1e-13,
                          multiplier=multiplier)
-        if path == l2x.FUSED:
+        if path == l2x.FUSED and self.work_shape is not None:
+            cb, rpb, cl, rpbs = self.work_shape
+            c.set_work_shape(cb, rpb, cl, rpbs)
+            self.tuned = dict(clip_block=cb, pcg_rows_per_block=rpb, pcg_cluster=cl, pcg_rows_per_block_step=rpbs,
+                              fixed=True)
+        elif path == l2x.FUSED:
             self.tuned = c.autotune()
         return c
 
@@ -450,7 +465,7 @@ def main():
     F32 = F.astype(np.float32)
     f32 = [torch.from_numpy(np.ascontiguousarray(F32[:, g])).to(dev) for g in range(3)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    arm = Arm(torch, l2x, grid, positions, E, u32, f32, dev, world, flush)
+    arm = Arm(torch, l2x, grid, positions, E, u32, f32, dev, world, flush, args.work_shape)
 
     # chosen form: captured step graph, fused, FP64 geometry + FP32 fields/SpMV/CG
     # with compensated dots and FP64 refinement

@@ -148,6 +148,8 @@ typedef struct l2x_info {
     int32_t pcg_cluster;       /* > 0: the solve runs in one thread-block cluster of this many CTAs */
     double tuned_clip_ms;      /* l2x_autotune: time of the chosen clip launch (0 before tuning) */
     double tuned_solve_ms;     /* l2x_autotune: time of the chosen mass-matrix solve of all components */
+    int32_t pcg_rows_per_block_step; /* rows per block of a captured step's combined solve (2G right-hand sides) */
+    int32_t reserved2;
 } l2x_info;
 
 typedef struct l2x_coupling* l2x_handle;
@@ -300,6 +302,12 @@ l2x_status l2x_autotune(l2x_handle h, void* stream);
  * pcg_rows_per_block in [1, 4096] (grid-wide PCG), pcg_cluster 0 (grid-wide)
  * or the CTAs of the single-cluster PCG (EINVAL if the system does not fit). */
 l2x_status l2x_set_work_shape(l2x_handle h, int32_t clip_block, int32_t pcg_rows_per_block, int32_t pcg_cluster);
+
+/* Sets the rows per thread block of the combined solve of captured steps (the
+ * 2G right-hand sides of both transfers), which l2x_autotune tunes on its own
+ * and l2x_set_work_shape sets to pcg_rows_per_block.  [1, 4096], else EINVAL.
+ * Applies to steps captured afterwards. */
+l2x_status l2x_set_step_work_shape(l2x_handle h, int32_t pcg_rows_per_block_step);
 
 /* Enables (1, also clears the totals) or disables (0) CUDA-event timing of the
  * phases listed above, recorded on the stream of each call; l2x_query resolves

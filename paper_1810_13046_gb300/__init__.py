@@ -62,7 +62,8 @@ class _Info(ctypes.Structure):
                 ("phase_ms", ctypes.c_double * 8), ("phase_calls", ctypes.c_int64 * 8),
                 ("clip_block", ctypes.c_int32), ("pcg_rows_per_block", ctypes.c_int32),
                 ("multiplier", ctypes.c_int32), ("pcg_cluster", ctypes.c_int32),
-                ("tuned_clip_ms", ctypes.c_double), ("tuned_solve_ms", ctypes.c_double)]
+                ("tuned_clip_ms", ctypes.c_double), ("tuned_solve_ms", ctypes.c_double),
+                ("pcg_rows_per_block_step", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 PHASES = ["pairs", "clip", "rows", "transpose", "mass", "spmv_B", "pcg", "spmv_BT"]
@@ -114,6 +115,7 @@ def load_library(build_if_missing: bool = True):
         "l2x_set_timing": ([P, ctypes.c_int32], ctypes.c_int),
         "l2x_autotune": ([P, P], ctypes.c_int),
         "l2x_set_work_shape": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "l2x_set_step_work_shape": ([P, ctypes.c_int32], ctypes.c_int),
         "l2x_graph_create": ([P, P, PP, PP, PP, PP, ctypes.c_double, ctypes.c_int32, P,
                               ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "l2x_graph_launch": ([P, P], ctypes.c_int),
@@ -261,7 +263,7 @@ class Coupling:
                     phase_calls={p: inf.phase_calls[i] for i, p in enumerate(PHASES)},
                     clip_block=inf.clip_block, pcg_rows_per_block=inf.pcg_rows_per_block,
                     multiplier=inf.multiplier, pcg_cluster=inf.pcg_cluster, tuned_clip_ms=inf.tuned_clip_ms,
-                    tuned_solve_ms=inf.tuned_solve_ms)
+                    tuned_solve_ms=inf.tuned_solve_ms, pcg_rows_per_block_step=inf.pcg_rows_per_block_step)
 
     def autotune(self):
         """Pick work-chunk sizes by timing candidates on this coupling."""
@@ -269,12 +271,18 @@ class Coupling:
             _check(load_library().l2x_autotune(self._h, _stream_ptr(self.device)))
         i = self.info()
         return dict(clip_block=i["clip_block"], pcg_rows_per_block=i["pcg_rows_per_block"],
-                    pcg_cluster=i["pcg_cluster"], clip_ms=i["tuned_clip_ms"], solve_ms=i["tuned_solve_ms"])
+                    pcg_cluster=i["pcg_cluster"], pcg_rows_per_block_step=i["pcg_rows_per_block_step"],
+                    clip_ms=i["tuned_clip_ms"], solve_ms=i["tuned_solve_ms"])
 
-    def set_work_shape(self, clip_block: int = 128, pcg_rows_per_block: int = 64, pcg_cluster: int = 0):
-        """Set the work shape explicitly (what :meth:`autotune` picks)."""
-        _check(load_library().l2x_set_work_shape(self._h, int(clip_block), int(pcg_rows_per_block),
-                                                 int(pcg_cluster)))
+    def set_work_shape(self, clip_block: int = 128, pcg_rows_per_block: int = 64, pcg_cluster: int = 0,
+                       pcg_rows_per_block_step: int | None = None):
+        """Set the work shape explicitly (what :meth:`autotune` picks).  The combined
+        solve of captured steps takes ``pcg_rows_per_block_step``, or
+        ``pcg_rows_per_block`` when it is None."""
+        lib = load_library()
+        _check(lib.l2x_set_work_shape(self._h, int(clip_block), int(pcg_rows_per_block), int(pcg_cluster)))
+        if pcg_rows_per_block_step is not None:
+            _check(lib.l2x_set_step_work_shape(self._h, int(pcg_rows_per_block_step)))
 
     def set_timing(self, enable: bool = True):
         """CUDA-event timing of the library's phases (totals in info()['phase_ms'])."""

@@ -1319,6 +1319,7 @@ l2x_status l2x_query(l2x_handle h, l2x_info* info) {
     info->multiplier = h->opts.multiplier;
     info->tuned_clip_ms = h->tuned_clip_ms;
     info->tuned_solve_ms = h->tuned_solve_ms;
+    info->pcg_rows_per_block_step = h->pcg_rpb_step;
     resolve_timing(h);
     for (int p = 0; p < L2X_NPHASE; ++p) {
         info->phase_ms[p] = h->phase_ms[p];
@@ -1455,6 +1456,14 @@ l2x_status l2x_set_work_shape(l2x_handle h, int32_t clip_block, int32_t pcg_rows
     h->pcg_rpb = pcg_rows_per_block;
     h->pcg_rpb_step = pcg_rows_per_block;
     h->pcg_clu = pcg_cluster;
+    return L2X_OK;
+}
+
+l2x_status l2x_set_step_work_shape(l2x_handle h, int32_t pcg_rows_per_block_step) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    if (pcg_rows_per_block_step < 1 || pcg_rows_per_block_step > 4096)
+        return fail(L2X_EINVAL, "pcg_rows_per_block_step must be in [1, 4096]");
+    h->pcg_rpb_step = pcg_rows_per_block_step;
     return L2X_OK;
 }
 

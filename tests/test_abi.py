@@ -67,6 +67,7 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert st == 1 and not h.value
     assert b"dim" in lib.l2x_last_error()
     assert lib.l2x_destroy(None) == 0
+    assert lib.l2x_set_step_work_shape(None, 64) == 1
 
 
 def test_bad_multiplier_space_is_rejected_without_a_gpu():

@@ -77,3 +77,31 @@ def test_work_shape_is_validated():
         c.set_work_shape(128, 0, 0)
     with pytest.raises(l2x.L2XError):
         c.set_work_shape(128, 64, 17)
+    with pytest.raises(l2x.L2XError):
+        c.set_work_shape(128, 64, 0, 0)
+    with pytest.raises(l2x.L2XError):
+        c.set_work_shape(128, 64, 0, 8192)
+
+
+def test_step_work_shape_is_honoured_and_does_not_change_the_result():
+    """The combined solve of a captured step at 32 and at 1024 rows per block
+    (set apart from the per-call solve's 64) gives the same transfers."""
+    l2x = _l2x()
+    w = workload("beam32")
+    res = {}
+    for rpbs in (32, 1024):
+        c = gpu_coupling(w, precision=l2x.MIXED, cg_rtol=1e-9)
+        c.set_work_shape(128, 64, 0, rpbs)
+        i = c.info()
+        assert (i["pcg_rows_per_block"], i["pcg_rows_per_block_step"]) == (64, rpbs)
+        u_f = [torch.from_numpy(f.astype(np.float32)).cuda() for f in w.fields]
+        f_s = [torch.from_numpy(np.ascontiguousarray(w.force[:, g].astype(np.float32))).cuda() for g in range(3)]
+        u_s = [torch.zeros(c.n_nodes, dtype=torch.float32, device="cuda") for _ in range(3)]
+        f_f = [torch.zeros(n, dtype=torch.float32, device="cuda") for n in c.fluid_sizes()]
+        g = c.capture_step(torch.from_numpy(w.coords).cuda(), u_f, u_s, f_s, f_f, margin=1.2)
+        g.launch()
+        g.status()
+        res[rpbs] = (torch.stack(u_s).cpu().numpy(), [x.cpu().numpy() for x in f_f])
+    assert rel_l2(res[32][0], res[1024][0]) <= 1e-6
+    for a, b in zip(res[32][1], res[1024][1]):
+        assert rel_l2(a, b) <= 2e-6
