@@ -255,8 +255,12 @@ l2x_status l2x_picard_converged(const double* norms, double eps_abs, double eps_
  * work, reported by l2x_graph_sync_status as L2X_ECAPACITY (create the graph
  * again).  Fused path only; `stream` must
  * not be the legacy default stream.  While a graph exists, use the handle only
- * through it.  l2x_graph_sync_status waits for the stream and returns the
- * status of the last replay (capacity, degenerate or out-of-grid elements, CG). */
+ * through it: l2x_update_geometry or another l2x_graph_create on the handle may
+ * move the buffers it uses, so afterwards l2x_graph_launch of the older graph
+ * returns L2X_EINVAL (on the host; nothing is launched).  Destroy the graphs of a
+ * handle before the handle.  l2x_graph_sync_status waits for the stream and
+ * returns the status of the last replay (capacity, degenerate or out-of-grid
+ * elements, CG). */
 l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* const* u_f, void* const* u_s,
                             const void* const* f_s, void* const* f_f, double capacity_margin, int32_t zero_force,
                             void* stream, l2x_graph* out);

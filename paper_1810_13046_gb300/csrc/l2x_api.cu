@@ -84,6 +84,10 @@ struct l2x_coupling {
     void* vec_tmp2 = nullptr;        // n_grids * n_nodes doubles (force side of a captured step)
     cudaStream_t aux_stream = nullptr;  // second branch of captured steps (values of S)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // bumped by every call that may move the buffers a captured step uses
+    // (l2x_update_geometry, l2x_graph_create); a graph launches only while it
+    // holds the current value
+    uint64_t graph_gen = 0;
     // captured steps: B_g^T of grid g >= 1 is formed on a branch of its own, with
     // its own scratch (grid 0 uses the main stream and tcursor / tflags / scan_tmp)
     cudaStream_t t_stream[kMaxGrids]{};
@@ -782,6 +786,7 @@ struct l2x_step_graph {
     l2x_coupling* h = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    uint64_t gen = 0;  // the handle's graph_gen at creation
 };
 
 extern "C" {
@@ -938,6 +943,7 @@ l2x_status l2x_update_geometry(l2x_handle h, const double* coords, void* stream)
     if (!h || !coords) return fail(L2X_EINVAL, "NULL handle or coordinates");
     cudaStream_t s = (cudaStream_t)stream;
     h->stream = s;
+    ++h->graph_gen;  // a re-assembly may reallocate what existing graphs use
     L2X_CUDA(cudaMemcpyAsync(h->X, coords, sizeof(double) * h->n_nodes * h->dim, cudaMemcpyDeviceToDevice, s));
     return build_geometry(h, s);
 }
@@ -1118,6 +1124,7 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
     L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
     cudaStream_t s = (cudaStream_t)stream;
     h->stream = s;
+    ++h->graph_gen;  // the capacities below may reallocate what earlier graphs use
     const int G = h->n_grids, d = h->dim;
     const int NS = (d + 1) << d;
     // capacities with margin (pairs and B entries), B^T over every fluid node
@@ -1245,6 +1252,7 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
         return st != L2X_OK ? st : cuda_fail(e, "cudaStreamEndCapture");
     }
     gr->graph = graph;
+    gr->gen = h->graph_gen;
     e = cudaGraphInstantiate(&gr->exec, graph, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(graph);
@@ -1257,6 +1265,9 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
 
 l2x_status l2x_graph_launch(l2x_graph g, void* stream) {
     if (!g) return fail(L2X_EINVAL, "NULL graph");
+    if (g->gen != g->h->graph_gen)
+        return fail(L2X_EINVAL, "the coupling was re-assembled (l2x_update_geometry) or captured again "
+                                "(l2x_graph_create) after this graph was created; create the graph again");
     L2X_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
     return L2X_OK;
 }

@@ -126,3 +126,36 @@ def test_step_graph_reports_a_mesh_leaving_its_node_box():
     graph.status()
     ref = c.transfer_velocity(u_f)
     assert rel_l2(torch.stack(u_s).cpu().numpy(), torch.stack(ref).cpu().numpy()) <= 1e-12
+
+
+def test_older_graph_is_refused_after_a_new_capture_or_a_rebuild():
+    """A second capture or an update_geometry may move the buffers a captured step
+    uses: launching the older graph then fails on the host (L2X_EINVAL), and the
+    newest graph replays correctly."""
+    import paper_1810_13046_gb300 as l2x
+    import synth as sy
+    w = sy.workload("beam16")
+    c = l2x.Coupling(w.grid, torch.from_numpy(w.coords).cuda(), torch.from_numpy(w.elems).cuda())
+    n = w.coords.shape[0]
+    u_f = [torch.from_numpy(f).cuda() for f in w.fields]
+    f_s = [torch.from_numpy(np.ascontiguousarray(w.force[:, g])).cuda() for g in range(3)]
+    u_s = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    f_f = [torch.zeros(m, dtype=torch.float64, device="cuda") for m in c.fluid_sizes()]
+    src = torch.from_numpy(w.coords).cuda()
+    g1 = c.capture_step(src, u_f, u_s, f_s, f_f, margin=1.2)
+    g1.launch()
+    g1.status()
+    g2 = c.capture_step(src, u_f, u_s, f_s, f_f, margin=2.0)
+    with pytest.raises(l2x.L2XError) as ei:
+        g1.launch()
+    assert ei.value.status == 1
+    for x in u_s:
+        x.zero_()
+    g2.launch()
+    g2.status()
+    ref = l2x.Coupling(w.grid, src, torch.from_numpy(w.elems).cuda()).transfer_velocity(u_f)
+    assert rel_l2(torch.stack(u_s).cpu().numpy(), torch.stack(ref).cpu().numpy()) <= 1e-12
+    c.update_geometry(src)
+    with pytest.raises(l2x.L2XError) as ei:
+        g2.launch()
+    assert ei.value.status == 1
