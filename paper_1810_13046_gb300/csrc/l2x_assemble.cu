@@ -57,7 +57,7 @@ __global__ void segment_sort_kernel(int64_t n, const int64_t* __restrict__ ptr, 
 // only: reproducible.  Boxes hold 8 to 27 nodes for elements about a cell in
 // size, so several elements share a warp (more elements in flight hide the
 // latency of their dependent loads).
-constexpr int kLocLanes = 4;
+constexpr int kLocLanes = 2;
 
 template <int D>
 __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, const int64_t* __restrict__ offsets,
