@@ -80,7 +80,10 @@ def parse():
                          "profiler runs, where the autotuner's timings are distorted")
     args = ap.parse_args()
     if args.work_shape is not None:
-        args.work_shape = tuple(int(x) for x in args.work_shape.split(","))
+        try:
+            args.work_shape = tuple(int(x) for x in args.work_shape.split(","))
+        except ValueError:
+            ap.error("--work-shape takes four integers")
         if len(args.work_shape) != 4:
             ap.error("--work-shape takes four integers")
     return args
