@@ -298,21 +298,26 @@ def lumped_mass(X, E):
     return sp.diags(diag, format="csr")
 
 
-def solve_mass(M, Y: np.ndarray, rtol: float = 1e-15, max_iter: int = 10000):
+def solve_mass(M, Y: np.ndarray, rtol: float = 1e-15, max_iter: int = 10000, method: str = "auto"):
     """Solve M W = Y column by column.
 
     Direct methods where they are cheap (dense Cholesky for n <= 4000, sparse LU
     for n <= 300000); plain conjugate gradients without preconditioning to
     ||r|| <= rtol ||b|| beyond that (P1 mass matrices are well conditioned).
+    ``method`` ("dense", "lu" or "cg") forces one of the three.
     """
+    if method not in ("auto", "dense", "lu", "cg"):
+        raise ValueError(method)
     Y = np.asarray(Y, dtype=np.float64)
     one = Y.ndim == 1
     Y2 = Y[:, None] if one else Y
     n = M.shape[0]
-    if n <= 4000:
+    if method == "auto":
+        method = "dense" if n <= 4000 else ("lu" if n <= 300000 else "cg")
+    if method == "dense":
         c = scipy.linalg.cho_factor(M.toarray())
         W = scipy.linalg.cho_solve(c, Y2)
-    elif n <= 300000:
+    elif method == "lu":
         lu = scipy.sparse.linalg.splu(M.tocsc())
         W = lu.solve(np.ascontiguousarray(Y2))
     else:

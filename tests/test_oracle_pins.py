@@ -223,6 +223,22 @@ def test_mass_matrix_matches_exact_quadrature():
         assert np.abs(single[np.ix_(idx, idx)] - Mloc).max() <= 1e-15 * np.abs(Mloc).max() * 10
 
 
+@pytest.mark.parametrize("method", ["dense", "lu", "cg"])
+def test_mass_solves_satisfy_the_defining_equation(method):
+    """Every branch of the oracle's solve with S = M_s (the equation S w = B v of
+    the algebraic transfer, Sec. 2.3) returns W with M W = Y to rounding, for
+    several right-hand sides at once and for one."""
+    w = synth.workload("beam16")
+    M = oracle.mass_matrix(w.coords, w.elems)
+    rng = np.random.default_rng(9)
+    Y = rng.standard_normal((M.shape[0], 3))
+    W = oracle.solve_mass(M, Y, method=method)
+    assert np.abs(M @ W - Y).max() <= 1e-13 * np.abs(Y).max()
+    w1 = oracle.solve_mass(M, Y[:, 1], method=method)
+    assert w1.shape == (M.shape[0],)
+    assert np.abs(w1 - W[:, 1]).max() <= 1e-12 * np.abs(W).max()
+
+
 @pytest.mark.parametrize("name", ["disk2d", "beam16"])
 def test_force_transfer_is_the_adjoint(name):
     """P6: f . (T u) = (T^T f) . u with T u from the velocity transfer and T^T f
@@ -465,6 +481,9 @@ def test_picard_norms_and_criteria_closed_form():
     assert not oracle.picard_converged(1.25, 1.0, 0.3, 4.0)
     assert not oracle.picard_converged(1.25, 1.0, 0.5, 0.0)      # no reference norm: (AC) only
     assert not oracle.picard_converged(float("nan"), 1.0, 0.5, 4.0)
+    # both criteria are strict inequalities in Eqs. (AC) and (RC)
+    assert not oracle.picard_converged(1.25, 1.25, 0.0, 4.0)
+    assert not oracle.picard_converged(1.25, 1.0, 1.25 / 4.0, 4.0)
 
 
 def test_picard_loop_reaches_the_fixed_point_of_a_linear_model():
