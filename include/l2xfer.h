@@ -35,6 +35,8 @@
  *   through a device status word that the call reads after synchronising
  *   `stream`; l2x_last_error() gives a one-line description.
  * - A handle is not thread-safe and must not be used from two streams at once.
+ * - One CUDA device per process: kernel attributes (shared-memory opt-ins) are
+ *   set once, on the device of the first launch.  Run one process per GPU.
  * - Velocity grids: with staggered = 0 there is one nodal Q1 grid (nodes at
  *   origin + i*h) and one scalar component; with staggered = 1 there are `dim`
  *   grids, grid g having nodes at origin_g + i*h along axis g and at cell
