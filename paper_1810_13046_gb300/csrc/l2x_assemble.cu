@@ -50,8 +50,9 @@ __global__ void segment_sort_kernel(int64_t n, const int64_t* __restrict__ ptr, 
     }
 }
 
-// kLocLanes lanes per element: node-box matrix of the element on one grid.  A
-// lane takes nodes of the box; for each it sums, over the (up to 2^d) candidate
+// kLocLanes lanes per (grid, element) slot: the node-box matrix of the element on
+// that grid (one launch covers the slots of all grids).  A lane takes nodes of
+// the box; for each it sums, over the (up to 2^d) candidate
 // cells of the element around that node in z, y, x order, block[a][corner] of
 // the pairs whose intersection volume is positive.  Fixed order, registers
 // only: reproducible.  Boxes hold 8 to 27 nodes for elements about a cell in
@@ -116,15 +117,15 @@ __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, 
     }
 }
 
-// One warp per solid node i (row of B_g).  The row's columns lie in the union of
-// the node boxes of the incident elements; every lane owns columns j and sums,
-// in adjacency order, the entry (local vertex of i, node j) of each incident
-// element's node-box matrix; registers only, so the result is reproducible and
-// needs no atomics.  Touched columns are emitted in ascending order.
+// One warp per solid node i of one grid g (row i of B_g); the rows of the n_grids
+// matrices share one launch, warp r taking row r % n_nodes of grid r / n_nodes.
+// The row's columns lie in the union of the node boxes of the incident elements;
+// every lane owns columns j and sums, in adjacency order, the entry (local
+// vertex of i, node j) of each incident element's node-box matrix; registers
+// only, so the result is reproducible and needs no atomics.  Touched columns are
+// emitted in ascending order.
 // pass 0: row_count[i] = number of touched columns; pass 1: columns and values;
 // pass 2: columns only, values zeroed (the plain path adds them with atomics).
-// Rows of the n_grids matrices B_g in one launch: warp r takes row r % n_nodes
-// of grid r / n_nodes.
 struct RowsSet {
     RowsGrid g[kMaxGrids];
 };
