@@ -159,3 +159,34 @@ def test_older_graph_is_refused_after_a_new_capture_or_a_rebuild():
     with pytest.raises(l2x.L2XError) as ei:
         g2.launch()
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_graph_in_2d_matches_fresh_assembly(precision):
+    """A captured step on the 2-D disk (one nodal grid: one transpose, on the
+    main branch of the graph) equals a fresh assembly at moved positions."""
+    import paper_1810_13046_gb300 as l2x
+    import synth as sy
+    w = sy.workload("disk2d")
+    mixed = precision == "mixed"
+    dt = torch.float32 if mixed else torch.float64
+    kw = dict(precision=l2x.MIXED if mixed else l2x.FP64, cg_rtol=1e-9 if mixed else 1e-13)
+    E = torch.from_numpy(w.elems).cuda()
+    c = l2x.Coupling(w.grid, torch.from_numpy(w.coords).cuda(), E, **kw)
+    n = w.coords.shape[0]
+    u_f = [torch.from_numpy(w.fields[0]).cuda().to(dt)]
+    f_s = [torch.from_numpy(np.ascontiguousarray(w.force[:, 0])).cuda().to(dt)]
+    u_s = [torch.zeros(n, dtype=dt, device="cuda")]
+    f_f = [torch.zeros(c.fluid_sizes()[0], dtype=dt, device="cuda")]
+    src = torch.from_numpy(w.coords).cuda()
+    graph = c.capture_step(src, u_f, u_s, f_s, f_f, margin=1.5)
+    X1 = w.coords + np.array([0.013, -0.007])
+    src.copy_(torch.from_numpy(X1).cuda())
+    graph.launch()
+    graph.status()
+    ref = l2x.Coupling(w.grid, torch.from_numpy(X1).cuda(), E, **kw)
+    ur = ref.transfer_velocity(u_f)
+    fr = ref.transfer_force(f_s)
+    tol = 1e-6 if mixed else 1e-12
+    assert rel_l2(u_s[0].cpu().numpy(), ur[0].cpu().numpy()) <= tol
+    assert rel_l2(f_f[0].cpu().numpy(), fr[0].cpu().numpy()) <= tol
