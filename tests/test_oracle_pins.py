@@ -143,6 +143,18 @@ def test_golden_2d_exact_block():
         assert abs(got[k] - ref[k]) <= 1e-15 * max(abs(v) for v in ref.values())
 
 
+def test_golden_file_is_what_its_script_writes():
+    """The stored fixture is exactly the output of tests/golden/make_golden.py,
+    which calls only the exact rational reference (oracle/exact.py)."""
+    import importlib.util, json, os
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(here, "two_triangles_4x4.json")) as f:
+        assert json.load(f) == json.loads(json.dumps(mod.build()))
+
+
 # --------------------------------------------------------------- invariants
 
 @pytest.mark.parametrize("name", ["disk2d", "beam16", "leaflet32"])
