@@ -102,3 +102,46 @@ def test_stretched_axis_is_validated_without_a_gpu():
     h = ctypes.c_void_p()
     assert lib.l2x_build_coupling(ctypes.byref(g), ctypes.byref(m), None, None, ctypes.byref(h)) == 1
     assert b"increase" in lib.l2x_last_error()
+
+
+_NULL_SWEEP = r'''
+import ctypes, sys
+import paper_1810_13046_gb300 as l2x
+lib = l2x.load_library()
+names = sys.argv[1].split(",")
+free_ok = {"l2x_destroy", "l2x_graph_destroy"}
+not_taking_a_handle = {"l2x_kernel_launch_count", "l2x_status_string", "l2x_last_error", "l2x_default_opts",
+                       "l2x_build_coupling"}
+checked = 0
+for n in names:
+    fn = getattr(lib, n)
+    if n in not_taking_a_handle or fn.argtypes is None:
+        continue
+    args = []
+    for t in fn.argtypes:
+        if t in (ctypes.c_double,):
+            args.append(0.0)
+        elif t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64):
+            args.append(0)
+        else:
+            args.append(None)
+    st = fn(*args)
+    want = 0 if n in free_ok else 1
+    if st != want:
+        print("BAD", n, st)
+        sys.exit(1)
+    checked += 1
+print("checked", checked)
+'''
+
+
+def test_every_entry_point_rejects_null_arguments_without_a_gpu():
+    """Every call that takes a handle, a graph or device norms returns
+    L2X_EINVAL for NULL on the host (the destroy calls accept NULL), so a
+    caller's mistake is a status, never a crash.  Runs in a child process."""
+    l2x.load_library()
+    names = ",".join(_declared())
+    out = subprocess.run([__import__("sys").executable, "-c", _NULL_SWEEP, names], capture_output=True, text=True,
+                         cwd=ROOT, timeout=300)
+    assert out.returncode == 0, (out.stdout[-2000:], out.stderr[-2000:])
+    assert int(out.stdout.split()[-1]) >= 25
