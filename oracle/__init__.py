@@ -77,6 +77,8 @@ def _load():
         lib.orc_pair_blocks.argtypes = [ctypes.c_int, P, P, P, P, P, P, ctypes.c_int64, P, P, P, P,
                                         ctypes.c_int]
         lib.orc_pair_blocks.restype = ctypes.c_int
+        lib.orc_pair_blocks_counted.argtypes = lib.orc_pair_blocks.argtypes + [P]
+        lib.orc_pair_blocks_counted.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -186,8 +188,15 @@ def candidate_pairs(sg: SubGrid, X: np.ndarray, E: np.ndarray):
 
 # ----------------------------------------------------------------------------- (II)+(III)
 
-def pair_blocks(sg: SubGrid, X, E, pe, pc, nthreads: int = 1):
-    """Local blocks B^loc[p, a, b] = int_{E cap C} lambda_a psi_b and vol(E cap C)."""
+# categories of the operation tallies of steps (II)-(III), in the order of the C code
+OP_CATEGORIES = ("frame", "clip", "volume", "bary", "quad")
+
+
+def pair_blocks(sg: SubGrid, X, E, pe, pc, nthreads: int = 1, ops: dict | None = None):
+    """Local blocks B^loc[p, a, b] = int_{E cap C} lambda_a psi_b and vol(E cap C).
+
+    With a dict ``ops``, the floating-point operations the C code executed for
+    these pairs are added into it by category (:data:`OP_CATEGORIES`)."""
     lib = _load()
     d = sg.dim
     X = np.ascontiguousarray(X, dtype=np.float64)
@@ -198,8 +207,12 @@ def pair_blocks(sg: SubGrid, X, E, pe, pc, nthreads: int = 1):
     blocks = np.zeros((n, d + 1, 1 << d))
     vols = np.zeros(n)
     ax, keep = sg._axis_ptrs()
-    st = lib.orc_pair_blocks(d, _ptr(sg.ncell), _ptr(sg.origin), _ptr(sg.h), ax, _ptr(X), _ptr(E), n,
-                             _ptr(pe), _ptr(pc), _ptr(blocks), _ptr(vols), int(nthreads))
+    tally = np.zeros(len(OP_CATEGORIES), dtype=np.uint64)
+    st = lib.orc_pair_blocks_counted(d, _ptr(sg.ncell), _ptr(sg.origin), _ptr(sg.h), ax, _ptr(X), _ptr(E), n,
+                                     _ptr(pe), _ptr(pc), _ptr(blocks), _ptr(vols), int(nthreads), _ptr(tally))
+    if ops is not None:
+        for name, v in zip(OP_CATEGORIES, tally):
+            ops[name] = ops.get(name, 0) + int(v)
     if st == EDEGENERATE:
         raise OracleError("degenerate element")
     if st != 0:
@@ -237,7 +250,7 @@ def dual_blocks(blocks: np.ndarray) -> np.ndarray:
 
 
 def assemble_B(sg: SubGrid, X, E, nthreads: int = 1, return_pairs: bool = False,
-               multiplier: str = "standard"):
+               multiplier: str = "standard", ops: dict | None = None):
     """Mixed coupling matrix B (n_solid x n_fluid) of one Q1 grid, Eq. of the mortar integrals.
 
     B_ij = int N_fsi,i psi_j with N_fsi,i = phi_i (``multiplier="standard"``) or
@@ -247,7 +260,7 @@ def assemble_B(sg: SubGrid, X, E, nthreads: int = 1, return_pairs: bool = False,
     if multiplier not in ("standard", "dual"):
         raise ValueError(multiplier)
     pe, pc = candidate_pairs(sg, X, E)
-    blocks, vols = pair_blocks(sg, X, E, pe, pc, nthreads)
+    blocks, vols = pair_blocks(sg, X, E, pe, pc, nthreads, ops)
     d = sg.dim
     keep = vols > 0.0
     w = dual_blocks(blocks[keep]) if multiplier == "dual" else blocks[keep]
@@ -348,9 +361,11 @@ class Coupling:
 
     ``multiplier="standard"``: S = M_s (multipliers in V_s); ``"dual"``: the dual
     basis of Eq. (biorth), S = diag(int phi_i).  ``self.M`` holds S.
+    ``self.ops`` holds the operation tallies of steps (II)-(III) over all grids.
     """
 
     def __init__(self, grid, X, E, nthreads: int = 1, multiplier: str = "standard"):
+        self.ops = {}
         self.grid = grid
         self.multiplier = multiplier
         self.X = np.ascontiguousarray(X, dtype=np.float64)
@@ -359,7 +374,8 @@ class Coupling:
         self.B = []
         self.pairs = []
         for sg in self.sub:
-            B, pr = assemble_B(sg, self.X, self.E, nthreads, return_pairs=True, multiplier=multiplier)
+            B, pr = assemble_B(sg, self.X, self.E, nthreads, return_pairs=True, multiplier=multiplier,
+                               ops=self.ops)
             self.B.append(B)
             self.pairs.append(pr)
         self.M = lumped_mass(self.X, self.E) if multiplier == "dual" else mass_matrix(self.X, self.E)

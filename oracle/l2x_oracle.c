@@ -41,6 +41,21 @@
 #define ORC_EDEGENERATE 5
 #define ORC_ENOMEM 2
 
+/* ------------------------------------------------------------------ operation tallies
+ * The floating-point operations (additions, subtractions, multiplications,
+ * divisions; not fabs, comparisons or copies) that steps (II) and (III) below
+ * execute, tallied per thread by category when a function runs, and summed over
+ * threads by orc_pair_blocks_counted.  Each tally is the operation count of the
+ * statement it stands beside.  Categories:
+ *   FRAME   the cell's lower corner and the element vertices relative to it;
+ *   CLIP    plane-side values and cut points (step II);
+ *   VOLUME  the determinant (volume) of every sub-simplex;
+ *   BARY    the barycentric map of the element (per pair here);
+ *   QUAD    the Gauss-Legendre evaluation of lambda_a psi_b (step III). */
+enum { ORC_OPS_FRAME, ORC_OPS_CLIP, ORC_OPS_VOLUME, ORC_OPS_BARY, ORC_OPS_QUAD, ORC_OPS_N };
+static _Thread_local uint64_t t_ops[ORC_OPS_N];
+#define TALLY(cat, n) (t_ops[cat] += (uint64_t)(n))
+
 /* ------------------------------------------------------------------ (I) */
 
 static void elem_bbox(int dim, const double* X, const int32_t* E, int64_t e, double* lo, double* hi) {
@@ -164,6 +179,7 @@ static int slist_push(slist* L, const simplex* s) {
 /* signed distance-like value of point p for half-space (axis k, bound c, side):
  * side 0: x_k >= c  ->  x_k - c ;  side 1: x_k <= c  ->  c - x_k.  Inside iff >= 0. */
 static double side_value(const double* p, int k, double c, int side) {
+    TALLY(ORC_OPS_CLIP, 1);
     return side == 0 ? p[k] - c : c - p[k];
 }
 
@@ -173,6 +189,7 @@ static void cut_point(int dim, const double* p, const double* q, double sp, doub
                       double c, double* r) {
     double t = sp / (sp - sq);
     for (int j = 0; j < dim; ++j) r[j] = p[j] + t * (q[j] - p[j]);
+    TALLY(ORC_OPS_CLIP, 2 + 3 * dim);
     r[k] = c;
 }
 
@@ -288,10 +305,12 @@ static int barycentric_map(int dim, double V[4][3], double Minv[4][4]) {
             for (int c = 0; c < 2 * n; ++c) { double t = A[col][c]; A[col][c] = A[piv][c]; A[piv][c] = t; }
         double d = A[col][col];
         for (int c = 0; c < 2 * n; ++c) A[col][c] /= d;
+        TALLY(ORC_OPS_BARY, 2 * n);
         for (int r = 0; r < n; ++r) {
             if (r == col) continue;
             double f = A[r][col];
             for (int c = 0; c < 2 * n; ++c) A[r][c] -= f * A[col][c];
+            TALLY(ORC_OPS_BARY, 4 * n);
         }
     }
     for (int r = 0; r < n; ++r)
@@ -317,6 +336,7 @@ static void integrate_simplex(int dim, const simplex* S, double Minv[4][4], cons
     if (dim == 2) D = fabs(A[0] * B[1] - A[1] * B[0]);
     else D = fabs(A[0] * (B[1] * C[2] - B[2] * C[1]) - A[1] * (B[0] * C[2] - B[2] * C[0]) +
                   A[2] * (B[0] * C[1] - B[1] * C[0]));
+    TALLY(ORC_OPS_VOLUME, dim == 3 ? 9 + 14 : 4 + 3);  /* edge vectors, determinant */
     if (D == 0.0) return;
     int nw = dim == 3 ? nq : 1;
     for (int iu = 0; iu < nq; ++iu)
@@ -325,6 +345,12 @@ static void integrate_simplex(int dim, const simplex* S, double Minv[4][4], cons
                 double u = gx[iu], v = gx[iv], w = dim == 3 ? gx[iw] : 0.0;
                 double wt = gw[iu] * gw[iv] * (dim == 3 ? gw[iw] : 1.0);
                 double jac = dim == 3 ? u * u * v * D : u * D;
+                /* per point: wt 2, jac 3 (2-D: 1), x 6 per axis, lambda 2*dim per
+                 * vertex, t 2 per axis, f 1, vol 1, psi dim products per corner
+                 * plus one 1-t per zero bit (dim*nb/2 over all corners), and
+                 * 3 per block entry */
+                TALLY(ORC_OPS_QUAD, 2 + (dim == 3 ? 3 : 1) + 6 * dim + na * 2 * dim + 2 * dim + 2 +
+                                        nb * dim + nb * dim / 2 + 3 * na * nb);
                 double x[3];
                 for (int j = 0; j < dim; ++j) x[j] = p[0][j] + u * (A[j] + v * (B[j] + w * C[j]));
                 double lam[4];
@@ -365,9 +391,11 @@ static int pair_block(int dim, const int64_t* ncell, const double* origin, const
         if (axis && axis[k]) {
             clo[k] = axis[k][ci[k]];
             h[k] = axis[k][ci[k] + 1] - axis[k][ci[k]];
+            TALLY(ORC_OPS_FRAME, 1);
         } else {
             clo[k] = origin[k] + (double)ci[k] * h_uniform[k];
             h[k] = h_uniform[k];
+            TALLY(ORC_OPS_FRAME, 2);
         }
     }
     simplex S;
@@ -375,6 +403,7 @@ static int pair_block(int dim, const int64_t* ncell, const double* origin, const
     for (int v = 0; v < na; ++v) {
         const double* p = X + (int64_t)E[e * na + v] * dim;
         for (int k = 0; k < dim; ++k) S.v[v][k] = p[k] - clo[k];
+        TALLY(ORC_OPS_FRAME, dim);
     }
     double Minv[4][4];
     if (barycentric_map(dim, S.v, Minv) != ORC_OK) return ORC_EDEGENERATE;
@@ -395,11 +424,13 @@ static int pair_block(int dim, const int64_t* ncell, const double* origin, const
     return ORC_OK;
 }
 
-/* Blocks of all pairs: blocks[p * (d+1) * 2^d + a * 2^d + b], vols[p]. */
-int orc_pair_blocks(int dim, const int64_t* ncell, const double* origin, const double* h,
-                    const double* const* axis, const double* X, const int32_t* E, int64_t n_pairs,
-                    const int32_t* pair_elem, const int64_t* pair_cell, double* blocks, double* vols,
-                    int nthreads) {
+/* Blocks of all pairs: blocks[p * (d+1) * 2^d + a * 2^d + b], vols[p].  With
+ * ops != NULL the per-thread operation tallies of this call are added into
+ * ops[0 .. ORC_OPS_N). */
+int orc_pair_blocks_counted(int dim, const int64_t* ncell, const double* origin, const double* h,
+                            const double* const* axis, const double* X, const int32_t* E, int64_t n_pairs,
+                            const int32_t* pair_elem, const int64_t* pair_cell, double* blocks, double* vols,
+                            int nthreads, uint64_t* ops) {
     int nbl = (dim + 1) << dim;
     int status = ORC_OK;
 #ifdef _OPENMP
@@ -407,6 +438,7 @@ int orc_pair_blocks(int dim, const int64_t* ncell, const double* origin, const d
 #endif
     {
         slist L0 = {0, 0, 0}, L1 = {0, 0, 0};
+        for (int c = 0; c < ORC_OPS_N; ++c) t_ops[c] = 0;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 256)
 #endif
@@ -422,7 +454,21 @@ int orc_pair_blocks(int dim, const int64_t* ncell, const double* origin, const d
         }
         free(L0.s);
         free(L1.s);
+        if (ops) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            for (int c = 0; c < ORC_OPS_N; ++c) ops[c] += t_ops[c];
+        }
     }
     (void)nthreads;
     return status;
+}
+
+int orc_pair_blocks(int dim, const int64_t* ncell, const double* origin, const double* h,
+                    const double* const* axis, const double* X, const int32_t* E, int64_t n_pairs,
+                    const int32_t* pair_elem, const int64_t* pair_cell, double* blocks, double* vols,
+                    int nthreads) {
+    return orc_pair_blocks_counted(dim, ncell, origin, h, axis, X, E, n_pairs, pair_elem, pair_cell, blocks, vols,
+                                   nthreads, NULL);
 }
