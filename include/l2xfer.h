@@ -199,6 +199,19 @@ l2x_status l2x_apply_BT(l2x_handle h, const void* const* z_s, void* const* f_f, 
                         void* stream);
 l2x_status l2x_solve_mass(l2x_handle h, const void* const* y_s, void* const* w_s, void* stream);
 
+/* Adjoint of the force transfer (the backward of a differentiable force
+ * transfer): for every grid g,
+ *   DUAL : g_s[g] = s * m ⊙ S^{-1} B_g g_f[g]
+ *   NODAL: g_s[g] = s * m ⊙ B_g g_f[g]
+ * with s = force_scale and m the interface mask of l2x_set_force_mask (all
+ * ones without one), so that <g_f, F f_s> = <g_s, f_s> for the force transfer
+ * f_f += F f_s of l2x_transfer_force (Step 4 of Sec. 3 is the transpose of the
+ * velocity transfer, and this is the transpose of Step 4).  g_f: n_grids fluid
+ * arrays; g_s: n_grids arrays of n_nodes entries (written).  Synchronises
+ * `stream` in the DUAL mode with S = M_s (CG status).  Errors as
+ * l2x_transfer_velocity. */
+l2x_status l2x_transfer_force_adjoint(l2x_handle h, const void* const* g_f, void* const* g_s, void* stream);
+
 /* Interface restriction of the force input (Sec. 2's interface Gamma_fsi; in
  * the plate benchmark of Sec. 4 only the reaction forces of the top and bottom
  * edges are communicated).  mask: device array of n_nodes bytes, nonzero =
@@ -322,6 +335,27 @@ l2x_status l2x_set_timing(l2x_handle h, int32_t enable);
 
 /* Number of kernels this library has launched in this process (all handles). */
 int64_t l2x_kernel_launch_count(void);
+
+/* Throughput probe of the FP64 (precision = L2X_FP64) or FP32 (L2X_MIXED)
+ * fused multiply-add pipe, the measured denominator of the ALU roofline of the
+ * clipping kernel.  No counterpart in the paper.  Enqueues one kernel of
+ * n_blocks blocks of 256 threads; every thread runs `iters` iterations of 8
+ * independent FMA chains, i.e. 2 * 8 * 256 * n_blocks * iters floating-point
+ * operations, and writes one value into sink (device, n_blocks * 256 doubles
+ * or floats, caller-owned).  Time it with events on `stream`.  Does not
+ * synchronise.  Errors: EINVAL (arguments), ECUDA (launch). */
+l2x_status l2x_fma_probe(int32_t precision, int32_t n_blocks, int32_t iters, void* sink, void* stream);
+
+/* Test hook for the arithmetic helpers of the clipping kernel (no counterpart
+ * in the paper): out[i] = op(a[i], b[i]) for i < n, device arrays of doubles,
+ * enqueued on `stream`.  op 0: the kernel's quotient (reciprocal by
+ * Newton-Raphson from an FP32 seed, then Markstein's correction of the
+ * quotient); 1: CUDA's a / b; 2: the kernel's double -> float conversion by
+ * integer instructions (round half away from zero, below 2^-126 to zero); 3:
+ * CUDA's __double2float_rn; 4: the low float of the kernel's double-float split
+ * (a - float(a)); 5: the kernel's float -> double conversion of
+ * __double2float_rn(a).  b is read by ops 0 and 1 only.  Errors: EINVAL, ECUDA. */
+l2x_status l2x_fp_selftest(int32_t op, int64_t n, const double* a, const double* b, double* out, void* stream);
 
 /* Jacobi-preconditioned CG that allocates no device memory.
  *

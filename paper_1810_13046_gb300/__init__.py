@@ -96,6 +96,9 @@ def load_library(build_if_missing: bool = True):
         "l2x_transfer_velocity": ([P, PP, PP, P], ctypes.c_int),
         "l2x_transfer_force": ([P, PP, PP, P], ctypes.c_int),
         "l2x_apply_B": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_transfer_force_adjoint": ([P, PP, PP, P], ctypes.c_int),
+        "l2x_fma_probe": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P], ctypes.c_int),
+        "l2x_fp_selftest": ([ctypes.c_int32, ctypes.c_int64, P, P, P, P], ctypes.c_int),
         "l2x_transfer_velocity_async": ([P, PP, PP, P], ctypes.c_int),
         "l2x_set_force_mask": ([P, P, P], ctypes.c_int),
         "l2x_transfer_force_async": ([P, PP, PP, P], ctypes.c_int),
@@ -131,6 +134,32 @@ def load_library(build_if_missing: bool = True):
         fn.restype = res
     _lib = lib
     return lib
+
+
+def fma_probe(precision: int, n_blocks: int, iters: int, sink: torch.Tensor):
+    """Enqueues the FMA-pipe throughput probe (FP64 for ``FP64``, FP32 for
+    ``MIXED``) on the current stream; returns its floating-point operations.
+    ``sink``: a CUDA tensor of n_blocks * 256 doubles (or floats)."""
+    dt = torch.float64 if precision == FP64 else torch.float32
+    if sink.dtype != dt or not sink.is_cuda or sink.numel() < n_blocks * 256:
+        raise ValueError("sink must be a CUDA tensor of n_blocks * 256 entries of the probe's type")
+    with torch.cuda.device(sink.device):
+        _check(load_library().l2x_fma_probe(int(precision), int(n_blocks), int(iters),
+                                            ctypes.c_void_p(sink.data_ptr()), _stream_ptr(sink.device)))
+    return 2 * 8 * 256 * int(n_blocks) * int(iters)
+
+
+def fp_selftest(op: int, a: torch.Tensor, b: torch.Tensor | None = None) -> torch.Tensor:
+    """Runs one of the clipping kernel's arithmetic helpers (or the CUDA operation
+    it stands in for) elementwise on CUDA float64 tensors; see l2x_fp_selftest."""
+    a = a.to(torch.float64).contiguous()
+    b = (a if b is None else b.to(torch.float64)).contiguous()
+    out = torch.empty_like(a)
+    with torch.cuda.device(a.device):
+        _check(load_library().l2x_fp_selftest(int(op), a.numel(), ctypes.c_void_p(a.data_ptr()),
+                                              ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                              _stream_ptr(a.device)))
+    return out
 
 
 def kernel_launch_count() -> int:
@@ -349,6 +378,16 @@ class Coupling:
             _check(load_library().l2x_apply_BT(self._h, _ptrs(z_s), _ptrs(f_f), float(scale), _stream_ptr(self.device)))
         return f_f
 
+    def transfer_force_adjoint(self, g_f, out=None):
+        """g_s[g] = s m ⊙ S^-1 B_g g_f[g] (DUAL) or s m ⊙ B_g g_f[g] (NODAL): the
+        transpose of :meth:`transfer_force` (m the interface mask, s the scale)."""
+        g_f = self._fields(g_f, self.fluid_sizes())
+        g_s = out if out is not None else self._solid()
+        with torch.cuda.device(self.device):
+            _check(load_library().l2x_transfer_force_adjoint(self._h, _ptrs(g_f), _ptrs(g_s),
+                                                             _stream_ptr(self.device)))
+        return g_s
+
     def solve_mass(self, y_s, out=None):
         y_s = self._fields(y_s, [self.n_nodes] * self.n_grids)
         w = out if out is not None else self._solid()
@@ -546,10 +585,4 @@ class ForceTransfer(torch.autograd.Function):
         c = ctx.coupling
         gf = [(g if g is not None else torch.zeros(n, dtype=c.dtype, device=c.device)).contiguous()
               for g, n in zip(grad_f_f, c.fluid_sizes())]
-        y = c.apply_B(gf)
-        if c.force_mode == DUAL:
-            y = c.solve_mass(y)
-        m = getattr(c, "force_mask", None)
-        if m is not None:  # adjoint of the restriction f -> mask * f
-            y = [v * m.to(v.dtype) for v in y]
-        return (None, *[c.force_scale * v for v in y])
+        return (None, *c.transfer_force_adjoint(gf))

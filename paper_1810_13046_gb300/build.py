@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libl2xfer.so")
-SOURCES = ["l2x_api.cu", "l2x_pairs.cu", "l2x_clip.cu", "l2x_assemble.cu", "l2x_apply.cu", "l2x_noalloc.cu"]
+SOURCES = ["l2x_api.cu", "l2x_pairs.cu", "l2x_clip.cu", "l2x_assemble.cu", "l2x_apply.cu", "l2x_noalloc.cu", "l2x_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

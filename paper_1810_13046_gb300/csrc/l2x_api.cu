@@ -1031,6 +1031,26 @@ l2x_status l2x_transfer_force(l2x_handle h, const void* const* f_s_in, void* con
     return l2x_apply_BT(h, (const void* const*)z, f_f, h->opts.force_scale, stream);
 }
 
+l2x_status l2x_transfer_force_adjoint(l2x_handle h, const void* const* g_f, void* const* g_s, void* stream) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    L2X_TRY(check_ptrs(g_f, h->n_grids, "g_f"));
+    L2X_TRY(check_ptrs((const void* const*)g_s, h->n_grids, "g_s"));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->opts.force_mode == L2X_FORCE_DUAL) {
+        const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+        void* y[kMaxGrids];
+        for (int g = 0; g < h->n_grids; ++g) y[g] = (char*)h->vec_tmp + es * h->n_nodes * g;
+        L2X_TRY(l2x_apply_B(h, g_f, y, stream));
+        L2X_TRY(l2x_solve_mass(h, (const void* const*)y, g_s, stream));
+    } else {
+        L2X_TRY(l2x_apply_B(h, g_f, g_s, stream));
+    }
+    launch_scale_mask(h->opts.precision, h->n_nodes, h->n_grids, h->has_fmask ? h->fmask : nullptr,
+                      h->opts.force_scale, g_s, h->st, s);
+    L2X_CUDA(cudaGetLastError());
+    return L2X_OK;
+}
+
 l2x_status l2x_set_force_mask(l2x_handle h, const uint8_t* mask, void* stream) {
     if (!h) return fail(L2X_EINVAL, "NULL handle");
     cudaStream_t s = (cudaStream_t)stream;

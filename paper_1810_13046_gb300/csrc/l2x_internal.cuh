@@ -206,6 +206,8 @@ void launch_mask_copy(int precision, int64_t n, int nr, const uint8_t* mask, con
                       const DevStatus* st, cudaStream_t s);
 // w_k = y_k / S_ii for a diagonal S (dinv = 1/S_ii), k < nr; vectors in the
 // precision's type, the product taken in FP64.
+void launch_scale_mask(int precision, int64_t n, int nr, const uint8_t* mask, double scale, void* const* v,
+                       const DevStatus* st, cudaStream_t s);
 void launch_diag_solve(int precision, int64_t n, int nr, const double* dinv, const void* const* y,
                        void* const* w, const DevStatus* st, cudaStream_t s);
 // f[g] += scale * B_g^T z[g].  Fused: gather over the rows of B_g^T (no atomics);
