@@ -29,7 +29,28 @@ struct SpmvPack {
     const double* scale;  // optional row scaling (1/S_ii of a diagonal S), shared by the grids
 };
 
-// 8 lanes per row; accumulation in the vector type.
+// Sum of FP32 products in double-float: every product enters exactly (FMA
+// two-product), the running sum by Knuth's two-sum, so the mixed form's only
+// roundings are those of the FP32 inputs and of the one final result.
+struct DFAcc {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, pe));
+    }
+    __device__ __forceinline__ void reduce_xor(int o) {
+        const DF r = df_add(DF{hi, lo}, df_shfl_xor(DF{hi, lo}, o));
+        hi = r.hi;
+        lo = r.lo;
+    }
+};
+
+// 8 lanes per row; FP64 accumulation in FP64, double-float in the mixed form.
 template <typename TV, typename TM>
 __global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM> P, const DevStatus* st) {
     if (st->flags & kAbortFlags) return;
@@ -39,18 +60,35 @@ __global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM
     const bool active = grp < n_rows * n_grids;
     const int g = active ? (int)(grp / n_rows) : 0;
     const int64_t row = active ? grp - g * n_rows : 0;
-    TV acc = TV(0);
-    if (active) {
-        const int64_t lo = P.ptr[g][row], hi = P.ptr[g][row + 1];
-        const int32_t* __restrict__ col = P.col[g];
-        const TM* __restrict__ val = P.val[g];
-        const TV* __restrict__ x = P.x[g];
-        for (int64_t q = lo + l8; q < hi; q += 8) acc += (TV)__ldg(val + q) * __ldg(x + __ldg(col + q));
+    if constexpr (sizeof(TV) == 4) {
+        DFAcc acc;
+        if (active) {
+            const int64_t lo = P.ptr[g][row], hi = P.ptr[g][row + 1];
+            const int32_t* __restrict__ col = P.col[g];
+            const TM* __restrict__ val = P.val[g];
+            const TV* __restrict__ x = P.x[g];
+            for (int64_t q = lo + l8; q < hi; q += 8) acc.add_prod((float)__ldg(val + q), __ldg(x + __ldg(col + q)));
+        }
+        acc.reduce_xor(4);
+        acc.reduce_xor(2);
+        acc.reduce_xor(1);
+        if (active && l8 == 0)
+            P.y[g][row] = P.scale ? d2f_int((f2d_int(acc.hi) + f2d_int(acc.lo)) * __ldg(P.scale + row))
+                                  : __fadd_rn(acc.hi, acc.lo);
+    } else {
+        TV acc = TV(0);
+        if (active) {
+            const int64_t lo = P.ptr[g][row], hi = P.ptr[g][row + 1];
+            const int32_t* __restrict__ col = P.col[g];
+            const TM* __restrict__ val = P.val[g];
+            const TV* __restrict__ x = P.x[g];
+            for (int64_t q = lo + l8; q < hi; q += 8) acc += (TV)__ldg(val + q) * __ldg(x + __ldg(col + q));
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (active && l8 == 0) P.y[g][row] = P.scale ? (TV)((double)acc * __ldg(P.scale + row)) : acc;
     }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    if (active && l8 == 0) P.y[g][row] = P.scale ? (TV)((double)acc * __ldg(P.scale + row)) : acc;
 }
 
 __global__ void spmv_B_plain_kernel(int64_t n_rows, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
@@ -87,6 +125,21 @@ __global__ void diag_solve_kernel(int64_t n, int nr, const double* __restrict__ 
     w0[i] = (TV)((double)y0[i] * di);
     if (nr > 1) w1[i] = (TV)((double)y1[i] * di);
     if (nr > 2) w2[i] = (TV)((double)y2[i] * di);
+}
+
+// v_k = s * m_i * v_k in place (m = 1 where no mask is given): the interface
+// restriction and the force scale of the force transfer's adjoint; the product
+// in FP64, one rounding to TV.
+template <typename TV>
+__global__ void scale_mask_kernel(int64_t n, int nr, const uint8_t* __restrict__ mask, double scale, TV* v0, TV* v1,
+                                  TV* v2, const DevStatus* st) {
+    if (st->flags & kAbortFlags) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double f = (mask && mask[i] == 0) ? 0.0 : scale;
+    v0[i] = (TV)((double)v0[i] * f);
+    if (nr > 1) v1[i] = (TV)((double)v1[i] * f);
+    if (nr > 2) v2[i] = (TV)((double)v2[i] * f);
 }
 
 // ------------------------------------------------------------------ Picard norms
@@ -166,6 +219,16 @@ struct SpmvTPack {
     int G;
 };
 
+// Fluid node of row r of the B_g^T box.
+template <typename TV, typename TM>
+__device__ __forceinline__ int64_t bt_node(const SpmvTPack<TV, TM>& P, int g, int64_t r) {
+    const int x = (int)(r % P.nb[g][0]);
+    const int64_t rr = r / P.nb[g][0];
+    const int y = (int)(rr % P.nb[g][1]);
+    const int zz = (int)(rr / P.nb[g][1]);
+    return (x + P.lo[g][0]) + (int64_t)P.nn[g][0] * ((y + P.lo[g][1]) + (int64_t)P.nn[g][1] * (zz + P.lo[g][2]));
+}
+
 template <typename TV, typename TM>
 __global__ void spmv_BT_fused_kernel(SpmvTPack<TV, TM> P, TV scale, const DevStatus* st) {
     if (st->flags & kAbortFlags) return;
@@ -188,18 +251,38 @@ __global__ void spmv_BT_fused_kernel(SpmvTPack<TV, TM> P, TV scale, const DevSta
         const bool active = slot < total;
         int g = 0;
         while (g + 1 < P.G && slot >= first[g + 1]) ++g;
-        TV acc = TV(0);
         int64_t r = 0;
-        if (active) {
-            r = P.list[g][slot - first[g]];
-            const int64_t hi = P.ptr[g][r + 1];
-            const int32_t* __restrict__ col = P.col[g];
-            const TM* __restrict__ val = P.val[g];
-            const TV* __restrict__ z = P.z[g];
-            for (int64_t q = P.ptr[g][r] + lane; q < hi; q += kBTLanes) acc += (TV)__ldg(val + q) * __ldg(z + __ldg(col + q));
-        }
+        TV acc = TV(0);
+        if constexpr (sizeof(TV) == 4) {  // double-float sum, one rounding at the end
+            DFAcc a2;
+            if (active) {
+                r = P.list[g][slot - first[g]];
+                const int64_t hi = P.ptr[g][r + 1];
+                const int32_t* __restrict__ col = P.col[g];
+                const TM* __restrict__ val = P.val[g];
+                const TV* __restrict__ z = P.z[g];
+                for (int64_t q = P.ptr[g][r] + lane; q < hi; q += kBTLanes)
+                    a2.add_prod((float)__ldg(val + q), __ldg(z + __ldg(col + q)));
+            }
 #pragma unroll
-        for (int o = kBTLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            for (int o = kBTLanes / 2; o > 0; o >>= 1) a2.reduce_xor(o);
+            if (active && lane == 0) {
+                const int64_t node = bt_node(P, g, r);
+                P.f[g][node] = __fmaf_rn(scale, a2.lo, __fmaf_rn(scale, a2.hi, P.f[g][node]));
+            }
+            continue;
+        } else {
+            if (active) {
+                r = P.list[g][slot - first[g]];
+                const int64_t hi = P.ptr[g][r + 1];
+                const int32_t* __restrict__ col = P.col[g];
+                const TM* __restrict__ val = P.val[g];
+                const TV* __restrict__ z = P.z[g];
+                for (int64_t q = P.ptr[g][r] + lane; q < hi; q += kBTLanes) acc += (TV)__ldg(val + q) * __ldg(z + __ldg(col + q));
+            }
+#pragma unroll
+            for (int o = kBTLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        }
         if (active && lane == 0) {
             const int x = (int)(r % P.nb[g][0]);
             const int64_t rr = r / P.nb[g][0];
@@ -926,18 +1009,30 @@ __global__ void plain_scalars_kernel(int nr, double* scal, const double* rr0, do
 
 // ------------------------------------------------------------------ mixed-precision refinement
 // r64 = y - M x64 (FP64), norms[k] += |r64|^2
+// Power of two by which the FP32 correction solves see the residual of right-hand
+// side k: about 2^30 over the typical entry of y_k (|y_k| / sqrt(n)), so that
+// residuals down to rtol |y| and the products of their entries stay far from
+// the FP32 subnormal range (where the FMA two-product of the double-float dots
+// is no longer exact).  Exact scaling by a power of two; 0 for y_k = 0.
+__device__ __forceinline__ int corr_exp(double ynorm2, int64_t n) {
+    if (!(ynorm2 > 0.0)) return 0;
+    const int lg_n = 63 - __clzll((unsigned long long)n);
+    return 30 - ((ilogb_int(ynorm2) - lg_n) >> 1);
+}
+
 __global__ void residual_f64_kernel(int64_t n, int nr, const int64_t* ptr, const int32_t* col, const double* val,
                                     VecPack<const float> y, const double* x64, double* r64, float* r32,
-                                    double* norms) {
+                                    double* norms, const double* ynorm2) {
     __shared__ double sh[32];
     for (int k = 0; k < nr; ++k) {
         double acc = 0.0;
+        const int ek = corr_exp(ynorm2[k], n);
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
             double s = 0.0;
             for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) s = fma(val[e], x64[k * n + col[e]], s);
             double ri = (double)y.p[k][i] - s;
             r64[k * n + i] = ri;
-            r32[k * n + i] = (float)ri;
+            r32[k * n + i] = (float)ldexp_d_int(ri, ek);
             acc = fma(ri, ri, acc);
         }
         acc = block_sum(acc, sh);
@@ -945,10 +1040,16 @@ __global__ void residual_f64_kernel(int64_t n, int nr, const int64_t* ptr, const
     }
 }
 
-__global__ void add_correction_kernel(int64_t n, int nr, double* x64, VecPack<const float> d, int first) {
+// x += d: the first solve's result as it is, a correction scaled back by the
+// power of two its right-hand side was scaled by (corr_exp).
+__global__ void add_correction_kernel(int64_t n, int nr, double* x64, VecPack<const float> d, int first,
+                                      const double* ynorm2) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int k = 0; k < nr; ++k) x64[k * n + i] = (first ? 0.0 : x64[k * n + i]) + (double)d.p[k][i];
+    for (int k = 0; k < nr; ++k) {
+        if (first) x64[k * n + i] = (double)d.p[k][i];
+        else x64[k * n + i] += ldexp_d_int((double)d.p[k][i], -corr_exp(ynorm2[k], n));
+    }
 }
 
 __global__ void norm2_f32_kernel(int64_t n, int nr, VecPack<const float> y, double* out) {
@@ -1202,6 +1303,18 @@ void launch_diag_solve(int precision, int64_t n, int nr, const double* dinv, con
     }
 }
 
+void launch_scale_mask(int precision, int64_t n, int nr, const uint8_t* mask, double scale, void* const* v,
+                       const DevStatus* st, cudaStream_t s) {
+    if (n <= 0 || nr <= 0) return;
+    if (precision == L2X_MIXED) {
+        float* vv[3] = {(float*)v[0], nr > 1 ? (float*)v[1] : nullptr, nr > 2 ? (float*)v[2] : nullptr};
+        { scale_mask_kernel<float><<<nblk(n, 256), 256, 0, s>>>(n, nr, mask, scale, vv[0], vv[1], vv[2], st); count_launch(); }
+    } else {
+        double* vv[3] = {(double*)v[0], nr > 1 ? (double*)v[1] : nullptr, nr > 2 ? (double*)v[2] : nullptr};
+        { scale_mask_kernel<double><<<nblk(n, 256), 256, 0, s>>>(n, nr, mask, scale, vv[0], vv[1], vv[2], st); count_launch(); }
+    }
+}
+
 void launch_spmv_B(int path, int precision, int n_grids, const Csr* B, const void* const* x, void* const* y,
                    const DevStatus* st, cudaStream_t s, const double* row_scale) {
     const int64_t n = B[0].n_rows;
@@ -1331,10 +1444,10 @@ void solve_mass_pcg_async(int precision, const Csr& M, const double* diag_inv, c
         }
         run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner, max_iter, st, s,
                              rpb, clu, ref == 0 ? nullptr : tau);
-        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dp, ref == 0); count_launch(); }
+        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dp, ref == 0, norms + kMaxRhs); count_launch(); }
         if (ref == 0) {
             cudaMemsetAsync(norms, 0, kMaxRhs * 8, s);
-            { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf, x64, r64, r32, norms); count_launch(); }
+            { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf, x64, r64, r32, norms, norms + kMaxRhs); count_launch(); }
             { inner_tol_kernel<<<1, 32, 0, s>>>(nr, rtol, norms, norms + kMaxRhs, tau); count_launch(); }
         }
     }
@@ -1458,9 +1571,9 @@ l2x_status solve_mass_pcg(int path, int precision, const Csr& M, const double* d
         ce = run_pcg_fused<float>(M.ptr, M.col, M.val32, diag_inv32, n, nr, rhs, dst, vecs, partial, inner,
                                   max_iter, st, s, rpb, clu, ref == 0 ? nullptr : tau);
         if (ce != cudaSuccess) return L2X_ECUDA;
-        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dp, ref == 0); count_launch(); }
+        { add_correction_kernel<<<nb, 256, 0, s>>>(n, nr, x64, dp, ref == 0, norms + kMaxRhs); count_launch(); }
         cudaMemsetAsync(norms, 0, kMaxRhs * 8, s);
-        { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf, x64, r64, r32, norms); count_launch(); }
+        { residual_f64_kernel<<<nbd, 256, 0, s>>>(n, nr, M.ptr, M.col, M.val, yf, x64, r64, r32, norms, norms + kMaxRhs); count_launch(); }
         if (cudaMemcpyAsync(st_host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
         if (cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess) return L2X_ECUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return L2X_ECUDA;

@@ -202,10 +202,9 @@ struct MomentLayout {
     static constexpr int kN = kMu + D * kSqPer;  // 8 (2-D) / 20 (3-D)
 };
 
-// Cone triangle (0, q, r) in 2-D: D2 = 2*signed area.  ∫_T = D2 / (2+deg)! * sum.
+// Cone triangle (0, q, r) in 2-D: Dv = 2*signed area.  ∫_T = Dv / (2+deg)! * sum.
 template <typename R>
-__device__ __forceinline__ void cone_accum2(const R* q, const R* r, R* acc) {
-    R Dv = q[0] * r[1] - q[1] * r[0];
+__device__ __forceinline__ void cone_accum2(const R* q, const R* r, R Dv, R* acc) {
     R s0 = q[0] + r[0], s1 = q[1] + r[1];
     R P00 = q[0] * q[0] + r[0] * r[0];
     R P11 = q[1] * q[1] + r[1] * r[1];
@@ -234,22 +233,42 @@ __device__ __forceinline__ void finish_moments2(R* acc) {
     acc[7] *= R(1.0 / 120.0);
 }
 
-// Cone tetrahedron (0, p, q, r) in 3-D: D6 = 6*signed volume.  ∫_T = D6/(3+deg)! * sum.
+// Cone tetrahedron (0, p, q, r) in 3-D: Dv = 6*signed volume.  ∫_T = Dv/(3+deg)! * sum.
 template <typename R>
-__device__ __forceinline__ void cone_accum3(const R* p, const R* q, const R* r, R* acc) {
-    R Dv = p[0] * (q[1] * r[2] - q[2] * r[1]) + p[1] * (q[2] * r[0] - q[0] * r[2]) +
-           p[2] * (q[0] * r[1] - q[1] * r[0]);
+__device__ __forceinline__ R det3(const R* p, const R* q, const R* r) {
+    return p[0] * (q[1] * r[2] - q[2] * r[1]) + p[1] * (q[2] * r[0] - q[0] * r[2]) + p[2] * (q[0] * r[1] - q[1] * r[0]);
+}
+
+// The same determinant in double-float arithmetic (FP32 instructions only): the
+// intersection volume of the mixed form keeps FP64-level accuracy without
+// issuing to the narrow FP64 unit.
+__device__ __forceinline__ DF df_det3(const DF* p, const DF* q, const DF* r) {
+    const DF c0 = df_add(df_mul(q[1], r[2]), df_neg(df_mul(q[2], r[1])));
+    const DF c1 = df_add(df_mul(q[2], r[0]), df_neg(df_mul(q[0], r[2])));
+    const DF c2 = df_add(df_mul(q[0], r[1]), df_neg(df_mul(q[1], r[0])));
+    return df_add(df_add(df_mul(p[0], c0), df_mul(p[1], c1)), df_mul(p[2], c2));
+}
+__device__ __forceinline__ DF df_det2(const DF* q, const DF* r) {
+    return df_add(df_mul(q[0], r[1]), df_neg(df_mul(q[1], r[0])));
+}
+
+// Moments of the tetrahedron (apex, p, q, r): the power sums run over all four
+// vertices; with ap == nullptr the apex is the origin and drops out, else it is
+// the point ap[0..2].
+template <typename R>
+__device__ __forceinline__ void cone_accum3(const R* p, const R* q, const R* r, R Dv, R* acc,
+                                            const R* ap = nullptr) {
     R s[3], P[3][3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) s[k] = p[k] + q[k] + r[k];
+    for (int k = 0; k < 3; ++k) s[k] = p[k] + q[k] + r[k] + (ap ? ap[k] : R(0));
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int l = k; l < 3; ++l) {
-            P[k][l] = p[k] * p[l] + q[k] * q[l] + r[k] * r[l];
+            P[k][l] = p[k] * p[l] + q[k] * q[l] + r[k] * r[l] + (ap ? ap[k] * ap[l] : R(0));
             P[l][k] = P[k][l];
         }
-    R Q012 = p[0] * p[1] * p[2] + q[0] * q[1] * q[2] + r[0] * r[1] * r[2];
+    R Q012 = p[0] * p[1] * p[2] + q[0] * q[1] * q[2] + r[0] * r[1] * r[2] + (ap ? ap[0] * ap[1] * ap[2] : R(0));
     acc[0] += Dv;
     acc[1] += Dv * s[0];
     acc[2] += Dv * s[1];
@@ -262,9 +281,10 @@ __device__ __forceinline__ void cone_accum3(const R* p, const R* q, const R* r, 
     for (int j = 0; j < 3; ++j) {
         const int a = (j + 1) % 3, b = (j + 2) % 3;
         R pj2 = p[j] * p[j], qj2 = q[j] * q[j], rj2 = r[j] * r[j];
-        R Qjja = pj2 * p[a] + qj2 * q[a] + rj2 * r[a];
-        R Qjjb = pj2 * p[b] + qj2 * q[b] + rj2 * r[b];
-        R Rjjab = pj2 * p[a] * p[b] + qj2 * q[a] * q[b] + rj2 * r[a] * r[b];
+        const R aj2 = ap ? ap[j] * ap[j] : R(0);
+        R Qjja = pj2 * p[a] + qj2 * q[a] + rj2 * r[a] + (ap ? aj2 * ap[a] : R(0));
+        R Qjjb = pj2 * p[b] + qj2 * q[b] + rj2 * r[b] + (ap ? aj2 * ap[b] : R(0));
+        R Rjjab = pj2 * p[a] * p[b] + qj2 * q[a] * q[b] + rj2 * r[a] * r[b] + (ap ? aj2 * ap[a] * ap[b] : R(0));
         R sj = s[j], sa = s[a], sb = s[b];
         acc[8 + 4 * j + 0] += Dv * (sj * sj + P[j][j]);
         acc[8 + 4 * j + 1] += Dv * (sj * sj * sa + R(2) * sj * P[j][a] + sa * P[j][j] + R(2) * Qjja);
@@ -308,37 +328,103 @@ __device__ __forceinline__ R moment_nu(const R* acc, int j, int S) {
     return acc[S | (1 << j)];
 }
 
+// Frame of the FP32 moments of the mixed 3-D form: they are taken about a point
+// c near the middle of E ∩ C (c given in apex coordinates, a float), not about
+// the apex, so that they carry no large offset that the contraction with
+// lambda_a psi_b would cancel (the apex sits on the crossed cell planes and can
+// lie a few element sizes from the element).  The apex becomes the fourth
+// vertex -c of every cone tetrahedron.
+struct ShiftFrame {
+    float c[3];   // the point, apex coordinates
+    float a[3];   // the apex in the frame: -c
+};
+
 // Fan a polygon given in apex coordinates (apex at the origin) into cone
 // simplices and accumulate their moments.  2-D: cone triangles (0, v_i, v_i+1);
-// 3-D: cone tetrahedra (0, v_0, v_i, v_i+1).
+// 3-D: cone tetrahedra (0, v_0, v_i, v_i+1).  With R = float the cone volumes
+// come from double-float determinants of the FP64 vertices (split into float
+// pairs by integer instructions) and their sum is kept in *vol_df; the other
+// moments take the vertices relative to the frame's point (3-D; in 2-D the
+// apex is a vertex of the polygon itself).
 template <int D, typename R>
-__device__ __forceinline__ void accum_polygon(const double (*poly)[D], int n, R* acc) {
+__device__ __forceinline__ void accum_polygon(const double (*poly)[D], int n, R* acc, DF* vol_df,
+                                              const ShiftFrame* fr = nullptr) {
+    constexpr bool kDF = sizeof(R) == 4;
     if constexpr (D == 2) {
         R q[2], r[2];
-        q[0] = to_r<R>(poly[0][0]);
-        q[1] = to_r<R>(poly[0][1]);
+        DF qd[2], rd[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if constexpr (kDF) {
+                qd[k] = df_split_int(poly[0][k]);
+                q[k] = qd[k].hi;
+            } else {
+                q[k] = to_r<R>(poly[0][k]);
+            }
+        }
         for (int i = 0; i < n; ++i) {
             const int j = i + 1 == n ? 0 : i + 1;
-            r[0] = to_r<R>(poly[j][0]);
-            r[1] = to_r<R>(poly[j][1]);
-            cone_accum2<R>(q, r, acc);
-            q[0] = r[0];
-            q[1] = r[1];
+            R Dv;
+            if constexpr (kDF) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    rd[k] = df_split_int(poly[j][k]);
+                    r[k] = rd[k].hi;
+                }
+                const DF dv = df_det2(qd, rd);
+                *vol_df = df_add(*vol_df, dv);
+                Dv = __fadd_rn(dv.hi, dv.lo);
+            } else {
+                r[0] = to_r<R>(poly[j][0]);
+                r[1] = to_r<R>(poly[j][1]);
+                Dv = q[0] * r[1] - q[1] * r[0];
+            }
+            cone_accum2<R>(q, r, Dv, acc);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                q[k] = r[k];
+                if constexpr (kDF) qd[k] = rd[k];
+            }
         }
     } else {
         if (n < 3) return;
         R p[3], q[3], r[3];
+        DF pd[3], qd[3], rd[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            p[k] = to_r<R>(poly[0][k]);
-            q[k] = to_r<R>(poly[1][k]);
+            if constexpr (kDF) {
+                pd[k] = df_split_int(poly[0][k]);
+                qd[k] = df_split_int(poly[1][k]);
+                p[k] = __fadd_rn(__fsub_rn(pd[k].hi, fr->c[k]), pd[k].lo);
+                q[k] = __fadd_rn(__fsub_rn(qd[k].hi, fr->c[k]), qd[k].lo);
+            } else {
+                p[k] = to_r<R>(poly[0][k]);
+                q[k] = to_r<R>(poly[1][k]);
+            }
         }
         for (int i = 1; i + 1 < n; ++i) {
+            R Dv;
+            if constexpr (kDF) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) r[k] = to_r<R>(poly[i + 1][k]);
-            cone_accum3<R>(p, q, r, acc);
+                for (int k = 0; k < 3; ++k) {
+                    rd[k] = df_split_int(poly[i + 1][k]);
+                    r[k] = __fadd_rn(__fsub_rn(rd[k].hi, fr->c[k]), rd[k].lo);
+                }
+                const DF dv = df_det3(pd, qd, rd);
+                *vol_df = df_add(*vol_df, dv);
+                Dv = __fadd_rn(dv.hi, dv.lo);
+                cone_accum3<R>(p, q, r, Dv, acc, reinterpret_cast<const R*>(fr->a));
+            } else {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) q[k] = r[k];
+                for (int k = 0; k < 3; ++k) r[k] = to_r<R>(poly[i + 1][k]);
+                Dv = det3<R>(p, q, r);
+                cone_accum3<R>(p, q, r, Dv, acc);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                q[k] = r[k];
+                if constexpr (kDF) qd[k] = rd[k];
+            }
         }
     }
 }
@@ -484,6 +570,27 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     R acc[L::kN];
 #pragma unroll
     for (int i = 0; i < L::kN; ++i) acc[i] = R(0);
+    DF vol_df{0.0f, 0.0f};  // D! x |E ∩ C| in double-float (mixed form)
+    // mixed 3-D form: the frame of the FP32 moments (a point near the middle of
+    // E ∩ C, apex coordinates) and lambda_a there in double-float
+    constexpr bool kShift = sizeof(R) == 4 && D == 3;
+    ShiftFrame fr;
+    if constexpr (kShift) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float ck = 0.0f;  // uncrossed axis: the apex is already at the middle of the overlap
+            if (apex_v >= 0)  // element inside the cell: its centroid
+                ck = __fsub_rn(0.25f * (d2f_int(T[0][k]) + d2f_int(T[1][k]) + d2f_int(T[2][k]) + d2f_int(T[3][k])),
+                               d2f_int(A[k]));
+            else if ((lower_mask >> k) & 1)  // apex at t_k = 0, E ∩ C within [0, min(t_max, 1)]
+                ck = 0.5f * d2f_int(from_order_key(min(kmax[k], K1)));
+            else if ((upper_mask >> k) & 1)  // apex at t_k = 1, E ∩ C within [max(t_min, 0), 1]
+                ck = 0.5f * __fsub_rn(d2f_int(from_order_key(max(kmin[k], 0LL))), 1.0f);
+            fr.c[k] = ck;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) fr.a[k] = -fr.c[k];
+    }
     // the two polygon buffers (2 * kMaxPoly vertices), owned by the caller
     double (*bufA)[D] = poly;
     double (*bufB)[D] = poly + kMaxPoly;
@@ -521,7 +628,7 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
             }
 #pragma unroll
             for (int k = 0; k < D; ++k) A[k] = P0[k];
-            accum_polygon<D, R>(cur, n, acc);
+            accum_polygon<D, R>(cur, n, acc, &vol_df);
         }
         finish_moments2<R>(acc);
     } else {
@@ -568,7 +675,7 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
                 n = clip_axis<D>(cur, n, nxt, plane_k[jp], plane_c[jp], plane_up[jp] != 0);
                 double (*t)[D] = cur; cur = nxt; nxt = t;
             }
-            accum_polygon<D, R>(cur, n, acc);
+            accum_polygon<D, R>(cur, n, acc, &vol_df, &fr);
         }
         // cell faces the element crosses, clipped to the element (a face whose
         // plane holds the apex spans a cone of zero volume and is skipped)
@@ -596,20 +703,43 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
                 n = clip_plane<D>(cur, n, nxt, g[a], cA[a]);
                 double (*t)[D] = cur; cur = nxt; nxt = t;
             }
-            accum_polygon<D, R>(cur, n, acc);
+            accum_polygon<D, R>(cur, n, acc, &vol_df, &fr);
         }
         finish_moments3<R>(acc);
     }
     // lambda_a = cA[a] + g[a].u and psi_b = prod_k (alpha_bk + sigma_bk u_k) around the apex
     const R scale_r = to_r<R>(scale);
-    if constexpr (sizeof(R) == 4) *vol = f2d_int(acc[0] * scale_r);
+    if constexpr (sizeof(R) == 4) *vol = df_to_double(vol_df) * (scale * (D == 3 ? 1.0 / 6.0 : 0.5));
     else *vol = (double)acc[0] * scale;
+    // lambda_a at the origin of the moments: at the apex, or (mixed 3-D form) at
+    // the frame's point, in double-float
+    R cC[NA];
+    if constexpr (kShift) {
+        DF c0{1.0f, 0.0f};
+#pragma unroll
+        for (int a = 1; a < NA; ++a) {
+            DF v = df_split_int(cA[a]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v = df_add(v, df_mul(df_split_int(g[a][k]), DF{fr.c[k], 0.0f}));
+            cC[a] = __fadd_rn(v.hi, v.lo);
+            c0 = df_add(c0, df_neg(v));
+        }
+        cC[0] = __fadd_rn(c0.hi, c0.lo);
+    } else {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) cC[a] = to_r<R>(cA[a]);
+    }
     R W[NB], Wj[NB][D];
-    R Ar[D], A1r[D];
+    R Ar[D], A1r[D];  // psi_b factors t_k and 1 - t_k at the origin of the moments
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        Ar[k] = to_r<R>(A[k]);
-        A1r[k] = to_r<R>(1.0 - A[k]);
+        if constexpr (kShift) {
+            Ar[k] = __fadd_rn(d2f_int(A[k]), fr.c[k]);
+            A1r[k] = __fsub_rn(1.0f, Ar[k]);
+        } else {
+            Ar[k] = to_r<R>(A[k]);
+            A1r[k] = to_r<R>(1.0 - A[k]);
+        }
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -639,7 +769,7 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     }
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
-        const R ca = to_r<R>(cA[a]);
+        const R ca = cC[a];
         R ga[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) ga[k] = to_r<R>(g[a][k]);

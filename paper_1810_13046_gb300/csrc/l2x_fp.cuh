@@ -58,8 +58,12 @@ template <>
 __device__ __forceinline__ float to_r<float>(double x) { return d2f_int(x); }
 
 // a / b by Newton-Raphson on the reciprocal (seed: single-precision reciprocal),
-// two refinements and one residual correction of the quotient.  Used for the
-// edge parameters of plane crossings, where |b| > 0 and a / b lies in [0, 1].
+// two refinements r <- r + r (1 - b r), then the quotient q = a r and one
+// correction q + r (a - b q) with the residual formed exactly by an FMA (P.
+// Markstein, "Computation of elementary functions on the IBM RISC System/6000
+// processor", IBM J. Res. Dev. 34(1), 1990).  Used for the edge parameters of
+// plane crossings, where |b| > 0 and a / b lies in [0, 1]; operands far from 1
+// in magnitude take the hardware division.
 __device__ __forceinline__ double div_nr(double a, double b) {
     const int eb = (__double2hiint(b) >> 20) & 0x7ff;
     if (eb < 1023 - 120 || eb > 1023 + 120) return a / b;
@@ -89,6 +93,18 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     return DF{h, __fsub_rn(lo, __fsub_rn(h, s))};
 }
 
+// Product of two double-float values, left unnormalised (|lo| stays within a few
+// ulps of |hi|): hi*hi exactly by the FMA two-product, plus the cross terms; the
+// dropped lo*lo term is below 2^-46 of the product.
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return DF{p, e};
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
 __device__ __forceinline__ DF df_from_double(double x) {
     const float hi = d2f_int(x);
     return DF{hi, d2f_int(x - f2d_int(hi))};
@@ -114,6 +130,28 @@ __device__ __forceinline__ double ldexp_d_int(double x, int e) {
     if (en <= 0) return __longlong_as_double((long long)(u & 0x8000000000000000ull));
     return __longlong_as_double((long long)((u & 0x800fffffffffffffull) | ((unsigned long long)en << 52)));
 }
+// The low part of the double-float split of x whose high part is d2f_int(x):
+// x - d2f_int(x) as a float, by integer instructions only.  d2f_int keeps the top
+// 24 mantissa bits, rounding on bit 28, so the remainder is the low 29 bits read
+// as a signed number of ulps of x; its top 23 bits are kept (the split then
+// holds 47 or more significant bits of x).  Zero where d2f_int flushes to zero.
+__device__ __forceinline__ float d2f_lo_int(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    int r = ((int)((unsigned int)(b & 0x1fffffffull) << 3)) >> 3;  // x - hi in ulps of x, in [-2^28, 2^28)
+    if (r == 0 || e <= 896) return 0.0f;
+    unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    if (r < 0) {
+        r = -r;
+        sign ^= 0x80000000u;
+    }
+    const unsigned int a = (unsigned int)r;
+    const int sh = max(0, 9 - __clz(a));  // a >> sh < 2^23
+    const float f = __fsub_rn(__uint_as_float(0x4b000000u | (a >> sh)), 8388608.0f);  // exactly a >> sh
+    return ldexp_f_int(__uint_as_float(__float_as_uint(f) | sign), sh + e - 1075);
+}
+__device__ __forceinline__ DF df_split_int(double x) { return DF{d2f_int(x), d2f_lo_int(x)}; }
+
 // binary exponent of a positive finite double (floor(log2 x))
 __device__ __forceinline__ int ilogb_int(double x) {
     return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
