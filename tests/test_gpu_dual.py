@@ -106,14 +106,22 @@ def test_dual_force_transfer(name, mode, path, precision):
     dt = np.float32 if mixed else np.float64
     F = w.force.astype(dt)
     ref = oc.transfer_force(F.astype(np.float64), mode=mode, scale=scale)
+    f_s = [torch.from_numpy(np.ascontiguousarray(F[:, g])).cuda() for g in range(F.shape[1])]
+    tol = TOL_MIXED if mixed else TOL64
+    f_f = c.transfer_force(f_s)
+    for g in range(len(ref)):
+        assert rel_l2(f_f[g].cpu().numpy(), ref[g]) <= tol
+    # accumulation: base + value up to the roundings of the sums
     rng = np.random.default_rng(6)
     base = [(0.5 * np.abs(r).max() * rng.random(r.shape[0])).astype(dt) for r in ref]
-    f_f = [torch.from_numpy(b.copy()).cuda() for b in base]
-    c.transfer_force([torch.from_numpy(np.ascontiguousarray(F[:, g])).cuda() for g in range(F.shape[1])], f_f)
-    tol = TOL_MIXED if mixed else TOL64
+    f_acc = [torch.from_numpy(b.copy()).cuda() for b in base]
+    c.transfer_force(f_s, f_acc)
+    eps = np.finfo(dt).eps
     for g in range(len(ref)):
-        got = f_f[g].cpu().numpy().astype(np.float64) - base[g].astype(np.float64)
-        assert rel_l2(got, ref[g]) <= (2 * tol if mixed else tol)
+        b64, v64 = base[g].astype(np.float64), f_f[g].cpu().numpy().astype(np.float64)
+        # roundings of the sums in the field type (the plain path adds term by term)
+        bound = 64 * eps * (np.linalg.norm(b64) + np.linalg.norm(v64))
+        assert np.linalg.norm(f_acc[g].cpu().numpy() - (b64 + v64)) <= bound
 
 
 def test_dual_autograd_is_the_adjoint():
@@ -165,11 +173,12 @@ def test_dual_step_graph_matches_fresh_assembly(precision):
         assert rel_l2(torch.stack(u_s).cpu().numpy(), torch.stack(ur).cpu().numpy()) <= tol
         for a, b in zip(f_f, fr):
             assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= tol
-    k = int(np.argmin([b["E"].shape[0] for b in bodies]))
-    n0, n1 = nr[k]
-    e0, e1 = er[k]
-    ok = oracle.Coupling(grid, Xt[n0:n1], E[e0:e1] - n0, nthreads=NTHREADS, multiplier="dual")
+    # every body against the oracle on that body alone (its rows of B and S
+    # involve only its own elements)
     src_fields = [f.astype(np.float32).astype(np.float64) if mixed else f for f in fields]
-    uk = ok.transfer_velocity(src_fields)
-    got = torch.stack(u_s).cpu().numpy().T[n0:n1]
-    assert rel_l2(got, uk) <= 10 * tol
+    got_all = torch.stack(u_s).cpu().numpy().T
+    for k in range(len(bodies)):
+        n0, n1 = nr[k]
+        e0, e1 = er[k]
+        ok = oracle.Coupling(grid, Xt[n0:n1], E[e0:e1] - n0, nthreads=NTHREADS, multiplier="dual")
+        assert rel_l2(got_all[n0:n1], ok.transfer_velocity(src_fields)) <= tol, k

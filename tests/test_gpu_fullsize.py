@@ -8,12 +8,14 @@ oracle computes one by one and on properties that hold at any size.
   several element ranges spread over the mesh, against the FP64 oracle.
 * At any size: partition-of-unity row sums of every B_g, reproduction of an affine
   field by the velocity transfer, FP64 vs mixed agreement of the transfers.
+* Whole leaflet: the chosen mixed form's transfers (velocity, dual and nodal
+  force) against the oracle's, node by node, to 1e-6.
 """
 import numpy as np
 import pytest
 
 import oracle
-from _helpers import rel_l2, workload
+from _helpers import oracle_coupling, rel_l2, workload
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,7 +53,8 @@ def test_sampled_pairs_and_blocks(name, precision):
             scale = vol_e[pe + e0]
             err = np.abs(b.cpu().numpy() - ob).max(axis=(1, 2)) / scale
             assert err.max() <= tol, (g, e0, float(err.max()))
-            assert (np.abs(v.cpu().numpy() - ov) <= tol * scale).all()
+            # volumes at FP64 level in both forms
+            assert (np.abs(v.cpu().numpy() - ov) <= 1e-12 * scale).all()
 
 
 @pytest.mark.parametrize("name,precision", CASES)
@@ -98,3 +101,29 @@ def test_mixed_form_agrees_with_fp64(name):
                               for g in range(3)])
     for a, b in zip(f32, f64):
         assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= 1e-6  # N(0,1) forces: no zero component
+
+
+def test_leaflet256_mixed_transfers_against_oracle():
+    """The chosen form (fused, FP64 geometry, FP32 fields) on the whole
+    952,200-tet leaflet: u_s of the Taylor-Green field and f_f of N(0,1) nodal
+    forces in both force modes, against the FP64 oracle's, to 1e-6."""
+    import paper_1810_13046_gb300 as l2x
+    w = workload("leaflet256")
+    oc = oracle_coupling("leaflet256")
+    X = torch.from_numpy(w.coords).cuda()
+    E = torch.from_numpy(w.elems).cuda()
+    fields32 = [f.astype(np.float32) for f in w.fields]
+    F32 = w.force.astype(np.float32)
+    f_s = [torch.from_numpy(np.ascontiguousarray(F32[:, g])).cuda() for g in range(3)]
+    c = l2x.Coupling(w.grid, X, E, path=l2x.FUSED, precision=l2x.MIXED, cg_rtol=1e-9)
+    u_s = c.transfer_velocity([torch.from_numpy(f).cuda() for f in fields32])
+    ref = oc.transfer_velocity([f.astype(np.float64) for f in fields32])
+    got = np.stack([u.cpu().numpy() for u in u_s], axis=1)
+    assert rel_l2(got, ref) <= 1e-6
+    for mode, fm in (("dual", l2x.DUAL), ("nodal", l2x.NODAL)):
+        cm = c if fm == l2x.DUAL else l2x.Coupling(w.grid, X, E, path=l2x.FUSED, precision=l2x.MIXED,
+                                                   cg_rtol=1e-9, force_mode=fm)
+        f_f = cm.transfer_force(f_s)
+        fref = oc.transfer_force(F32.astype(np.float64), mode=mode)
+        for g in range(3):
+            assert rel_l2(f_f[g].cpu().numpy(), fref[g]) <= 1e-6, (mode, g)

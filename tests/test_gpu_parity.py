@@ -61,8 +61,9 @@ def test_pair_blocks(name, path, precision):
         b, v = b.cpu().numpy(), v.cpu().numpy()
         ob, ov = oc.pairs[g][2], oc.pairs[g][3]
         scale = vol_e[oc.pairs[g][0]]
-        assert np.abs(v - ov).max() / 1.0 <= tol * scale.max()
-        assert (np.abs(v - ov) <= tol * scale + 1e-300).all()
+        # intersection volumes: FP64-level in every form (the mixed form keeps them
+        # in double-float), so that no sliver is lost to FP32 rounding
+        assert (np.abs(v - ov) <= TOL64 * scale + 1e-300).all()
         err = np.abs(b - ob).max(axis=(1, 2)) / scale
         assert err.max() <= tol, (int(err.argmax()), float(err.max()))
 
@@ -142,15 +143,24 @@ def test_force_transfer(name, mode, path, precision):
     dt = np.float32 if mixed else np.float64
     F = w.force.astype(dt)
     ref = oc.transfer_force(F.astype(np.float64), mode=mode, scale=scale)
-    # the call accumulates: start from a non-zero array of the result's magnitude
+    f_s = [torch.from_numpy(np.ascontiguousarray(F[:, g])).cuda() for g in range(F.shape[1])]
+    tol = TOL_MIXED if mixed else TOL64
+    # the value, into zeroed fluid arrays
+    f_f = c.transfer_force(f_s)
+    for g in range(len(ref)):
+        assert rel_l2(f_f[g].cpu().numpy(), ref[g]) <= tol
+    # the call accumulates: from a non-zero array of the result's magnitude the
+    # result is base + value, up to the roundings of the sums in the field type
     rng = np.random.default_rng(4)
     base = [(0.5 * np.abs(r).max() * rng.random(r.shape[0])).astype(dt) for r in ref]
-    f_f = [torch.from_numpy(b.copy()).cuda() for b in base]
-    c.transfer_force([torch.from_numpy(np.ascontiguousarray(F[:, g])).cuda() for g in range(F.shape[1])], f_f)
-    tol = TOL_MIXED if mixed else TOL64
+    f_acc = [torch.from_numpy(b.copy()).cuda() for b in base]
+    c.transfer_force(f_s, f_acc)
+    eps = np.finfo(dt).eps
     for g in range(len(ref)):
-        got = f_f[g].cpu().numpy().astype(np.float64) - base[g].astype(np.float64)
-        assert rel_l2(got, ref[g]) <= (tol if not mixed else 2 * tol)
+        b64, v64 = base[g].astype(np.float64), f_f[g].cpu().numpy().astype(np.float64)
+        # roundings of the sums in the field type (the plain path adds term by term)
+        bound = 64 * eps * (np.linalg.norm(b64) + np.linalg.norm(v64))
+        assert np.linalg.norm(f_acc[g].cpu().numpy() - (b64 + v64)) <= bound
 
 
 def test_fused_build_is_deterministic():
