@@ -9,11 +9,14 @@ The chosen form runs a step as one replay of a captured CUDA graph (new node
 positions copied in, no host synchronisation); the per-call form (one library
 call per operation) is timed beside it with per-phase CUDA events.
 
-Workload (default): 128^3-cell staggered grids on [0,1]^3 (h = 1/128), a
-0.4 x 0.1 x 0.02 beam of 48,000 P1 tetrahedra under a seeded random rotation, a
+Workload (default, the largest single-GPU configuration): 512 x 512 x 256-cell
+staggered grids on [0,1]^2 x [0,0.5] (h = 1/512), a 0.4 x 0.1 x 0.02 beam of
+3,993,600 P1 tetrahedra with smoothed random node displacements, a
 Taylor-Green velocity field (float32) and N(0,1) nodal forces; synthetic data.
-Each rank (torchrun, N > 1) transfers its own independently rotated beam: weak
-scaling, no collective on the data path.
+The 48k-tet beam on 128^3 grids, the 952k-tet leaflet on 256^3 grids (with the
+differentiable transfer) and the 64 moving bodies on 256^3 grids are reported
+as extra keys of the same line.  Each rank (torchrun, N > 1) transfers its own
+body: weak scaling, no collective on the data path.
 
 value = candidate pairs per second over whole steps (summed over ranks);
 assembly pairs/s and apply ms are reported beside it, together with the plain
@@ -23,6 +26,7 @@ every timed step.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -39,7 +43,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "L2-transfer assembly pairs/s & apply ms, 1 GB300, fused vs plain at rel≤1e-6"
 UNIT = "pairs/s"
-WORKLOAD = "beam128"
+WORKLOAD = "beam512"
+EXTRA_WORKLOADS = ("beam128", "leaflet256", "batch64")
 WORKLOAD_DESCS = {
     "beam128": ("3-D staggered Q1 grids 128^3 cells (h=1/128) on [0,1]^3; rotated beam 0.4x0.1x0.02, "
                 "48,000 P1 tets / 10,206 nodes; Taylor-Green u_f (f32); N(0,1) nodal forces"),
@@ -54,15 +59,18 @@ WORKLOAD_DESCS = {
                 "log-uniform 1k-200k tets; 2,234,256 tets / 535,718 nodes in all), rigid motion plus a travelling "
                 "wave, 8 configurations of a 200-step motion replayed in turn; B_g, M_s rebuilt every step"),
 }
-WORKLOAD_DESC = WORKLOAD_DESCS[WORKLOAD]
-# FP64 pipe peak derived from the unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# FP64 flops per candidate pair executed by the fused clip kernel (mixed form) on this workload:
-# ncu SASS instruction counters of one launch over the three grids,
-# (2*DFMA + DADD + DMUL) / pairs = 266.4e6 / 716130; DRAM bytes per pair from the same capture
-# (read + write, 186.7e6 / 716130).  profiles/clip_fused_beam128.md.
-FP64_FLOPS_PER_PAIR = 372.0
-CLIP_DRAM_BYTES_PER_PAIR = 260.7
+# Elements of the CPU oracle's sample: the slab of tetrahedra nearest one end of
+# the body along x, taken as a mesh of its own (about 10 s of single-thread work
+# on the 4M-tet beam).
+CPU_SAMPLE_ELEMS = 30000
+# Elements of the smaller samples whose operation tallies give the extra
+# workloads' algorithmic work per pair.
+TALLY_SAMPLE_ELEMS = 4000
+# DRAM bytes per candidate pair of the clipping kernel (read + write), from one
+# capture of it on the 48k-tet beam (ncu --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum -k regex:clip_fused); None until taken for the kernel as
+# it stands.
+CLIP_DRAM_BYTES_PER_PAIR = None
 
 
 def parse():
@@ -72,8 +80,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--plain-steps", type=int, default=20)
+    ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", default=",".join(EXTRA_WORKLOADS),
+                    help="comma-separated extra workloads reported as keys of the same line ('none': no extras)")
+    ap.add_argument("--extra-steps", type=int, default=10)
     ap.add_argument("--work-shape", default=None, metavar="CB,RPB,CL,RPBS",
                     help="fix the fused forms' work shape (clip block, PCG rows per block, PCG cluster, rows "
                          "per block of the captured step's combined solve) instead of autotuning it; for "
@@ -86,6 +97,10 @@ def parse():
             ap.error("--work-shape takes four integers")
         if len(args.work_shape) != 4:
             ap.error("--work-shape takes four integers")
+    args.extras = [] if args.extras in ("", "none") else args.extras.split(",")
+    for x in args.extras:
+        if x not in WORKLOAD_DESCS:
+            ap.error(f"unknown extra workload {x!r}")
     return args
 
 
@@ -221,6 +236,15 @@ def spmv_bytes(c, torch):
     return bB, bT
 
 
+def pcg_bytes(c, iters: int, n_rhs: int):
+    """Algorithmic bytes of a Jacobi-PCG solve in the mixed form: per iteration
+    one product with M_s (FP32 values, int32 columns, int64 row pointers) and the
+    vector passes of the Chronopoulos-Gear recurrences (u, w, r, p, s, x, m read
+    or written once per right-hand side, FP32)."""
+    n, nnz = c.n_nodes, c.info()["nnz_M"]
+    return iters * ((n + 1) * 8 + nnz * 8 + 7 * n * n_rhs * 4)
+
+
 def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -229,44 +253,94 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def oracle_step(w, elems, nthreads):
-    """One step of the plain FP64 CPU oracle (assembly + both transfers).  A
-    subset of the elements is taken as a mesh of its own: the nodes it uses,
-    renumbered (nodes outside it would give empty rows of M_s)."""
+def cpu_model():
+    """CPU model name from lscpu (Arm hosts have no 'model name' in /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def slab_sample(coords, elems, n_max: int):
+    """The n_max elements with the lowest centroid x (a slab at one end of the
+    body), or all of them."""
+    if elems.shape[0] <= n_max:
+        return elems, "the whole mesh"
+    cx = coords[elems].mean(axis=1)[:, 0]
+    keep = np.sort(np.argpartition(cx, n_max)[:n_max])
+    return elems[keep], f"the {n_max} of {elems.shape[0]} tetrahedra with the lowest centroid x (a slab at one end), as a mesh of its own"
+
+
+def oracle_step(grid, coords, elems, force, nthreads, fields=None):
+    """One step of the plain FP64 CPU oracle (assembly + both transfers) on the
+    mesh made of ``elems``: the nodes it uses, renumbered (nodes outside it would
+    give empty rows of M_s).  Returns the oracle's coupling, u_s, f_f, pairs,
+    the assembly and apply seconds, and the operation tallies."""
     import oracle
     used = np.unique(elems)
-    if used.size == w.coords.shape[0]:
-        X, E, force = w.coords, elems, w.force
+    if used.size == coords.shape[0]:
+        X, E, F = coords, elems, force
     else:
-        remap = np.full(w.coords.shape[0], -1, dtype=np.int64)
+        remap = np.full(coords.shape[0], -1, dtype=np.int64)
         remap[used] = np.arange(used.size)
-        X, E, force = w.coords[used], remap[elems].astype(np.int32), w.force[used]
+        X, E, F = coords[used], remap[elems].astype(np.int32), force[used]
     t0 = time.perf_counter()
-    oc = oracle.Coupling(w.grid, X, E, nthreads=nthreads)
+    oc = oracle.Coupling(grid, X, E, nthreads=nthreads)
     t1 = time.perf_counter()
-    fields = [f.astype(np.float32).astype(np.float64) for f in w.fields]
-    us = oc.transfer_velocity(fields)
-    ff = oc.transfer_force(force.astype(np.float32).astype(np.float64), mode="dual")
+    us = ff = None
+    if fields is not None:
+        us = oc.transfer_velocity([f.astype(np.float32).astype(np.float64) for f in fields])
+        ff = oc.transfer_force(F.astype(np.float32).astype(np.float64), mode="dual")
     t2 = time.perf_counter()
     npairs = sum(len(p[0]) for p in oc.pairs)
-    return oc, us, ff, npairs, t1 - t0, t2 - t1
+    return oc, us, ff, npairs, t1 - t0, t2 - t1, dict(oc.ops)
+
+
+def fp64_flops_per_pair(ops: dict, npairs: int):
+    """Algorithmic FP64 work of the clipping step per candidate pair: the
+    oracle's tallies of the cell frame, the plane-side values and cut points and
+    the sub-simplex volumes (the geometry the method keeps in FP64)."""
+    return (ops["frame"] + ops["clip"] + ops["volume"]) / max(1, npairs)
+
+
+def cpu_baseline_leg(grid, coords, elems, force, fields, n_max=CPU_SAMPLE_ELEMS, single=True):
+    """The oracle as it stands on a bounded sample of the workload: one step on
+    all host cores and, with ``single``, one on a single thread; its operation
+    tallies give the algorithmic FP64 work per pair."""
+    cores = os.cpu_count() or 1
+    sub, what = slab_sample(coords, elems, n_max)
+    _, _, _, npairs, tb, ta, ops = oracle_step(grid, coords, sub, force, cores, fields)
+    out = {"value": npairs / (tb + ta), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"one full step (assembly + velocity + dual force transfer) on {what}; {npairs} candidate pairs",
+           "assembly_s": tb, "apply_s": ta, "nproc": cores, "cpu_model": cpu_model(),
+           "fp64_flops_per_pair": fp64_flops_per_pair(ops, npairs),
+           "op_tallies_per_pair": {k: v / max(1, npairs) for k, v in ops.items()}}
+    if single:
+        _, _, _, n1, tb1, ta1, _ = oracle_step(grid, coords, sub, force, 1, fields)
+        out["single_thread"] = {"value": n1 / (tb1 + ta1), "unit": UNIT, "cores": 1, "assembly_s": tb1,
+                                "apply_s": ta1}
+    return out
 
 
 def reference_arm(args, rank, world):
-    """The oracle as it stands, on the host cores: each step a bounded sample
-    (the first quarter of the beam's tetrahedra) of the same workload."""
+    """The oracle as it stands, on the host cores: each step the same bounded
+    sample of the workload as the CPU baseline (a slab of the body)."""
     if rank != 0:
         return 0
     import synth
     w = synth.workload(args.workload, 0)
-    m = w.elems.shape[0] // 4
-    elems = w.elems[:m]
     cores = os.cpu_count() or 1
+    sub, what = slab_sample(w.coords, w.elems, CPU_SAMPLE_ELEMS)
     for _ in range(args.warmup):
-        oracle_step(w, elems, cores)
+        oracle_step(w.grid, w.coords, sub, w.force, cores, w.fields)
     times, pairs = [], 0
     for _ in range(args.steps):
-        _, _, _, npairs, tb, ta = oracle_step(w, elems, cores)
+        _, _, _, npairs, tb, ta, _ = oracle_step(w.grid, w.coords, sub, w.force, cores, w.fields)
         times.append(tb + ta)
         pairs = npairs
     total = sum(times)
@@ -274,13 +348,37 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "desc": WORKLOAD_DESCS.get(args.workload, args.workload),
-                                            "sample": f"first {m} of {w.elems.shape[0]} tetrahedra per step"},
+            "data": "synthetic", "config": {"workload": args.workload,
+                                            "desc": WORKLOAD_DESCS.get(args.workload, args.workload),
+                                            "sample": f"{what} per step ({pairs} candidate pairs)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {m} of {w.elems.shape[0]} tetrahedra per step, {args.steps} steps"},
+                             "sample": f"{what} per step, {args.steps} steps", "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def fma_peaks(torch, l2x, dev):
+    """FP64 and FP32 FMA-pipe throughput of this GPU (the library's probe kernel,
+    CUDA events, best of three launches of about 20 ms), in TFLOP/s."""
+    out = {}
+    n_blocks = 152 * 8
+    stream = torch.cuda.current_stream(dev)
+    for name, prec, iters in (("fp64", l2x.FP64, 5000), ("fp32", l2x.MIXED, 300000)):
+        sink = torch.empty(n_blocks * 256, dtype=torch.float64 if prec == l2x.FP64 else torch.float32, device=dev)
+        l2x.fma_probe(prec, n_blocks, max(1, iters // 10), sink)
+        best = 0.0
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flops = l2x.fma_probe(prec, n_blocks, iters, sink)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out[name + "_tflops"] = best
+    out["how"] = ("library FMA probe: 1216 blocks x 256 threads x 8 independent FMA chains, best of 3 "
+                  "CUDA-event-timed launches (burst, kernel timed alone)")
+    return out
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -436,13 +534,278 @@ class Arm:
                     buffers=(src, uf, us, fs, ff), kernels_per_step=kernels_per_step)
 
 
+def load_workload(name, rank, dev, torch):
+    """Host inputs and device tensors of one rank's workload."""
+    import synth
+    batch = name == "batch64"
+    if batch:
+        grid, bodies, Eh, nr, er = synth.batch_workload(64, 256, 1000, 200000, seed=workload_seed(rank))
+        n_steps, n_conf = 200, 8
+        coords = [synth.batch_coords(bodies, k * (n_steps // n_conf), n_steps) for k in range(n_conf)]
+        fields = [synth.taylor_green(synth.grid_node_coords(grid, g), g) for g in range(3)]
+        rng = np.random.default_rng(100 + rank)
+        F = rng.standard_normal((coords[0].shape[0], 3))
+    else:
+        w = synth.workload(name, seed=workload_seed(rank))
+        grid, Eh, fields, F = w.grid, w.elems, w.fields, w.force
+        coords = [w.coords]
+    positions = [torch.from_numpy(c).to(dev) for c in coords]
+    E = torch.from_numpy(Eh).to(dev)
+    u32 = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in fields]
+    F32 = F.astype(np.float32)
+    f32 = [torch.from_numpy(np.ascontiguousarray(F32[:, g])).to(dev) for g in range(3)]
+    return dict(name=name, batch=batch, grid=grid, coords=coords, Eh=Eh, fields=fields, F=F,
+                positions=positions, E=E, u32=u32, f32=f32)
+
+
+def clip_roofline(ph, calls, pairs_per_step, n_steps, flops_per_pair, peak, peak_source):
+    """ALU roofline of the clipping kernel from per-call phase times: the oracle's
+    algorithmic FP64 operations per pair x pairs per launch / launch time."""
+    launch_ms = ph["clip"] / max(1, calls["clip"])
+    pairs_per_launch = pairs_per_step / max(1, calls["clip"] // n_steps)
+    achieved = flops_per_pair * pairs_per_launch / (launch_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "kernel": "clip_fused_kernel<3,float> (FP64 pipe)", "launch_ms": launch_ms,
+            "pairs_per_launch": pairs_per_launch, "flops_per_pair": flops_per_pair,
+            "flops_per_pair_source": "oracle operation tallies (cell frame, plane-side values, cut points, "
+                                     "sub-simplex volumes) on the CPU sample of this workload",
+            "peak_source": peak_source,
+            "traffic": (CLIP_DRAM_BYTES_PER_PAIR * pairs_per_launch if CLIP_DRAM_BYTES_PER_PAIR is not None
+                        else None)}
+
+
+def apply_roofline(pc, ph, calls, torch, peak_hbm, peak_src):
+    """HBM rooflines of the sparse products and the mass-matrix solve of the apply
+    (per-call phase times, mixed form)."""
+    c = pc["c"]
+    bB, bT = spmv_bytes(c, torch)
+    tB = ph["spmv_B"] / max(1, calls["spmv_B"])
+    tT = ph["spmv_BT"] / max(1, calls["spmv_BT"])
+    tP = ph["pcg"] / max(1, calls["pcg"])
+    iters = pc["info"]["cg_iters"]
+    bP = pcg_bytes(c, iters, c.n_grids)
+
+    def entry(b, t):
+        return {"bytes": b, "ms": t, "achieved": b / (t * 1e-3) / 1e9, "frac": b / (t * 1e-3) / 1e9 / peak_hbm}
+    return {"bound": "hbm", "unit": "GB/s", "peak": peak_hbm, "peak_source": peak_src,
+            "spmv_B": entry(bB, tB), "spmv_BT": entry(bT, tT),
+            "pcg": dict(entry(bP, tP), iters_per_solve=iters,
+                        note="one 3-component solve; bytes: per iteration the M_s product and 7 vector passes"),
+            "pcg_ms_per_solve": tP}
+
+
+def autograd_ms(l2x, torch, cg, uf, dev, n=10):
+    """Forward + hand-written backward of the differentiable velocity transfer."""
+    ua = [u.clone().requires_grad_(True) for u in uf]
+    gw = [torch.ones(cg.n_nodes, dtype=ua[0].dtype, device=dev) for _ in ua]
+    for _ in range(3):
+        out = l2x.VelocityTransfer.apply(cg, *ua)
+        torch.autograd.backward(out, gw)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(torch.cuda.current_stream(dev))
+    for _ in range(n):
+        out = l2x.VelocityTransfer.apply(cg, *ua)
+        torch.autograd.backward(out, gw)
+    a1.record(torch.cuda.current_stream(dev))
+    a1.synchronize()
+    return {"forward_backward_ms": a0.elapsed_time(a1) / n,
+            "form": "VelocityTransfer forward (B, S^-1) + backward (S^-1, B^T), mixed precision"}
+
+
+def sample_vs_oracle(l2x, torch, wl, dev, cpu):
+    """The chosen (mixed) form on the CPU baseline's sample mesh, against the
+    oracle's results on it: relative L2 error per result."""
+    sub, _ = slab_sample(wl["coords"][0], wl["Eh"], CPU_SAMPLE_ELEMS)
+    used = np.unique(sub)
+    remap = np.full(wl["coords"][0].shape[0], -1, dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    X, E, F = wl["coords"][0][used], remap[sub].astype(np.int32), wl["F"][used]
+    c = l2x.Coupling(wl["grid"], torch.from_numpy(X).to(dev), torch.from_numpy(E).to(dev), path=l2x.FUSED,
+                     precision=l2x.MIXED, cg_rtol=1e-9)
+    uf = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in wl["fields"]]
+    us = c.transfer_velocity(uf)
+    fs = [torch.from_numpy(np.ascontiguousarray(F[:, g].astype(np.float32))).to(dev) for g in range(3)]
+    ff = c.transfer_force(fs)
+    ref_us, ref_ff = cpu.pop("_us"), cpu.pop("_ff")
+    got = np.stack([u.double().cpu().numpy() for u in us], axis=1)
+    err_u = float(np.linalg.norm(got - ref_us) / np.linalg.norm(ref_us))
+    err_f = max(float(np.linalg.norm(ff[k].double().cpu().numpy() - ref_ff[k]) / np.linalg.norm(ref_ff[k]))
+                for k in range(3))
+    del c
+    return err_u, err_f
+
+
+def run_workload(args, name, rank, world, local, dev, torch, l2x, flush, steps, warmup, headline, peaks):
+    """Times one workload; ``headline`` adds the plain/FP64/dual/Picard/e2e arms
+    and the full CPU baseline."""
+    wl = load_workload(name, rank, dev, torch)
+    batch = wl["batch"]
+    arm = Arm(torch, l2x, wl["grid"], wl["positions"], wl["E"], wl["u32"], wl["f32"], dev, world, flush,
+              args.work_shape)
+    res = {}
+    with ClockSampler(local) as clocks:
+        gr = arm.graph(l2x.MIXED, steps, warmup)
+    res["clocks"] = clocks.summary()
+    res["autotuned"] = dict(arm.tuned)
+    step_ms, total_pairs, value = aggregate(gr["step_ms"], gr["pairs"], world)
+    res.update(value=value, ms_per_step=step_ms, pairs_per_step=gr["pairs"], steps=steps,
+               kernels_per_step=gr["kernels_per_step"])
+
+    # per-call form of the same precision, with per-phase timing
+    n_pc = max(3, steps // 4)
+    pc = arm.per_call(l2x.FUSED, l2x.MIXED, n_pc, 3, timing=True)
+    ph, calls = pc["info"]["phase_ms"], pc["info"]["phase_calls"]
+    res["per_call_mixed"] = {"build_ms": pc["build_ms"], "apply_ms": pc["apply_ms"],
+                             "pairs_per_s": pc["pairs"] / ((pc["build_ms"] + pc["apply_ms"]) * 1e-3),
+                             "assembly_pairs_per_s": pc["pairs"] / (pc["build_ms"] * 1e-3),
+                             "phase_ms_per_step": {k: v / n_pc for k, v in ph.items()},
+                             "cg_iters": pc["info"]["cg_iters"]}
+    peak_hbm, peak_src = hbm_peak()
+    res["apply_roofline"] = apply_roofline(pc, ph, calls, torch, peak_hbm, peak_src)
+
+    # the oracle on a bounded sample: CPU baseline and algorithmic work per pair
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        coords0 = wl["coords"][0]
+        if headline:
+            cpu = cpu_baseline_leg(wl["grid"], coords0, wl["Eh"], wl["F"], wl["fields"])
+            # results of the sample for the accuracy check below
+            sub, _ = slab_sample(coords0, wl["Eh"], CPU_SAMPLE_ELEMS)
+            _, us_o, ff_o, _, _, _, _ = oracle_step(wl["grid"], coords0, sub, wl["F"], os.cpu_count() or 1,
+                                                    wl["fields"])
+            cpu["_us"], cpu["_ff"] = us_o, ff_o
+            eu, ef = sample_vs_oracle(l2x, torch, wl, dev, cpu)
+            cpu["rel_err_u_s"], cpu["rel_err_f_f"] = eu, ef
+            cpu["rel_err_note"] = "chosen mixed form on the sample mesh vs the oracle's FP64 results on it"
+        else:
+            cpu = cpu_baseline_leg(wl["grid"], coords0, wl["Eh"], wl["F"], wl["fields"], n_max=TALLY_SAMPLE_ELEMS,
+                                   single=False)
+        res["roofline"] = clip_roofline(ph, calls, pc["pairs"], n_pc, cpu["fp64_flops_per_pair"],
+                                        peaks["fp64_tflops"], "measured: library FMA probe, FP64, burst")
+        fp32_flops = cpu["op_tallies_per_pair"]["quad"]
+        res["roofline"]["oracle_quadrature_flops_per_pair"] = fp32_flops
+    res["cpu_baseline"] = cpu
+
+    if name == "leaflet256" or headline:
+        res["autograd"] = autograd_ms(l2x, torch, pc["c"], pc["uf"], dev)
+
+    if headline:
+        picard_ms = arm.picard(pc["c"], pc["uf"], pc["fs"], 20)
+        res["picard"] = {"iteration_ms": picard_ms, "iterations_per_time_step": 3,
+                         "time_step_ms": pc["build_ms"] + 3 * picard_ms,
+                         "pairs_per_s": pc["pairs"] / ((pc["build_ms"] + 3 * picard_ms) * 1e-3),
+                         "form": "per-call assembly, then 3 x (enqueue-only velocity + force transfer + Step-6 "
+                                 "norms), mixed precision, standard multipliers"}
+
+        def results(r):
+            c = r["c"]
+            c.update_geometry(wl["positions"][0])
+            u = c.transfer_velocity(r["uf"])
+            f = c.transfer_force(r["fs"])
+            return [x.double() for x in u], [x.double() for x in f]
+
+        def rel(a, b):
+            nb = float(torch.linalg.norm(b))
+            return float(torch.linalg.norm(a - b)) / nb if nb > 0 else None  # None: a zero reference component
+
+        um, fm = results(pc)
+        del pc
+        gc.collect()
+        f64 = arm.per_call(l2x.FUSED, l2x.FP64, args.plain_steps, 2)
+        u64, f64r = results(f64)
+        res["mixed_vs_fp64"] = {"u_s": [rel(a, b) for a, b in zip(um, u64)],
+                                "f_f": [rel(a, b) for a, b in zip(fm, f64r)],
+                                "u_s_all": rel(torch.cat(um), torch.cat(u64)),
+                                "f_f_all": rel(torch.cat(fm), torch.cat(f64r)),
+                                "against": "fused FP64 GPU path on the same configuration (which matches the FP64 "
+                                           "oracle to 1e-12)"}
+        del um, fm, u64, f64r
+        res["fused_fp64"] = {"assembly_ms": f64["build_ms"], "apply_ms": f64["apply_ms"],
+                             "pairs_per_s": f64["pairs"] / ((f64["build_ms"] + f64["apply_ms"]) * 1e-3),
+                             "assembly_pairs_per_s": f64["pairs"] / (f64["build_ms"] * 1e-3),
+                             "cg_iters": f64["info"]["cg_iters"]}
+        del f64
+        gc.collect()
+        plain = arm.per_call(l2x.PLAIN, l2x.FP64, args.plain_steps, 2)
+        res["plain_fp64"] = {"assembly_ms": plain["build_ms"], "apply_ms": plain["apply_ms"],
+                             "pairs_per_s": plain["pairs"] / ((plain["build_ms"] + plain["apply_ms"]) * 1e-3),
+                             "assembly_pairs_per_s": plain["pairs"] / (plain["build_ms"] * 1e-3),
+                             "cg_iters": plain["info"]["cg_iters"]}
+        del plain
+        gc.collect()
+
+        # the dual multiplier basis (pseudo L2 projection, S diagonal: no CG), same step
+        n_dual = max(3, steps // 4)
+        dgr = arm.graph(l2x.MIXED, n_dual, 3, multiplier=l2x.DUAL_BASIS)
+        d_ms, d_pairs, d_value = aggregate(dgr["step_ms"], dgr["pairs"], world)
+        del dgr
+        gc.collect()
+        res["pseudo_l2_dual"] = {"form": "fused, captured step graph, mixed precision, dual multiplier basis",
+                                 "value": d_value, "unit": UNIT, "ms_per_step": d_ms, "steps": n_dual}
+
+        # end to end through the public API from pinned host buffers (the captured step):
+        # positions, velocities and forces in; solid velocities and fluid forces out
+        c, g = gr["c"], gr["g"]
+        src, uf, us, fs, ff = gr["buffers"]
+        Ph = [p.cpu().pin_memory() for p in wl["positions"]]
+        uh = [u.cpu().pin_memory() for u in uf]
+        fh = [f.cpu().pin_memory() for f in fs]
+        us_h = [torch.empty(c.n_nodes, dtype=torch.float32).pin_memory() for _ in range(3)]
+        ff_h = [torch.empty(n, dtype=torch.float32).pin_memory() for n in c.fluid_sizes()]
+        stream = torch.cuda.current_stream(dev)
+
+        def e2e_step(i):
+            src.copy_(Ph[i % len(Ph)], non_blocking=True)
+            for a, b in zip(uf, uh):
+                a.copy_(b, non_blocking=True)
+            for a, b in zip(fs, fh):
+                a.copy_(b, non_blocking=True)
+            g.launch()
+            for a, b in zip(us_h, us):
+                a.copy_(b, non_blocking=True)
+            for a, b in zip(ff_h, ff):
+                a.copy_(b, non_blocking=True)
+
+        for i in range(2):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        barrier(world)
+        e_ms = 0.0
+        n_e2e = max(3, steps // 4)
+        e2e_pairs = 0
+        for i in range(n_e2e):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            e2e_step(i)
+            e1.record(stream)
+            e1.synchronize()
+            e_ms += e0.elapsed_time(e1)
+            e2e_pairs += gr["pairs_at"][i % len(gr["pairs_at"])]
+        g.status()
+        e_ms = e_ms / n_e2e
+        e_step_ms, e_total, e_value = aggregate(e_ms, e2e_pairs / n_e2e, world)
+        h2d = (wl["positions"][0].numel() * 8 + sum(t.numel() * 4 for t in uh) + sum(t.numel() * 4 for t in fh))
+        d2h = sum(t.numel() * 4 for t in us_h) + sum(t.numel() * 4 for t in ff_h)
+        res["e2e"] = {"value": e_value, "unit": UNIT, "ms_per_step": e_step_ms,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        del Ph, uh, fh, us_h, ff_h
+    else:
+        del pc
+    del gr, arm, wl
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
     import torch
-    import synth
     import paper_1810_13046_gb300 as l2x
 
     torch.cuda.set_device(local)
@@ -450,213 +813,53 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    batch = args.workload == "batch64"
-    if batch:
-        grid, bodies, Eh, nr, er = synth.batch_workload(64, 256, 1000, 200000, seed=workload_seed(rank))
-        n_steps, n_conf = 200, 8
-        positions = [torch.from_numpy(synth.batch_coords(bodies, k * (n_steps // n_conf), n_steps)).to(dev)
-                     for k in range(n_conf)]
-        fields = [synth.taylor_green(synth.grid_node_coords(grid, g), g) for g in range(3)]
-        rng = np.random.default_rng(100 + rank)
-        F = rng.standard_normal((positions[0].shape[0], 3))
-        w = None
-    else:
-        w = synth.workload(args.workload, seed=workload_seed(rank))
-        grid, Eh, fields, F = w.grid, w.elems, w.fields, w.force
-        positions = [torch.from_numpy(w.coords).to(dev)]
-    E = torch.from_numpy(Eh).to(dev)
-    u32 = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in fields]
-    F32 = F.astype(np.float32)
-    f32 = [torch.from_numpy(np.ascontiguousarray(F32[:, g])).to(dev) for g in range(3)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    arm = Arm(torch, l2x, grid, positions, E, u32, f32, dev, world, flush, args.work_shape)
+    peaks = fma_peaks(torch, l2x, dev)
 
-    # chosen form: captured step graph, fused, FP64 geometry + FP32 fields/SpMV/CG
-    # with compensated dots and FP64 refinement
-    with ClockSampler(local) as clocks:
-        gr = arm.graph(l2x.MIXED, args.steps, args.warmup)
-    tuned = dict(arm.tuned)  # the chosen form's work shape
-    step_ms, total_pairs, value = aggregate(gr["step_ms"], gr["pairs"], world)
-
-    # per-call form of the same precision, with per-phase timing (roofline of the clip kernel)
-    pc = arm.per_call(l2x.FUSED, l2x.MIXED, max(3, args.steps // 4), 3, timing=True)
-    ph, calls = pc["info"]["phase_ms"], pc["info"]["phase_calls"]
-    n_pc = max(3, args.steps // 4)
-    clip_launch_ms = ph["clip"] / max(1, calls["clip"])
-    clip_pairs_per_launch = pc["pairs"] / max(1, calls["clip"] // n_pc)
-    picard_ms = arm.picard(pc["c"], pc["uf"], pc["fs"], 20)
-    picard = {"iteration_ms": picard_ms, "iterations_per_time_step": 3,
-              "time_step_ms": pc["build_ms"] + 3 * picard_ms,
-              "pairs_per_s": pc["pairs"] / ((pc["build_ms"] + 3 * picard_ms) * 1e-3),
-              "form": "per-call assembly, then 3 x (enqueue-only velocity + force transfer + Step-6 norms), "
-                      "mixed precision, standard multipliers"}
-    plain = arm.per_call(l2x.PLAIN, l2x.FP64, args.plain_steps, 2)
-    f64 = arm.per_call(l2x.FUSED, l2x.FP64, args.plain_steps, 2)
-
-    # HBM rooflines of the two sparse products of the apply (per-call phase times)
-    peak_hbm, peak_src = hbm_peak()
-    bB, bT = spmv_bytes(pc["c"], torch)
-    tB = ph["spmv_B"] / max(1, calls["spmv_B"])
-    tT = ph["spmv_BT"] / max(1, calls["spmv_BT"])
-    apply_roof = {"bound": "hbm", "unit": "GB/s", "peak": peak_hbm, "peak_source": peak_src,
-                  "spmv_B": {"bytes": bB, "ms": tB, "achieved": bB / (tB * 1e-3) / 1e9,
-                             "frac": bB / (tB * 1e-3) / 1e9 / peak_hbm},
-                  "spmv_BT": {"bytes": bT, "ms": tT, "achieved": bT / (tT * 1e-3) / 1e9,
-                              "frac": bT / (tT * 1e-3) / 1e9 / peak_hbm},
-                  "pcg_ms_per_solve": ph["pcg"] / max(1, calls["pcg"]),
-                  "note": "the mass-matrix solve is latency-bound at these sizes (grid barriers per iteration)"}
-
-    # per-result error of the chosen (mixed) form against the FP64 GPU path, same configuration
-    def results(r):
-        c = r["c"]
-        c.update_geometry(positions[0])
-        u = c.transfer_velocity(r["uf"])
-        f = c.transfer_force(r["fs"])
-        return [x.double() for x in u], [x.double() for x in f]
-    um, fm = results(pc)
-    u64, f64r = results(f64)
-    def rel(a, b):
-        nb = float(torch.linalg.norm(b))
-        return float(torch.linalg.norm(a - b)) / nb if nb > 0 else None  # None: a zero reference component
-
-    mixed_err = {"u_s": [rel(a, b) for a, b in zip(um, u64)], "f_f": [rel(a, b) for a, b in zip(fm, f64r)],
-                 "u_s_all": rel(torch.cat(um), torch.cat(u64)), "f_f_all": rel(torch.cat(fm), torch.cat(f64r)),
-                 "against": "fused FP64 GPU path on the same configuration (which matches the FP64 oracle to 1e-12)"}
-
-    # differentiable transfer: forward u_s = S^-1 B u_f and the hand-written backward
-    cg = pc["c"]
-    ua = [u.clone().requires_grad_(True) for u in pc["uf"]]
-    gw = [torch.ones(cg.n_nodes, dtype=ua[0].dtype, device=dev) for _ in ua]
-    for _ in range(3):
-        out = l2x.VelocityTransfer.apply(cg, *ua)
-        torch.autograd.backward(out, gw)
-    torch.cuda.synchronize()
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_ag = 10
-    a0.record(torch.cuda.current_stream(dev))
-    for _ in range(n_ag):
-        out = l2x.VelocityTransfer.apply(cg, *ua)
-        torch.autograd.backward(out, gw)
-    a1.record(torch.cuda.current_stream(dev))
-    a1.synchronize()
-    autograd = {"forward_backward_ms": a0.elapsed_time(a1) / n_ag,
-                "form": "VelocityTransfer forward (B, S^-1) + backward (S^-1, B^T), mixed precision"}
-
-    # the dual multiplier basis (pseudo L2 projection, S diagonal: no CG), same step
-    n_dual = max(3, args.steps // 4)
-    dgr = arm.graph(l2x.MIXED, n_dual, 3, multiplier=l2x.DUAL_BASIS)
-    dpc = arm.per_call(l2x.FUSED, l2x.MIXED, n_dual, 3, multiplier=l2x.DUAL_BASIS)
-    d_ms, d_pairs, d_value = aggregate(dgr["step_ms"], dgr["pairs"], world)
-    dual = {"form": "fused, captured step graph, mixed precision, dual multiplier basis",
-            "value": d_value, "unit": UNIT, "ms_per_step": d_ms, "steps": n_dual,
-            "per_call_build_ms": dpc["build_ms"], "per_call_apply_ms": dpc["apply_ms"]}
-    del dgr, dpc
-
-    # end to end through the public API from pinned host buffers (the captured step):
-    # positions, velocities and forces in; solid velocities and fluid forces out
-    c, g = gr["c"], gr["g"]
-    src, uf, us, fs, ff = gr["buffers"]
-    Ph = [p.cpu().pin_memory() for p in positions]
-    uh = [u.cpu().pin_memory() for u in uf]
-    fh = [f.cpu().pin_memory() for f in fs]
-    us_h = [torch.empty(c.n_nodes, dtype=torch.float32).pin_memory() for _ in range(3)]
-    ff_h = [torch.empty(n, dtype=torch.float32).pin_memory() for n in c.fluid_sizes()]
-    stream = torch.cuda.current_stream(dev)
-
-    def e2e_step(i):
-        src.copy_(Ph[i % len(Ph)], non_blocking=True)
-        for a, b in zip(uf, uh):
-            a.copy_(b, non_blocking=True)
-        for a, b in zip(fs, fh):
-            a.copy_(b, non_blocking=True)
-        g.launch()
-        for a, b in zip(us_h, us):
-            a.copy_(b, non_blocking=True)
-        for a, b in zip(ff_h, ff):
-            a.copy_(b, non_blocking=True)
-
-    for i in range(2):
-        e2e_step(i)
-    torch.cuda.synchronize()
-    barrier(world)
-    e_ms = 0.0
-    n_e2e = max(3, args.steps // 4)
-    e2e_pairs = 0
-    for i in range(n_e2e):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        e2e_step(i)
-        e1.record(stream)
-        e1.synchronize()
-        e_ms += e0.elapsed_time(e1)
-        e2e_pairs += gr["pairs_at"][i % len(gr["pairs_at"])]
-    g.status()
-    e_ms = e_ms / n_e2e
-    e_step_ms, e_total, e_value = aggregate(e_ms, e2e_pairs / n_e2e, world)
-    h2d = positions[0].numel() * 8 + sum(t.numel() * 4 for t in uh) + sum(t.numel() * 4 for t in fh)
-    d2h = sum(t.numel() * 4 for t in us_h) + sum(t.numel() * 4 for t in ff_h)
-
-    roof = None
-    if FP64_FLOPS_PER_PAIR is not None and not batch:
-        achieved = FP64_FLOPS_PER_PAIR * clip_pairs_per_launch / (clip_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "clip_fused_kernel<3,float>",
-                "launch_ms": clip_launch_ms, "pairs_per_launch": clip_pairs_per_launch,
-                "flops_per_pair": FP64_FLOPS_PER_PAIR,
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and clock)",
-                "traffic": (CLIP_DRAM_BYTES_PER_PAIR * clip_pairs_per_launch
-                            if CLIP_DRAM_BYTES_PER_PAIR is not None else None)}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not batch:
-        cores = os.cpu_count() or 1
-        oc, us_ref, ff_ref, npairs_o, tb_o, ta_o = oracle_step(w, w.elems, cores)
-        got = np.stack([u.cpu().numpy() for u in us], axis=1)
-        err_u = float(np.linalg.norm(got - us_ref) / np.linalg.norm(us_ref))
-        err_f = max(float(np.linalg.norm(ff[k].cpu().numpy() - ff_ref[k]) / np.linalg.norm(ff_ref[k]))
-                    for k in range(3))
-        cpu = {"value": npairs_o / (tb_o + ta_o), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "one full step (assembly + velocity + dual force transfer) of the same workload",
-               "assembly_s": tb_o, "apply_s": ta_o, "rel_err_u_s": err_u, "rel_err_f_f": err_f}
+    # the chosen form on the headline workload: captured step graph, fused, FP64
+    # geometry + FP32 fields/SpMV/CG with compensated dots and FP64 refinement
+    h = run_workload(args, args.workload, rank, world, local, dev, torch, l2x, flush, args.steps, args.warmup,
+                     True, peaks)
+    extras = {}
+    if world == 1:
+        for name in args.extras:
+            if name == args.workload:
+                continue
+            r = run_workload(args, name, rank, world, local, dev, torch, l2x, flush, args.extra_steps,
+                             max(3, args.warmup // 2), False, peaks)
+            r["desc"] = WORKLOAD_DESCS[name]
+            r["gpu_launches_per_step"] = r.pop("kernels_per_step")
+            extras[name] = r
 
     if rank == 0:
-        per_call = {"build_ms": pc["build_ms"], "apply_ms": pc["apply_ms"],
-                    "pairs_per_s": pc["pairs"] / ((pc["build_ms"] + pc["apply_ms"]) * 1e-3),
-                    "assembly_pairs_per_s": pc["pairs"] / (pc["build_ms"] * 1e-3),
-                    "phase_ms_per_step": {k: v / n_pc for k, v in ph.items()}}
+        pcm = h["per_call_mixed"]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOAD_DESCS.get(args.workload, args.workload),
                        "form": "fused, captured step graph; FP64 geometry, FP32 fields/SpMV/CG with compensated "
-                               "dots and FP64 refinement", "pairs_per_step": gr["pairs"],
+                               "dots and FP64 refinement", "pairs_per_step": h["pairs_per_step"],
                        "l2": "flushed (256 MB write) before every timed step"},
-            "assembly_pairs_per_s": per_call["assembly_pairs_per_s"], "apply_ms": per_call["apply_ms"],
-            "per_call_mixed": per_call,
-            "plain_fp64": {"assembly_ms": plain["build_ms"], "apply_ms": plain["apply_ms"],
-                           "pairs_per_s": plain["pairs"] / ((plain["build_ms"] + plain["apply_ms"]) * 1e-3),
-                           "assembly_pairs_per_s": plain["pairs"] / (plain["build_ms"] * 1e-3),
-                           "cg_iters": plain["info"]["cg_iters"]},
-            "fused_fp64": {"assembly_ms": f64["build_ms"], "apply_ms": f64["apply_ms"],
-                           "pairs_per_s": f64["pairs"] / ((f64["build_ms"] + f64["apply_ms"]) * 1e-3),
-                           "assembly_pairs_per_s": f64["pairs"] / (f64["build_ms"] * 1e-3),
-                           "cg_iters": f64["info"]["cg_iters"]},
-            "e2e": {"value": e_value, "unit": UNIT, "ms_per_step": e_step_ms,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "autotuned": tuned,
-            "pseudo_l2_dual": dual,
-            "picard": picard,
-            "gpu_launches": int(gr["kernels_per_step"] * args.steps),
-            "gpu_launches_note": f"{gr['kernels_per_step']} kernel nodes per captured step (counted by the "
+            "assembly_pairs_per_s": pcm["assembly_pairs_per_s"], "apply_ms": pcm["apply_ms"],
+            "per_call_mixed": pcm,
+            "plain_fp64": h["plain_fp64"],
+            "fused_fp64": h["fused_fp64"],
+            "e2e": h["e2e"],
+            "autotuned": h["autotuned"],
+            "pseudo_l2_dual": h["pseudo_l2_dual"],
+            "picard": h["picard"],
+            "gpu_launches": int(h["kernels_per_step"] * args.steps),
+            "gpu_launches_note": f"{h['kernels_per_step']} kernel nodes per captured step (counted by the "
                                  f"library as they were recorded) x {args.steps} timed replays",
-            "roofline": roof,
-            "apply_roofline": apply_roof,
-            "mixed_vs_fp64": mixed_err,
-            "autograd": autograd,
-            "cpu_baseline": cpu,
-            "clocks": clocks.summary(),
+            "roofline": h.get("roofline"),
+            "apply_roofline": h["apply_roofline"],
+            "peaks_measured": peaks,
+            "mixed_vs_fp64": h["mixed_vs_fp64"],
+            "autograd": h["autograd"],
+            "cpu_baseline": h["cpu_baseline"],
+            "clocks": h["clocks"],
+            "workloads": extras,
         }
         print(json.dumps(line))
     if world > 1:
