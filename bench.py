@@ -85,18 +85,19 @@ def parse():
     ap.add_argument("--extras", default=",".join(EXTRA_WORKLOADS),
                     help="comma-separated extra workloads reported as keys of the same line ('none': no extras)")
     ap.add_argument("--extra-steps", type=int, default=10)
-    ap.add_argument("--work-shape", default=None, metavar="CB,RPB,CL,RPBS",
+    ap.add_argument("--work-shape", default=None, metavar="CB,RPB,CL,RPBS[,CC]",
                     help="fix the fused forms' work shape (clip block, PCG rows per block, PCG cluster, rows "
-                         "per block of the captured step's combined solve) instead of autotuning it; for "
-                         "profiler runs, where the autotuner's timings are distorted")
+                         "per block of the captured step's combined solve, optionally the clip kernel's "
+                         "work-queue chunk) instead of autotuning it; for profiler runs, where the autotuner's "
+                         "timings are distorted")
     args = ap.parse_args()
     if args.work_shape is not None:
         try:
             args.work_shape = tuple(int(x) for x in args.work_shape.split(","))
         except ValueError:
-            ap.error("--work-shape takes four integers")
-        if len(args.work_shape) != 4:
-            ap.error("--work-shape takes four integers")
+            ap.error("--work-shape takes four or five integers")
+        if len(args.work_shape) not in (4, 5):
+            ap.error("--work-shape takes four or five integers")
     args.extras = [] if args.extras in ("", "none") else args.extras.split(",")
     for x in args.extras:
         if x not in WORKLOAD_DESCS:
@@ -399,10 +400,11 @@ class Arm:
                          precision=precision, cg_rtol=1e-9 if precision == l2x.MIXED else 1e-13,
                          multiplier=multiplier)
         if path == l2x.FUSED and self.work_shape is not None:
-            cb, rpb, cl, rpbs = self.work_shape
-            c.set_work_shape(cb, rpb, cl, rpbs)
-            self.tuned = dict(clip_block=cb, pcg_rows_per_block=rpb, pcg_cluster=cl, pcg_rows_per_block_step=rpbs,
-                              fixed=True)
+            cb, rpb, cl, rpbs = self.work_shape[:4]
+            cc = self.work_shape[4] if len(self.work_shape) > 4 else None
+            c.set_work_shape(cb, rpb, cl, rpbs, clip_chunk=cc)
+            self.tuned = dict(clip_block=cb, clip_chunk=c.info()["clip_chunk"], pcg_rows_per_block=rpb,
+                              pcg_cluster=cl, pcg_rows_per_block_step=rpbs, fixed=True)
         elif path == l2x.FUSED:
             self.tuned = c.autotune()
         return c

@@ -151,7 +151,7 @@ typedef struct l2x_info {
     double tuned_clip_ms;      /* l2x_autotune: time of the chosen clip launch (0 before tuning) */
     double tuned_solve_ms;     /* l2x_autotune: time of the chosen mass-matrix solve of all components */
     int32_t pcg_rows_per_block_step; /* rows per block of a captured step's combined solve (2G right-hand sides) */
-    int32_t reserved2;
+    int32_t clip_chunk;        /* blocks' worth of pairs per work-queue fetch of the persistent clip kernel */
 } l2x_info;
 
 typedef struct l2x_coupling* l2x_handle;
@@ -308,7 +308,10 @@ l2x_status l2x_export_csr(l2x_handle h, int32_t which, int64_t* row_ptr, int32_t
 
 /* Picks work-chunk sizes for this coupling by timing candidates on it (CUDA
  * events, best of two after a warm-up run): pairs per block of the clip kernel
- * (64, 128, 256) and the form of the Jacobi-PCG: the grid-wide cooperative
+ * (64, 128, 256) and the chunk it takes per fetch from its work queue (1, 4 or
+ * 16 blocks' worth of pairs: the clip kernel is a persistent launch of the CTAs
+ * that fit on the SMs, which take chunks of the class-ordered pairs from a device
+ * counter until none are left), and the form of the Jacobi-PCG: the grid-wide cooperative
  * kernel with 32 to 1024 rows per block, or, when the search direction fits,
  * one thread-block cluster of 8 or 16 CTAs holding it in distributed shared
  * memory.  The combined solve of a captured step (both transfers at once) gets
@@ -321,6 +324,11 @@ l2x_status l2x_autotune(l2x_handle h, void* stream);
  * pcg_rows_per_block in [1, 4096] (grid-wide PCG), pcg_cluster 0 (grid-wide)
  * or the CTAs of the single-cluster PCG (EINVAL if the system does not fit). */
 l2x_status l2x_set_work_shape(l2x_handle h, int32_t clip_block, int32_t pcg_rows_per_block, int32_t pcg_cluster);
+
+/* Sets the chunk of the clip kernel's work queue (see l2x_autotune): clip_chunk
+ * blocks' worth of pairs per fetch, in [1, 1024], else EINVAL.  Applies to
+ * builds and steps captured afterwards. */
+l2x_status l2x_set_clip_chunk(l2x_handle h, int32_t clip_chunk);
 
 /* Sets the rows per thread block of the combined solve of captured steps (the
  * 2G right-hand sides of both transfers), which l2x_autotune tunes on its own
@@ -356,6 +364,17 @@ l2x_status l2x_fma_probe(int32_t precision, int32_t n_blocks, int32_t iters, voi
  * (a - float(a)); 5: the kernel's float -> double conversion of
  * __double2float_rn(a).  b is read by ops 0 and 1 only.  Errors: EINVAL, ECUDA. */
 l2x_status l2x_fp_selftest(int32_t op, int64_t n, const double* a, const double* b, double* out, void* stream);
+
+/* Test hook of the library's single-pass prefix sum (no counterpart in the
+ * paper; the scan behind the pair offsets, the CSR row pointers and the B^T
+ * row lists): out[0..n) = exclusive prefix sums of in[0..n) (device int64,
+ * non-negative values), out[n] = total.  Each tile waits for its predecessors'
+ * prefixes with at most spin_limit polls; with missing_first != 0 the first tile
+ * is left out, so the second tile's wait runs out and the call returns
+ * L2X_ETIMEOUT without hanging (the device stays usable).  Allocates and frees
+ * its own workspace; synchronises `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
+l2x_status l2x_scan_selftest(int64_t n, const int64_t* in, int64_t* out, int32_t missing_first, int64_t spin_limit,
+                             void* stream);
 
 /* Jacobi-preconditioned CG that allocates no device memory.
  *

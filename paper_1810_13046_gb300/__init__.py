@@ -63,7 +63,7 @@ class _Info(ctypes.Structure):
                 ("clip_block", ctypes.c_int32), ("pcg_rows_per_block", ctypes.c_int32),
                 ("multiplier", ctypes.c_int32), ("pcg_cluster", ctypes.c_int32),
                 ("tuned_clip_ms", ctypes.c_double), ("tuned_solve_ms", ctypes.c_double),
-                ("pcg_rows_per_block_step", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("pcg_rows_per_block_step", ctypes.c_int32), ("clip_chunk", ctypes.c_int32)]
 
 
 PHASES = ["pairs", "clip", "rows", "transpose", "mass", "spmv_B", "pcg", "spmv_BT"]
@@ -99,6 +99,7 @@ def load_library(build_if_missing: bool = True):
         "l2x_transfer_force_adjoint": ([P, PP, PP, P], ctypes.c_int),
         "l2x_fma_probe": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P], ctypes.c_int),
         "l2x_fp_selftest": ([ctypes.c_int32, ctypes.c_int64, P, P, P, P], ctypes.c_int),
+        "l2x_scan_selftest": ([ctypes.c_int64, P, P, ctypes.c_int32, ctypes.c_int64, P], ctypes.c_int),
         "l2x_transfer_velocity_async": ([P, PP, PP, P], ctypes.c_int),
         "l2x_set_force_mask": ([P, P, P], ctypes.c_int),
         "l2x_transfer_force_async": ([P, PP, PP, P], ctypes.c_int),
@@ -119,6 +120,7 @@ def load_library(build_if_missing: bool = True):
         "l2x_autotune": ([P, P], ctypes.c_int),
         "l2x_set_work_shape": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "l2x_set_step_work_shape": ([P, ctypes.c_int32], ctypes.c_int),
+        "l2x_set_clip_chunk": ([P, ctypes.c_int32], ctypes.c_int),
         "l2x_graph_create": ([P, P, PP, PP, PP, PP, ctypes.c_double, ctypes.c_int32, P,
                               ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "l2x_graph_launch": ([P, P], ctypes.c_int),
@@ -160,6 +162,17 @@ def fp_selftest(op: int, a: torch.Tensor, b: torch.Tensor | None = None) -> torc
                                               ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                               _stream_ptr(a.device)))
     return out
+
+
+def scan_selftest(x: torch.Tensor, missing_first: bool = False, spin_limit: int = 1 << 22):
+    """The library's single-pass prefix sum on a CUDA int64 tensor: returns
+    (status, out) with out[i] = sum(x[:i]) for i <= len(x); see l2x_scan_selftest."""
+    x = x.to(torch.int64).contiguous()
+    out = torch.full((x.numel() + 1,), -1, dtype=torch.int64, device=x.device)
+    with torch.cuda.device(x.device):
+        st = load_library().l2x_scan_selftest(x.numel(), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                              int(bool(missing_first)), int(spin_limit), _stream_ptr(x.device))
+    return int(st), out
 
 
 def kernel_launch_count() -> int:
@@ -292,26 +305,30 @@ class Coupling:
                     phase_calls={p: inf.phase_calls[i] for i, p in enumerate(PHASES)},
                     clip_block=inf.clip_block, pcg_rows_per_block=inf.pcg_rows_per_block,
                     multiplier=inf.multiplier, pcg_cluster=inf.pcg_cluster, tuned_clip_ms=inf.tuned_clip_ms,
-                    tuned_solve_ms=inf.tuned_solve_ms, pcg_rows_per_block_step=inf.pcg_rows_per_block_step)
+                    tuned_solve_ms=inf.tuned_solve_ms, pcg_rows_per_block_step=inf.pcg_rows_per_block_step,
+                    clip_chunk=inf.clip_chunk)
 
     def autotune(self):
         """Pick work-chunk sizes by timing candidates on this coupling."""
         with torch.cuda.device(self.device):
             _check(load_library().l2x_autotune(self._h, _stream_ptr(self.device)))
         i = self.info()
-        return dict(clip_block=i["clip_block"], pcg_rows_per_block=i["pcg_rows_per_block"],
+        return dict(clip_block=i["clip_block"], clip_chunk=i["clip_chunk"], pcg_rows_per_block=i["pcg_rows_per_block"],
                     pcg_cluster=i["pcg_cluster"], pcg_rows_per_block_step=i["pcg_rows_per_block_step"],
                     clip_ms=i["tuned_clip_ms"], solve_ms=i["tuned_solve_ms"])
 
     def set_work_shape(self, clip_block: int = 128, pcg_rows_per_block: int = 64, pcg_cluster: int = 0,
-                       pcg_rows_per_block_step: int | None = None):
+                       pcg_rows_per_block_step: int | None = None, clip_chunk: int | None = None):
         """Set the work shape explicitly (what :meth:`autotune` picks).  The combined
         solve of captured steps takes ``pcg_rows_per_block_step``, or
-        ``pcg_rows_per_block`` when it is None."""
+        ``pcg_rows_per_block`` when it is None; ``clip_chunk`` (blocks' worth of
+        pairs per work-queue fetch of the clip kernel) is left as it is when None."""
         lib = load_library()
         _check(lib.l2x_set_work_shape(self._h, int(clip_block), int(pcg_rows_per_block), int(pcg_cluster)))
         if pcg_rows_per_block_step is not None:
             _check(lib.l2x_set_step_work_shape(self._h, int(pcg_rows_per_block_step)))
+        if clip_chunk is not None:
+            _check(lib.l2x_set_clip_chunk(self._h, int(clip_chunk)))
 
     def set_timing(self, enable: bool = True):
         """CUDA-event timing of the library's phases (totals in info()['phase_ms'])."""

@@ -103,6 +103,8 @@ struct l2x_coupling {
     DevStatus* st_host = nullptr;    // pinned
     // work-chunk sizes (l2x_autotune)
     int clip_block = 128;            // threads (= pairs) per block of the clip kernel
+    int clip_chunk = 4;              // blocks' worth of pairs per work-queue fetch of the clip kernel
+    unsigned long long* clip_work = nullptr;  // work-queue counter of the clip kernel
     int pcg_rpb = 64;                // rows per block of the cooperative PCG
     int pcg_clu = 0;                 // > 0: single-cluster PCG with this many CTAs
     int pcg_rpb_step = 64;           // rows per block of a captured step's combined (2G right-hand sides) solve
@@ -219,6 +221,8 @@ l2x_status ensure_scan(l2x_coupling* h, int64_t n) {
     if (h->scan_tmp) cudaFree(h->scan_tmp);
     h->scan_tmp = nullptr;
     if (cudaMalloc(&h->scan_tmp, need) != cudaSuccess) return fail(L2X_ENOMEM, "scan scratch");
+    // the single-pass scan expects a zeroed workspace and leaves it zeroed
+    L2X_CUDA(cudaMemsetAsync(h->scan_tmp, 0, need, h->stream));
     h->scan_tmp_cap = need;
     return L2X_OK;
 }
@@ -348,7 +352,7 @@ l2x_status build_topology(l2x_coupling* h, cudaStream_t s) {
     if (h->opts.multiplier == L2X_MULT_STANDARD) {
         // sparsity of M_s
         launch_mass_structure(0, h->dim, n, h->E, h->adj_ptr, h->adj, h->row_count, nullptr, nullptr, h->st, s);
-        launch_scan_i64(h->row_count, h->M.ptr, n, h->scan_tmp, s);
+        launch_scan_i64(h->row_count, h->M.ptr, n, h->scan_tmp, s, h->st);
         L2X_CUDA(cudaMemcpyAsync(&nnz, h->M.ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     }
     L2X_TRY(read_status(h, s));
@@ -394,8 +398,8 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
     auto ph_pairs = std::make_unique<PhaseScope>(h, L2X_PH_PAIRS, s);
     launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->nbox, h->node_box, h->elem_vol,
                       h->elem_grad, h->elem_flag, h->st, s);
-    launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
-    launch_scan_i64(h->nbox, h->loc_off, (int64_t)G * m, h->scan_tmp, s);
+    launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s, h->st);
+    launch_scan_i64(h->nbox, h->loc_off, (int64_t)G * m, h->scan_tmp, s, h->st);
     int64_t loc_total = 0;
     L2X_CUDA(cudaMemcpyAsync(&loc_total, h->loc_off + (int64_t)G * m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     std::vector<int64_t> gb(G + 1);
@@ -451,7 +455,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         }
         PhaseScope ph(h, L2X_PH_CLIP, s);
         launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, NP, h->pair_cap, h->X, h->E, h->elem_grad,
-                          h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st, s, h->clip_block);
+                          h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st, s, h->clip_block, h->clip_chunk, h->clip_work);
     }
     // (IV) B_g by rows.  The element-local matrices of all grids in one launch:
     // boxes, pair offsets and local offsets run over the G*m (grid, element) slots
@@ -476,7 +480,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
         }
         launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
         for (int g = 0; g < G; ++g) {
-            launch_scan_i64(rg[g].row_count, h->B[g].ptr, n, h->scan_tmp, s);
+            launch_scan_i64(rg[g].row_count, h->B[g].ptr, n, h->scan_tmp, s, h->st);
             L2X_CUDA(cudaMemcpyAsync(&nnz_g[g], h->B[g].ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         }
         ph_rows.reset();
@@ -555,7 +559,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
             L2X_TRY(ensure_tlist(h, T, rows, nnz));
             launch_transpose_count(B, h->sg[g], T, T.ptr, h->st, s);
             launch_transpose_list(T, T.ptr, h->tflags, h->scan_tmp, h->st, s);
-            launch_scan_i64(T.ptr, T.ptr, rows, h->scan_tmp, s);
+            launch_scan_i64(T.ptr, T.ptr, rows, h->scan_tmp, s, h->st);
             launch_transpose_fill(B, h->sg[g], T, h->tcursor, h->st, s);
             launch_transpose_sort(T, h->st, s);
             if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, nnz, s);
@@ -690,14 +694,14 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     L2X_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
     launch_S_values(h, h->aux_stream);
     L2X_CUDA(cudaEventRecord(h->ev_join, h->aux_stream));
-    launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s);
-    launch_scan_i64(h->nbox, h->loc_off, (int64_t)G * m, h->scan_tmp, s);
+    launch_scan_i64(h->counts, h->offsets, (int64_t)G * m, h->scan_tmp, s, h->st);
+    launch_scan_i64(h->nbox, h->loc_off, (int64_t)G * m, h->scan_tmp, s, h->st);
     launch_emit_pairs(d, G, h->sg, m, h->boxes, h->offsets, h->pair_elem, h->pair_cell, h->pair_cap, h->st, s);
     launch_pair_classes(d, G, h->sg, m, h->offsets, h->pair_cap, h->pair_cap, h->X, h->E, h->pair_elem, h->pair_cell,
                         h->pair_key, h->pair_perm, h->buckets, s);
     launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, h->pair_cap, h->pair_cap, h->X, h->E,
                       h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks, h->vols, h->st,
-                      s, h->clip_block);
+                      s, h->clip_block, h->clip_chunk, h->clip_work);
     launch_elem_local(d, (int64_t)G * m, h->boxes, h->offsets, h->loc_off, h->loc_cap, h->blocks, h->vols,
                       h->loc_val, h->loc_flag, h->opts.multiplier == L2X_MULT_DUAL, h->st, s);
     // rows of all grids per launch (the B_g arrays are fixed by the capture)
@@ -714,7 +718,7 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     }
     launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
     for (int g = 0; g < G; ++g) {
-        launch_scan_i64(rg[g].row_count, h->B[g].ptr, n, h->scan_tmp, s);
+        launch_scan_i64(rg[g].row_count, h->B[g].ptr, n, h->scan_tmp, s, h->st);
         launch_check_capacity(h->B[g].ptr + n, h->B_cap[g], h->st, s);
     }
     launch_b_rows(1, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
@@ -734,7 +738,7 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         CsrT& T = h->T[g];
         launch_transpose_count(B, h->sg[g], T, T.ptr, h->st, ts);
         launch_transpose_list(T, T.ptr, flags, scan, h->st, ts);
-        launch_scan_i64(T.ptr, T.ptr, T.n_rows, scan, ts);
+        launch_scan_i64(T.ptr, T.ptr, T.n_rows, scan, ts, h->st);
         launch_transpose_fill(B, h->sg[g], T, cursor, h->st, ts);
         launch_transpose_sort(T, h->st, ts);
         if (h->opts.precision == L2X_MIXED) launch_to_f32(T.val, T.val32, h->T_cap[g], ts);
@@ -830,7 +834,7 @@ l2x_status l2x_destroy(l2x_handle h) {
     dfree(h->elem_grad); dfree(h->elem_flag); dfree(h->buckets); dfree(h->pair_key); dfree(h->pair_perm);
     dfree(h->nbox); dfree(h->loc_off); dfree(h->loc_val); dfree(h->loc_flag);
     dfree(h->boxes); dfree(h->counts); dfree(h->offsets); dfree(h->node_box); dfree(h->pair_elem);
-    dfree(h->pair_cell); dfree(h->blocks); dfree(h->vols);
+    dfree(h->pair_cell); dfree(h->blocks); dfree(h->vols); dfree(h->clip_work);
     for (int g = 0; g < kMaxGrids; ++g) {
         dfree(h->B[g].ptr); dfree(h->B[g].col); dfree(h->B[g].val); dfree(h->B[g].val32);
         dfree(h->T[g].ptr); dfree(h->T[g].col); dfree(h->T[g].val); dfree(h->T[g].val32);
@@ -901,6 +905,7 @@ l2x_status l2x_build_coupling(const l2x_grid* grid, const l2x_mesh* mesh, const 
         L2X_TRY(dalloc(&h->elem_grad, (size_t)(m * (d + 1) * d)));
         L2X_TRY(dalloc(&h->elem_flag, m));
         L2X_TRY(dalloc(&h->buckets, 2 * kClasses));
+        L2X_TRY(dalloc(&h->clip_work, 1));
         L2X_TRY(dalloc(&h->boxes, (size_t)(G * m)));
         L2X_TRY(dalloc(&h->counts, (size_t)(G * m)));
         L2X_TRY(dalloc(&h->offsets, (size_t)(G * m + 1)));
@@ -1241,6 +1246,7 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
         L2X_TRY(dalloc(&h->t_cursor[g], rows));
         L2X_TRY(dalloc(&h->t_flags[g], rows + 1));
         if (cudaMalloc(&h->t_scan[g], scan_tmp_bytes(rows)) != cudaSuccess) return fail(L2X_ENOMEM, "scan scratch");
+        L2X_CUDA(cudaMemsetAsync(h->t_scan[g], 0, scan_tmp_bytes(rows), s));
         h->t_rows_cap[g] = rows;
     }
     L2X_CUDA(cudaStreamSynchronize(s));
@@ -1351,6 +1357,7 @@ l2x_status l2x_query(l2x_handle h, l2x_info* info) {
     info->tuned_clip_ms = h->tuned_clip_ms;
     info->tuned_solve_ms = h->tuned_solve_ms;
     info->pcg_rows_per_block_step = h->pcg_rpb_step;
+    info->clip_chunk = h->clip_chunk;
     resolve_timing(h);
     for (int p = 0; p < L2X_NPHASE; ++p) {
         info->phase_ms[p] = h->phase_ms[p];
@@ -1384,21 +1391,25 @@ l2x_status l2x_autotune(l2x_handle h, void* stream) {
     };
     l2x_status status = L2X_OK;
     if (h->opts.path == L2X_PATH_FUSED && h->n_pairs > 0) {
-        // clip kernel: pairs per block, on the current pairs (class order of the last build)
+        // clip kernel: pairs per block and blocks' worth of pairs per work-queue
+        // fetch, on the current pairs (class order of the last build)
         float best = 1e30f;
-        int best_blk = h->clip_block;
-        for (int blk : {64, 128, 256}) {
-            const float ms = timed([&] {
-                launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, h->n_pairs, h->pair_cap, h->X, h->E,
-                                  h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm, h->blocks,
-                                  h->vols, h->st, s, blk);
-            });
-            if (ms < best) {
-                best = ms;
-                best_blk = blk;
+        int best_blk = h->clip_block, best_chunk = h->clip_chunk;
+        for (int blk : {64, 128, 256})
+            for (int chunk : {1, 4, 16}) {
+                const float ms = timed([&] {
+                    launch_clip_fused(d, h->opts.precision, G, h->sg, m, h->offsets, h->n_pairs, h->pair_cap, h->X,
+                                      h->E, h->elem_grad, h->elem_flag, h->pair_elem, h->pair_cell, h->pair_perm,
+                                      h->blocks, h->vols, h->st, s, blk, chunk, h->clip_work);
+                });
+                if (ms < best) {
+                    best = ms;
+                    best_blk = blk;
+                    best_chunk = chunk;
+                }
             }
-        }
         h->clip_block = best_blk;
+        h->clip_chunk = best_chunk;
         h->tuned_clip_ms = best;
     }
     if (h->opts.multiplier == L2X_MULT_STANDARD) {
@@ -1487,6 +1498,13 @@ l2x_status l2x_set_work_shape(l2x_handle h, int32_t clip_block, int32_t pcg_rows
     h->pcg_rpb = pcg_rows_per_block;
     h->pcg_rpb_step = pcg_rows_per_block;
     h->pcg_clu = pcg_cluster;
+    return L2X_OK;
+}
+
+l2x_status l2x_set_clip_chunk(l2x_handle h, int32_t clip_chunk) {
+    if (!h) return fail(L2X_EINVAL, "NULL handle");
+    if (clip_chunk < 1 || clip_chunk > 1024) return fail(L2X_EINVAL, "clip_chunk must be in [1, 1024]");
+    h->clip_chunk = clip_chunk;
     return L2X_OK;
 }
 

@@ -127,29 +127,18 @@ __global__ void pair_scatter_kernel(int G, int64_t m, const int64_t* __restrict_
     if (i < n) perm[base[key] + rank] = (int32_t)i;
 }
 
-// Fused, step 4: one thread per pair, in class order.  Gradients come from the
-// element pass; every thread writes its pair's block as one contiguous run
-// (pair-major), i.e. whole cache lines.
+// Fused, step 4: clip + integrate pair i of the class order.  Gradients come
+// from the element pass; the thread writes its pair's block as one contiguous
+// run (pair-major), i.e. whole cache lines.
 template <int D, typename R>
-__global__ void __launch_bounds__(256) clip_fused_kernel(int G, SubGridSet sgs, int64_t m,
-                                                                  const int64_t* __restrict__ offsets, int64_t n_cap,
-                                                                  const double* __restrict__ X,
-                                                                  const int32_t* __restrict__ E,
-                                                                  const double* __restrict__ elem_grad,
-                                                                  const int8_t* __restrict__ elem_flag,
-                                                                  const int32_t* __restrict__ perm,
-                                                                  const int32_t* __restrict__ pair_elem,
-                                                                  const int32_t* __restrict__ pair_cell,
-                                                                  double* __restrict__ blocks,
-                                                                  double* __restrict__ vols, DevStatus* st) {
+__device__ __forceinline__ void clip_pair(int64_t i, int G, const SubGridSet& sgs, int64_t m,
+                                          const int64_t* __restrict__ offsets, const double* __restrict__ X,
+                                          const int32_t* __restrict__ E, const double* __restrict__ elem_grad,
+                                          const int8_t* __restrict__ elem_flag, const int32_t* __restrict__ perm,
+                                          const int32_t* __restrict__ pair_elem, const int32_t* __restrict__ pair_cell,
+                                          double* __restrict__ blocks, double* __restrict__ vols, DevStatus* st,
+                                          double (*poly)[D]) {
     constexpr int NA = D + 1, NB = 1 << D;
-    // this thread's polygon buffers: on-chip shared memory instead of local
-    // memory (whose lines the resident threads would evict from L1)
-    extern __shared__ double s_poly[];
-    double (*poly)[D] = reinterpret_cast<double (*)[D]>(s_poly + threadIdx.x * PolySlot<D>::kDoubles);
-    const int64_t n = min(offsets[(int64_t)G * m], n_cap);
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
     const int64_t p = perm[i];
     const int g = grid_of_pair(p, G, m, offsets);
     const SubGrid& sg = sgs.g[g];
@@ -175,6 +164,45 @@ __global__ void __launch_bounds__(256) clip_fused_kernel(int G, SubGridSet sgs, 
 #pragma unroll
     for (int j = 0; j < NA * NB; ++j) blocks[p * (NA * NB) + j] = blk[j];
     vols[p] = vol;
+}
+
+// Persistent launch over a work queue: the CTAs resident on the SMs take chunks
+// of `chunk` x blockDim pairs (in class order) from a device counter until the
+// pairs run out.  The counter only grows, so every CTA ends after at most
+// n / (chunk x blockDim) + 1 fetches.  The chunk size is a work shape the
+// autotuner picks: small chunks balance the uneven cost of the classes, large
+// ones take fewer counter atomics.
+template <int D, typename R>
+__global__ void __launch_bounds__(256) clip_fused_kernel(int G, SubGridSet sgs, int64_t m,
+                                                         const int64_t* __restrict__ offsets, int64_t n_cap,
+                                                         const double* __restrict__ X, const int32_t* __restrict__ E,
+                                                         const double* __restrict__ elem_grad,
+                                                         const int8_t* __restrict__ elem_flag,
+                                                         const int32_t* __restrict__ perm,
+                                                         const int32_t* __restrict__ pair_elem,
+                                                         const int32_t* __restrict__ pair_cell,
+                                                         double* __restrict__ blocks, double* __restrict__ vols,
+                                                         DevStatus* st, unsigned long long* work, int chunk) {
+    // this thread's polygon buffers: on-chip shared memory instead of local
+    // memory (whose lines the resident threads would evict from L1)
+    extern __shared__ double s_poly[];
+    __shared__ long long s_base;
+    double (*poly)[D] = reinterpret_cast<double (*)[D]>(s_poly + threadIdx.x * PolySlot<D>::kDoubles);
+    const int64_t n = min(offsets[(int64_t)G * m], n_cap);
+    const long long per = (long long)blockDim.x * chunk;
+    for (;;) {
+        if (threadIdx.x == 0) s_base = (long long)atomicAdd(work, (unsigned long long)per);
+        __syncthreads();
+        const long long base = s_base;
+        __syncthreads();  // every thread has read s_base before the next fetch writes it
+        if (base >= n) break;
+        for (int k = 0; k < chunk; ++k) {
+            const int64_t i = base + (int64_t)k * blockDim.x + threadIdx.x;
+            if (i < n)
+                clip_pair<D, R>(i, G, sgs, m, offsets, X, E, elem_grad, elem_flag, perm, pair_elem, pair_cell, blocks,
+                                vols, st, poly);
+        }
+    }
 }
 
 // Plain: one thread per pair, element data from global memory, FP64 throughout,
@@ -276,16 +304,20 @@ void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t
                        int64_t n_launch, int64_t n_cap, const double* X, const int32_t* E, const double* elem_grad,
                        const int8_t* elem_flag, const int32_t* pair_elem, const int32_t* pair_cell,
                        const int32_t* perm, double* blocks, double* vols, DevStatus* st,
-                       cudaStream_t s, int block) {
+                       cudaStream_t s, int block, int chunk, unsigned long long* work) {
     if (n_launch <= 0) return;
     SubGridSet sgs{};
     for (int g = 0; g < G; ++g) sgs.g[g] = sg[g];
     if (block != 64 && block != 128 && block != 256) block = kClipThreads;
-    const int kClipThreads = block;
-    const unsigned nb = (unsigned)((n_launch + kClipThreads - 1) / kClipThreads);
-    // dynamic shared memory of the polygon buffers (opt-in above 48 KB, set once,
-    // outside stream capture: the first launch comes from a build)
+    if (chunk < 1) chunk = 1;
+    const size_t sm2 = (size_t)block * PolySlot<2>::kDoubles * sizeof(double);
+    const size_t sm3 = (size_t)block * PolySlot<3>::kDoubles * sizeof(double);
+    // kernel attributes and resident CTAs per SM, set once per (form, block),
+    // outside stream capture (the first launch of a shape comes from a build or
+    // the autotuner)
     static bool smem_set = false;
+    static int resident[2][2][3] = {};
+    static int n_sm = 0;
     if (!smem_set) {
         const int mx2 = 256 * PolySlot<2>::kDoubles * (int)sizeof(double);
         const int mx3 = 256 * PolySlot<3>::kDoubles * (int)sizeof(double);
@@ -293,17 +325,36 @@ void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t
         cudaFuncSetAttribute(clip_fused_kernel<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx2);
         cudaFuncSetAttribute(clip_fused_kernel<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx3);
         cudaFuncSetAttribute(clip_fused_kernel<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx3);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        const void* fns[2][2] = {{(const void*)clip_fused_kernel<2, double>, (const void*)clip_fused_kernel<2, float>},
+                                 {(const void*)clip_fused_kernel<3, double>, (const void*)clip_fused_kernel<3, float>}};
+        const int blocks3[3] = {64, 128, 256};
+        for (int dd = 0; dd < 2; ++dd)
+            for (int pr = 0; pr < 2; ++pr)
+                for (int b = 0; b < 3; ++b) {
+                    int r = 0;
+                    const size_t smb = (size_t)blocks3[b] * (dd ? PolySlot<3>::kDoubles : PolySlot<2>::kDoubles) * sizeof(double);
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fns[dd][pr], blocks3[b], smb);
+                    resident[dd][pr][b] = r > 0 ? r : 1;
+                }
         smem_set = true;
     }
-    const size_t sm2 = (size_t)kClipThreads * PolySlot<2>::kDoubles * sizeof(double);
-    const size_t sm3 = (size_t)kClipThreads * PolySlot<3>::kDoubles * sizeof(double);
-#define L2X_CLIP_ARGS G, sgs, m, offsets, n_cap, X, E, elem_grad, elem_flag, perm, pair_elem, pair_cell, blocks, vols, st
+    const int bi = block == 64 ? 0 : block == 128 ? 1 : 2;
+    const int res = resident[dim == 3][precision == L2X_MIXED][bi];
+    const int64_t per = (int64_t)block * chunk;
+    const int64_t want = (n_launch + per - 1) / per;
+    const int64_t cap = (int64_t)res * (n_sm > 0 ? n_sm : 1);
+    const unsigned nb = (unsigned)(want < cap ? want : cap);
+    cudaMemsetAsync(work, 0, sizeof(unsigned long long), s);
+#define L2X_CLIP_ARGS G, sgs, m, offsets, n_cap, X, E, elem_grad, elem_flag, perm, pair_elem, pair_cell, blocks, vols, st, work, chunk
     if (dim == 2) {
-        if (precision == L2X_MIXED) { clip_fused_kernel<2, float><<<nb, kClipThreads, sm2, s>>>(L2X_CLIP_ARGS); count_launch(); }
-        else { clip_fused_kernel<2, double><<<nb, kClipThreads, sm2, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        if (precision == L2X_MIXED) { clip_fused_kernel<2, float><<<nb, block, sm2, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        else { clip_fused_kernel<2, double><<<nb, block, sm2, s>>>(L2X_CLIP_ARGS); count_launch(); }
     } else {
-        if (precision == L2X_MIXED) { clip_fused_kernel<3, float><<<nb, kClipThreads, sm3, s>>>(L2X_CLIP_ARGS); count_launch(); }
-        else { clip_fused_kernel<3, double><<<nb, kClipThreads, sm3, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        if (precision == L2X_MIXED) { clip_fused_kernel<3, float><<<nb, block, sm3, s>>>(L2X_CLIP_ARGS); count_launch(); }
+        else { clip_fused_kernel<3, double><<<nb, block, sm3, s>>>(L2X_CLIP_ARGS); count_launch(); }
     }
 #undef L2X_CLIP_ARGS
 }

@@ -574,7 +574,7 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     // mixed 3-D form: the frame of the FP32 moments (a point near the middle of
     // E ∩ C, apex coordinates) and lambda_a there in double-float
     constexpr bool kShift = sizeof(R) == 4 && D == 3;
-    ShiftFrame fr;
+    ShiftFrame fr{};
     if constexpr (kShift) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

@@ -93,7 +93,9 @@ void count_launch();
 void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const double* X,
                        const int32_t* E, ElemBox* boxes, int64_t* counts, int64_t* nbox, int32_t* node_box,
                        double* elem_vol, double* elem_grad, int8_t* elem_flag, DevStatus* st, cudaStream_t s);
-void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
+void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s, DevStatus* st = nullptr);
+void launch_scan_i64_test(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s, DevStatus* st,
+                          int missing_first, long long spin_limit);
 size_t scan_tmp_bytes(int64_t n);
 void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const ElemBox* boxes,
                        const int64_t* offsets, int32_t* pair_elem, int32_t* pair_cell, int64_t cap, DevStatus* st,
@@ -128,7 +130,7 @@ void launch_clip_fused(int dim, int precision, int G, const SubGrid* sg, int64_t
                        int64_t n_launch, int64_t n_cap, const double* X, const int32_t* E, const double* elem_grad,
                        const int8_t* elem_flag, const int32_t* pair_elem, const int32_t* pair_cell,
                        const int32_t* perm, double* blocks, double* vols, DevStatus* st, cudaStream_t s,
-                       int block = 128);
+                       int block, int chunk, unsigned long long* work);
 void launch_clip_plain(int dim, const SubGrid& sg, const double* X, const int32_t* E, int64_t p_begin,
                        int64_t p_end, const int32_t* pair_elem, const int32_t* pair_cell, double* blocks,
                        double* vols, DevStatus* st, cudaStream_t s);

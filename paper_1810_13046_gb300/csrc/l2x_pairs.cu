@@ -198,50 +198,101 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* tota
     return warp_prefix + x - v;
 }
 
-__global__ void scan_reduce_kernel(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ partial) {
-    int64_t base = blockIdx.x * (int64_t)kScanTile;
-    int64_t s = 0;
-    for (int i = 0; i < kScanItems; ++i) {
-        int64_t idx = base + (int64_t)i * kScanThreads + threadIdx.x;
-        if (idx < n) s += in[idx];
-    }
-    int64_t tot;
-    block_exclusive_scan(s, &tot);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+// Single-pass exclusive scan with decoupled look-back (D. Merrill and M.
+// Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back", NVIDIA
+// technical report NVR-2016-002).  Workspace ws: [0] tile counter, [1] finished
+// blocks, [2 .. 2 + nb) one word per tile: status in the top two bits (0 none,
+// 1 the tile's own total, 2 the inclusive prefix through the tile), the value
+// in the low 62 bits (the scanned values are non-negative counts).
+// * Tiles are numbered in the order blocks start (atomic counter), so a tile
+//   only waits on tiles whose blocks are already running.
+// * Each wait polls at most spin_limit times; a wait that gives up sets
+//   FLAG_TIMEOUT in the status word (when given) and the scan goes on with
+//   what it has, so no launch can hang.
+// * The last block to finish clears the workspace for the next launch (the
+//   workspace is zeroed once when it is allocated), so captured steps need no
+//   memset node per scan.
+constexpr unsigned long long kScanVal = (1ull << 62) - 1;
+constexpr long long kScanSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ void scan_publish(unsigned long long* w, unsigned long long status, int64_t v) {
+    __threadfence();
+    atomicExch(w, (status << 62) | ((unsigned long long)v & kScanVal));
 }
 
-__global__ void scan_partials_kernel(int64_t* partial, int64_t nb) {
-    // single block: exclusive scan of the block totals in place; partial[nb] = grand total
-    int64_t carry = 0;
-    for (int64_t base = 0; base < nb; base += kScanThreads) {
-        int64_t idx = base + threadIdx.x;
-        int64_t v = idx < nb ? partial[idx] : 0;
-        int64_t tot;
-        int64_t ex = block_exclusive_scan(v, &tot);
-        if (idx < nb) partial[idx] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) partial[nb] = carry;
-}
-
-__global__ void scan_apply_kernel(const int64_t* __restrict__ in, int64_t n, const int64_t* __restrict__ partial,
-                                  int64_t* __restrict__ out, int64_t nb) {
-    int64_t base = blockIdx.x * (int64_t)kScanTile + (int64_t)threadIdx.x * kScanItems;
+__global__ void __launch_bounds__(kScanThreads) scan_onepass_kernel(const int64_t* in, int64_t n, int64_t* out,
+                                                                   unsigned long long* ws, int64_t nb,
+                                                                   DevStatus* st, long long spin_limit) {
+    __shared__ int64_t s_tile, s_excl;
+    __shared__ int s_last;
+    unsigned long long* ctr = ws;
+    unsigned long long* done = ws + 1;
+    unsigned long long* state = ws + 2;
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(ctr, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const bool valid = tile < nb;
     int64_t v[kScanItems];
-    int64_t s = 0;
+    int64_t sum = 0;
+    const int64_t base = tile * (int64_t)kScanTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        int64_t idx = base + i;
-        v[i] = idx < n ? in[idx] : 0;
-        s += v[i];
+        const int64_t idx = base + i;
+        v[i] = valid && idx < n ? in[idx] : 0;  // all inputs read before any output is written (in place allowed)
+        sum += v[i];
     }
     int64_t tot;
-    int64_t ex = block_exclusive_scan(s, &tot) + partial[blockIdx.x];
-    for (int i = 0; i < kScanItems; ++i) {
-        int64_t idx = base + i;
-        if (idx < n) out[idx] = ex;
-        ex += v[i];
+    int64_t ex = block_exclusive_scan(sum, &tot);
+    if (threadIdx.x == 0) {
+        int64_t excl = 0;
+        if (valid) {
+            if (tile == 0) {
+                scan_publish(state, 2ull, tot);
+            } else {
+                scan_publish(state + tile, 1ull, tot);
+                int64_t j = tile - 1;
+                long long spins = 0;
+                for (;;) {
+                    const unsigned long long word = *(volatile unsigned long long*)(state + j);
+                    const unsigned long long f = word >> 62;
+                    if (f == 0) {
+                        if (++spins > spin_limit) {
+                            if (st) atomicOr(&st->flags, FLAG_TIMEOUT);
+                            break;
+                        }
+                        continue;
+                    }
+                    excl += (int64_t)(word & kScanVal);
+                    if (f == 2 || j == 0) break;
+                    --j;
+                }
+                scan_publish(state + tile, 2ull, excl + tot);
+            }
+        }
+        s_excl = excl;
+        __threadfence();
+        s_last = atomicAdd(done, 1ull) == (unsigned long long)nb;  // nb + 1 blocks run (see the launch)
     }
-    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = partial[nb];
+    __syncthreads();
+    if (valid) {
+        ex += s_excl;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int64_t idx = base + i;
+            if (idx < n) out[idx] = ex;
+            ex += v[i];
+        }
+        if (tile == nb - 1 && threadIdx.x == 0) out[n] = s_excl + tot;
+    }
+    if (s_last) {  // every other block has finished its look-back: reset for the next launch
+        for (int64_t t = threadIdx.x; t < nb; t += kScanThreads) state[t] = 0ull;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ctr = 0ull;
+            *done = 0ull;
+            __threadfence();
+        }
+    }
 }
 
 __global__ void reset_status_kernel(DevStatus* st) {
@@ -311,17 +362,34 @@ void launch_elem_boxes(int dim, int n_grids, const SubGrid* sg_host, int64_t m, 
 size_t scan_tmp_bytes(int64_t n) {
     int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb < 1) nb = 1;
-    return (size_t)(nb + 1) * sizeof(int64_t);
+    return (size_t)(nb + 2) * sizeof(int64_t);
 }
 
 // out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total.  n >= 1.
-void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s) {
-    int64_t nb = (n + kScanTile - 1) / kScanTile;
-    if (nb < 1) nb = 1;
-    int64_t* partial = (int64_t*)tmp;
-    { scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial); count_launch(); }
-    { scan_partials_kernel<<<1, kScanThreads, 0, s>>>(partial, nb); count_launch(); }
-    { scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, partial, out, nb); count_launch(); }
+// tmp: scan_tmp_bytes(n) bytes, zeroed when allocated and left zeroed by every
+// launch.  One block more than the tiles is launched: it finds no tile and only
+// counts itself, so the block that clears the workspace is always the last.
+void launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s, DevStatus* st) {
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (n <= 0) return;
+    { scan_onepass_kernel<<<(unsigned)(nb + 1), kScanThreads, 0, s>>>(in, n, out, (unsigned long long*)tmp, nb, st,
+                                                                      kScanSpinLimit); count_launch(); }
+}
+
+// Test hook of the look-back's bounded wait: with `missing_first`, the tile
+// counter starts at 1, so tile 0 never publishes and tile 1's wait runs out
+// after spin_limit polls (FLAG_TIMEOUT); the workspace is reset as usual.
+void launch_scan_i64_test(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s, DevStatus* st,
+                          int missing_first, long long spin_limit) {
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (n <= 0) return;
+    if (missing_first) {
+        const unsigned long long one = 1ull;
+        cudaMemcpyAsync(tmp, &one, sizeof(one), cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+    }
+    { scan_onepass_kernel<<<(unsigned)(nb + 1), kScanThreads, 0, s>>>(in, n, out, (unsigned long long*)tmp, nb, st,
+                                                                      spin_limit); count_launch(); }
 }
 
 void launch_emit_pairs(int dim, int n_grids, const SubGrid* sg_host, int64_t m, const ElemBox* boxes,

@@ -6,11 +6,8 @@
 #include <cuda_runtime.h>
 
 #include "l2x_fp.cuh"
+#include "l2x_internal.cuh"
 #include "l2xfer.h"
-
-namespace l2x {
-void count_launch();
-}
 
 namespace {
 
@@ -75,4 +72,37 @@ extern "C" l2x_status l2x_fma_probe(int32_t precision, int32_t n_blocks, int32_t
         fma_probe_kernel<float><<<n_blocks, kProbeThreads, 0, s>>>(iters, (float*)sink);
     l2x::count_launch();
     return cudaGetLastError() == cudaSuccess ? L2X_OK : L2X_ECUDA;
+}
+
+extern "C" l2x_status l2x_scan_selftest(int64_t n, const int64_t* in, int64_t* out, int32_t missing_first,
+                                       int64_t spin_limit, void* stream) {
+    if (n <= 0 || !in || !out || spin_limit <= 0) return L2X_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t ws_bytes = l2x::scan_tmp_bytes(n);
+    void* ws = nullptr;
+    l2x::DevStatus* st = nullptr;
+    if (cudaMalloc(&ws, ws_bytes) != cudaSuccess) return L2X_ENOMEM;
+    if (cudaMalloc((void**)&st, sizeof(l2x::DevStatus)) != cudaSuccess) {
+        cudaFree(ws);
+        return L2X_ENOMEM;
+    }
+    l2x::DevStatus h{};
+    l2x_status r = L2X_OK;
+    if (cudaMemsetAsync(ws, 0, ws_bytes, s) != cudaSuccess || cudaMemsetAsync(st, 0, sizeof(l2x::DevStatus), s) != cudaSuccess)
+        r = L2X_ECUDA;
+    if (r == L2X_OK) {
+        l2x::launch_scan_i64_test(in, out, n, ws, s, st, missing_first, (long long)spin_limit);
+        unsigned long long left[2] = {1, 1};
+        if (cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(left, ws, sizeof(left), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            r = L2X_ECUDA;
+        else if (h.flags & l2x::FLAG_TIMEOUT)
+            r = L2X_ETIMEOUT;
+        else if (left[0] != 0 || left[1] != 0)  // the workspace must be left zeroed
+            r = L2X_ECUDA;
+    }
+    cudaFree(st);
+    cudaFree(ws);
+    return r;
 }

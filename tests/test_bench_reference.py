@@ -38,7 +38,7 @@ def test_work_shape_option_is_parsed_and_checked():
         assert bench.parse().work_shape is None
     finally:
         sys.argv = argv
-    for bad in ("64,64,0", "64,x,0,64"):
+    for bad in ("64,64,0", "64,x,0,64", "64,64,0,64,4,1"):
         out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--work-shape", bad],
                              capture_output=True, text=True, cwd=ROOT, timeout=120)
         assert out.returncode == 2, (bad, out.stderr[-500:])

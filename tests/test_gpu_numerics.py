@@ -228,3 +228,32 @@ def test_fma_probe_runs_and_is_deterministic():
         assert torch.isfinite(sink).all() and torch.equal(a, sink)
     with pytest.raises(l2x.L2XError):  # an unknown precision is refused by the library
         l2x.fma_probe(7, 4, 100, torch.zeros(4 * 256, dtype=torch.float32, device="cuda"))
+
+
+# ---------------------------------------------------------------- single-pass scan
+
+@pytest.mark.parametrize("n", [1, 7, 4096, 4097, 3 * 4096 + 5, (1 << 20) + 3])
+def test_scan_matches_cumsum(n):
+    """The single-pass decoupled look-back scan (pair offsets, CSR row pointers):
+    exclusive prefix sums and the total, twice in a row on one workspace
+    (each launch leaves it zeroed for the next)."""
+    l2x = _l2x()
+    rng = np.random.default_rng(n)
+    x = rng.integers(0, 1000, n).astype(np.int64)
+    want = np.concatenate([[0], np.cumsum(x)])
+    for _ in range(2):
+        st, out = l2x.scan_selftest(torch.from_numpy(x).cuda())
+        assert st == 0
+        assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_scan_bounded_wait_reports_timeout():
+    """A tile whose predecessor never publishes gives up after its poll limit:
+    the call returns L2X_ETIMEOUT instead of hanging, and the device and the
+    scan keep working afterwards."""
+    l2x = _l2x()
+    x = torch.ones(3 * 4096 + 5, dtype=torch.int64, device="cuda")
+    st, _ = l2x.scan_selftest(x, missing_first=True, spin_limit=20000)
+    assert st == 7  # L2X_ETIMEOUT
+    st, out = l2x.scan_selftest(x)
+    assert st == 0 and int(out[-1]) == x.numel()
