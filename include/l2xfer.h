@@ -390,14 +390,18 @@ l2x_status l2x_scan_selftest(int64_t n, const int64_t* in, int64_t* out, int32_t
  * the largest relative residual.
  *
  * Its work vectors live in one fixed device array of L2X_NOALLOC_MAX_DOUBLES
- * doubles (about 6.3 MB) that every GPU which loads the library holds until the
- * process exits; n and n * n_rhs must not exceed L2X_NOALLOC_MAX_ENTRIES, larger
- * problems return L2X_ECAPACITY.  The first call on a device looks up that array's
- * device address (once per device, with that device current), so make the first
- * call on each device before any stream capture.  All calls share the array and
- * the kernel initialises everything it reads; two calls whose kernels overlap on
- * the GPU (different streams or threads) race on it and give wrong results.
- * The call synchronises `stream` to read the solver status.
+ * doubles (about 6.3 MB) that every GPU holds from the moment the library's
+ * module is loaded on it until the process exits; n and n * n_rhs must not exceed
+ * L2X_NOALLOC_MAX_ENTRIES, larger problems return L2X_ECAPACITY.  Under lazy
+ * module loading (CUDA's default) the module, and with it the array, is loaded
+ * by the first call on a device, so a caller whose pool will reserve the device
+ * memory should make one small warm-up call on each device first.  Every call
+ * looks up the array's device address with the device current.  The call reads
+ * the solver status back and synchronises `stream`, so it cannot be captured
+ * into a CUDA graph: on a capturing stream it returns L2X_EINVAL.  All calls
+ * share the array and the kernel initialises everything it reads; two calls whose
+ * kernels overlap on the GPU (different streams or threads) race on it and give
+ * wrong results.
  * Errors: EINVAL, ECAPACITY, ENOTCONVERGED, ECUDA (l2x_noalloc_last_error()). */
 #define L2X_NOALLOC_MAX_ENTRIES 131072
 #define L2X_NOALLOC_MAX_DOUBLES (6 * L2X_NOALLOC_MAX_ENTRIES + 1024 * 9 + 16)

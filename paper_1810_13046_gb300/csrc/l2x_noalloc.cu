@@ -9,7 +9,6 @@
 // solve.  The caller passes the matrix, the right-hand sides and the outputs.
 #include <cooperative_groups.h>
 
-#include <mutex>
 #include <string>
 
 #include "l2x_internal.cuh"
@@ -28,12 +27,8 @@ constexpr int64_t kScratchDoubles = 5 * kMaxEntries + kMaxEntries + (int64_t)kMa
 static_assert(kScratchDoubles == L2X_NOALLOC_MAX_DOUBLES, "scratch size differs from the header");
 
 // Device-side scratch of every call.  Host code must not use this name as an
-// address: it is resolved per device with cudaGetSymbolAddress below.
+// address: its device address is looked up with cudaGetSymbolAddress below.
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
 
 struct Args {
     int64_t n;
@@ -183,29 +178,19 @@ __global__ void __launch_bounds__(kThreads) pcg_noalloc_kernel(Args A) {
 
 thread_local std::string g_err;
 
-// Resolves the device address of g_scratch for the current device (once per device).
+// Device address of g_scratch on the current device.  Looked up on every call:
+// once the module is loaded on the device this is a table lookup, and it stays
+// right after cudaDeviceReset or a new primary context (a cached pointer would
+// then name the old context's memory).  Under lazy module loading the first
+// lookup on a device loads the module and so creates the array.
 l2x_status scratch_for_current_device(double** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        g_err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        g_err = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
         return L2X_ECUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        g_err = "device index out of range";
-        return L2X_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            g_err = std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e);
-            return L2X_ECUDA;
-        }
-        g_scratch_addr[dev] = (double*)p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = (double*)p;
     return L2X_OK;
 }
 
@@ -233,10 +218,22 @@ extern "C" l2x_status l2x_solve_mass_noalloc(int64_t n, const int64_t* row_ptr, 
                 std::to_string(kMaxEntries) + " entries (n <= " + std::to_string(kMaxEntries) + ")";
         return L2X_ECAPACITY;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the call reads the solver status back and synchronises the stream, which a
+    // capturing stream does not allow
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &capturing);
+    if (ce != cudaSuccess) {
+        g_err = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce);
+        return L2X_ECUDA;
+    }
+    if (capturing != cudaStreamCaptureStatusNone) {
+        g_err = "the stream is capturing: this call synchronises it and cannot be captured";
+        return L2X_EINVAL;
+    }
     double* scratch = nullptr;
     l2x_status st = scratch_for_current_device(&scratch);
     if (st != L2X_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
