@@ -66,11 +66,12 @@ CPU_SAMPLE_ELEMS = 30000
 # Elements of the smaller samples whose operation tallies give the extra
 # workloads' algorithmic work per pair.
 TALLY_SAMPLE_ELEMS = 4000
-# DRAM bytes per candidate pair of the clipping kernel (read + write), from one
-# capture of it on the 48k-tet beam (ncu --metrics dram__bytes_read.sum,
-# dram__bytes_write.sum -k regex:clip_fused); None until taken for the kernel as
-# it stands.
-CLIP_DRAM_BYTES_PER_PAIR = None
+# DRAM bytes per candidate pair of the clipping kernel (read + write) from one
+# capture of its first launch on the 48k-tet beam (716,130 pairs; ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum -k regex:clip_fused_kernel -c 1):
+# 24.4 MB read + 196.8 MB written.  The traffic grows with the pairs (each pair
+# writes its block and volume once), so it scales to a launch by the pair count.
+CLIP_DRAM_BYTES_PER_PAIR = 308.9
 
 
 def parse():
