@@ -356,9 +356,9 @@ l2x_status l2x_fma_probe(int32_t precision, int32_t n_blocks, int32_t iters, voi
 
 /* Test hook for the arithmetic helpers of the clipping kernel (no counterpart
  * in the paper): out[i] = op(a[i], b[i]) for i < n, device arrays of doubles,
- * enqueued on `stream`.  op 0: the kernel's quotient (reciprocal by
- * Newton-Raphson from an FP32 seed, then Markstein's correction of the
- * quotient); 1: CUDA's a / b; 2: the kernel's double -> float conversion by
+ * enqueued on `stream`.  op 0: the kernel's quotient (reciprocal by two
+ * Newton-Raphson steps from an FP32 seed, then a * r: within two ulps);
+ * 1: CUDA's a / b; 2: the kernel's double -> float conversion by
  * integer instructions (round half away from zero, below 2^-126 to zero); 3:
  * CUDA's __double2float_rn; 4: the low float of the kernel's double-float split
  * (a - float(a)); 5: the kernel's float -> double conversion of

@@ -506,14 +506,15 @@ __device__ __forceinline__ bool classify_pair(const double (&T)[D + 1][D], long 
     return live;
 }
 
-// Scheduling class of a pair (pairs of one class run similar code paths):
-// 0 = no overlap, else 1 + 2 * (crossed cell planes) + (a vertex inside the cell).
+// Scheduling class of a pair (pairs of one class run the same plane lists):
+// 0 = no overlap, else 1 + 2 * (the crossed lower and upper cell planes as a
+// 2d-bit mask) + (a vertex inside the cell); at most 2^(2d+1) + 1 classes.
 template <int D>
 __device__ __forceinline__ int pair_class(const double (&T)[D + 1][D]) {
     long long kmin[D], kmax[D];
     int lo, up, in;
     if (!classify_pair<D>(T, kmin, kmax, lo, up, in)) return 0;
-    return 1 + 2 * (__popc(lo) + __popc(up)) + (in ? 1 : 0);
+    return 1 + 2 * (lo | (up << D)) + (in ? 1 : 0);
 }
 
 // Clip + integrate one pair.  T: element vertices in cell-local coordinates;

