@@ -279,6 +279,8 @@ void make_subgrids(l2x_coupling* h) {
             s.nnode[k] = k < G.dim ? s.ncell[k] + 1 : 1;
             s.ax[k] = nullptr;
             s.inv_w[k] = nullptr;
+            int ex = 0;
+            s.pow2[k] = !stretched && k < G.dim && std::frexp(s.h[k], &ex) == 0.5 && s.inv_h[k] * s.h[k] == 1.0;
         }
     }
 }

@@ -86,9 +86,52 @@ __global__ void pair_class_kernel(int G, SubGridSet sgs, int64_t m, const int64_
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p < n) {
         const int g = grid_of_pair(p, G, m, offsets);
-        double T[D + 1][D], w[3];
-        pair_vertices<D>(sgs.g[g], X, E, pair_elem[p], pair_cell[p], T, w);
-        const int key = min(pair_class<D>(T), kClasses - 1);
+        // the class only orders the pairs for the clip kernel, which classifies
+        // every pair again in FP64: single precision suffices here
+        const SubGrid& sg = sgs.g[g];
+        const int32_t e = pair_elem[p];
+        int c = pair_cell[p], ci[3];
+        ci[0] = c % sg.ncell[0];
+        c /= sg.ncell[0];
+        ci[1] = c % sg.ncell[1];
+        ci[2] = D == 3 ? c / sg.ncell[1] : 0;
+        float clo[3], iw[3];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (sg.ax[0]) {
+                clo[k] = d2f_int(__ldg(sg.ax[k] + ci[k]));
+                iw[k] = d2f_int(__ldg(sg.inv_w[k] + ci[k]));
+            } else {
+                clo[k] = d2f_int(sg.origin[k]) + (float)ci[k] * d2f_int(sg.h[k]);
+                iw[k] = d2f_int(sg.inv_h[k]);
+            }
+        }
+        int lo = 0, up = 0, in = (1 << (D + 1)) - 1;
+        bool live = true;
+        float mn[D], mx[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            mn[k] = 3.0e38f;
+            mx[k] = -3.0e38f;
+        }
+#pragma unroll
+        for (int a = 0; a <= D; ++a) {
+            const int32_t v = __ldg(E + (int64_t)e * (D + 1) + a);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float t = (d2f_int(__ldg(X + (int64_t)v * D + k)) - clo[k]) * iw[k];
+                mn[k] = fminf(mn[k], t);
+                mx[k] = fmaxf(mx[k], t);
+                if (t < 0.0f || t > 1.0f) in &= ~(1 << a);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (mx[k] <= 0.0f || mn[k] >= 1.0f) live = false;
+            if (mn[k] < 0.0f) lo |= 1 << k;
+            if (mx[k] > 1.0f) up |= 1 << k;
+        }
+        const int key = live ? min(1 + 2 * (lo | (up << D)) + (in ? 1 : 0), kClasses - 1) : 0;
         keys[p] = (uint8_t)key;
         atomicAdd(&hist[key], 1);
     }

@@ -111,11 +111,22 @@ __device__ __forceinline__ int clip_axis(const double (*in)[D], int n, double (*
             const int i = r == 0 ? e0 : e1;
             const double* p = in[i];
             const double* q = in[i + 1 == n ? 0 : i + 1];
-            const double sp = p[k] - c, sq = q[k] - c;
-            const double t = div_nr(sp, sp - sq);
-#pragma unroll
-            for (int j = 0; j < D; ++j) X[r][j] = fma(t, q[j] - p[j], p[j]);
-            X[r][k] = c;
+            const double sp = p[k] - c;
+            const double t = div_nr(sp, p[k] - q[k]);
+            // the coordinate on the plane is the plane's (snapped); only the other
+            // axes interpolate, placed by integer selects
+            if constexpr (D == 3) {
+                const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+                const double v1 = fma(t, q[j1] - p[j1], p[j1]);
+                const double v2 = fma(t, q[j2] - p[j2], p[j2]);
+                X[r][0] = k == 0 ? c : v1;
+                X[r][1] = k == 1 ? c : (k == 0 ? v1 : v2);
+                X[r][2] = k == 2 ? c : v2;
+            } else {
+                const double v1 = fma(t, q[1 - k] - p[1 - k], p[1 - k]);
+                X[r][0] = k == 0 ? c : v1;
+                X[r][1] = k == 1 ? c : v1;
+            }
         }
         return clip_emit<D>(in, n, inside, e0, X[0], e1, X[1], out);
     }
@@ -444,7 +455,7 @@ __device__ __forceinline__ bool elem_gradients(const double (&X)[D + 1][D], cons
     if constexpr (D == 2) {
         det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
         if (det == 0.0) return false;
-        const double id = 1.0 / det;
+        const double id = div_nr(1.0, det);
         g[1][0] = e[1][1] * id;
         g[1][1] = -e[1][0] * id;
         g[2][0] = -e[0][1] * id;
@@ -454,7 +465,7 @@ __device__ __forceinline__ bool elem_gradients(const double (&X)[D + 1][D], cons
                               e[1][0] * e[2][1] - e[1][1] * e[2][0]};
         det = e[0][0] * c0[0] + e[0][1] * c0[1] + e[0][2] * c0[2];
         if (det == 0.0) return false;
-        const double id = 1.0 / det;
+        const double id = div_nr(1.0, det);
         const double c1[3] = {e[2][1] * e[0][2] - e[2][2] * e[0][1], e[2][2] * e[0][0] - e[2][0] * e[0][2],
                               e[2][0] * e[0][1] - e[2][1] * e[0][0]};
         const double c2[3] = {e[0][1] * e[1][2] - e[0][2] * e[1][1], e[0][2] * e[1][0] - e[0][0] * e[1][2],
@@ -546,9 +557,10 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
         } else if (D == 3 && ((upper_mask >> k) & 1)) {
             A[k] = 1.0;
         } else {
-            const double lo = from_order_key(max(kmin[k], 0LL));
-            const double hi = from_order_key(min(kmax[k], K1));
-            A[k] = 0.5 * (lo + hi);
+            // any point of the overlap serves: a float midpoint, no FP64 arithmetic
+            const float lo = d2f_int(from_order_key(max(kmin[k], 0LL)));
+            const float hi = d2f_int(from_order_key(min(kmax[k], K1)));
+            A[k] = f2d_int(0.5f * (lo + hi));
         }
     }
     // lambda_a at the apex: c'_a = -g_a . (T_0 - A) for a >= 1, c'_0 = 1 - sum

@@ -44,6 +44,9 @@ struct SubGrid {
     // the ncell inverse cell widths (device arrays); null on a uniform grid
     const double* ax[3];
     const double* inv_w[3];
+    // uniform axis whose h is a power of two: (x - o) / h == (x - o) * inv_h exactly,
+    // so the candidate index rule multiplies instead of dividing
+    int32_t pow2[3];
 };
 
 // Per-element candidate box on one grid: lowest cell index and extent per axis.

@@ -38,6 +38,28 @@ __device__ __forceinline__ int count_lt(const double* __restrict__ x, int n, dou
     return l;
 }
 
+// floor(q) of a finite double by integer operations on its bits, and whether q
+// is an integer; -1 for q < 0 (below the grid), 2^40 for q >= 2^40 (beyond it);
+// NaN counts as beyond.
+__device__ __forceinline__ long long floor_bits(double q, bool& integral) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(q);
+    const int e = (int)((u >> 52) & 0x7ff) - 1023;
+    integral = false;
+    if (u >> 63) {  // negative (or -0.0: the floor of -0.0 is 0)
+        integral = (u << 1) == 0;
+        return integral ? 0 : -1;
+    }
+    if (e < 0) {
+        integral = u == 0;
+        return 0;
+    }
+    if (e >= 40) return 1ll << 40;
+    const unsigned long long mant = (u & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = 52 - e;
+    integral = (mant & ((1ull << sh) - 1)) == 0;
+    return (long long)(mant >> sh);
+}
+
 template <int D>
 __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const double* __restrict__ X,
                                   const int32_t* __restrict__ E, ElemBox* __restrict__ boxes,
@@ -103,10 +125,16 @@ __global__ void elem_boxes_kernel(int n_grids, SubGridSet sgs, int64_t m, const 
                 ih = count_lt(sg.ax[k], sg.nnode[k], hi[k]) - 1;
                 if (il < 0 || ih >= sg.ncell[k]) { ok = false; break; }
             } else {
-                double qlo = __ddiv_rn(__dsub_rn(lo[k], sg.origin[k]), sg.h[k]);
-                double qhi = __ddiv_rn(__dsub_rn(hi[k], sg.origin[k]), sg.h[k]);
-                double flo = floor(qlo), chi = ceil(qhi) - 1.0;
-                if (!(flo >= 0.0) || !(chi < (double)sg.ncell[k])) { ok = false; break; }
+                // one rounded subtraction and one correctly rounded division (a
+                // product by the exact 1/h when h is a power of two: the same value)
+                const double dlo = __dsub_rn(lo[k], sg.origin[k]), dhi = __dsub_rn(hi[k], sg.origin[k]);
+                const double qlo = sg.pow2[k] ? __dmul_rn(dlo, sg.inv_h[k]) : __ddiv_rn(dlo, sg.h[k]);
+                const double qhi = sg.pow2[k] ? __dmul_rn(dhi, sg.inv_h[k]) : __ddiv_rn(dhi, sg.h[k]);
+                // floor(qlo) and ceil(qhi) - 1 from the bits of the exact quotients
+                bool int_lo, int_hi;
+                const long long flo = floor_bits(qlo, int_lo), fhi = floor_bits(qhi, int_hi);
+                const long long chi = int_hi ? fhi - 1 : fhi;
+                if (flo < 0 || chi >= (long long)sg.ncell[k]) { ok = false; break; }
                 il = (int)flo;
                 ih = (int)chi;
             }
