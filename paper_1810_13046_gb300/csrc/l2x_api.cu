@@ -480,7 +480,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
             rg[g].nnode0 = h->sg[g].nnode[0];
             rg[g].nnode1 = h->sg[g].nnode[1];
         }
-        launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
+        launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_cap, h->loc_flag, h->st, s);
         for (int g = 0; g < G; ++g) {
             launch_scan_i64(rg[g].row_count, h->B[g].ptr, n, h->scan_tmp, s, h->st);
             L2X_CUDA(cudaMemcpyAsync(&nnz_g[g], h->B[g].ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -509,7 +509,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
     }
     {
         PhaseScope ph_rows2(h, L2X_PH_ROWS, s);
-        launch_b_rows(plain ? 2 : 1, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
+        launch_b_rows(plain ? 2 : 1, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_cap, h->loc_flag, h->st, s);
         for (int g = 0; g < G; ++g) {
             if (plain)
                 launch_scatter_plain(d, h->sg[g], h->E, gb[g], gb[g + 1], h->pair_elem, h->pair_cell, h->blocks,
@@ -718,12 +718,12 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         rg[g].nnode0 = h->sg[g].nnode[0];
         rg[g].nnode1 = h->sg[g].nnode[1];
     }
-    launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
+    launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_cap, h->loc_flag, h->st, s);
     for (int g = 0; g < G; ++g) {
         launch_scan_i64(rg[g].row_count, h->B[g].ptr, n, h->scan_tmp, s, h->st);
         launch_check_capacity(h->B[g].ptr + n, h->B_cap[g], h->st, s);
     }
-    launch_b_rows(1, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_flag, h->st, s);
+    launch_b_rows(1, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_cap, h->loc_flag, h->st, s);
     // the G grids' FP32 copies and transposes are independent: one graph branch
     // per grid
     L2X_CUDA(cudaEventRecord(h->ev_tfork, s));

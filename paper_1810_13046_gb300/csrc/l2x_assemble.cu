@@ -11,6 +11,7 @@ namespace {
 
 constexpr int kRowWarps = 4;
 constexpr int kRowAdj = 64;     // incident elements staged in shared memory per warp
+constexpr int kRowUnion = 128;  // nodes of a row's union box accumulated in shared memory per warp
 constexpr int kMassMaxCand = 256;
 
 __global__ void adj_count_kernel(int NA, int64_t total, const int32_t* __restrict__ E, int64_t* cnt) {
@@ -51,7 +52,8 @@ __global__ void segment_sort_kernel(int64_t n, const int64_t* __restrict__ ptr, 
 }
 
 // kLocLanes lanes per (grid, element) slot: the node-box matrix of the element on
-// that grid (one launch covers the slots of all grids).  A lane takes nodes of
+// that grid (one launch covers the slots of all grids), stored as one plane per
+// element vertex a (entry L of plane a at loc_val[a * loc_cap + L]).  A lane takes nodes of
 // the box; for each it sums, over the (up to 2^d) candidate
 // cells of the element around that node in z, y, x order, block[a][corner] of
 // the pairs whose intersection volume is positive.  Fixed order, registers
@@ -113,32 +115,42 @@ __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, 
         }
         loc_flag[L0 + jj] = touched ? 1 : 0;
 #pragma unroll
-        for (int a = 0; a < NA; ++a) loc_val[(L0 + jj) * NA + a] = acc[a];
+        for (int a = 0; a < NA; ++a) loc_val[a * loc_cap + L0 + jj] = acc[a];  // one plane per vertex
     }
 }
 
 // One warp per solid node i of one grid g (row i of B_g); the rows of the n_grids
 // matrices share one launch, warp r taking row r % n_nodes of grid r / n_nodes.
-// The row's columns lie in the union of the node boxes of the incident elements;
-// every lane owns columns j and sums, in adjacency order, the entry (local
-// vertex of i, node j) of each incident element's node-box matrix; registers
-// only, so the result is reproducible and needs no atomics.  Touched columns are
-// emitted in ascending order.
+// The row's columns lie in the union of the node boxes of the incident elements.
+// Entry (i, j) sums, in adjacency order, the entry (local vertex of i, node j)
+// of each incident element's node-box matrix, so the result is reproducible and
+// needs no atomics:
+//  * usual rows (at most kRowAdj incident elements, a union box of at most
+//    kRowUnion nodes, element boxes of at most 3 nodes per axis): the warp walks
+//    the incident elements in adjacency order, its lanes covering the element's
+//    box nodes, and adds into the union box held in shared memory (distinct
+//    nodes within one element; __syncwarp between elements);
+//  * other rows: every lane owns columns j of the union box and loops over the
+//    incident elements.
+// Touched columns are emitted in ascending order.
 // pass 0: row_count[i] = number of touched columns; pass 1: columns and values;
 // pass 2: columns only, values zeroed (the plain path adds them with atomics).
 struct RowsSet {
     RowsGrid g[kMaxGrids];
 };
 
+constexpr int kRowGroup = 4;  // incident elements whose loads are issued together
+
 template <int D>
 __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
     int pass, int n_grids, RowsSet rs, int64_t n_nodes, const int64_t* __restrict__ adj_ptr,
-    const int32_t* __restrict__ adj, const double* __restrict__ loc_val, const uint8_t* __restrict__ loc_flag,
-    DevStatus* st) {
-    constexpr int NA = D + 1;
+    const int32_t* __restrict__ adj, const double* __restrict__ loc_val, int64_t loc_cap,
+    const uint8_t* __restrict__ loc_flag, DevStatus* st) {
     __shared__ ElemBox s_box[kRowWarps][kRowAdj];
     __shared__ int64_t s_off[kRowWarps][kRowAdj];
     __shared__ int32_t s_ea[kRowWarps][kRowAdj];
+    __shared__ double s_acc[kRowWarps][kRowUnion];
+    __shared__ uint8_t s_hit[kRowWarps][kRowUnion];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t r_all = blockIdx.x * (int64_t)kRowWarps + w;
     if (r_all >= n_grids * n_nodes) return;
@@ -151,6 +163,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
     const int64_t a0 = adj_ptr[i], a1 = adj_ptr[i + 1];
     const bool staged = a1 - a0 <= kRowAdj;
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    bool wide = false;  // an element box with more than 3 nodes on some axis
     for (int64_t t = a0 + lane; t < a1; t += 32) {
         const int32_t ea = adj[t];
         const int32_t e = ea >> 2;
@@ -164,8 +177,10 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
         for (int k = 0; k < D; ++k) {
             lo[k] = min(lo[k], b.lo[k]);
             hi[k] = max(hi[k], b.lo[k] + box_ext(b, k));
+            wide |= box_ext(b, k) > 2;
         }
     }
+    wide = __any_sync(0xffffffffu, wide);
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -183,38 +198,90 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
     if (a0 < a1) {
         const int nx = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1, nz = hi[2] - lo[2] + 1;
         const int64_t total = (int64_t)nx * ny * nz;
-        for (int64_t base = 0; base < total; base += 32) {
-            const int64_t idx = base + lane;
-            bool touched = false;
-            double acc = 0.0;
-            int jx = 0, jy = 0, jz = 0;
-            if (idx < total) {
-                jx = lo[0] + (int)(idx % nx);
-                const int64_t r = idx / nx;
-                jy = lo[1] + (int)(r % ny);
-                jz = lo[2] + (int)(r / ny);
-                // the element-local matrices hold exact zeros at untouched nodes, so
-                // the value is read without waiting for the flag (same sums)
-#pragma unroll 4
-                for (int64_t t = a0; t < a1; ++t) {
-                    const int32_t ea = staged ? s_ea[w][t - a0] : adj[t];
-                    const ElemBox b = staged ? s_box[w][t - a0] : boxes[ea >> 2];
-                    const int ux = jx - b.lo[0], uy = jy - b.lo[1], uz = D == 3 ? jz - b.lo[2] : 0;
-                    const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = box_ext(b, 2);
-                    if (ux < 0 || ux > ex || uy < 0 || uy > ey || uz < 0 || (D == 3 && uz > ez)) continue;
-                    const int64_t L0 = staged ? s_off[w][t - a0] : loc_off[ea >> 2];
-                    const int64_t li = L0 + ux + (int64_t)(ex + 1) * (uy + (int64_t)(ey + 1) * uz);
-                    touched |= loc_flag[li] != 0;
-                    if (pass == 1) acc += loc_val[li * NA + (ea & 3)];
+        if (staged && !wide && total <= kRowUnion) {
+            for (int u = lane; u < total; u += 32) {
+                s_acc[w][u] = 0.0;
+                s_hit[w][u] = 0;
+            }
+            __syncwarp();
+            // this lane's node of an element box (at most 3 nodes per axis)
+            const int lx = lane % 3, ly = (lane / 3) % 3, lz = D == 3 ? lane / 9 : 0;
+            const bool lane_ok = lane < (D == 3 ? 27 : 9);
+            for (int64_t t0 = a0; t0 < a1; t0 += kRowGroup) {
+                int u[kRowGroup];
+                uint8_t f[kRowGroup];
+                double v[kRowGroup];
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    u[q] = -1;
+                    f[q] = 0;
+                    v[q] = 0.0;
+                    const int64_t t = t0 + q;
+                    if (t >= a1 || !lane_ok) continue;
+                    const ElemBox b = s_box[w][t - a0];
+                    const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = D == 3 ? box_ext(b, 2) : 0;
+                    if (lx > ex || ly > ey || lz > ez) continue;
+                    const int64_t L = s_off[w][t - a0] + lx + (ex + 1) * (ly + (ey + 1) * lz);
+                    u[q] = (b.lo[0] + lx - lo[0]) + nx * ((b.lo[1] + ly - lo[1]) + ny * (D == 3 ? b.lo[2] + lz - lo[2] : 0));
+                    f[q] = loc_flag[L];
+                    // the element-local matrices hold exact zeros at untouched nodes, so
+                    // the value is read without waiting for the flag (same sums)
+                    if (pass == 1) v[q] = loc_val[(int64_t)(s_ea[w][t - a0] & 3) * loc_cap + L];
+                }
+#pragma unroll
+                for (int q = 0; q < kRowGroup; ++q) {
+                    if (u[q] >= 0) {
+                        if (pass == 1) s_acc[w][u[q]] += v[q];
+                        if (f[q]) s_hit[w][u[q]] = 1;
+                    }
+                    __syncwarp();
                 }
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, touched);
-            if (pass >= 1 && touched) {
-                const int pos = __popc(bal & ((1u << lane) - 1u));
-                rg.cols[out0 + cnt + pos] = jx + rg.nnode0 * (jy + rg.nnode1 * jz);
-                rg.vals[out0 + cnt + pos] = pass == 1 ? acc : 0.0;
+            for (int64_t base = 0; base < total; base += 32) {
+                const int idx = (int)base + lane;
+                const bool touched = idx < total && s_hit[w][idx] != 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, touched);
+                if (pass >= 1 && touched) {
+                    const int jx = lo[0] + idx % nx, r = idx / nx;
+                    const int jy = lo[1] + r % ny, jz = lo[2] + r / ny;
+                    const int pos = __popc(bal & ((1u << lane) - 1u));
+                    rg.cols[out0 + cnt + pos] = jx + rg.nnode0 * (jy + rg.nnode1 * jz);
+                    rg.vals[out0 + cnt + pos] = pass == 1 ? s_acc[w][idx] : 0.0;
+                }
+                cnt += __popc(bal);
             }
-            cnt += __popc(bal);
+        } else {
+            for (int64_t base = 0; base < total; base += 32) {
+                const int64_t idx = base + lane;
+                bool touched = false;
+                double acc = 0.0;
+                int jx = 0, jy = 0, jz = 0;
+                if (idx < total) {
+                    jx = lo[0] + (int)(idx % nx);
+                    const int64_t r = idx / nx;
+                    jy = lo[1] + (int)(r % ny);
+                    jz = lo[2] + (int)(r / ny);
+#pragma unroll 4
+                    for (int64_t t = a0; t < a1; ++t) {
+                        const int32_t ea = staged ? s_ea[w][t - a0] : adj[t];
+                        const ElemBox b = staged ? s_box[w][t - a0] : boxes[ea >> 2];
+                        const int ux = jx - b.lo[0], uy = jy - b.lo[1], uz = D == 3 ? jz - b.lo[2] : 0;
+                        const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = box_ext(b, 2);
+                        if (ux < 0 || ux > ex || uy < 0 || uy > ey || uz < 0 || (D == 3 && uz > ez)) continue;
+                        const int64_t L0 = staged ? s_off[w][t - a0] : loc_off[ea >> 2];
+                        const int64_t li = L0 + ux + (int64_t)(ex + 1) * (uy + (int64_t)(ey + 1) * uz);
+                        touched |= loc_flag[li] != 0;
+                        if (pass == 1) acc += loc_val[(int64_t)(ea & 3) * loc_cap + li];
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, touched);
+                if (pass >= 1 && touched) {
+                    const int pos = __popc(bal & ((1u << lane) - 1u));
+                    rg.cols[out0 + cnt + pos] = jx + rg.nnode0 * (jy + rg.nnode1 * jz);
+                    rg.vals[out0 + cnt + pos] = pass == 1 ? acc : 0.0;
+                }
+                cnt += __popc(bal);
+            }
         }
     }
     if (pass == 0 && lane == 0) rg.row_count[i] = cnt;
@@ -481,16 +548,16 @@ void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t
 }
 
 void launch_b_rows(int pass, int dim, int n_grids, const RowsGrid* grids, int64_t n_nodes, const int64_t* adj_ptr,
-                   const int32_t* adj, const double* loc_val, const uint8_t* loc_flag, DevStatus* st,
-                   cudaStream_t s) {
+                   const int32_t* adj, const double* loc_val, int64_t loc_cap, const uint8_t* loc_flag,
+                   DevStatus* st, cudaStream_t s) {
     if (n_nodes <= 0 || n_grids <= 0) return;
     RowsSet rs{};
     for (int g = 0; g < n_grids; ++g) rs.g[g] = grids[g];
     const unsigned nb = nblk(n_grids * n_nodes, kRowWarps);
     if (dim == 2)
-        { b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, n_grids, rs, n_nodes, adj_ptr, adj, loc_val, loc_flag, st); count_launch(); }
+        { b_rows_kernel<2><<<nb, kRowWarps * 32, 0, s>>>(pass, n_grids, rs, n_nodes, adj_ptr, adj, loc_val, loc_cap, loc_flag, st); count_launch(); }
     else
-        { b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, n_grids, rs, n_nodes, adj_ptr, adj, loc_val, loc_flag, st); count_launch(); }
+        { b_rows_kernel<3><<<nb, kRowWarps * 32, 0, s>>>(pass, n_grids, rs, n_nodes, adj_ptr, adj, loc_val, loc_cap, loc_flag, st); count_launch(); }
 }
 
 void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,

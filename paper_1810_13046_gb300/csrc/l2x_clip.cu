@@ -186,14 +186,13 @@ __device__ __forceinline__ void clip_pair(int64_t i, int G, const SubGridSet& sg
     const int g = grid_of_pair(p, G, m, offsets);
     const SubGrid& sg = sgs.g[g];
     const int32_t e = pair_elem[p];
-    double blk[NA * NB];
+    double* blk = blocks + p * (NA * NB);  // the pair's block, written in place
     double vol = 0.0;
     const int flag = elem_flag[e];
     if (flag < 0) {
         atomicOr(&st->flags, FLAG_DEGENERATE);
         atomicMin(&st->bad_elem, e);
-#pragma unroll
-        for (int j = 0; j < NA * NB; ++j) blk[j] = 0.0;
+        store_zero_block<D>(blk);
     } else {
         double T[NA][D], gr[NA][D], w[3];
         pair_vertices<D>(sg, X, E, e, pair_cell[p], T, w);
@@ -204,8 +203,6 @@ __device__ __forceinline__ void clip_pair(int64_t i, int G, const SubGridSet& sg
         const double scale = frame_scale<D>(sg, w, gr);
         pair_integrals<D, R>(T, gr, flag == 1, scale, blk, &vol, poly);
     }
-#pragma unroll
-    for (int j = 0; j < NA * NB; ++j) blocks[p * (NA * NB) + j] = blk[j];
     vols[p] = vol;
 }
 
@@ -269,19 +266,18 @@ __global__ void clip_plain_kernel(SubGrid sg, const double* __restrict__ X, cons
             T[a][k] = (Xe[a][k] - clo[k]) * iw[k];
         }
     }
-    double blk[NA * NB];
+    double* blk = blocks + p * (NA * NB);
     double vol = 0.0;
     bool pos = true;
     if (!elem_gradients<D>(Xe, sg.inv_h, ge, pos)) {
         atomicOr(&st->flags, FLAG_DEGENERATE);
         atomicMin(&st->bad_elem, e);
-        for (int i = 0; i < NA * NB; ++i) blk[i] = 0.0;
+        store_zero_block<D>(blk);
     } else {
         const double scale = frame_scale<D>(sg, w, ge);
         double poly[2 * kMaxPoly][D];
         pair_integrals<D, double>(T, ge, pos, scale, blk, &vol, poly);
     }
-    for (int i = 0; i < NA * NB; ++i) blocks[p * (NA * NB) + i] = blk[i];
     vols[p] = vol;
 }
 

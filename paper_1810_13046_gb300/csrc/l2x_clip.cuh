@@ -34,7 +34,7 @@
 
 namespace l2x {
 
-constexpr int kMaxPoly = 10;  // triangle + 6 planes -> 9; square + 4 planes -> 8
+constexpr int kMaxPoly = 9;  // one vertex added per cut: triangle + 6 planes -> 9; square + 4 planes -> 8
 // doubles of one thread's polygon buffers in shared memory: 2 * kMaxPoly
 // vertices plus one pad (an odd stride keeps a warp's accesses conflict-free)
 template <int D>
@@ -47,15 +47,23 @@ struct ElemT {
     double T[D + 1][D];   // vertices in cell-local coordinates
 };
 
-// Sutherland-Hodgman clipping of a convex polygon against one half-space, in
-// three phases so that a warp runs the FP64 crossing arithmetic together:
-// (1) the inside flags of all vertices as a bit mask, (2) the two crossings (a
-// convex polygon cut by a plane has exactly one exit edge, inside -> outside,
-// and one entry edge), (3) the output in traversal order: every inside vertex,
-// each crossing point after the first vertex of its edge.  The crossing on
-// edge (p, q) is p + t (q - p), t = s_p / (s_p - s_q), s the signed plane
-// values.  When rounding leaves the inside vertices in more than one run the
-// edges are handled one by one (same formula, same order).
+// Sutherland-Hodgman clipping of a convex polygon against one half-space.  The
+// inside vertices of a convex polygon cut by a plane form one cyclic run, so the
+// output is that run with the crossing point of the exit edge (inside ->
+// outside) after its last vertex and that of the entry edge before its first: a
+// cut adds at most one vertex.  The crossing on edge (p, q) is p + t (q - p),
+// t = s_p / (s_p - s_q), s the signed plane values; a warp computes the two
+// crossings together.
+//
+// Rounding can split the computed inside flags into several runs, but only
+// through vertices within rounding distance of the plane (the signed value of a
+// convex polygon is unimodal along its boundary, so a vertex between two outside
+// runs, or in an outside run that does not hold the farthest vertex, is within
+// rounding of the plane).  Such a split is repaired: the outside run holding the
+// vertex farthest outside is kept and the vertices of the other outside runs are
+// counted inside, which moves the polygon by rounding only and keeps the bound of
+// one added vertex per cut; t is then clamped to [0, 1].  So a triangle cut by the
+// six cell planes, or a cell face cut by the four element planes, fits kMaxPoly.
 
 // Emits the clipped polygon: inside vertices of `in`, crossing points X0 (after
 // vertex e0) and X1 (after vertex e1).
@@ -91,72 +99,89 @@ __device__ __forceinline__ bool one_run(unsigned inside, int n, int& e_exit, int
     return true;
 }
 
+// Repaired inside mask: everything but the cyclic run of outside vertices that
+// holds vertex j (bit j of `outside` set; at least one bit of the n clear).
+__device__ __forceinline__ unsigned keep_outside_run(unsigned outside, int n, int j) {
+    unsigned run = 1u << j;
+    for (int i = j + 1 == n ? 0 : j + 1; (outside >> i) & 1u; i = i + 1 == n ? 0 : i + 1) run |= 1u << i;
+    for (int i = j == 0 ? n - 1 : j - 1; ((outside >> i) & 1u) && !((run >> i) & 1u); i = i == 0 ? n - 1 : i - 1)
+        run |= 1u << i;
+    return ((1u << n) - 1u) & ~run;
+}
+
+__device__ __forceinline__ double clamp01(double t) { return fmin(fmax(t, 0.0), 1.0); }  // NaN -> 0
+
 // Against an axis plane at coordinate c: keep v[k] >= c (upper = false) or
 // v[k] <= c (upper = true).  Inside tests are integer comparisons of order keys;
-// crossing points are snapped onto the plane.
+// crossing points are snapped onto the plane.  `same` is set when every vertex
+// is inside: then `out` is left untouched and the polygon is `in` as it was.
 template <int D>
 __device__ __forceinline__ int clip_axis(const double (*in)[D], int n, double (*out)[D], int k, double c,
-                                         bool upper) {
+                                         bool upper, bool& same) {
     const long long kc = order_key(c);
     unsigned inside = 0;
     for (int i = 0; i < n; ++i) {
         const long long kk = order_key(in[i][k]);
         inside |= (unsigned)(upper ? kk <= kc : kk >= kc) << i;
     }
+    const unsigned all = (1u << n) - 1u;
+    same = inside == all;
+    if (same) return n;
+    if (inside == 0) return 0;
     int e0, e1;
-    if (inside != 0 && inside != (1u << n) - 1u && one_run(inside, n, e0, e1)) {
-        double X[2][D];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int i = r == 0 ? e0 : e1;
-            const double* p = in[i];
-            const double* q = in[i + 1 == n ? 0 : i + 1];
-            const double sp = p[k] - c;
-            const double t = div_nr(sp, p[k] - q[k]);
-            // the coordinate on the plane is the plane's (snapped); only the other
-            // axes interpolate, placed by integer selects
-            if constexpr (D == 3) {
-                const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
-                const double v1 = fma(t, q[j1] - p[j1], p[j1]);
-                const double v2 = fma(t, q[j2] - p[j2], p[j2]);
-                X[r][0] = k == 0 ? c : v1;
-                X[r][1] = k == 1 ? c : (k == 0 ? v1 : v2);
-                X[r][2] = k == 2 ? c : v2;
-            } else {
-                const double v1 = fma(t, q[1 - k] - p[1 - k], p[1 - k]);
-                X[r][0] = k == 0 ? c : v1;
-                X[r][1] = k == 1 ? c : v1;
-            }
+    const bool repaired = !one_run(inside, n, e0, e1);
+    if (repaired) {
+        int j = -1;
+        long long kj = 0;
+        for (int i = 0; i < n; ++i) {
+            if ((inside >> i) & 1u) continue;
+            const long long kk = order_key(in[i][k]);
+            if (j < 0 || (upper ? kk > kj : kk < kj)) { j = i; kj = kk; }
         }
-        return clip_emit<D>(in, n, inside, e0, X[0], e1, X[1], out);
+        inside = keep_outside_run(~inside & all, n, j);
+        one_run(inside, n, e0, e1);
     }
-    int m = 0;
-    for (int i = 0; i < n; ++i) {
+    // both quotients before the one branch, so that their latencies overlap
+    double t[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = r == 0 ? e0 : e1;
         const double* p = in[i];
         const double* q = in[i + 1 == n ? 0 : i + 1];
-        const bool ip = (inside >> i) & 1u;
-        const bool iq = (inside >> (i + 1 == n ? 0 : i + 1)) & 1u;
-        if (ip) {
+        t[r] = div_nr(p[k] - c, p[k] - q[k]);
+    }
+    if (repaired) {
+        t[0] = clamp01(t[0]);
+        t[1] = clamp01(t[1]);
+    }
+    double X[2][D];
 #pragma unroll
-            for (int j = 0; j < D; ++j) out[m][j] = p[j];
-            ++m;
-        }
-        if (ip != iq) {
-            const double sp = p[k] - c, sq = q[k] - c;
-            const double t = div_nr(sp, sp - sq);
-#pragma unroll
-            for (int j = 0; j < D; ++j) out[m][j] = fma(t, q[j] - p[j], p[j]);
-            out[m][k] = c;
-            ++m;
+    for (int r = 0; r < 2; ++r) {
+        const int i = r == 0 ? e0 : e1;
+        const double* p = in[i];
+        const double* q = in[i + 1 == n ? 0 : i + 1];
+        // the coordinate on the plane is the plane's (snapped); only the other
+        // axes interpolate, placed by integer selects
+        if constexpr (D == 3) {
+            const int j1 = k == 0 ? 1 : 0, j2 = k == 2 ? 1 : 2;
+            const double v1 = fma(t[r], q[j1] - p[j1], p[j1]);
+            const double v2 = fma(t[r], q[j2] - p[j2], p[j2]);
+            X[r][0] = k == 0 ? c : v1;
+            X[r][1] = k == 1 ? c : (k == 0 ? v1 : v2);
+            X[r][2] = k == 2 ? c : v2;
+        } else {
+            const double v1 = fma(t[r], q[1 - k] - p[1 - k], p[1 - k]);
+            X[r][0] = k == 0 ? c : v1;
+            X[r][1] = k == 1 ? c : v1;
         }
     }
-    return m;
+    return clip_emit<D>(in, n, inside, e0, X[0], e1, X[1], out);
 }
 
-// Against the half-space g.v + c0 >= 0.
+// Against the half-space g.v + c0 >= 0 (`same` as for clip_axis).
 template <int D>
 __device__ __forceinline__ int clip_plane(const double (*in)[D], int n, double (*out)[D], const double* g,
-                                          double c0) {
+                                          double c0, bool& same) {
     double sv[kMaxPoly];
     unsigned inside = 0;
     for (int i = 0; i < n; ++i) {
@@ -166,41 +191,40 @@ __device__ __forceinline__ int clip_plane(const double (*in)[D], int n, double (
         sv[i] = s;
         inside |= (unsigned)nonneg_d(s) << i;
     }
+    const unsigned all = (1u << n) - 1u;
+    same = inside == all;
+    if (same) return n;
+    if (inside == 0) return 0;
     int e0, e1;
-    if (inside != 0 && inside != (1u << n) - 1u && one_run(inside, n, e0, e1)) {
-        double X[2][D];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int i = r == 0 ? e0 : e1;
-            const int i1 = i + 1 == n ? 0 : i + 1;
-            const double* p = in[i];
-            const double* q = in[i1];
-            const double sp = sv[i], sq = sv[i1];
-            const double t = div_nr(sp, sp - sq);
-#pragma unroll
-            for (int j = 0; j < D; ++j) X[r][j] = fma(t, q[j] - p[j], p[j]);
-        }
-        return clip_emit<D>(in, n, inside, e0, X[0], e1, X[1], out);
+    const bool repaired = !one_run(inside, n, e0, e1);
+    if (repaired) {
+        int j = -1;
+        for (int i = 0; i < n; ++i)
+            if (!((inside >> i) & 1u) && (j < 0 || sv[i] < sv[j])) j = i;
+        inside = keep_outside_run(~inside & all, n, j);
+        one_run(inside, n, e0, e1);
     }
-    int m = 0;
-    for (int i = 0; i < n; ++i) {
+    double t[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = r == 0 ? e0 : e1;
         const int i1 = i + 1 == n ? 0 : i + 1;
-        const double* p = in[i];
-        const double* q = in[i1];
-        const bool ip = (inside >> i) & 1u, iq = (inside >> i1) & 1u;
-        if (ip) {
-#pragma unroll
-            for (int j = 0; j < D; ++j) out[m][j] = p[j];
-            ++m;
-        }
-        if (ip != iq) {
-            const double t = div_nr(sv[i], sv[i] - sv[i1]);
-#pragma unroll
-            for (int j = 0; j < D; ++j) out[m][j] = fma(t, q[j] - p[j], p[j]);
-            ++m;
-        }
+        t[r] = div_nr(sv[i], sv[i] - sv[i1]);
     }
-    return m;
+    if (repaired) {
+        t[0] = clamp01(t[0]);
+        t[1] = clamp01(t[1]);
+    }
+    double X[2][D];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = r == 0 ? e0 : e1;
+        const double* p = in[i];
+        const double* q = in[i + 1 == n ? 0 : i + 1];
+#pragma unroll
+        for (int j = 0; j < D; ++j) X[r][j] = fma(t[r], q[j] - p[j], p[j]);
+    }
+    return clip_emit<D>(in, n, inside, e0, X[0], e1, X[1], out);
 }
 
 // ------------------------------------------------------------------ moments
@@ -528,9 +552,17 @@ __device__ __forceinline__ int pair_class(const double (&T)[D + 1][D]) {
     return 1 + 2 * (lo | (up << D)) + (in ? 1 : 0);
 }
 
+// Zero block of a pair without overlap, in 16-byte stores.
+template <int D>
+__device__ __forceinline__ void store_zero_block(double* block) {
+#pragma unroll
+    for (int i = 0; i < (D + 1) << D; i += 2) reinterpret_cast<double2*>(block)[i / 2] = make_double2(0.0, 0.0);
+}
+
 // Clip + integrate one pair.  T: element vertices in cell-local coordinates;
 // g, positive: from elem_gradients; scale = volume of the cell.  Writes the
-// (d+1)*2^d block and the intersection volume.
+// (d+1)*2^d block straight to `block` (16-byte aligned, row-major by element
+// vertex) and the intersection volume to *vol.
 template <int D, typename R>
 __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D + 1][D], bool positive,
                                double scale, double* block, double* vol, double (*poly)[D]) {
@@ -538,12 +570,13 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     constexpr int NA = D + 1;
     using L = MomentLayout<D>;
     constexpr long long K1 = 0x3ff0000000000000LL;  // order key of 1.0 (key of +0.0 is 0)
-    *vol = 0.0;
-#pragma unroll
-    for (int i = 0; i < NA * NB; ++i) block[i] = 0.0;
     long long kmin[D], kmax[D];
     int lower_mask, upper_mask, inside_mask;
-    if (!classify_pair<D>(T, kmin, kmax, lower_mask, upper_mask, inside_mask)) return;  // no overlap of positive measure
+    if (!classify_pair<D>(T, kmin, kmax, lower_mask, upper_mask, inside_mask)) {  // no overlap of positive measure
+        store_zero_block<D>(block);
+        *vol = 0.0;
+        return;
+    }
     // 3-D: an element vertex is the apex only when the element crosses no cell
     // plane; otherwise the apex sits on the crossed planes (fewer faces to clip)
     const int apex_v = (inside_mask && (D == 2 || (lower_mask | upper_mask) == 0)) ? __ffs(inside_mask) - 1 : -1;
@@ -621,8 +654,9 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
         double (*nxt)[D] = bufB;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            if ((lower_mask >> k) & 1) { n = clip_axis<D>(cur, n, nxt, k, 0.0, false); double (*t)[D] = cur; cur = nxt; nxt = t; }
-            if ((upper_mask >> k) & 1) { n = clip_axis<D>(cur, n, nxt, k, 1.0, true); double (*t)[D] = cur; cur = nxt; nxt = t; }
+            bool same;
+            if ((lower_mask >> k) & 1) { n = clip_axis<D>(cur, n, nxt, k, 0.0, false, same); if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; } }
+            if ((upper_mask >> k) & 1) { n = clip_axis<D>(cur, n, nxt, k, 1.0, true, same); if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; } }
         }
         if (n >= 3) {
             double P0[D];
@@ -667,54 +701,57 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
             if ((lower_mask >> k) & 1) { plane_k[n_planes] = k; plane_up[n_planes] = 0; plane_c[n_planes] = clo[k]; ++n_planes; }
             if ((upper_mask >> k) & 1) { plane_k[n_planes] = k; plane_up[n_planes] = 1; plane_c[n_planes] = chi[k]; ++n_planes; }
         }
-        // element faces: face opposite vertex f, outward for a positive element;
-        // with an element vertex as apex only the face opposite it has a cone
+        // The polygons of the boundary of E ∩ C in one loop, so that the clipping and
+        // integration code is inlined once: the element faces (face opposite vertex
+        // f, outward for a positive element; with an element vertex as apex only
+        // the face opposite it has a cone) clipped to the crossed cell planes, then
+        // the cell faces the element crosses clipped to the element (a face whose
+        // plane holds the apex spans a cone of zero volume and is skipped).
         const int faces[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
         const int n_faces = apex_v >= 0 ? 1 : 4;
 #pragma unroll 1
-        for (int jf = 0; jf < n_faces; ++jf) {
-            const int f = apex_v >= 0 ? apex_v : jf;
-            int n = 3;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const int v = faces[f][positive ? i : 2 - i];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) bufA[i][k] = U[v][k];
-            }
+        for (int jj = 0; jj < n_faces + n_planes; ++jj) {
             double (*cur)[D] = bufA;
             double (*nxt)[D] = bufB;
-#pragma unroll 1
-            for (int jp = 0; jp < n_planes; ++jp) {
-                n = clip_axis<D>(cur, n, nxt, plane_k[jp], plane_c[jp], plane_up[jp] != 0);
-                double (*t)[D] = cur; cur = nxt; nxt = t;
-            }
-            accum_polygon<D, R>(cur, n, acc, &vol_df, &fr);
-        }
-        // cell faces the element crosses, clipped to the element (a face whose
-        // plane holds the apex spans a cone of zero volume and is skipped)
-#pragma unroll 1
-        for (int jp = 0; jp < n_planes; ++jp) {
-            if (plane_c[jp] == 0.0) continue;
-            const int k = plane_k[jp];
-            const int side = plane_up[jp];
-            const int j1 = (k + 1) % 3, j2 = (k + 2) % 3;
-            const double ck = plane_c[jp];
-            const double a1[4] = {clo[j1], chi[j1], chi[j1], clo[j1]};
-            const double a2[4] = {clo[j2], clo[j2], chi[j2], chi[j2]};
+            int n;
+            if (jj < n_faces) {
+                const int f = apex_v >= 0 ? apex_v : jj;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int sidx = side == 1 ? v : 3 - v;  // outward: +e_k on t_k = 1, -e_k on t_k = 0
-                bufA[v][k] = ck;
-                bufA[v][j1] = a1[sidx];
-                bufA[v][j2] = a2[sidx];
-            }
-            int n = 4;
-            double (*cur)[D] = bufA;
-            double (*nxt)[D] = bufB;
+                for (int i = 0; i < 3; ++i) {
+                    const int v = faces[f][positive ? i : 2 - i];
 #pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                n = clip_plane<D>(cur, n, nxt, g[a], cA[a]);
-                double (*t)[D] = cur; cur = nxt; nxt = t;
+                    for (int k = 0; k < 3; ++k) bufA[i][k] = U[v][k];
+                }
+                n = 3;
+#pragma unroll 1
+                for (int jp = 0; jp < n_planes; ++jp) {
+                    bool same;
+                    n = clip_axis<D>(cur, n, nxt, plane_k[jp], plane_c[jp], plane_up[jp] != 0, same);
+                    if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; }
+                }
+            } else {
+                const int jp = jj - n_faces;
+                if ((__double_as_longlong(plane_c[jp]) << 1) == 0) continue;  // c = +-0: the apex's plane
+                const int k = plane_k[jp];
+                const int side = plane_up[jp];
+                const int j1 = (k + 1) % 3, j2 = (k + 2) % 3;
+                const double ck = plane_c[jp];
+                const double a1[4] = {clo[j1], chi[j1], chi[j1], clo[j1]};
+                const double a2[4] = {clo[j2], clo[j2], chi[j2], chi[j2]};
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int sidx = side == 1 ? v : 3 - v;  // outward: +e_k on t_k = 1, -e_k on t_k = 0
+                    bufA[v][k] = ck;
+                    bufA[v][j1] = a1[sidx];
+                    bufA[v][j2] = a2[sidx];
+                }
+                n = 4;
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    bool same;
+                    n = clip_plane<D>(cur, n, nxt, g[a], cA[a], same);
+                    if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; }
+                }
             }
             accum_polygon<D, R>(cur, n, acc, &vol_df, &fr);
         }
@@ -786,14 +823,18 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
         R ga[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) ga[k] = to_r<R>(g[a][k]);
+        double row[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             R v = ca * W[b];
 #pragma unroll
             for (int j = 0; j < D; ++j) v += ga[j] * Wj[b][j];
-            if constexpr (sizeof(R) == 4) block[a * NB + b] = f2d_int(v * scale_r);
-            else block[a * NB + b] = (double)v * scale;
+            if constexpr (sizeof(R) == 4) row[b] = f2d_int(v * scale_r);
+            else row[b] = (double)v * scale;
         }
+#pragma unroll
+        for (int b = 0; b < NB; b += 2)
+            reinterpret_cast<double2*>(block + a * NB)[b / 2] = make_double2(row[b], row[b + 1]);
     }
 }
 

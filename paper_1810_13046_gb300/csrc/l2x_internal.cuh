@@ -149,8 +149,9 @@ void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E
                            int32_t* adj, int32_t* cursor, void* scan_tmp, cudaStream_t s);
 // Element-local matrices of grid g: for every element and every node of its
 // candidate node box, the sums over the element's pairs of block[a][b] at that
-// node (loc_val, (d+1) per node) and whether a pair of positive volume touches
-// it (loc_flag).  loc_off_g: offsets of the elements' node boxes.
+// node (loc_val: d+1 planes of loc_cap entries, one per element vertex a) and
+// whether a pair of positive volume touches it (loc_flag).  loc_off_g: offsets
+// of the elements' node boxes.
 void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t* offsets_g,
                        const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
                        double* loc_val, uint8_t* loc_flag, int dual, DevStatus* st, cudaStream_t s);
@@ -170,8 +171,8 @@ struct RowsGrid {
 // in one launch.  pass 0: row_count[i] = nonzeros of row i; pass 1: cols + vals;
 // pass 2: cols only, vals zeroed (the plain path adds them with atomics).
 void launch_b_rows(int pass, int dim, int n_grids, const RowsGrid* grids, int64_t n_nodes, const int64_t* adj_ptr,
-                   const int32_t* adj, const double* loc_val, const uint8_t* loc_flag, DevStatus* st,
-                   cudaStream_t s);
+                   const int32_t* adj, const double* loc_val, int64_t loc_cap, const uint8_t* loc_flag,
+                   DevStatus* st, cudaStream_t s);
 // P1 mass matrix structure (pass 0 counts, pass 1 columns) and values.
 void launch_mass_structure(int pass, int dim, int64_t n_nodes, const int32_t* E, const int64_t* adj_ptr,
                            const int32_t* adj, int64_t* row_count, const int64_t* row_ptr, int32_t* cols,
