@@ -75,6 +75,7 @@ struct l2x_coupling {
     void* scan_tmp = nullptr;
     size_t scan_tmp_cap = 0;
     int64_t* row_count = nullptr;    // kMaxGrids * (n_nodes + 1): row counts per grid
+    RowCache* row_cache = nullptr;   // n_grids * n_nodes: rows of B_g kept between the two row passes
     int32_t* tcursor = nullptr;      // fill cursors of the B^T rows
     int64_t tcursor_cap = 0;
     int64_t* tflags = nullptr;       // non-empty-row flags of B^T (scan scratch)
@@ -347,6 +348,7 @@ l2x_status build_topology(l2x_coupling* h, cudaStream_t s) {
     L2X_TRY(dalloc(&h->adj, (size_t)(m * NA)));
     L2X_TRY(dalloc(&h->cursor, n));
     L2X_TRY(dalloc(&h->row_count, (int64_t)kMaxGrids * (n + 1)));  // row counts of B_g, or of M_s
+    L2X_TRY(dalloc(&h->row_cache, (size_t)h->n_grids * n));
     L2X_TRY(ensure_scan(h, n));
     launch_node_adjacency(h->dim, n, m, h->E, h->adj_ptr, h->adj, h->cursor, h->scan_tmp, s);
     L2X_TRY(dalloc(&h->M.ptr, n + 1));
@@ -479,6 +481,7 @@ l2x_status build_geometry(l2x_coupling* h, cudaStream_t s) {
             rg[g].row_count = h->row_count + (int64_t)g * (n + 1);
             rg[g].nnode0 = h->sg[g].nnode[0];
             rg[g].nnode1 = h->sg[g].nnode[1];
+            rg[g].cache = h->row_cache + (int64_t)g * n;
         }
         launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_cap, h->loc_flag, h->st, s);
         for (int g = 0; g < G; ++g) {
@@ -717,6 +720,7 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         rg[g].vals = h->B[g].val;
         rg[g].nnode0 = h->sg[g].nnode[0];
         rg[g].nnode1 = h->sg[g].nnode[1];
+        rg[g].cache = h->row_cache + (int64_t)g * n;
     }
     launch_b_rows(0, d, G, rg, n, h->adj_ptr, h->adj, h->loc_val, h->loc_cap, h->loc_flag, h->st, s);
     for (int g = 0; g < G; ++g) {
@@ -850,6 +854,7 @@ l2x_status l2x_destroy(l2x_handle h) {
         }
     if (h->scan_tmp) cudaFree(h->scan_tmp);
     dfree(h->row_count);
+    dfree(h->row_cache);
     dfree(h->tcursor);
     dfree(h->tflags);
     if (h->pcg_ws) cudaFree(h->pcg_ws);

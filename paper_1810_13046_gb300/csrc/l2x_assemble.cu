@@ -1,6 +1,7 @@
 // Step (IV) of Sec. 2.3: assembly of the mortar matrices B_g (one per velocity
 // grid) and S = M_s (P1 mass matrix, Sec. 2.1 "Spatial Discretization") into
 // CSR, and the transpose of B_g used by the force transfer.
+#include <algorithm>
 #include <climits>
 
 #include "l2x_internal.cuh"
@@ -11,7 +12,7 @@ namespace {
 
 constexpr int kRowWarps = 4;
 constexpr int kRowAdj = 64;     // incident elements staged in shared memory per warp
-constexpr int kRowUnion = 128;  // nodes of a row's union box accumulated in shared memory per warp
+constexpr int kRowUnion = kRowKeep;  // nodes of a row's union box accumulated in shared memory per warp
 constexpr int kMassMaxCand = 256;
 
 __global__ void adj_count_kernel(int NA, int64_t total, const int32_t* __restrict__ E, int64_t* cnt) {
@@ -51,71 +52,156 @@ __global__ void segment_sort_kernel(int64_t n, const int64_t* __restrict__ ptr, 
     }
 }
 
-// kLocLanes lanes per (grid, element) slot: the node-box matrix of the element on
-// that grid (one launch covers the slots of all grids), stored as one plane per
-// element vertex a (entry L of plane a at loc_val[a * loc_cap + L]).  A lane takes nodes of
-// the box; for each it sums, over the (up to 2^d) candidate
-// cells of the element around that node in z, y, x order, block[a][corner] of
-// the pairs whose intersection volume is positive.  Fixed order, registers
-// only: reproducible.  Boxes hold 8 to 27 nodes for elements about a cell in
-// size, so several elements share a warp (more elements in flight hide the
-// latency of their dependent loads).
-constexpr int kLocLanes = 2;
+// The node-box matrix of every (grid, element) slot (one launch covers the slots
+// of all grids), stored as one plane per element vertex a (entry L of plane a at
+// loc_val[a * loc_cap + L]).  Entry (a, node) sums block[a][corner] over the
+// element's candidate cells around the node whose pair has a positive
+// intersection volume, in ascending cell order (z, y, x): fixed order, so the
+// result is reproducible.
+//  * usual elements (at most 3 box nodes per axis, so at most 2^d cells): one
+//    warp per element; the lanes load each pair's block as one coalesced run
+//    (lane = block entry) and add it into the node box held in shared memory,
+//    cell after cell (the entries of one block go to distinct (a, node));
+//  * larger boxes: the warp's lanes take nodes of the box and sum over the
+//    candidate cells around each.
+constexpr int kLocWarps = 8;
+constexpr int kLocBox = 27;  // nodes of a box with at most 3 per axis
 
+// An element slot's header: its node box, local offsets and first pair.
+struct LocHead {
+    ElemBox b;
+    int64_t L0, L1, q0;
+};
+
+__device__ __forceinline__ LocHead loc_head(int64_t e, const ElemBox* __restrict__ boxes,
+                                            const int64_t* __restrict__ offsets, const int64_t* __restrict__ loc_off) {
+    LocHead h;
+    h.b = boxes[e];
+    h.L0 = loc_off[e];
+    h.L1 = loc_off[e + 1];
+    h.q0 = offsets[e];
+    return h;
+}
+
+// Persistent: warp w of the grid takes slots w, w + n_warps, ...; the next
+// slot's header is loaded while the current slot is summed.
 template <int D>
-__global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, const int64_t* __restrict__ offsets,
-                                  const int64_t* __restrict__ loc_off, int64_t loc_cap,
-                                  const double* __restrict__ blocks, const double* __restrict__ vols,
-                                  double* __restrict__ loc_val, uint8_t* __restrict__ loc_flag, int dual,
-                                  DevStatus* st) {
-    constexpr int NA = D + 1, NB = 1 << D;
-    const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kLocLanes;
-    const int lane = threadIdx.x % kLocLanes;
-    if (e >= m || (st->flags & kAbortFlags)) return;
-    const ElemBox b = boxes[e];
-    const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = D == 3 ? box_ext(b, 2) : 1;
-    const int64_t L0 = loc_off[e], L1 = loc_off[e + 1];
-    if (L1 == L0) return;
-    if (L1 > loc_cap) {
-        if (lane == 0) atomicOr(&st->flags, FLAG_CAPACITY);
-        return;
-    }
-    const int nbx = ex + 1, nby = ey + 1;
-    const int64_t nbox = L1 - L0;
-    const int64_t q0 = offsets[e];
-    for (int64_t jj = lane; jj < nbox; jj += kLocLanes) {
-        const int jx = (int)(jj % nbx);
-        const int64_t r = jj / nbx;
-        const int jy = (int)(r % nby), jz = (int)(r / nby);
-        double acc[NA];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) acc[a] = 0.0;
-        bool touched = false;
-        const int cz0 = D == 3 ? max(jz - 1, 0) : 0, cz1 = D == 3 ? min(jz, ez - 1) : 0;
-        for (int cz = cz0; cz <= cz1; ++cz)
-            for (int cy = max(jy - 1, 0); cy <= min(jy, ey - 1); ++cy)
-                for (int cx = max(jx - 1, 0); cx <= min(jx, ex - 1); ++cx) {
-                    const int64_t q = q0 + cx + (int64_t)ex * (cy + (int64_t)ey * cz);
-                    if (__double_as_longlong(vols[q]) > 0) {  // volume > 0
-                        touched = true;
-                        const int cb = (jx - cx) | ((jy - cy) << 1) | (D == 3 ? (jz - cz) << 2 : 0);
-                        const double* blk = blocks + q * (NA * NB) + cb;
-#pragma unroll
-                        for (int a = 0; a < NA; ++a) acc[a] += blk[a * NB];
-                    }
-                }
-        if (dual) {
-            // dual multiplier basis (d+2) lambda_a - 1: the lambda integrals sum
-            // to the integral of psi (partition of unity of the barycentrics)
-            double sum = 0.0;
-#pragma unroll
-            for (int a = 0; a < NA; ++a) sum += acc[a];
-#pragma unroll
-            for (int a = 0; a < NA; ++a) acc[a] = (double)(D + 2) * acc[a] - sum;
+__global__ void __launch_bounds__(kLocWarps * 32) elem_local_kernel(
+    int64_t m, const ElemBox* __restrict__ boxes, const int64_t* __restrict__ offsets,
+    const int64_t* __restrict__ loc_off, int64_t loc_cap, const double* __restrict__ blocks,
+    const double* __restrict__ vols, double* __restrict__ loc_val, uint8_t* __restrict__ loc_flag, int dual,
+    DevStatus* st) {
+    constexpr int NA = D + 1, NB = 1 << D, NS = NA * NB;
+    constexpr int kCells = 1 << D;  // cells of a usual box
+    __shared__ double s_acc[kLocWarps][NA][kLocBox];
+    __shared__ uint8_t s_hit[kLocWarps][kLocBox];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (st->flags & kAbortFlags) return;
+    const int64_t stride = (int64_t)gridDim.x * kLocWarps;
+    int64_t e = blockIdx.x * (int64_t)kLocWarps + w;
+    if (e >= m) return;
+    LocHead cur = loc_head(e, boxes, offsets, loc_off);
+    for (; e < m; e += stride) {
+        const LocHead nxt = e + stride < m ? loc_head(e + stride, boxes, offsets, loc_off) : cur;
+        const ElemBox b = cur.b;
+        const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = D == 3 ? box_ext(b, 2) : 1;
+        const int64_t L0 = cur.L0, L1 = cur.L1, q0 = cur.q0;
+        cur = nxt;
+        if (L1 == L0) continue;
+        if (L1 > loc_cap) {
+            if (lane == 0) atomicOr(&st->flags, FLAG_CAPACITY);
+            return;
         }
-        loc_flag[L0 + jj] = touched ? 1 : 0;
+        const int nbx = ex + 1, nby = ey + 1;
+        const int64_t nbox = L1 - L0;
+        if (ex <= 2 && ey <= 2 && ez <= 2) {
+            for (int j = lane; j < nbox; j += 32) {
 #pragma unroll
-        for (int a = 0; a < NA; ++a) loc_val[a * loc_cap + L0 + jj] = acc[a];  // one plane per vertex
+                for (int a = 0; a < NA; ++a) s_acc[w][a][j] = 0.0;
+                s_hit[w][j] = 0;
+            }
+            __syncwarp();
+            const int ncell = ex * ey * ez;
+            const bool act = lane < NS;
+            const int a = lane / NB, cb = lane % NB;  // this lane's block entry block[a][cb]
+            const int bx = cb & 1, by = (cb >> 1) & 1, bz = D == 3 ? cb >> 2 : 0;
+            // every pair's loads first (at most 2^d pairs), then the sums in cell order
+            double v[kCells];
+            bool live[kCells];
+#pragma unroll
+            for (int c = 0; c < kCells; ++c) {
+                v[c] = 0.0;
+                live[c] = false;
+                if (c < ncell) {
+                    const int64_t q = q0 + c;
+                    live[c] = __double_as_longlong(vols[q]) > 0;  // volume > 0
+                    if (act) v[c] = blocks[q * NS + lane];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kCells; ++c) {
+                if (c < ncell && live[c]) {
+                    // cell c = cx + ex (cy + ey cz) with ex, ey in {1, 2}
+                    const int cx = ex == 2 ? (c & 1) : 0, r = ex == 2 ? c >> 1 : c;
+                    const int cy = ey == 2 ? (r & 1) : 0, cz = ey == 2 ? r >> 1 : r;
+                    const int jj = (cx + bx) + nbx * ((cy + by) + nby * (cz + bz));
+                    if (act) s_acc[w][a][jj] += v[c];
+                    if (act && a == 0) s_hit[w][jj] = 1;
+                }
+                __syncwarp();
+            }
+            for (int j = lane; j < nbox; j += 32) {
+                double acc[NA];
+#pragma unroll
+                for (int a2 = 0; a2 < NA; ++a2) acc[a2] = s_acc[w][a2][j];
+                if (dual) {
+                    // dual multiplier basis (d+2) lambda_a - 1: the lambda integrals sum
+                    // to the integral of psi (partition of unity of the barycentrics)
+                    double sum = 0.0;
+#pragma unroll
+                    for (int a2 = 0; a2 < NA; ++a2) sum += acc[a2];
+#pragma unroll
+                    for (int a2 = 0; a2 < NA; ++a2) acc[a2] = (double)(D + 2) * acc[a2] - sum;
+                }
+                loc_flag[L0 + j] = s_hit[w][j];
+#pragma unroll
+                for (int a2 = 0; a2 < NA; ++a2) loc_val[a2 * loc_cap + L0 + j] = acc[a2];
+            }
+            __syncwarp();  // the box is read out before the next slot clears it
+            continue;
+        }
+        for (int64_t jj = lane; jj < nbox; jj += 32) {
+            const int jx = (int)(jj % nbx);
+            const int64_t r = jj / nbx;
+            const int jy = (int)(r % nby), jz = (int)(r / nby);
+            double acc[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) acc[a] = 0.0;
+            bool touched = false;
+            const int cz0 = D == 3 ? max(jz - 1, 0) : 0, cz1 = D == 3 ? min(jz, ez - 1) : 0;
+            for (int cz = cz0; cz <= cz1; ++cz)
+                for (int cy = max(jy - 1, 0); cy <= min(jy, ey - 1); ++cy)
+                    for (int cx = max(jx - 1, 0); cx <= min(jx, ex - 1); ++cx) {
+                        const int64_t q = q0 + cx + (int64_t)ex * (cy + (int64_t)ey * cz);
+                        if (__double_as_longlong(vols[q]) > 0) {  // volume > 0
+                            touched = true;
+                            const int cb = (jx - cx) | ((jy - cy) << 1) | (D == 3 ? (jz - cz) << 2 : 0);
+                            const double* blk = blocks + q * NS + cb;
+#pragma unroll
+                            for (int a = 0; a < NA; ++a) acc[a] += blk[a * NB];
+                        }
+                    }
+            if (dual) {
+                double sum = 0.0;
+#pragma unroll
+                for (int a = 0; a < NA; ++a) sum += acc[a];
+#pragma unroll
+                for (int a = 0; a < NA; ++a) acc[a] = (double)(D + 2) * acc[a] - sum;
+            }
+            loc_flag[L0 + jj] = touched ? 1 : 0;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) loc_val[a * loc_cap + L0 + jj] = acc[a];
+        }
     }
 }
 
@@ -129,9 +215,11 @@ __global__ void elem_local_kernel(int64_t m, const ElemBox* __restrict__ boxes, 
 //    kRowUnion nodes, element boxes of at most 3 nodes per axis): the warp walks
 //    the incident elements in adjacency order, its lanes covering the element's
 //    box nodes, and adds into the union box held in shared memory (distinct
-//    nodes within one element; __syncwarp between elements);
+//    nodes within one element; __syncwarp between elements).  The counting pass
+//    keeps the row (union box, touched mask, sums) in the cache, from which the
+//    emitting pass writes it;
 //  * other rows: every lane owns columns j of the union box and loops over the
-//    incident elements.
+//    incident elements, in both passes.
 // Touched columns are emitted in ascending order.
 // pass 0: row_count[i] = number of touched columns; pass 1: columns and values;
 // pass 2: columns only, values zeroed (the plain path adds them with atomics).
@@ -139,10 +227,10 @@ struct RowsSet {
     RowsGrid g[kMaxGrids];
 };
 
-constexpr int kRowGroup = 4;  // incident elements whose loads are issued together
+constexpr int kRowGroup = 8;  // incident elements whose loads are issued together
 
 template <int D>
-__global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
+__global__ void __launch_bounds__(kRowWarps * 32, 8) b_rows_kernel(
     int pass, int n_grids, RowsSet rs, int64_t n_nodes, const int64_t* __restrict__ adj_ptr,
     const int32_t* __restrict__ adj, const double* __restrict__ loc_val, int64_t loc_cap,
     const uint8_t* __restrict__ loc_flag, DevStatus* st) {
@@ -158,6 +246,30 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
     const int g = (int)(r_all / n_nodes);
     const int64_t i = r_all - g * n_nodes;
     const RowsGrid& rg = rs.g[g];
+    RowCache* __restrict__ rc = rg.cache + i;
+    int64_t cnt = 0;
+    const int64_t out0 = pass >= 1 ? rg.row_ptr[i] : 0;
+    if (pass >= 1) {
+        const int dims = rc->dims;
+        if (dims != 0) {  // kept by the counting pass
+            const int nx = dims & 255, ny = (dims >> 8) & 255, nz = dims >> 16;
+            const int total = nx * ny * nz;
+            const int lo0 = rc->lo[0], lo1 = rc->lo[1], lo2 = rc->lo[2];
+            for (int base = 0; base < total; base += 32) {
+                const unsigned bal = rc->hit[base >> 5];
+                if ((bal >> lane) & 1u) {
+                    const int idx = base + lane;
+                    const int jx = lo0 + idx % nx, r = idx / nx;
+                    const int jy = lo1 + r % ny, jz = lo2 + r / ny;
+                    const int pos = __popc(bal & ((1u << lane) - 1u));
+                    rg.cols[out0 + cnt + pos] = jx + rg.nnode0 * (jy + rg.nnode1 * jz);
+                    rg.vals[out0 + cnt + pos] = pass == 1 ? rc->val[idx] : 0.0;
+                }
+                cnt += __popc(bal);
+            }
+            return;
+        }
+    }
     const ElemBox* __restrict__ boxes = rg.boxes;
     const int64_t* __restrict__ loc_off = rg.loc_off;
     const int64_t a0 = adj_ptr[i], a1 = adj_ptr[i + 1];
@@ -193,12 +305,12 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
         lo[2] = 0;
         hi[2] = 0;
     }
-    int64_t cnt = 0;
-    const int64_t out0 = pass >= 1 ? rg.row_ptr[i] : 0;
+    bool kept = false;
     if (a0 < a1) {
         const int nx = hi[0] - lo[0] + 1, ny = hi[1] - lo[1] + 1, nz = hi[2] - lo[2] + 1;
         const int64_t total = (int64_t)nx * ny * nz;
         if (staged && !wide && total <= kRowUnion) {
+            kept = pass == 0;
             for (int u = lane; u < total; u += 32) {
                 s_acc[w][u] = 0.0;
                 s_hit[w][u] = 0;
@@ -226,22 +338,25 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
                     f[q] = loc_flag[L];
                     // the element-local matrices hold exact zeros at untouched nodes, so
                     // the value is read without waiting for the flag (same sums)
-                    if (pass == 1) v[q] = loc_val[(int64_t)(s_ea[w][t - a0] & 3) * loc_cap + L];
+                    if (pass != 2) v[q] = loc_val[(int64_t)(s_ea[w][t - a0] & 3) * loc_cap + L];
                 }
 #pragma unroll
                 for (int q = 0; q < kRowGroup; ++q) {
                     if (u[q] >= 0) {
-                        if (pass == 1) s_acc[w][u[q]] += v[q];
+                        if (pass != 2) s_acc[w][u[q]] += v[q];
                         if (f[q]) s_hit[w][u[q]] = 1;
                     }
                     __syncwarp();
                 }
             }
-            for (int64_t base = 0; base < total; base += 32) {
-                const int idx = (int)base + lane;
+            for (int base = 0; base < (int)total; base += 32) {
+                const int idx = base + lane;
                 const bool touched = idx < total && s_hit[w][idx] != 0;
                 const unsigned bal = __ballot_sync(0xffffffffu, touched);
-                if (pass >= 1 && touched) {
+                if (kept) {
+                    if (lane == 0) rc->hit[base >> 5] = bal;
+                    if (touched) rc->val[idx] = s_acc[w][idx];
+                } else if (pass >= 1 && touched) {
                     const int jx = lo[0] + idx % nx, r = idx / nx;
                     const int jy = lo[1] + r % ny, jz = lo[2] + r / ny;
                     const int pos = __popc(bal & ((1u << lane) - 1u));
@@ -249,6 +364,12 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
                     rg.vals[out0 + cnt + pos] = pass == 1 ? s_acc[w][idx] : 0.0;
                 }
                 cnt += __popc(bal);
+            }
+            if (kept && lane == 0) {
+                rc->lo[0] = lo[0];
+                rc->lo[1] = lo[1];
+                rc->lo[2] = lo[2];
+                rc->dims = nx | (ny << 8) | (nz << 16);
             }
         } else {
             for (int64_t base = 0; base < total; base += 32) {
@@ -284,7 +405,10 @@ __global__ void __launch_bounds__(kRowWarps * 32) b_rows_kernel(
             }
         }
     }
-    if (pass == 0 && lane == 0) rg.row_count[i] = cnt;
+    if (pass == 0 && lane == 0) {
+        if (!kept) rc->dims = 0;
+        rg.row_count[i] = cnt;
+    }
 }
 
 template <int D>
@@ -542,9 +666,19 @@ void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t
                        const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
                        double* loc_val, uint8_t* loc_flag, int dual, DevStatus* st, cudaStream_t s) {
     if (m <= 0) return;
-    const unsigned nb = nblk(m * kLocLanes, 256);
-    if (dim == 2) { elem_local_kernel<2><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
-    else { elem_local_kernel<3><<<nb, 256, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
+    // persistent grid: the blocks resident on the SMs at once (counted once per form)
+    static int resident[2] = {0, 0};
+    if (resident[dim == 3] == 0) {
+        int dev = 0, n_sm = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, elem_local_kernel<2>, kLocWarps * 32, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, elem_local_kernel<3>, kLocWarps * 32, 0);
+        resident[dim == 3] = std::max(1, n_sm) * std::max(1, per);
+    }
+    const unsigned nb = (unsigned)std::min<int64_t>(nblk(m, kLocWarps), resident[dim == 3]);
+    if (dim == 2) { elem_local_kernel<2><<<nb, kLocWarps * 32, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
+    else { elem_local_kernel<3><<<nb, kLocWarps * 32, 0, s>>>(m, boxes_g, offsets_g, loc_off_g, loc_cap, blocks, vols, loc_val, loc_flag, dual, st); count_launch(); }
 }
 
 void launch_b_rows(int pass, int dim, int n_grids, const RowsGrid* grids, int64_t n_nodes, const int64_t* adj_ptr,

@@ -155,9 +155,21 @@ void launch_node_adjacency(int dim, int64_t n_nodes, int64_t m, const int32_t* E
 void launch_elem_local(int dim, int64_t m, const ElemBox* boxes_g, const int64_t* offsets_g,
                        const int64_t* loc_off_g, int64_t loc_cap, const double* blocks, const double* vols,
                        double* loc_val, uint8_t* loc_flag, int dual, DevStatus* st, cudaStream_t s);
+// A row of B_g as the counting pass of launch_b_rows leaves it for the emitting
+// pass: the union box of the incident element boxes (lower corner, extents
+// nx | ny << 8 | nz << 16, 0 = not kept), its touched nodes as a bit mask and
+// the sums at the touched nodes (box order, x fastest).
+constexpr int kRowKeep = 64;  // union-box nodes of a kept row
+struct RowCache {
+    int32_t lo[3];
+    int32_t dims;
+    uint32_t hit[kRowKeep / 32];
+    double val[kRowKeep];
+};
 // One grid's matrix for launch_b_rows: its element boxes and local offsets (the
 // slots of grid g), its row counts (pass 0) or row pointers, columns and values
-// (passes 1, 2), and the node counts of its first two axes.
+// (passes 1, 2), its kept rows (n_nodes of them) and the node counts of its
+// first two axes.
 struct RowsGrid {
     const ElemBox* boxes = nullptr;
     const int64_t* loc_off = nullptr;
@@ -165,11 +177,15 @@ struct RowsGrid {
     const int64_t* row_ptr = nullptr;
     int32_t* cols = nullptr;
     double* vals = nullptr;
+    RowCache* cache = nullptr;
     int32_t nnode0 = 1, nnode1 = 1;
 };
 // Row-wise assembly of the n_grids matrices B_g from the element-local matrices,
-// in one launch.  pass 0: row_count[i] = nonzeros of row i; pass 1: cols + vals;
-// pass 2: cols only, vals zeroed (the plain path adds them with atomics).
+// in one launch.  pass 0: row_count[i] = nonzeros of row i (and the row kept in
+// the grid's cache when its union box has at most kRowKeep nodes); pass 1: cols
+// + vals; pass 2: cols only, vals zeroed (the plain path adds them with atomics).
+// Passes 1 and 2 emit kept rows from the cache, so they follow a pass 0 of the
+// same element-local matrices.
 void launch_b_rows(int pass, int dim, int n_grids, const RowsGrid* grids, int64_t n_nodes, const int64_t* adj_ptr,
                    const int32_t* adj, const double* loc_val, int64_t loc_cap, const uint8_t* loc_flag,
                    DevStatus* st, cudaStream_t s);
