@@ -747,53 +747,56 @@ def run_workload(args, name, rank, world, local, dev, torch, l2x, flush, steps, 
         res["pseudo_l2_dual"] = {"form": "fused, captured step graph, mixed precision, dual multiplier basis",
                                  "value": d_value, "unit": UNIT, "ms_per_step": d_ms, "steps": n_dual}
 
-        # end to end through the public API from pinned host buffers (the captured step):
-        # positions, velocities and forces in; solid velocities and fluid forces out
-        c, g = gr["c"], gr["g"]
+        # end to end through the public API with host buffers: the captured step of
+        # l2x_graph_create_host, whose replay copies the positions, u_f and f_s in from
+        # page-locked host arrays and u_s and f_f back (graph nodes, inside the timed
+        # region); a caller with a host-side fluid solver makes this call
+        c = gr["c"]
         src, uf, us, fs, ff = gr["buffers"]
-        Ph = [p.cpu().pin_memory() for p in wl["positions"]]
+        dt = uf[0].dtype
+        gr["g"] = None  # the new capture retires the device-array graph
+        Ph = [p.cpu() for p in wl["positions"]]
+        coords_h = torch.empty_like(Ph[0]).pin_memory()
         uh = [u.cpu().pin_memory() for u in uf]
         fh = [f.cpu().pin_memory() for f in fs]
-        us_h = [torch.empty(c.n_nodes, dtype=torch.float32).pin_memory() for _ in range(3)]
-        ff_h = [torch.empty(n, dtype=torch.float32).pin_memory() for n in c.fluid_sizes()]
+        us_h = [torch.empty(c.n_nodes, dtype=dt).pin_memory() for _ in range(3)]
+        ff_h = [torch.empty(n, dtype=dt).pin_memory() for n in c.fluid_sizes()]
+        coords_h.copy_(Ph[0])
+        gh = c.capture_step_host(coords_h, uh, us_h, fh, ff_h, margin=1.3)
         stream = torch.cuda.current_stream(dev)
 
         def e2e_step(i):
-            src.copy_(Ph[i % len(Ph)], non_blocking=True)
-            for a, b in zip(uf, uh):
-                a.copy_(b, non_blocking=True)
-            for a, b in zip(fs, fh):
-                a.copy_(b, non_blocking=True)
-            g.launch()
-            for a, b in zip(us_h, us):
-                a.copy_(b, non_blocking=True)
-            for a, b in zip(ff_h, ff):
-                a.copy_(b, non_blocking=True)
+            coords_h.copy_(Ph[i % len(Ph)])  # the caller's new positions (host memory, before the launch)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gh.launch()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1)
 
         for i in range(2):
             e2e_step(i)
-        torch.cuda.synchronize()
+        gh.status()
         barrier(world)
         e_ms = 0.0
         n_e2e = max(3, steps // 4)
         e2e_pairs = 0
         for i in range(n_e2e):
             flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            e2e_step(i)
-            e1.record(stream)
-            e1.synchronize()
-            e_ms += e0.elapsed_time(e1)
+            e_ms += e2e_step(i)
             e2e_pairs += gr["pairs_at"][i % len(gr["pairs_at"])]
-        g.status()
+        gh.status()
         e_ms = e_ms / n_e2e
         e_step_ms, e_total, e_value = aggregate(e_ms, e2e_pairs / n_e2e, world)
-        h2d = (wl["positions"][0].numel() * 8 + sum(t.numel() * 4 for t in uh) + sum(t.numel() * 4 for t in fh))
-        d2h = sum(t.numel() * 4 for t in us_h) + sum(t.numel() * 4 for t in ff_h)
+        h2d = (coords_h.numel() * 8 + sum(t.numel() * t.element_size() for t in uh)
+               + sum(t.numel() * t.element_size() for t in fh))
+        d2h = sum(t.numel() * t.element_size() for t in us_h) + sum(t.numel() * t.element_size() for t in ff_h)
         res["e2e"] = {"value": e_value, "unit": UNIT, "ms_per_step": e_step_ms,
-                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-        del Ph, uh, fh, us_h, ff_h
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "form": "l2x_graph_create_host: copies in and out are nodes of the step graph "
+                              "(u_f, f_s in beside the assembly; u_s out beside the force transfer; f_f out last)"}
+        del gh, Ph, uh, fh, us_h, ff_h, coords_h
     else:
         del pc
     del gr, arm, wl

@@ -123,6 +123,8 @@ def load_library(build_if_missing: bool = True):
         "l2x_set_clip_chunk": ([P, ctypes.c_int32], ctypes.c_int),
         "l2x_graph_create": ([P, P, PP, PP, PP, PP, ctypes.c_double, ctypes.c_int32, P,
                               ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "l2x_graph_create_host": ([P, P, PP, PP, PP, PP, ctypes.c_double, ctypes.c_int32, P,
+                                   ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "l2x_graph_launch": ([P, P], ctypes.c_int),
         "l2x_graph_sync_status": ([P, P], ctypes.c_int),
         "l2x_graph_destroy": ([P], ctypes.c_int),
@@ -476,6 +478,23 @@ class Coupling:
         ``coords_src`` and runs both transfers; see :class:`StepGraph`."""
         return StepGraph(self, coords_src, u_f, u_s, f_s, f_f, margin, zero_force, stream)
 
+    def capture_step_host(self, coords_h, u_f, u_s, f_s, f_f, margin: float = 1.5, zero_force: bool = True,
+                          stream=None):
+        """The captured step with page-locked CPU tensors as its inputs and outputs
+        (``coords_h`` float64 n_nodes x dim; u_f, f_f per grid over its fluid nodes;
+        u_s, f_s per grid over the solid nodes; fields in the coupling's dtype): every
+        launch copies them in and out as part of the graph."""
+        fl = self.fluid_sizes()
+        want = [(coords_h, torch.float64, self.n_nodes * self.dim, "coords_h")]
+        for g in range(self.n_grids):
+            want += [(u_f[g], self.dtype, fl[g], "u_f"), (f_f[g], self.dtype, fl[g], "f_f"),
+                     (u_s[g], self.dtype, self.n_nodes, "u_s"), (f_s[g], self.dtype, self.n_nodes, "f_s")]
+        for t, dt, numel, what in want:
+            if t.device.type != "cpu" or not t.is_pinned() or not t.is_contiguous() or t.dtype != dt \
+                    or t.numel() != numel:
+                raise ValueError(f"{what}: expected a contiguous page-locked CPU tensor of {numel} {dt}")
+        return StepGraph(self, coords_h, u_f, u_s, f_s, f_f, margin, zero_force, stream, host=True)
+
     # ------------------------------------------------------------------ exports (tests)
     def export_pairs(self, g: int):
         n = self.info()["n_pairs"][g]
@@ -534,7 +553,7 @@ class StepGraph:
     and raises :class:`L2XError` if the last replay overflowed the capacities
     (create a new graph with a larger margin) or CG did not converge."""
 
-    def __init__(self, c: Coupling, coords_src, u_f, u_s, f_s, f_f, margin, zero_force, stream):
+    def __init__(self, c: Coupling, coords_src, u_f, u_s, f_s, f_f, margin, zero_force, stream, host=False):
         lib = load_library()
         self.c = c
         self.stream = stream if stream is not None else torch.cuda.Stream(device=c.device)
@@ -542,10 +561,11 @@ class StepGraph:
         self.buffers = (coords_src, list(u_f), list(u_s), list(f_s), list(f_f))
         g = ctypes.c_void_p()
         torch.cuda.current_stream(c.device).synchronize()
+        create = lib.l2x_graph_create_host if host else lib.l2x_graph_create
         with torch.cuda.device(c.device):
-            _check(lib.l2x_graph_create(c._h, ctypes.c_void_p(coords_src.data_ptr()), _ptrs(u_f), _ptrs(u_s),
-                                        _ptrs(f_s), _ptrs(f_f), float(margin), int(bool(zero_force)),
-                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(g)))
+            _check(create(c._h, ctypes.c_void_p(coords_src.data_ptr()), _ptrs(u_f), _ptrs(u_s),
+                          _ptrs(f_s), _ptrs(f_f), float(margin), int(bool(zero_force)),
+                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(g)))
         self._g = g
 
     def launch(self):

@@ -98,6 +98,10 @@ struct l2x_coupling {
     void* t_scan[kMaxGrids]{};
     int64_t t_rows_cap[kMaxGrids]{};
     void* vec_mask = nullptr;        // n_grids * n_nodes doubles: the masked force input
+    // captured steps with host buffers: the branch that copies the transfer inputs
+    // in beside the assembly and the solid velocities out beside the force transfer
+    cudaStream_t io_stream = nullptr;
+    cudaEvent_t ev_io_fork = nullptr, ev_io_in = nullptr, ev_io_us = nullptr, ev_io_out = nullptr;
     uint8_t* fmask = nullptr;        // interface mask of the force input (n_nodes), when has_fmask
     bool has_fmask = false;
     DevStatus* st = nullptr;
@@ -673,11 +677,40 @@ void enqueue_force(l2x_coupling* h, const void* const* f_s_in, void* const* f_f,
 // node positions, re-assembly with the capacities of the handle (overflow sets
 // FLAG_CAPACITY and later kernels skip their work), velocity transfer and dual
 // or nodal force transfer.  Used under stream capture by l2x_graph_create.
+// Host ends of a captured step with host buffers (page-locked): positions in,
+// u_f and f_s in, u_s and f_f out, per grid.
+struct HostIO {
+    const void* u_f[kMaxGrids];
+    void* u_s[kMaxGrids];
+    const void* f_s[kMaxGrids];
+    void* f_f[kMaxGrids];
+};
+
+// With `io`, coords_src is a host array and u_f .. f_f are the graph's device
+// copies: the step copies the positions in first, u_f and f_s in on a branch
+// beside the assembly (joined before the transfers), u_s out on that branch
+// beside the force transfer, and f_f out at the end, one grid per stream.
 l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* const* u_f, void* const* u_s,
-                       const void* const* f_s, void* const* f_f, bool zero_force, cudaStream_t s) {
+                       const void* const* f_s, void* const* f_f, bool zero_force, cudaStream_t s,
+                       const HostIO* io = nullptr) {
     const int64_t n = h->n_nodes, m = h->n_elems;
     const int G = h->n_grids, d = h->dim;
-    L2X_CUDA(cudaMemcpyAsync(h->X, coords_src, sizeof(double) * n * d, cudaMemcpyDeviceToDevice, s));
+    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+    L2X_CUDA(cudaMemcpyAsync(h->X, coords_src, sizeof(double) * n * d,
+                             io ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (io) {
+        // forked after the positions are in: copies in one direction share a copy
+        // engine, and the assembly waits for the positions only
+        L2X_CUDA(cudaEventRecord(h->ev_io_fork, s));
+        L2X_CUDA(cudaStreamWaitEvent(h->io_stream, h->ev_io_fork, 0));
+        for (int g = 0; g < G; ++g)
+            L2X_CUDA(cudaMemcpyAsync(const_cast<void*>(u_f[g]), io->u_f[g], es * fluid_nodes(h->sg[g]),
+                                     cudaMemcpyHostToDevice, h->io_stream));
+        for (int g = 0; g < G; ++g)
+            L2X_CUDA(cudaMemcpyAsync(const_cast<void*>(f_s[g]), io->f_s[g], es * n, cudaMemcpyHostToDevice,
+                                     h->io_stream));
+        L2X_CUDA(cudaEventRecord(h->ev_io_in, h->io_stream));
+    }
     launch_reset_status(h->st, s);
     launch_node_box_reset(h->node_box, G, s);
     launch_elem_boxes(d, G, h->sg, m, h->X, h->E, h->boxes, h->counts, h->nbox, h->node_box, h->elem_vol,
@@ -752,8 +785,34 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
     }
     for (int g = 1; g < G; ++g) L2X_CUDA(cudaStreamWaitEvent(s, h->ev_tjoin[g], 0));
     L2X_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));  // S is formed
+    if (io) L2X_CUDA(cudaStreamWaitEvent(s, h->ev_io_in, 0));  // u_f and f_s are in
+    // u_s out on the copy branch once the velocity transfer is done
+    auto copy_us_out = [&]() -> l2x_status {
+        if (!io) return L2X_OK;
+        L2X_CUDA(cudaEventRecord(h->ev_io_us, s));
+        L2X_CUDA(cudaStreamWaitEvent(h->io_stream, h->ev_io_us, 0));
+        for (int g = 0; g < G; ++g)
+            L2X_CUDA(cudaMemcpyAsync(io->u_s[g], u_s[g], es * n, cudaMemcpyDeviceToHost, h->io_stream));
+        L2X_CUDA(cudaEventRecord(h->ev_io_out, h->io_stream));
+        return L2X_OK;
+    };
+    // f_f out, grid g >= 1 on the stream of its transpose branch, then every
+    // branch joins the main stream
+    auto copy_ff_out = [&]() -> l2x_status {
+        if (!io) return L2X_OK;
+        L2X_CUDA(cudaEventRecord(h->ev_tfork, s));
+        for (int g = 1; g < G; ++g) {
+            L2X_CUDA(cudaStreamWaitEvent(h->t_stream[g], h->ev_tfork, 0));
+            L2X_CUDA(cudaMemcpyAsync(io->f_f[g], f_f[g], es * fluid_nodes(h->sg[g]), cudaMemcpyDeviceToHost,
+                                     h->t_stream[g]));
+            L2X_CUDA(cudaEventRecord(h->ev_tjoin[g], h->t_stream[g]));
+        }
+        L2X_CUDA(cudaMemcpyAsync(io->f_f[0], f_f[0], es * fluid_nodes(h->sg[0]), cudaMemcpyDeviceToHost, s));
+        for (int g = 1; g < G; ++g) L2X_CUDA(cudaStreamWaitEvent(s, h->ev_tjoin[g], 0));
+        L2X_CUDA(cudaStreamWaitEvent(s, h->ev_io_out, 0));
+        return L2X_OK;
+    };
     // transfers
-    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
     if (h->opts.multiplier == L2X_MULT_STANDARD && h->opts.force_mode == L2X_FORCE_DUAL) {
         // the two solves with M_s are independent: one PCG on the 2G right-hand
         // sides [B u_f ; f_s] (its iterations are latency-bound, so this costs
@@ -777,17 +836,19 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         }
         solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, 2 * G, ys, ws, h->opts.cg_rtol,
                              h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb_step, 0);
+        L2X_TRY(copy_us_out());
         if (zero_force)
             for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * fluid_nodes(h->sg[g]), s));
         launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)zf, f_f,
                        h->opts.force_scale, h->st, s);
-        return L2X_OK;
+        return copy_ff_out();
     }
     enqueue_velocity(h, u_f, u_s, s);
+    L2X_TRY(copy_us_out());
     if (zero_force)
         for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * fluid_nodes(h->sg[g]), s));
     enqueue_force(h, f_s, f_f, s);
-    return L2X_OK;
+    return copy_ff_out();
 }
 
 }  // namespace
@@ -797,6 +858,10 @@ struct l2x_step_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t gen = 0;  // the handle's graph_gen at creation
+    std::vector<void*> owned;  // device copies of the host-buffer form's arrays
+    ~l2x_step_graph() {
+        for (void* p : owned) cudaFree(p);
+    }
 };
 
 extern "C" {
@@ -873,6 +938,9 @@ l2x_status l2x_destroy(l2x_handle h) {
     }
     if (h->vec_mask) cudaFree(h->vec_mask);
     dfree(h->fmask);
+    if (h->io_stream) cudaStreamDestroy(h->io_stream);
+    for (cudaEvent_t e : {h->ev_io_fork, h->ev_io_in, h->ev_io_us, h->ev_io_out})
+        if (e) cudaEventDestroy(e);
     dfree(h->st);
     if (h->st_host) cudaFreeHost(h->st_host);
     delete h;
@@ -1142,18 +1210,16 @@ l2x_status l2x_picard_converged(const double* norms, double eps_abs, double eps_
     return L2X_OK;
 }
 
-l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* const* u_f, void* const* u_s,
-                            const void* const* f_s, void* const* f_f, double capacity_margin, int32_t zero_force,
-                            void* stream, l2x_graph* out) {
-    g_last_error.clear();
-    if (!h || !out || !coords_src) return fail(L2X_EINVAL, "NULL argument");
-    *out = nullptr;
-    if (h->opts.path != L2X_PATH_FUSED) return fail(L2X_EINVAL, "step graphs need the fused path");
-    if (!(capacity_margin >= 1.0)) return fail(L2X_EINVAL, "capacity_margin must be >= 1");
-    L2X_TRY(check_ptrs(u_f, h->n_grids, "u_f"));
-    L2X_TRY(check_ptrs((const void* const*)u_s, h->n_grids, "u_s"));
-    L2X_TRY(check_ptrs(f_s, h->n_grids, "f_s"));
-    L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
+}  // extern "C"
+
+namespace {
+
+// l2x_graph_create and l2x_graph_create_host: capacities, scratch, capture.  With
+// `io`, u_f .. f_f are the graph's own device arrays (`owned`, freed with it).
+l2x_status graph_create_common(l2x_handle h, const double* coords_src, const void* const* u_f, void* const* u_s,
+                               const void* const* f_s, void* const* f_f, double capacity_margin,
+                               int32_t zero_force, void* stream, l2x_graph* out, const HostIO* io,
+                               std::vector<void*>& owned) {
     cudaStream_t s = (cudaStream_t)stream;
     h->stream = s;
     ++h->graph_gen;  // the capacities below may reallocate what earlier graphs use
@@ -1267,15 +1333,21 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
             L2X_CUDA(cudaEventCreateWithFlags(&h->ev_tjoin[g], cudaEventDisableTiming));
         }
     }
+    if (io && !h->io_stream) {
+        L2X_CUDA(cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&h->ev_io_fork, &h->ev_io_in, &h->ev_io_us, &h->ev_io_out})
+            L2X_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
     // capture one step
     l2x_step_graph* gr = new l2x_step_graph();
     gr->h = h;
+    gr->owned.swap(owned);
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
         delete gr;
         return cuda_fail(e, "cudaStreamBeginCapture (use a non-default stream)");
     }
-    l2x_status st = record_step(h, coords_src, u_f, u_s, f_s, f_f, zero_force != 0, s);
+    l2x_status st = record_step(h, coords_src, u_f, u_s, f_s, f_f, zero_force != 0, s, io);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(s, &graph);
     if (st != L2X_OK || e != cudaSuccess) {
@@ -1294,6 +1366,91 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
     }
     *out = gr;
     return L2X_OK;
+}
+
+// true if p is page-locked host memory (cudaHostAlloc or cudaHostRegister)
+bool page_locked(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+}  // namespace
+
+extern "C" {
+
+l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* const* u_f, void* const* u_s,
+                            const void* const* f_s, void* const* f_f, double capacity_margin, int32_t zero_force,
+                            void* stream, l2x_graph* out) {
+    g_last_error.clear();
+    if (!h || !out || !coords_src) return fail(L2X_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (h->opts.path != L2X_PATH_FUSED) return fail(L2X_EINVAL, "step graphs need the fused path");
+    if (!(capacity_margin >= 1.0)) return fail(L2X_EINVAL, "capacity_margin must be >= 1");
+    L2X_TRY(check_ptrs(u_f, h->n_grids, "u_f"));
+    L2X_TRY(check_ptrs((const void* const*)u_s, h->n_grids, "u_s"));
+    L2X_TRY(check_ptrs(f_s, h->n_grids, "f_s"));
+    L2X_TRY(check_ptrs((const void* const*)f_f, h->n_grids, "f_f"));
+    std::vector<void*> none;
+    return graph_create_common(h, coords_src, u_f, u_s, f_s, f_f, capacity_margin, zero_force, stream, out, nullptr,
+                               none);
+}
+
+l2x_status l2x_graph_create_host(l2x_handle h, const double* coords_host, const void* const* u_f_host,
+                                 void* const* u_s_host, const void* const* f_s_host, void* const* f_f_host,
+                                 double capacity_margin, int32_t zero_force, void* stream, l2x_graph* out) {
+    g_last_error.clear();
+    if (!h || !out || !coords_host) return fail(L2X_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (h->opts.path != L2X_PATH_FUSED) return fail(L2X_EINVAL, "step graphs need the fused path");
+    if (!(capacity_margin >= 1.0)) return fail(L2X_EINVAL, "capacity_margin must be >= 1");
+    const int G = h->n_grids;
+    L2X_TRY(check_ptrs(u_f_host, G, "u_f_host"));
+    L2X_TRY(check_ptrs((const void* const*)u_s_host, G, "u_s_host"));
+    L2X_TRY(check_ptrs(f_s_host, G, "f_s_host"));
+    L2X_TRY(check_ptrs((const void* const*)f_f_host, G, "f_f_host"));
+    if (!page_locked(coords_host)) return fail(L2X_EINVAL, "coords_host is not page-locked host memory");
+    for (int g = 0; g < G; ++g)
+        if (!page_locked(u_f_host[g]) || !page_locked(u_s_host[g]) || !page_locked(f_s_host[g]) ||
+            !page_locked(f_f_host[g]))
+            return fail(L2X_EINVAL, "a host array is not page-locked host memory (cudaHostAlloc / cudaHostRegister)");
+    const size_t es = h->opts.precision == L2X_MIXED ? sizeof(float) : sizeof(double);
+    const int64_t n = h->n_nodes;
+    HostIO io{};
+    std::vector<void*> owned;
+    void* uf[kMaxGrids];
+    void* us[kMaxGrids];
+    void* fs[kMaxGrids];
+    void* ff[kMaxGrids];
+    auto take = [&](void** p, size_t bytes) -> l2x_status {
+        *p = nullptr;
+        if (cudaMalloc(p, bytes ? bytes : 1) != cudaSuccess) {
+            cudaGetLastError();
+            for (void* q : owned) cudaFree(q);
+            owned.clear();
+            return fail(L2X_ENOMEM, "device copies of the host arrays");
+        }
+        owned.push_back(*p);
+        return L2X_OK;
+    };
+    for (int g = 0; g < G; ++g) {
+        const size_t nf = es * (size_t)fluid_nodes(h->sg[g]);
+        L2X_TRY(take(&uf[g], nf));
+        L2X_TRY(take(&ff[g], nf));
+        L2X_TRY(take(&us[g], es * (size_t)n));
+        L2X_TRY(take(&fs[g], es * (size_t)n));
+        io.u_f[g] = u_f_host[g];
+        io.u_s[g] = u_s_host[g];
+        io.f_s[g] = f_s_host[g];
+        io.f_f[g] = f_f_host[g];
+    }
+    const l2x_status st = graph_create_common(h, coords_host, (const void* const*)uf, us, (const void* const*)fs, ff,
+                                              capacity_margin, zero_force, stream, out, &io, owned);
+    for (void* q : owned) cudaFree(q);  // left here only when the graph was not made
+    return st;
 }
 
 l2x_status l2x_graph_launch(l2x_graph g, void* stream) {

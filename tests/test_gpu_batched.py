@@ -195,3 +195,72 @@ def test_step_graph_in_2d_matches_fresh_assembly(precision):
     tol = 1e-6 if mixed else 1e-12
     assert rel_l2(u_s[0].cpu().numpy(), ur[0].cpu().numpy()) <= tol
     assert rel_l2(f_f[0].cpu().numpy(), fr[0].cpu().numpy()) <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_buffer_graph_matches_the_device_buffer_graph(precision):
+    """l2x_graph_create_host: the same step with page-locked host arrays in and
+    out (the copies are graph nodes) gives the results of the device-array graph
+    on the same positions, step after step."""
+    grid, bodies, E, nr, er, fields, n_steps = _setup(n_bodies=4, seed=8)
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    X0 = synth.batch_coords(bodies, 0, n_steps)
+    cd = _coupling(grid, X0, E, precision)
+    ch = _coupling(grid, X0, E, precision)
+    n = X0.shape[0]
+    rng = np.random.default_rng(9)
+    F = rng.standard_normal((n, 3))
+    u_f = [torch.from_numpy(f).to(dt) for f in fields]
+    f_s = [torch.from_numpy(np.ascontiguousarray(F[:, g])).to(dt) for g in range(3)]
+    # device-array graph
+    src = torch.from_numpy(X0).cuda()
+    du_f = [u.cuda() for u in u_f]
+    df_s = [f.cuda() for f in f_s]
+    du_s = [torch.zeros(n, dtype=dt, device="cuda") for _ in range(3)]
+    df_f = [torch.zeros(m, dtype=dt, device="cuda") for m in cd.fluid_sizes()]
+    gd = cd.capture_step(src, du_f, du_s, df_s, df_f, margin=1.5)
+    # host-array graph
+    hsrc = torch.from_numpy(X0.copy()).pin_memory()
+    hu_f = [u.pin_memory() for u in u_f]
+    hf_s = [f.pin_memory() for f in f_s]
+    hu_s = [torch.full((n,), float("nan"), dtype=dt).pin_memory() for _ in range(3)]
+    hf_f = [torch.full((m,), float("nan"), dtype=dt).pin_memory() for m in ch.fluid_sizes()]
+    gh = ch.capture_step_host(hsrc, hu_f, hu_s, hf_s, hf_f, margin=1.5)
+    tol = 1e-6 if precision == "mixed" else 1e-12
+    for step in (1, 2, 3):
+        Xt = synth.batch_coords(bodies, step, n_steps)
+        src.copy_(torch.from_numpy(Xt).cuda())
+        hsrc.copy_(torch.from_numpy(Xt))
+        gd.launch()
+        gd.status()
+        gh.launch()
+        gh.status()
+        # norm-wise (u_s of the third grid is zero: the flow has no z-component);
+        # every value was copied back (the host arrays started as NaN)
+        for a, b in list(zip(hu_s, du_s)) + list(zip(hf_f, df_f)):
+            a, b = a.numpy(), b.cpu().numpy()
+            assert np.all(np.isfinite(a)), step
+            assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b), step
+
+
+def test_host_buffer_graph_refuses_pageable_memory():
+    import ctypes
+
+    import paper_1810_13046_gb300 as l2x
+    grid, bodies, E, nr, er, fields, n_steps = _setup(n_bodies=2, seed=4)
+    X0 = synth.batch_coords(bodies, 0, n_steps)
+    c = _coupling(grid, X0, E, "fp64")
+    n = X0.shape[0]
+    pageable = torch.from_numpy(X0.copy())  # not page-locked
+    pin_n = [torch.zeros(n, dtype=torch.float64).pin_memory() for _ in range(3)]
+    pin_f = [torch.zeros(m, dtype=torch.float64).pin_memory() for m in c.fluid_sizes()]
+    lib = l2x.load_library()
+    g = ctypes.c_void_p()
+    stream = torch.cuda.Stream()
+    st = lib.l2x_graph_create_host(c._h, ctypes.c_void_p(pageable.data_ptr()), l2x._ptrs(pin_f), l2x._ptrs(pin_n),
+                                   l2x._ptrs(pin_n), l2x._ptrs(pin_f), 1.5, 1, ctypes.c_void_p(stream.cuda_stream),
+                                   ctypes.byref(g))
+    assert st == 1 and not g.value  # L2X_EINVAL
+    assert b"page-locked" in lib.l2x_last_error()
+    with pytest.raises(ValueError):
+        c.capture_step_host(pageable, pin_f, pin_n, pin_n, pin_f)
