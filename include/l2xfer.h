@@ -380,7 +380,9 @@ l2x_status l2x_fma_probe(int32_t precision, int32_t n_blocks, int32_t iters, voi
  * integer instructions (round half away from zero, below 2^-126 to zero); 3:
  * CUDA's __double2float_rn; 4: the low float of the kernel's double-float split
  * (a - float(a)); 5: the kernel's float -> double conversion of
- * __double2float_rn(a).  b is read by ops 0 and 1 only.  Errors: EINVAL, ECUDA. */
+ * __double2float_rn(a); 6: the mixed precision form's quotient (an FP32
+ * quotient and one FP64 correction: within about 2^-45 relative).  b is read by
+ * ops 0, 1 and 6 only.  Errors: EINVAL, ECUDA. */
 l2x_status l2x_fp_selftest(int32_t op, int64_t n, const double* a, const double* b, double* out, void* stream);
 
 /* Test hook of the library's single-pass prefix sum (no counterpart in the

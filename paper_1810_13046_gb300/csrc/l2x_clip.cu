@@ -33,9 +33,40 @@ __device__ __forceinline__ void cell_frame(const SubGrid& sg, int dim, int32_t c
 }
 
 // Element vertices of pair p in cell-local coordinates; w receives the cell widths.
+// Uniform grid whose spacing is a power of two on every used axis (h = 2^-e).
+template <int D>
+__device__ __forceinline__ bool pow2_grid(const SubGrid& sg) {
+    return !sg.ax[0] && sg.pow2[0] && sg.pow2[1] && (D == 2 || sg.pow2[2]);
+}
+
 template <int D>
 __device__ __forceinline__ void pair_vertices(const SubGrid& sg, const double* __restrict__ X, const int32_t* __restrict__ E,
                                               int32_t e, int32_t cell, double (&T)[D + 1][D], double* w) {
+    if (pow2_grid<D>(sg)) {
+        // the cell corner origin + i h and the scaling by 1/h = 2^e on the exponent
+        // field: both products are exact, so the values are those of the general
+        // branch, with integer instructions in place of FP64 ones
+        int c = cell, ci[3];
+        ci[0] = c % sg.ncell[0];
+        c /= sg.ncell[0];
+        ci[1] = c % sg.ncell[1];
+        ci[2] = D == 3 ? c / sg.ncell[1] : 0;
+        double clo[3];
+        int es[3];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            es[k] = ilogb_int(sg.inv_h[k]);
+            clo[k] = __dadd_rn(sg.origin[k], ldexp_normal_int(i2d_int(ci[k]), -es[k]));
+            w[k] = sg.h[k];
+        }
+#pragma unroll
+        for (int a = 0; a <= D; ++a) {
+            const int32_t v = __ldg(E + (int64_t)e * (D + 1) + a);
+#pragma unroll
+            for (int k = 0; k < D; ++k) T[a][k] = ldexp_normal_int(__ldg(X + (int64_t)v * D + k) - clo[k], es[k]);
+        }
+        return;
+    }
     double clo[3], iw[3];
     cell_frame(sg, D, cell, clo, w, iw);
 #pragma unroll
@@ -200,7 +231,14 @@ __device__ __forceinline__ void clip_pair(int64_t i, int G, const SubGridSet& sg
         for (int a = 0; a < NA; ++a)
 #pragma unroll
             for (int k = 0; k < D; ++k) gr[a][k] = __ldg(elem_grad + ((int64_t)e * NA + a) * D + k);
-        const double scale = frame_scale<D>(sg, w, gr);
+        double scale;
+        if (pow2_grid<D>(sg)) {  // the cell volume 2^-(e0 + e1 + e2), exactly
+            int es = ilogb_int(sg.inv_h[0]) + ilogb_int(sg.inv_h[1]);
+            if (D == 3) es += ilogb_int(sg.inv_h[2]);
+            scale = ldexp_normal_int(1.0, -es);
+        } else {
+            scale = frame_scale<D>(sg, w, gr);
+        }
         pair_integrals<D, R>(T, gr, flag == 1, scale, blk, &vol, poly);
     }
     vols[p] = vol;

@@ -115,7 +115,7 @@ __device__ __forceinline__ double clamp01(double t) { return fmin(fmax(t, 0.0), 
 // v[k] <= c (upper = true).  Inside tests are integer comparisons of order keys;
 // crossing points are snapped onto the plane.  `same` is set when every vertex
 // is inside: then `out` is left untouched and the polygon is `in` as it was.
-template <int D>
+template <int D, bool kFastDiv>
 __device__ __forceinline__ int clip_axis(const double (*in)[D], int n, double (*out)[D], int k, double c,
                                          bool upper, bool& same) {
     const long long kc = order_key(c);
@@ -148,7 +148,7 @@ __device__ __forceinline__ int clip_axis(const double (*in)[D], int n, double (*
         const int i = r == 0 ? e0 : e1;
         const double* p = in[i];
         const double* q = in[i + 1 == n ? 0 : i + 1];
-        t[r] = div_nr(p[k] - c, p[k] - q[k]);
+        t[r] = kFastDiv ? div_fast(p[k] - c, p[k] - q[k]) : div_nr(p[k] - c, p[k] - q[k]);
     }
     if (repaired) {
         t[0] = clamp01(t[0]);
@@ -179,7 +179,7 @@ __device__ __forceinline__ int clip_axis(const double (*in)[D], int n, double (*
 }
 
 // Against the half-space g.v + c0 >= 0 (`same` as for clip_axis).
-template <int D>
+template <int D, bool kFastDiv>
 __device__ __forceinline__ int clip_plane(const double (*in)[D], int n, double (*out)[D], const double* g,
                                           double c0, bool& same) {
     double sv[kMaxPoly];
@@ -209,7 +209,7 @@ __device__ __forceinline__ int clip_plane(const double (*in)[D], int n, double (
     for (int r = 0; r < 2; ++r) {
         const int i = r == 0 ? e0 : e1;
         const int i1 = i + 1 == n ? 0 : i + 1;
-        t[r] = div_nr(sv[i], sv[i] - sv[i1]);
+        t[r] = kFastDiv ? div_fast(sv[i], sv[i] - sv[i1]) : div_nr(sv[i], sv[i] - sv[i1]);
     }
     if (repaired) {
         t[0] = clamp01(t[0]);
@@ -570,6 +570,9 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
     constexpr int NA = D + 1;
     using L = MomentLayout<D>;
     constexpr long long K1 = 0x3ff0000000000000LL;  // order key of 1.0 (key of +0.0 is 0)
+    // the mixed precision form takes the crossing parameters to about 2^-45
+    // (div_fast), the FP64 form to two ulps (div_nr)
+    constexpr bool kFast = sizeof(R) == 4;
     long long kmin[D], kmax[D];
     int lower_mask, upper_mask, inside_mask;
     if (!classify_pair<D>(T, kmin, kmax, lower_mask, upper_mask, inside_mask)) {  // no overlap of positive measure
@@ -655,8 +658,8 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             bool same;
-            if ((lower_mask >> k) & 1) { n = clip_axis<D>(cur, n, nxt, k, 0.0, false, same); if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; } }
-            if ((upper_mask >> k) & 1) { n = clip_axis<D>(cur, n, nxt, k, 1.0, true, same); if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; } }
+            if ((lower_mask >> k) & 1) { n = clip_axis<D, kFast>(cur, n, nxt, k, 0.0, false, same); if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; } }
+            if ((upper_mask >> k) & 1) { n = clip_axis<D, kFast>(cur, n, nxt, k, 1.0, true, same); if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; } }
         }
         if (n >= 3) {
             double P0[D];
@@ -726,7 +729,7 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
 #pragma unroll 1
                 for (int jp = 0; jp < n_planes; ++jp) {
                     bool same;
-                    n = clip_axis<D>(cur, n, nxt, plane_k[jp], plane_c[jp], plane_up[jp] != 0, same);
+                    n = clip_axis<D, kFast>(cur, n, nxt, plane_k[jp], plane_c[jp], plane_up[jp] != 0, same);
                     if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; }
                 }
             } else {
@@ -749,7 +752,7 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
 #pragma unroll
                 for (int a = 0; a < NA; ++a) {
                     bool same;
-                    n = clip_plane<D>(cur, n, nxt, g[a], cA[a], same);
+                    n = clip_plane<D, kFast>(cur, n, nxt, g[a], cA[a], same);
                     if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; }
                 }
             }

@@ -78,6 +78,37 @@ __device__ __forceinline__ double div_nr(double a, double b) {
     return a * r;
 }
 
+// a / b to about 2^-45 relative with two FP64 instructions, for the crossing
+// parameters of the mixed precision form: the FP32 quotient t0 = a r0 (r0 the
+// FP32 reciprocal of b) and one correction t0 + (a - t0 b) r0, the residual of
+// t0 times the approximate reciprocal (the Newton step for the quotient, as in
+// the division of Markstein 1990 cited above).  The step squares the relative
+// error of t0 (a few 2^-24) times that of r0.  |b| > 0; operands far from 1 in
+// magnitude take the hardware division.
+__device__ __forceinline__ double div_fast(double a, double b) {
+    const int eb = (__double2hiint(b) >> 20) & 0x7ff;
+    if (eb < 1023 - 120 || eb > 1023 + 120) return a / b;
+    const float rf = __frcp_rn(d2f_int(b));
+    const double r0 = f2d_int(rf);
+    const double t0 = f2d_int(__fmul_rn(d2f_int(a), rf));
+    return fma(fma(-t0, b, a), r0, t0);
+}
+
+// x * 2^e for x = 0 or x * 2^e and x both normal: one integer add on the
+// exponent field of the high word (zero stays zero)
+__device__ __forceinline__ double ldexp_normal_int(double x, int e) {
+    const int hi = __double2hiint(x);
+    return __hiloint2double(hi + ((hi & 0x7ff00000) ? (e << 20) : 0), __double2loint(x));
+}
+
+// non-negative int -> double, exact, by integer instructions
+__device__ __forceinline__ double i2d_int(int v) {
+    if (v <= 0) return 0.0;
+    const int e = 31 - __clz(v);
+    const unsigned long long m = ((unsigned long long)(unsigned int)v << (52 - e)) & 0x000fffffffffffffull;
+    return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | m));
+}
+
 
 // Double-float value (hi + lo) and its sum with a second one (Knuth's two-sum,
 // renormalised); single-precision instructions only.

@@ -46,6 +46,7 @@ __global__ void fp_selftest_kernel(int32_t op, int64_t n, const double* __restri
         case 3: r = (double)__double2float_rn(x); break;
         case 4: r = (double)l2x::d2f_lo_int(x); break;
         case 5: r = l2x::f2d_int(__double2float_rn(x)); break;
+        case 6: r = l2x::div_fast(x, y); break;
         default: break;
     }
     out[i] = r;
@@ -55,7 +56,7 @@ __global__ void fp_selftest_kernel(int32_t op, int64_t n, const double* __restri
 
 extern "C" l2x_status l2x_fp_selftest(int32_t op, int64_t n, const double* a, const double* b, double* out,
                                       void* stream) {
-    if (op < 0 || op > 5 || n < 0 || !a || !b || !out) return L2X_EINVAL;
+    if (op < 0 || op > 6 || n < 0 || !a || !b || !out) return L2X_EINVAL;
     if (n == 0) return L2X_OK;
     fp_selftest_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(op, n, a, b, out);
     l2x::count_launch();

@@ -59,6 +59,30 @@ def test_quotient_matches_division():
     assert np.all(np.abs(q[64:128] - 1.0) <= 2 * np.spacing(1.0))
 
 
+def test_fast_quotient_of_the_mixed_form():
+    """The mixed precision form's crossing parameter: an FP32 quotient and one
+    FP64 correction, within 2^-44 of the correctly rounded a / b on operands with
+    a / b in [-1, 1] (both crossing formulas), exact for a = 0, to 2^-44 of 1 for a = b; the
+    hardware division outside the refined range."""
+    l2x = _l2x()
+    rng = np.random.default_rng(13)
+    n = 1 << 20
+    b = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-30, 30, n)
+    t = rng.uniform(-1.0, 1.0, n)
+    t[:64] = 0.0
+    t[64:128] = 1.0
+    a = t * b
+    b[-64:] = 10.0 ** rng.uniform(40, 60, 64)
+    a[-64:] = b[-64:] * rng.random(64)
+    A, Bt = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    q = l2x.fp_selftest(6, A, Bt).cpu().numpy()
+    ref = l2x.fp_selftest(1, A, Bt).cpu().numpy()
+    rel = np.abs(q - ref) / np.maximum(np.abs(ref), 1e-300)
+    assert np.all(rel[128:-64] <= 2.0 ** -44), float(rel[128:-64].max())
+    assert np.array_equal(q[:64], ref[:64]) and np.array_equal(q[-64:], ref[-64:])
+    assert np.all(np.abs(q[64:128] - 1.0) <= 2.0 ** -44)
+
+
 def test_double_to_float_conversion():
     """Integer-instruction conversion: equal to __double2float_rn away from ties;
     on an exact tie it rounds away from zero; below 2^-126 it gives zero."""
