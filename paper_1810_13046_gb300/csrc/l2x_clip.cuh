@@ -552,16 +552,17 @@ __device__ __forceinline__ int pair_class(const double (&T)[D + 1][D]) {
     return 1 + 2 * (lo | (up << D)) + (in ? 1 : 0);
 }
 
-// Zero block of a pair without overlap, in 16-byte stores.
+// Zero block of a pair without overlap, in 32-byte stores.
 template <int D>
 __device__ __forceinline__ void store_zero_block(double* block) {
 #pragma unroll
-    for (int i = 0; i < (D + 1) << D; i += 2) reinterpret_cast<double2*>(block)[i / 2] = make_double2(0.0, 0.0);
+    for (int i = 0; i < (D + 1) << D; i += 4)
+        reinterpret_cast<double4_32a*>(block)[i / 4] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
 }
 
 // Clip + integrate one pair.  T: element vertices in cell-local coordinates;
 // g, positive: from elem_gradients; scale = volume of the cell.  Writes the
-// (d+1)*2^d block straight to `block` (16-byte aligned, row-major by element
+// (d+1)*2^d block straight to `block` (32-byte aligned, row-major by element
 // vertex) and the intersection volume to *vol.
 template <int D, typename R>
 __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D + 1][D], bool positive,
@@ -836,8 +837,8 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
             else row[b] = (double)v * scale;
         }
 #pragma unroll
-        for (int b = 0; b < NB; b += 2)
-            reinterpret_cast<double2*>(block + a * NB)[b / 2] = make_double2(row[b], row[b + 1]);
+        for (int b = 0; b < NB; b += 4)
+            reinterpret_cast<double4_32a*>(block + a * NB)[b / 4] = make_double4_32a(row[b], row[b + 1], row[b + 2], row[b + 3]);
     }
 }
 
