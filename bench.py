@@ -69,9 +69,9 @@ TALLY_SAMPLE_ELEMS = 4000
 # DRAM bytes per candidate pair of the clipping kernel (read + write) from one
 # capture of its first launch on the 48k-tet beam (716,130 pairs; ncu --metrics
 # dram__bytes_read.sum,dram__bytes_write.sum -k regex:clip_fused_kernel -c 1):
-# 23.3 MB read + 196.6 MB written.  The traffic grows with the pairs (each pair
+# 24.9 MB read + 201.7 MB written.  The traffic grows with the pairs (each pair
 # writes its block and volume once), so it scales to a launch by the pair count.
-CLIP_DRAM_BYTES_PER_PAIR = 307.1
+CLIP_DRAM_BYTES_PER_PAIR = 316.4
 
 
 def parse():
