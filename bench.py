@@ -789,13 +789,12 @@ def run_workload(args, name, rank, world, local, dev, torch, l2x, flush, steps, 
         gh.status()
         e_ms = e_ms / n_e2e
         e_step_ms, e_total, e_value = aggregate(e_ms, e2e_pairs / n_e2e, world)
-        h2d = (coords_h.numel() * 8 + sum(t.numel() * t.element_size() for t in uh)
-               + sum(t.numel() * t.element_size() for t in fh))
-        d2h = sum(t.numel() * t.element_size() for t in us_h) + sum(t.numel() * t.element_size() for t in ff_h)
+        h2d, d2h = gh.io_bytes()  # counted by the library from the copies the graph holds
         res["e2e"] = {"value": e_value, "unit": UNIT, "ms_per_step": e_step_ms,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "form": "l2x_graph_create_host: copies in and out are nodes of the step graph "
-                              "(u_f, f_s in beside the assembly; u_s out beside the force transfer; f_f out last)"}
+                              "(positions, f_s and the touched-node box of u_f in beside the assembly; u_s out "
+                              "beside the force transfer; the box of f_f out last)"}
         del gh, Ph, uh, fh, us_h, ff_h, coords_h
     else:
         del pc

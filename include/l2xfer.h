@@ -280,23 +280,32 @@ l2x_status l2x_graph_create(l2x_handle h, const double* coords_src, const void* 
                             const void* const* f_s, void* const* f_f, double capacity_margin, int32_t zero_force,
                             void* stream, l2x_graph* out);
 /* The same step with its inputs and outputs in HOST memory, for a caller whose
- * fluid solver runs on the host: every replay copies the positions in
- * (coords_host, n_nodes x dim doubles), u_f_host[g] (the fluid nodes of grid g)
- * and f_s_host[g] (n_nodes) in, and u_s_host[g] (n_nodes) and f_f_host[g] (the
- * fluid nodes of grid g) out; field elements are float in the mixed precision
- * form and double otherwise.  The copies are nodes of the graph: u_f and f_s
- * are copied on a branch that runs beside the assembly (it needs only the
- * positions), u_s on that branch beside the force transfer, f_f at the end
- * (one grid per stream); the host arrays are read and written at replay time
- * and are complete once the stream has passed the launch (for instance after
- * l2x_graph_sync_status).  Every host array must be page-locked
- * (cudaHostAlloc / cudaHostRegister), else L2X_EINVAL; they must stay allocated
- * while the graph exists.  The graph owns the device copies of the fields (freed
- * by l2x_graph_destroy); L2X_ENOMEM if they do not fit.  Everything else as for
- * l2x_graph_create, whose launch, status and destroy calls serve this graph. */
+ * fluid solver runs on the host.  Arrays as for l2x_graph_create, in host
+ * memory: coords_host (n_nodes x dim doubles), u_f_host[g] and f_f_host[g]
+ * (the fluid nodes of grid g, x fastest), u_s_host[g] and f_s_host[g]
+ * (n_nodes); field elements are float in the mixed precision form and double
+ * otherwise.  Every replay copies the positions, f_s and, of u_f, the box of
+ * fluid nodes that the rows of B_g^T cover (fixed here: the nodes the mesh
+ * touches, padded by the capacity margin; B_g reads u_f only there) in, and u_s
+ * and the box of f_f (B_g^T writes f_f only there) out.  zero_force != 0:
+ * f_f_host = s B^T ...; its entries outside the box are set to zero here, once,
+ * and no replay writes them again (the caller keeps them zero).  zero_force ==
+ * 0: f_f_host += s B^T ...; the box is copied in, added to and copied back.
+ * The copies are nodes of the graph: the inputs on a branch beside the
+ * assembly (which needs only the positions), u_s on that branch beside the
+ * force transfer, f_f at the end (one grid per stream); host arrays are read
+ * and written at replay time and complete once the stream has passed the
+ * launch (for instance after l2x_graph_sync_status).  Every host array must be
+ * page-locked (cudaHostAlloc / cudaHostRegister), else L2X_EINVAL, and stay
+ * allocated while the graph exists.  The graph owns the device copies of the
+ * fields (freed by l2x_graph_destroy); L2X_ENOMEM if they do not fit.
+ * Everything else as for l2x_graph_create, whose launch, status and destroy
+ * calls serve this graph.  l2x_graph_io_bytes gives the bytes a replay copies
+ * in and out (0 for a graph of device arrays). */
 l2x_status l2x_graph_create_host(l2x_handle h, const double* coords_host, const void* const* u_f_host,
                                  void* const* u_s_host, const void* const* f_s_host, void* const* f_f_host,
                                  double capacity_margin, int32_t zero_force, void* stream, l2x_graph* out);
+l2x_status l2x_graph_io_bytes(l2x_graph g, int64_t* h2d_bytes, int64_t* d2h_bytes);
 l2x_status l2x_graph_launch(l2x_graph g, void* stream);
 l2x_status l2x_graph_sync_status(l2x_graph g, void* stream);
 l2x_status l2x_graph_destroy(l2x_graph g);

@@ -125,6 +125,7 @@ def load_library(build_if_missing: bool = True):
                               ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
         "l2x_graph_create_host": ([P, P, PP, PP, PP, PP, ctypes.c_double, ctypes.c_int32, P,
                                    ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "l2x_graph_io_bytes": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "l2x_graph_launch": ([P, P], ctypes.c_int),
         "l2x_graph_sync_status": ([P, P], ctypes.c_int),
         "l2x_graph_destroy": ([P], ctypes.c_int),
@@ -483,7 +484,9 @@ class Coupling:
         """The captured step with page-locked CPU tensors as its inputs and outputs
         (``coords_h`` float64 n_nodes x dim; u_f, f_f per grid over its fluid nodes;
         u_s, f_s per grid over the solid nodes; fields in the coupling's dtype): every
-        launch copies them in and out as part of the graph."""
+        launch copies them in and out as part of the graph, of u_f and f_f the box of
+        fluid nodes the mesh can touch (see l2x_graph_create_host: with zero_force, f_f
+        outside the box is zeroed once, here)."""
         fl = self.fluid_sizes()
         want = [(coords_h, torch.float64, self.n_nodes * self.dim, "coords_h")]
         for g in range(self.n_grids):
@@ -579,6 +582,12 @@ class StepGraph:
 
     def status(self):
         _check(load_library().l2x_graph_sync_status(self._g, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def io_bytes(self):
+        """(bytes copied host to device, device to host) per replay of a host-array graph."""
+        h2d, d2h = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(load_library().l2x_graph_io_bytes(self._g, ctypes.byref(h2d), ctypes.byref(d2h)))
+        return h2d.value, d2h.value
 
     def __del__(self):
         g = getattr(self, "_g", None)

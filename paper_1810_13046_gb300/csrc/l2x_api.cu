@@ -677,6 +677,29 @@ void enqueue_force(l2x_coupling* h, const void* const* f_s_in, void* const* f_f,
 // node positions, re-assembly with the capacities of the handle (overflow sets
 // FLAG_CAPACITY and later kernels skip their work), velocity transfer and dual
 // or nodal force transfer.  Used under stream capture by l2x_graph_create.
+// The box of fluid nodes that the rows of B_g^T cover (fixed when a step graph
+// is created) as a 3-D region of a fluid array of grid g (x fastest, es bytes an
+// entry).
+cudaPitchedPtr fluid_pitched(void* p, const SubGrid& sg, size_t es) {
+    return make_cudaPitchedPtr(p, es * (size_t)sg.nnode[0], (size_t)sg.nnode[0], (size_t)sg.nnode[1]);
+}
+cudaExtent box_extent(const CsrT& T, size_t es) { return make_cudaExtent(es * (size_t)T.n[0], T.n[1], T.n[2]); }
+
+// Copies the box of grid g's fluid array between host and device arrays of the
+// same layout.
+l2x_status copy_fluid_box(void* dst, const void* src, const SubGrid& sg, const CsrT& T, size_t es,
+                          cudaMemcpyKind kind, cudaStream_t s) {
+    cudaMemcpy3DParms p{};
+    p.srcPtr = fluid_pitched(const_cast<void*>(src), sg, es);
+    p.dstPtr = fluid_pitched(dst, sg, es);
+    p.srcPos = make_cudaPos(es * (size_t)T.lo[0], T.lo[1], T.lo[2]);
+    p.dstPos = p.srcPos;
+    p.extent = box_extent(T, es);
+    p.kind = kind;
+    L2X_CUDA(cudaMemcpy3DAsync(&p, s));
+    return L2X_OK;
+}
+
 // Host ends of a captured step with host buffers (page-locked): positions in,
 // u_f and f_s in, u_s and f_f out, per grid.
 struct HostIO {
@@ -703,12 +726,18 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         // engine, and the assembly waits for the positions only
         L2X_CUDA(cudaEventRecord(h->ev_io_fork, s));
         L2X_CUDA(cudaStreamWaitEvent(h->io_stream, h->ev_io_fork, 0));
+        // B_g reads u_f only inside the box, and B_g^T writes f_f only there (a
+        // replay whose mesh leaves the box is flagged and skipped)
         for (int g = 0; g < G; ++g)
-            L2X_CUDA(cudaMemcpyAsync(const_cast<void*>(u_f[g]), io->u_f[g], es * fluid_nodes(h->sg[g]),
-                                     cudaMemcpyHostToDevice, h->io_stream));
+            L2X_TRY(copy_fluid_box(const_cast<void*>(u_f[g]), io->u_f[g], h->sg[g], h->T[g], es,
+                                   cudaMemcpyHostToDevice, h->io_stream));
         for (int g = 0; g < G; ++g)
             L2X_CUDA(cudaMemcpyAsync(const_cast<void*>(f_s[g]), io->f_s[g], es * n, cudaMemcpyHostToDevice,
                                      h->io_stream));
+        if (!zero_force)  // f_f += ...: the host's values are the base
+            for (int g = 0; g < G; ++g)
+                L2X_TRY(copy_fluid_box(f_f[g], io->f_f[g], h->sg[g], h->T[g], es, cudaMemcpyHostToDevice,
+                                       h->io_stream));
         L2X_CUDA(cudaEventRecord(h->ev_io_in, h->io_stream));
     }
     launch_reset_status(h->st, s);
@@ -796,6 +825,11 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         L2X_CUDA(cudaEventRecord(h->ev_io_out, h->io_stream));
         return L2X_OK;
     };
+    // f_f = 0 before the force transfer adds into it
+    auto zero_forces = [&](void* const* ff) -> l2x_status {
+        for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(ff[g], 0, es * fluid_nodes(h->sg[g]), s));
+        return L2X_OK;
+    };
     // f_f out, grid g >= 1 on the stream of its transpose branch, then every
     // branch joins the main stream
     auto copy_ff_out = [&]() -> l2x_status {
@@ -803,11 +837,11 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         L2X_CUDA(cudaEventRecord(h->ev_tfork, s));
         for (int g = 1; g < G; ++g) {
             L2X_CUDA(cudaStreamWaitEvent(h->t_stream[g], h->ev_tfork, 0));
-            L2X_CUDA(cudaMemcpyAsync(io->f_f[g], f_f[g], es * fluid_nodes(h->sg[g]), cudaMemcpyDeviceToHost,
-                                     h->t_stream[g]));
+            L2X_TRY(copy_fluid_box(io->f_f[g], f_f[g], h->sg[g], h->T[g], es, cudaMemcpyDeviceToHost,
+                                   h->t_stream[g]));
             L2X_CUDA(cudaEventRecord(h->ev_tjoin[g], h->t_stream[g]));
         }
-        L2X_CUDA(cudaMemcpyAsync(io->f_f[0], f_f[0], es * fluid_nodes(h->sg[0]), cudaMemcpyDeviceToHost, s));
+        L2X_TRY(copy_fluid_box(io->f_f[0], f_f[0], h->sg[0], h->T[0], es, cudaMemcpyDeviceToHost, s));
         for (int g = 1; g < G; ++g) L2X_CUDA(cudaStreamWaitEvent(s, h->ev_tjoin[g], 0));
         L2X_CUDA(cudaStreamWaitEvent(s, h->ev_io_out, 0));
         return L2X_OK;
@@ -837,16 +871,14 @@ l2x_status record_step(l2x_coupling* h, const double* coords_src, const void* co
         solve_mass_pcg_async(h->opts.precision, h->M, h->M_dinv, h->M_dinv32, 2 * G, ys, ws, h->opts.cg_rtol,
                              h->opts.cg_max_iter, h->pcg_ws, h->st, s, h->pcg_rpb_step, 0);
         L2X_TRY(copy_us_out());
-        if (zero_force)
-            for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * fluid_nodes(h->sg[g]), s));
+        if (zero_force) L2X_TRY(zero_forces(f_f));
         launch_spmv_BT(L2X_PATH_FUSED, h->opts.precision, G, h->B, h->T, h->sg, (const void* const*)zf, f_f,
                        h->opts.force_scale, h->st, s);
         return copy_ff_out();
     }
     enqueue_velocity(h, u_f, u_s, s);
     L2X_TRY(copy_us_out());
-    if (zero_force)
-        for (int g = 0; g < G; ++g) L2X_CUDA(cudaMemsetAsync(f_f[g], 0, es * fluid_nodes(h->sg[g]), s));
+    if (zero_force) L2X_TRY(zero_forces(f_f));
     enqueue_force(h, f_s, f_f, s);
     return copy_ff_out();
 }
@@ -859,6 +891,7 @@ struct l2x_step_graph {
     cudaGraphExec_t exec = nullptr;
     uint64_t gen = 0;  // the handle's graph_gen at creation
     std::vector<void*> owned;  // device copies of the host-buffer form's arrays
+    int64_t io_h2d = 0, io_d2h = 0;  // host-buffer form: bytes copied in and out per replay
     ~l2x_step_graph() {
         for (void* p : owned) cudaFree(p);
     }
@@ -1447,10 +1480,32 @@ l2x_status l2x_graph_create_host(l2x_handle h, const double* coords_host, const 
         io.f_s[g] = f_s_host[g];
         io.f_f[g] = f_f_host[g];
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int g = 0; g < G; ++g) {  // defined values outside the boxes the replays copy
+        const size_t nf = es * (size_t)fluid_nodes(h->sg[g]);
+        if (cudaMemsetAsync(uf[g], 0, nf, s) != cudaSuccess || cudaMemsetAsync(ff[g], 0, nf, s) != cudaSuccess) {
+            for (void* q : owned) cudaFree(q);
+            return cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
+        }
+        // f_f = ...: only the box is written back by a replay, the rest is zeroed here
+        if (zero_force) memset(f_f_host[g], 0, nf);
+    }
     const l2x_status st = graph_create_common(h, coords_host, (const void* const*)uf, us, (const void* const*)fs, ff,
                                               capacity_margin, zero_force, stream, out, &io, owned);
     for (void* q : owned) cudaFree(q);  // left here only when the graph was not made
-    return st;
+    if (st != L2X_OK) return st;
+    int64_t box = 0;
+    for (int g = 0; g < G; ++g) box += h->T[g].n_rows * (int64_t)es;
+    (*out)->io_h2d = (int64_t)sizeof(double) * n * h->dim + box + (int64_t)es * n * G + (zero_force ? 0 : box);
+    (*out)->io_d2h = (int64_t)es * n * G + box;
+    return L2X_OK;
+}
+
+l2x_status l2x_graph_io_bytes(l2x_graph g, int64_t* h2d_bytes, int64_t* d2h_bytes) {
+    if (!g || !h2d_bytes || !d2h_bytes) return fail(L2X_EINVAL, "NULL argument");
+    *h2d_bytes = g->io_h2d;
+    *d2h_bytes = g->io_d2h;
+    return L2X_OK;
 }
 
 l2x_status l2x_graph_launch(l2x_graph g, void* stream) {

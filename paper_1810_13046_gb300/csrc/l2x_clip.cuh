@@ -750,10 +750,15 @@ __device__ void pair_integrals(const double (&T)[D + 1][D], const double (&g)[D 
                     bufA[v][j2] = a2[sidx];
                 }
                 n = 4;
-#pragma unroll
+#pragma unroll 1
                 for (int a = 0; a < NA; ++a) {
+                    // the plane's coefficients by selects: registers, not a local array
+                    const double ca = a == 0 ? cA[0] : a == 1 ? cA[1] : a == 2 ? cA[2] : cA[3];
+                    double ga[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) ga[k] = a == 0 ? g[0][k] : a == 1 ? g[1][k] : a == 2 ? g[2][k] : g[3][k];
                     bool same;
-                    n = clip_plane<D, kFast>(cur, n, nxt, g[a], cA[a], same);
+                    n = clip_plane<D, kFast>(cur, n, nxt, ga, ca, same);
                     if (!same) { double (*t)[D] = cur; cur = nxt; nxt = t; }
                 }
             }

@@ -264,3 +264,46 @@ def test_host_buffer_graph_refuses_pageable_memory():
     assert b"page-locked" in lib.l2x_last_error()
     with pytest.raises(ValueError):
         c.capture_step_host(pageable, pin_f, pin_n, pin_n, pin_f)
+
+
+def test_host_buffer_graph_accumulates_into_the_host_forces():
+    """zero_force off: f_f_host += s B^T ... (the box of touched fluid nodes is
+    copied in, added to and copied back), equal to the device-array graph started
+    from the same forces; the bytes a replay copies are those of the boxes."""
+    grid, bodies, E, nr, er, fields, n_steps = _setup(n_bodies=3, seed=10)
+    dt = torch.float64
+    X0 = synth.batch_coords(bodies, 0, n_steps)
+    cd = _coupling(grid, X0, E, "fp64")
+    ch = _coupling(grid, X0, E, "fp64")
+    n = X0.shape[0]
+    rng = np.random.default_rng(12)
+    F = rng.standard_normal((n, 3))
+    base = [rng.standard_normal(m) for m in cd.fluid_sizes()]
+    src = torch.from_numpy(X0).cuda()
+    du_f = [torch.from_numpy(f).cuda() for f in fields]
+    df_s = [torch.from_numpy(np.ascontiguousarray(F[:, g])).cuda() for g in range(3)]
+    du_s = [torch.zeros(n, dtype=dt, device="cuda") for _ in range(3)]
+    df_f = [torch.from_numpy(b.copy()).cuda() for b in base]
+    gd = cd.capture_step(src, du_f, du_s, df_s, df_f, margin=1.5, zero_force=False)
+    hsrc = torch.from_numpy(X0.copy()).pin_memory()
+    hu_f = [torch.from_numpy(f).pin_memory() for f in fields]
+    hf_s = [torch.from_numpy(np.ascontiguousarray(F[:, g])).pin_memory() for g in range(3)]
+    hu_s = [torch.zeros(n, dtype=dt).pin_memory() for _ in range(3)]
+    hf_f = [torch.from_numpy(b.copy()).pin_memory() for b in base]
+    gh = ch.capture_step_host(hsrc, hu_f, hu_s, hf_s, hf_f, margin=1.5, zero_force=False)
+    for step in (1, 2):
+        Xt = synth.batch_coords(bodies, step, n_steps)
+        src.copy_(torch.from_numpy(Xt).cuda())
+        hsrc.copy_(torch.from_numpy(Xt))
+        gd.launch()
+        gd.status()
+        gh.launch()
+        gh.status()
+        for a, b in list(zip(hu_s, du_s)) + list(zip(hf_f, df_f)):
+            a, b = a.numpy(), b.cpu().numpy()
+            assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b), step
+    h2d, d2h = gh.io_bytes()
+    full = sum(8 * m for m in ch.fluid_sizes())
+    assert 0 < d2h - 8 * 3 * n < full  # u_s, then the f_f boxes only
+    assert h2d > d2h
+    assert gd.io_bytes() == (0, 0)
