@@ -315,10 +315,22 @@ __global__ void __launch_bounds__(kRowWarps * 32, 8) b_rows_kernel(
                 s_acc[w][u] = 0.0;
                 s_hit[w][u] = 0;
             }
+            // per staged element, packed in place of its (element, vertex) word: the
+            // union-box index of its box corner (< kRowUnion), its box extents (<= 2)
+            // and the local vertex
+            for (int64_t t = a0 + lane; t < a1; t += 32) {
+                const ElemBox b = s_box[w][t - a0];
+                const int u0 = (b.lo[0] - lo[0]) + nx * ((b.lo[1] - lo[1]) + ny * (D == 3 ? b.lo[2] - lo[2] : 0));
+                const int ez = D == 3 ? box_ext(b, 2) : 0;
+                s_ea[w][t - a0] = u0 | (box_ext(b, 0) << 8) | (box_ext(b, 1) << 10) | (ez << 12) |
+                                  ((s_ea[w][t - a0] & 3) << 14);
+            }
             __syncwarp();
-            // this lane's node of an element box (at most 3 nodes per axis)
+            // this lane's node of an element box (at most 3 nodes per axis) and its
+            // offset in the union box
             const int lx = lane % 3, ly = (lane / 3) % 3, lz = D == 3 ? lane / 9 : 0;
             const bool lane_ok = lane < (D == 3 ? 27 : 9);
+            const int lane_u = lx + nx * (ly + ny * lz);
             for (int64_t t0 = a0; t0 < a1; t0 += kRowGroup) {
                 int u[kRowGroup];
                 uint8_t f[kRowGroup];
@@ -330,15 +342,15 @@ __global__ void __launch_bounds__(kRowWarps * 32, 8) b_rows_kernel(
                     v[q] = 0.0;
                     const int64_t t = t0 + q;
                     if (t >= a1 || !lane_ok) continue;
-                    const ElemBox b = s_box[w][t - a0];
-                    const int ex = box_ext(b, 0), ey = box_ext(b, 1), ez = D == 3 ? box_ext(b, 2) : 0;
+                    const int pk = s_ea[w][t - a0];
+                    const int ex = (pk >> 8) & 3, ey = (pk >> 10) & 3, ez = (pk >> 12) & 3;
                     if (lx > ex || ly > ey || lz > ez) continue;
                     const int64_t L = s_off[w][t - a0] + lx + (ex + 1) * (ly + (ey + 1) * lz);
-                    u[q] = (b.lo[0] + lx - lo[0]) + nx * ((b.lo[1] + ly - lo[1]) + ny * (D == 3 ? b.lo[2] + lz - lo[2] : 0));
+                    u[q] = (pk & 255) + lane_u;
                     f[q] = loc_flag[L];
                     // the element-local matrices hold exact zeros at untouched nodes, so
                     // the value is read without waiting for the flag (same sums)
-                    if (pass != 2) v[q] = loc_val[(int64_t)(s_ea[w][t - a0] & 3) * loc_cap + L];
+                    if (pass != 2) v[q] = loc_val[(int64_t)(pk >> 14) * loc_cap + L];
                 }
 #pragma unroll
                 for (int q = 0; q < kRowGroup; ++q) {
