@@ -58,7 +58,7 @@ __global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM
     const int64_t grp = tid >> 3;
     const int l8 = threadIdx.x & 7;
     const bool active = grp < n_rows * n_grids;
-    const int g = active ? (int)(grp / n_rows) : 0;
+    const int g = !active ? 0 : grp >= 2 * n_rows ? 2 : grp >= n_rows ? 1 : 0;  // n_grids <= 3
     const int64_t row = active ? grp - g * n_rows : 0;
     if constexpr (sizeof(TV) == 4) {
         DFAcc acc;
@@ -67,6 +67,7 @@ __global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM
             const int32_t* __restrict__ col = P.col[g];
             const TM* __restrict__ val = P.val[g];
             const TV* __restrict__ x = P.x[g];
+#pragma unroll 4
             for (int64_t q = lo + l8; q < hi; q += 8) acc.add_prod((float)__ldg(val + q), __ldg(x + __ldg(col + q)));
         }
         acc.reduce_xor(4);
@@ -82,6 +83,7 @@ __global__ void spmv_B_fused_kernel(int n_grids, int64_t n_rows, SpmvPack<TV, TM
             const int32_t* __restrict__ col = P.col[g];
             const TM* __restrict__ val = P.val[g];
             const TV* __restrict__ x = P.x[g];
+#pragma unroll 4
             for (int64_t q = lo + l8; q < hi; q += 8) acc += (TV)__ldg(val + q) * __ldg(x + __ldg(col + q));
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 4);
@@ -222,10 +224,12 @@ struct SpmvTPack {
 // Fluid node of row r of the B_g^T box.
 template <typename TV, typename TM>
 __device__ __forceinline__ int64_t bt_node(const SpmvTPack<TV, TM>& P, int g, int64_t r) {
-    const int x = (int)(r % P.nb[g][0]);
-    const int64_t rr = r / P.nb[g][0];
-    const int y = (int)(rr % P.nb[g][1]);
-    const int zz = (int)(rr / P.nb[g][1]);
+    // box rows number below 2^31 (int32 fluid-node columns): 32-bit division
+    const unsigned int ru = (unsigned int)r, n0 = (unsigned int)P.nb[g][0], n1 = (unsigned int)P.nb[g][1];
+    const unsigned int rr = ru / n0;
+    const int x = (int)(ru - rr * n0);
+    const int zz = (int)(rr / n1);
+    const int y = (int)(rr - (unsigned int)zz * n1);
     return (x + P.lo[g][0]) + (int64_t)P.nn[g][0] * ((y + P.lo[g][1]) + (int64_t)P.nn[g][1] * (zz + P.lo[g][2]));
 }
 
@@ -261,6 +265,7 @@ __global__ void spmv_BT_fused_kernel(SpmvTPack<TV, TM> P, TV scale, const DevSta
                 const int32_t* __restrict__ col = P.col[g];
                 const TM* __restrict__ val = P.val[g];
                 const TV* __restrict__ z = P.z[g];
+#pragma unroll 4
                 for (int64_t q = P.ptr[g][r] + lane; q < hi; q += kBTLanes)
                     a2.add_prod((float)__ldg(val + q), __ldg(z + __ldg(col + q)));
             }
@@ -278,6 +283,7 @@ __global__ void spmv_BT_fused_kernel(SpmvTPack<TV, TM> P, TV scale, const DevSta
                 const int32_t* __restrict__ col = P.col[g];
                 const TM* __restrict__ val = P.val[g];
                 const TV* __restrict__ z = P.z[g];
+#pragma unroll 4
                 for (int64_t q = P.ptr[g][r] + lane; q < hi; q += kBTLanes) acc += (TV)__ldg(val + q) * __ldg(z + __ldg(col + q));
             }
 #pragma unroll

@@ -168,6 +168,39 @@ def test_sliver_volumes_match_oracle(precision):
     assert n_sliver > 100  # the mesh does produce slivers
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_faces_within_ulps_of_cell_planes_match_oracle(precision):
+    """Nodes on the base and staggered cell planes, each coordinate then moved by
+    -4..4 ulps: element faces lie within rounding of cell faces, where the
+    computed inside flags of a cut can split into several runs (repaired by the
+    clipping; see the clip kernel).  Pair lists equal the oracle's, volumes
+    within 1e-12 |E|, blocks within 1e-12 |E| (FP64) or 1e-6 |E| (mixed)."""
+    l2x = _l2x()
+    n = 16
+    h = 1.0 / n
+    grid = synth.Grid(3, (n, n, n), (h,) * 3, (0.0,) * 3, True)
+    rng = np.random.default_rng(15)
+    X, E = synth.beam_mesh(8, 8, 4, (4 * h, 4 * h, 2 * h))
+    X = X + 0.5
+    X = X + rng.integers(-4, 5, X.shape) * np.spacing(X)
+    c = l2x.Coupling(grid, torch.from_numpy(X).cuda(), torch.from_numpy(E).cuda(), path=l2x.FUSED,
+                     precision=l2x.MIXED if precision == "mixed" else l2x.FP64)
+    oc = oracle.Coupling(grid, X, E, nthreads=NTHREADS)
+    vol_e = oracle.element_volumes(X, E)
+    tol_b = 1e-6 if precision == "mixed" else 1e-12
+    for g in range(3):
+        e, cell = c.export_pairs(g)
+        assert np.array_equal(e.cpu().numpy(), oc.pairs[g][0])
+        assert np.array_equal(cell.cpu().numpy().astype(np.int64), oc.pairs[g][1])
+        b, v = c.export_pair_blocks(g)
+        b, v = b.cpu().numpy(), v.cpu().numpy()
+        scale = vol_e[oc.pairs[g][0]]
+        assert np.all(np.isfinite(b)) and np.all(np.isfinite(v))
+        assert np.all(np.abs(v - oc.pairs[g][3]) <= 1e-12 * scale)
+        ob = np.asarray(oc.pairs[g][2]).reshape(b.shape)
+        assert np.all(np.abs(b - ob) <= tol_b * scale[:, None, None])
+
+
 # ---------------------------------------------------------------- solver status
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
